@@ -252,6 +252,23 @@ class Dycore:
         theta_new = theta * (rho / rho_new) * (1.0 + (p.cvd / p.rd) * (pr_new - pr) / exner)
         return dict(w=w_full_new, rho=rho_new, exner=exner_new, theta_v=theta_new)
 
+    def flux_velocity(self, vn):
+        """Velocity of the horizontal mass and theta fluxes:
+        vn + divflux_fac * Abar * grad_n(div vn), Abar the mean cell area.
+
+        A reading: a rhombus average of vn that is exact for uniform flow reduces
+        to vn plus a multiple of grad_n(div vn); this form damps the divergent
+        grid-scale (acoustic) modes in the continuity equations only, keeps the
+        fluxes edge-based (mass stays conserved exactly) and changes smooth flow
+        at second order.  It lowers the largest eigenvalue of the discrete
+        acoustic operator grad(div(.)) so that the forward-backward substep
+        stays stable at horizontal acoustic Courant numbers near 0.7."""
+        p = self.p
+        if p.divflux_fac == 0.0:
+            return vn
+        am = np.mean(self.g.cell_area)
+        return vn + p.divflux_fac * am * self.grad_n(self.div(vn))
+
     # ------------------------------------------------------------------
     # one dynamical substep: predictor + corrector (rows A5-A9, A7)
     # ------------------------------------------------------------------
@@ -288,8 +305,9 @@ class Dycore:
         rho_ic = v.interp_ic(rho)
         theta_ic = v.interp_ic(theta)
         thp_ic = v.interp_ic(theta - v.theta_ref[None, :])
-        div_m = self.div(rho_e * vn_pred)
-        div_t = self.div(rho_e * theta_e * vn_pred)
+        vn_flx = self.flux_velocity(vn_pred)
+        div_m = self.div(rho_e * vn_flx)
+        div_t = self.div(rho_e * theta_e * vn_flx)
         pred = self.vertical_solve(st, rho_ic, theta_ic, thp_ic, div_m, div_t, ddt_w_now, dt)
 
         # ---------------- corrector ----------------
@@ -306,8 +324,9 @@ class Dycore:
         rho_ic = v.interp_ic(rho_avg)
         theta_ic = v.interp_ic(th_avg)
         thp_ic = v.interp_ic(th_avg - v.theta_ref[None, :])
-        div_m = self.div(rho_e * vn_new)
-        div_t = self.div(rho_e * theta_e * vn_new)
+        vn_flx = self.flux_velocity(vn_new)
+        div_m = self.div(rho_e * vn_flx)
+        div_t = self.div(rho_e * theta_e * vn_flx)
         ddt_w = p.wgt_nnow_vel * ddt_w_now + p.wgt_nnew_vel * ddt_w_pred
         new = self.vertical_solve(st, rho_ic, theta_ic, thp_ic, div_m, div_t, ddt_w, dt)
         new["vn"] = vn_new

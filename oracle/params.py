@@ -3,7 +3,8 @@
 Values are ICON-like defaults (the paper gives none, Sec. 4.1):
 implicit weight beta = 0.65, velocity-tendency weights 0.25/0.75 (now/new),
 rho/theta time weights 0.6/0.4 in the corrector, exner extrapolation 1/3,
-fourth-order divergence damping 0.0025, Smagorinsky factor 0.015,
+fourth-order divergence damping 0.0025, mass-flux divergence filter 0.07,
+Smagorinsky factor 0.015,
 fourth-order background diffusion A^2/288.
 """
 from dataclasses import dataclass
@@ -28,6 +29,8 @@ class DycoreParams:
     wgt_nnew_rth: float = 0.4
     exner_exfac: float = 1.0 / 3.0
     divdamp_fac: float = 0.0025
+    # divergence filter of the mass-flux velocity, vn + divflux_fac * Abar * grad_n(div vn)
+    divflux_fac: float = 0.07
     # Rayleigh damping of w above damp_height (coefficient 0 switches it off)
     rayleigh_coeff: float = 0.0
     damp_height: float = 20000.0
