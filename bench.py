@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 ICON-type dycore step on R2B6 L90.
+
+Workload (the configuration the headline metric is quoted on): icosahedral
+R2B6 grid (327 680 cells, 491 520 edges), 90 levels to 30 km, dt = 360 s,
+5 dynamical substeps + diffusion per step, Rayleigh damping above 20 km,
+balanced JW-type baroclinic jet with the seeded Gaussian perturbation
+(seed 2).  Synthetic inputs (no dataset exists in this environment).
+
+A "step" is one full dycore time step.  The device-resident leg times K
+steps replayed as one CUDA graph each, with CUDA events on the stream the
+library launches on; the state (1.5 GB) is larger than L2, so no flush is
+needed.  The end-to-end leg calls the C-ABI with HOST arrays: the library
+copies the state in and out around every step.  N>1 (torchrun) runs N
+independent replicas (ensemble members), one per GPU.
+
+``--impl reference`` times the FP64 CPU oracle instead (on the host cores),
+each step a bounded sample: one substep and one diffusion call on R2B4 L90,
+scaled to a full R2B6 L90 step (x5 substeps, x16 cells).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(bisections=6, nlev=90, dtime=360.0, ndyn=5, seed=2, rayleigh=0.05)
+SAMPLE_BISECTIONS = 4          # reference / cpu_baseline sample grid (1/16 of the R2B6 columns)
+METRIC = "dycore steps/s + HBM GB/s fraction at R2B6 L90: FP64 vs mixed+learned"
+FP64_PEAK_TFLOPS = 1.25        # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+
+# Algorithmic FP64 flops per unit (FMA = 2, add/mul/div/sqrt = 1), counted
+# from the formulas each kernel evaluates; the unit is one (point, level).
+FLOPS_PER_UNIT = {
+    "va_edge_pre": 13, "va_cell_vert": 17, "va_edge_tend": 38, "va_cell_w": 13,
+    "sn_cell_grad": 28, "sn_edge_pred": 38, "sn_column_pred": 110, "sn_edge_corr": 17,
+    "sn_column_corr": 105, "diff_div_curl_uv": 30, "diff_edge_smag": 46, "diff_second": 30,
+    "diff_edge_update": 12, "diff_cell_update": 12,
+}
+
+
+def units_per_launch(name, nc, ne, nv, nlev):
+    full = {"c": nc * nlev, "e": ne * nlev, "v": nv * nlev}
+    half = {"c": nc * (nlev + 1), "e": ne * (nlev + 1), "v": nv * (nlev + 1)}
+    return {
+        "va_edge_pre": full["e"], "va_cell_vert": full["c"] + half["v"], "va_edge_tend": half["e"],
+        "va_cell_w": half["c"], "sn_cell_grad": full["c"], "sn_edge_pred": full["e"],
+        "sn_column_pred": full["c"], "sn_edge_corr": full["e"], "sn_column_corr": full["c"],
+        "diff_div_curl_uv": full["c"] + full["v"], "diff_edge_smag": full["e"],
+        "diff_second": half["c"] + full["v"], "diff_edge_update": full["e"], "diff_cell_update": half["c"],
+    }[name]
+
+
+def state_bytes(nc, ne, nlev):
+    return 8 * (ne * nlev + nc * (nlev + 1) + 4 * nc * nlev)
+
+
+# Compulsory HBM bytes of one step: every prognostic (vn, w, rho, exner,
+# theta_v, exner_pr) read and written once per substep, plus once more for
+# the diffusion.
+def compulsory_bytes_per_step(nc, ne, nlev, ndyn):
+    return 2 * state_bytes(nc, ne, nlev) * (ndyn + 1)
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].strip().lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def oracle_sample(bisections, nlev, reps):
+    """Time the oracle (as it stands) on one substep and one diffusion call of
+    the given grid, in a fresh single-threaded process; returns seconds."""
+    code = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+from icon_inputs import make_grid, make_vct, jw_type_state
+from oracle import Dycore, DycoreParams
+g = make_grid(%d); z = make_vct(%d)
+d = Dycore(g, z, DycoreParams(dtime=%r, ndyn_substeps=%d, rayleigh_coeff=%r))
+st = jw_type_state(g, z, seed=%d); st['exner_pr'] = d.initial_exner_pr(st['exner'])
+out = []
+for _ in range(%d):
+    t0 = time.perf_counter(); s1 = d.substep(st); t1 = time.perf_counter(); d.diffusion(s1); t2 = time.perf_counter()
+    out.append((t1 - t0, t2 - t1))
+print(json.dumps(out))
+""" % (ROOT, bisections, nlev, WORKLOAD["dtime"], WORKLOAD["ndyn"], WORKLOAD["rayleigh"], WORKLOAD["seed"], reps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if p.returncode != 0:
+        raise RuntimeError(p.stderr)
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def sample_to_steps_per_s(t_sub, t_diff, scale):
+    return 1.0 / (scale * (WORKLOAD["ndyn"] * t_sub + t_diff))
+
+
+def cpu_baseline(nlev):
+    samples = oracle_sample(SAMPLE_BISECTIONS, nlev, 1)
+    t_sub, t_diff = samples[0]
+    scale = 4 ** (WORKLOAD["bisections"] - SAMPLE_BISECTIONS)
+    return {"value": sample_to_steps_per_s(t_sub, t_diff, scale), "unit": "steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "one substep (%.1f s) + one diffusion (%.1f s) of the numpy FP64 oracle on R2B4 L90 "
+                      "(1/16 of the R2B6 columns), scaled to an R2B6 L90 step as 16 x (5 substeps + diffusion)"
+                      % (t_sub, t_diff)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    nlev = WORKLOAD["nlev"]
+    reps = args.warmup + args.steps
+    samples = oracle_sample(SAMPLE_BISECTIONS, nlev, reps)[args.warmup:]
+    scale = 4 ** (WORKLOAD["bisections"] - SAMPLE_BISECTIONS)
+    step_s = [scale * (WORKLOAD["ndyn"] * a + b) for a, b in samples]
+    total = sum(step_s)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict("fp64"),
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: one substep + one diffusion of the numpy FP64 oracle on R2B4 L90, "
+                                   "scaled x16 (cells) and x5 (substeps) to an R2B6 L90 step"},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(prec):
+    w = WORKLOAD
+    return {"workload": "R2B6 L90 (327680 cells, 491520 edges), dt=%gs, %d substeps + diffusion, %s, "
+                        "JW-type jet seed %d" % (w["dtime"], w["ndyn"], prec.upper(), w["seed"]),
+            "grid": "R2B6", "nlev": w["nlev"], "dtime_s": w["dtime"], "ndyn_substeps": w["ndyn"],
+            "precision": prec, "cuda_graph": True,
+            "l2": "inputs larger than L2 (FP64 state 1.5 GB, scratch ~9 GB); no flush"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2608_21150_gb300.build import build
+    build()
+    import paper_2608_21150_gb300 as P
+    from icon_inputs import make_grid, make_vct, jw_type_state
+
+    w = WORKLOAD
+    grid = make_grid(w["bisections"])
+    z = make_vct(w["nlev"])
+    nlev = w["nlev"]
+    nc, ne, nv = grid.n_cells, grid.n_edges, grid.n_verts
+    st0 = jw_type_state(grid, z, seed=w["seed"])
+    stream = torch.cuda.current_stream(dev)
+    G = P.Grid(grid)
+    D = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
+                            use_graph=1, synchronous=0, stream=stream.cuda_stream))
+    th_ref, ex_ref = D.reference_state()
+    st0["exner_pr"] = st0["exner"] - ex_ref[None, :]
+    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
+
+    for _ in range(args.warmup):
+        D.step(t)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        D.step(t)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms = float(mt.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    finite = all(bool(torch.isfinite(x).all()) for x in t.values())
+
+    # per-kernel device time over a few steps (events around every launch)
+    prof = D.profile(t, min(args.steps, 3))
+    nsteps_prof = min(args.steps, 3)
+    launches_per_step = sum(n for n, _ in prof.values()) // nsteps_prof
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tot_ms) = top
+    avg_s = tot_ms / nl / 1000.0
+    achieved = FLOPS_PER_UNIT[name] * units_per_launch(name, nc, ne, nv, nlev) / avg_s / 1e12
+    prof_ms_step = sum(v[1] for v in prof.values()) / nsteps_prof
+    kernels = {k: {"launches_per_step": n // nsteps_prof, "ms_per_step": round(m / nsteps_prof, 3),
+                   "share": round(m / nsteps_prof / prof_ms_step, 4)} for k, (n, m) in
+               sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # end to end through the C-ABI with host arrays (copies inside the timed region)
+    e2e_steps = max(1, min(args.steps, 5))
+    host = {k: torch.from_numpy(v.copy()).pin_memory() for k, v in st0.items()}
+    D2 = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
+                             use_graph=1, synchronous=1, stream=stream.cuda_stream))
+    D2.step(host)  # warm-up: allocates the device staging copy and captures the graph
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        D2.step(host)
+    e2e_s = time.perf_counter() - t0
+    sb = state_bytes(nc, ne, nlev)
+
+    hbm_bytes = compulsory_bytes_per_step(nc, ne, nlev, w["ndyn"])
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict("fp64"),
+        "sdpd": value / world * w["dtime"],
+        "hbm": {"compulsory_bytes_per_step": hbm_bytes,
+                "achieved_gbs": hbm_bytes / (ms_per_step / 1000.0) / 1e9,
+                "peak_gbs": 6663.9, "frac": hbm_bytes / (ms_per_step / 1000.0) / 1e9 / 6663.9,
+                "note": "compulsory (state read+write per substep and diffusion) bytes / step time; "
+                        "of measured peak"},
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "note": "FP64 algorithmic flops per launch / event-timed launch duration; peak = nominal "
+                             "FP64 rate from unit counts and clock (1.2 TFLOP/s measured by a DFMA probe)"},
+        "kernels": kernels,
+        "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": sb,
+                "d2h_bytes_per_step": sb},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks, "finite": finite,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(nlev)
+    if rank == 0:
+        print(json.dumps(line))
+    D2.close()
+    D.close()
+    G.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * icon_dycore.h -- C-ABI of the GB300 ICON-type nonhydrostatic dynamical core.
+ *
+ * The paper (Sec. 4.3) plugs a dynamical core into the ICON Fortran model
+ * through a C-ABI function: the host gathers pointers to the fields the
+ * dynamics needs and passes them, scalars by value and arrays by reference
+ * without copies, device arrays included (Sec. 4.3.1); setup-phase arrays
+ * (connectivity, geometry) are passed once.  This header is that boundary for
+ * a hand-written CUDA dycore: plain C types, no C++ or torch types, callable
+ * from Fortran through iso_c_binding.
+ *
+ * The step it advances (Sec. 4.1, Fig. 1): ndyn_substeps dynamical substeps
+ * (``nh_solve``, each a predictor and a corrector: velocity advection,
+ * horizontal momentum update with pressure gradient and upwind rho/theta_v
+ * fluxes, divergence damping in the corrector, vertically implicit solve for
+ * w and the thermodynamic state) followed by one diffusion call (``nh_diff``,
+ * Smagorinsky plus fourth-order background), Sec. 5.1.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: ICON_OK (0) on success, a negative ICON_ERR_* code on
+ *    failure; icon_last_error() then returns a message (thread-local,
+ *    valid until the next failing call on the same thread).  On failure
+ *    no output is written unless stated otherwise.
+ *  - Ownership: every array passed in stays owned by the caller.  The
+ *    library copies what it keeps (grid tables, vertical grid) and owns its
+ *    coefficient arrays, scratch and CUDA graphs, freed by *_destroy.
+ *  - Field layout: level-contiguous, X[h * nlev_x + k], h the horizontal
+ *    index (cell, edge or vertex), k the level; k = 0 is the model top.
+ *    Full levels: nlev_x = nlev.  Half levels (w): nlev_x = nlev + 1, with
+ *    k = nlev the ground.  This is the Fortran array X(nlev_x, n_h).
+ *  - Index tables are int32 in the caller's index_base (0 for C, 1 for
+ *    Fortran); "pad" entries of the 6-wide vertex tables equal
+ *    index_base - 1 (pentagon vertices have 5 neighbours).
+ *  - Logical flags are int32 (Fortran LOGICAL is 4 bytes; Sec. 4.3.1).
+ */
+#ifndef ICON_DYCORE_H
+#define ICON_DYCORE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ICON_OK 0
+#define ICON_ERR_ARG (-1)          /* NULL / out-of-range argument */
+#define ICON_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define ICON_ERR_GRID (-3)         /* grid tables or coordinates inconsistent */
+#define ICON_ERR_NUMERIC (-4)      /* non-finite or out-of-range state detected */
+#define ICON_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement */
+
+#define ICON_PREC_FP64 0           /* every stencil and update in FP64 */
+#define ICON_PREC_MIXED 1          /* FP32 stencils, FP64 column solve and updates */
+
+typedef struct icon_grid icon_grid_t;      /* opaque */
+typedef struct icon_dycore icon_dycore_t;  /* opaque */
+
+/*
+ * Horizontal grid (Sec. 5.1: icosahedral RnBm triangular grid).
+ * All pointers are HOST pointers, read during icon_grid_create only.
+ *   c2v [n_cells*3]  cell vertices, counter-clockwise seen from outside
+ *   c2e [n_cells*3]  cell edges
+ *   e2c [n_edges*2]  the two cells of an edge; the edge normal points
+ *                    from e2c[2e] to e2c[2e+1]  (sign convention of vn)
+ *   e2v [n_edges*2]  the two vertices of an edge (any order)
+ *   v2e [n_verts*6]  edges around a vertex, pad = index_base - 1
+ *   v2c [n_verts*6]  cells around a vertex, pad = index_base - 1
+ *   cell_xyz [n_cells*3]  cell circumcentres, unit vectors
+ *   vert_xyz [n_verts*3]  vertices, unit vectors
+ *   edge_xyz [n_edges*3]  edge (arc) midpoints, unit vectors
+ * The library derives every geometric factor (areas, lengths, normals,
+ * interpolation and reconstruction weights) from these.
+ */
+typedef struct icon_grid_desc {
+  int32_t n_cells, n_edges, n_verts;
+  int32_t index_base;
+  double sphere_radius; /* m */
+  const int32_t* c2v;
+  const int32_t* c2e;
+  const int32_t* e2c;
+  const int32_t* e2v;
+  const int32_t* v2e;
+  const int32_t* v2c;
+  const double* cell_xyz;
+  const double* vert_xyz;
+  const double* edge_xyz;
+} icon_grid_desc_t;
+
+/* Validate the tables (ranges, cell/edge/vertex consistency, unit vectors)
+ * and build the grid.  Errors: ICON_ERR_ARG (NULL pointer, bad counts or
+ * index_base), ICON_ERR_GRID (inconsistent tables), ICON_ERR_CUDA. */
+int icon_grid_create(const icon_grid_desc_t* desc, icon_grid_t** out);
+/* NULL-safe.  A grid must outlive every dycore created on it. */
+int icon_grid_destroy(icon_grid_t* grid);
+
+/*
+ * Time-step and scheme parameters (Sec. 4.1 names the parts, not the
+ * values; the defaults are ICON-like).  Fill with icon_dycore_params_default
+ * and override.  Times in s, lengths in m.
+ */
+typedef struct icon_dycore_params {
+  double dtime;            /* time step; the substep is dtime/ndyn_substeps */
+  int32_t ndyn_substeps;   /* dynamical substeps per step (Sec. 4.1, 5.1) */
+  /* physical constants */
+  double grav, rd, cpd, p00, omega;
+  /* solve_nonhydro */
+  double vwind_impl_wgt;   /* implicit weight beta of the vertical solve */
+  double wgt_nnow_vel, wgt_nnew_vel;  /* corrector weights of the advective tendencies */
+  double wgt_nnow_rth, wgt_nnew_rth;  /* corrector weights of rho, theta_v */
+  double exner_exfac;      /* exner-perturbation time extrapolation factor */
+  double divdamp_fac;      /* fourth-order divergence damping (corrector only) */
+  double divflux_fac;      /* mass-flux velocity filter vn + fac*Abar*grad_n(div vn); 0 = off */
+  double rayleigh_coeff;   /* Rayleigh damping of w, 1/s; 0 = off */
+  double damp_height;      /* Rayleigh damping acts above this height */
+  /* diffusion */
+  double hdiff_smag_fac;   /* Smagorinsky factor */
+  double hdiff_k4;         /* fourth-order background coefficient of vn (x A_e^2) */
+  double hdiff_w_k4;       /* fourth-order coefficient of w (x A_c^2) */
+  int32_t hdiff_temp;      /* logical: diffuse theta_v and adjust exner */
+  /* reference state theta_ref(z) = ref_T0 exp(z/H), H = cpd ref_T0 / grav */
+  double ref_T0;
+  /* execution */
+  int32_t precision;       /* ICON_PREC_FP64 or ICON_PREC_MIXED */
+  int32_t use_graph;       /* logical: replay a captured CUDA graph per step */
+  int32_t synchronous;     /* logical: return only after the GPU work ended */
+  void* stream;            /* cudaStream_t to enqueue on; NULL = default stream */
+} icon_dycore_params_t;
+
+/* Writes the defaults: dtime 1800, ndyn_substeps 5, beta 0.65, tendency
+ * weights 0.25/0.75, rho/theta weights 0.6/0.4, exner_exfac 1/3,
+ * divdamp_fac 0.0025, divflux_fac 0.07, Rayleigh off (coeff 0, height 20 km), Smagorinsky
+ * 0.015, k4 = k4w = 1/288, hdiff_temp 1, ref_T0 250, FP64, graph on,
+ * synchronous, default stream.  NULL-safe (does nothing). */
+void icon_dycore_params_default(icon_dycore_params_t* p);
+
+/*
+ * Create a dycore on a grid with nlev flat height levels.
+ *   z_ifc [nlev+1]: HOST pointer, half-level heights in m, top first,
+ *                   strictly decreasing, z_ifc[nlev] = 0 (flat ground).
+ * Derives the vertical metrics and the reference state, uploads all
+ * coefficients, allocates scratch for one step.  The parameters are copied.
+ * Errors: ICON_ERR_ARG, ICON_ERR_UNSUPPORTED (precision mode not built),
+ * ICON_ERR_CUDA (e.g. out of device memory).
+ */
+int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
+                       const icon_dycore_params_t* params, icon_dycore_t** out);
+/* NULL-safe; frees library-owned memory only. */
+int icon_dycore_destroy(icon_dycore_t* dycore);
+
+/*
+ * Prognostic state, FP64, caller-owned, updated IN PLACE by the step calls.
+ *   vn       [n_edges*nlev]      edge-normal wind, m/s
+ *   w        [n_cells*(nlev+1)]  vertical wind at half levels, m/s
+ *   rho      [n_cells*nlev]      density, kg/m^3
+ *   exner    [n_cells*nlev]      Exner pressure
+ *   theta_v  [n_cells*nlev]      virtual potential temperature, K
+ *   exner_pr [n_cells*nlev]      exner - exner_ref of the previous substep
+ *                                (extrapolation history; at a cold start
+ *                                set it to exner - exner_ref, see
+ *                                icon_dycore_reference_state)
+ * Either all six are device pointers (no copies; the calls enqueue on the
+ * dycore's stream), or all six are host pointers (the library copies in and
+ * out around the call, a slow path for testing and end-to-end timing).
+ */
+typedef struct icon_state {
+  double* vn;
+  double* w;
+  double* rho;
+  double* exner;
+  double* theta_v;
+  double* exner_pr;
+} icon_state_t;
+
+/* One full time step: ndyn_substeps calls of the substep, then diffusion
+ * (Sec. 4.1, Sec. 5.1), as one CUDA graph when params.use_graph is set.
+ * Errors: ICON_ERR_ARG (NULL field, mixed host/device pointers),
+ * ICON_ERR_CUDA. */
+int icon_dycore_step(icon_dycore_t* dycore, const icon_state_t* state);
+
+/* One dynamical substep, predictor + corrector, of length
+ * dtime/ndyn_substeps: the paper's nh_solve (Sec. 4.1, 5.1). */
+int icon_nh_solve(icon_dycore_t* dycore, const icon_state_t* state);
+
+/* Horizontal diffusion over dtime: the paper's nh_diff (Sec. 4.1, 5.1). */
+int icon_nh_diff(icon_dycore_t* dycore, const icon_state_t* state);
+
+/* Advective tendencies alone (the first part of every predictor and
+ * corrector, Sec. 4.1), for stage-level verification as in Sec. 4.4:
+ *   vn [n_edges*nlev], w [n_cells*(nlev+1)]        inputs
+ *   ddt_vn [n_edges*nlev], ddt_w [n_cells*(nlev+1)] outputs
+ * All four DEVICE pointers. */
+int icon_velocity_tendencies(icon_dycore_t* dycore, const double* vn, const double* w,
+                             double* ddt_vn, double* ddt_w);
+
+/* The reference state the dycore derived (HOST outputs, [nlev] each):
+ * theta_ref and exner_ref at full levels; exner_ref is in exact discrete
+ * hydrostatic balance with theta_ref on this vertical grid. */
+int icon_dycore_reference_state(const icon_dycore_t* dycore, double* theta_ref,
+                                double* exner_ref);
+
+/* Measurement aid: run nsteps full steps on a DEVICE state (kernel by
+ * kernel, not as a graph) with a CUDA event pair around every kernel launch
+ * on the dycore's stream, then synchronize and report per kernel name:
+ *   names    [max_kernels*64] NUL-terminated names (host buffer)
+ *   launches [max_kernels]    number of launches
+ *   ms       [max_kernels]    summed device time in milliseconds
+ *   *n_kernels                number of distinct kernels reported
+ * The state advances by nsteps steps.  Errors: ICON_ERR_ARG (NULL, host
+ * state, max_kernels too small), ICON_ERR_CUDA. */
+int icon_dycore_profile(icon_dycore_t* dycore, const icon_state_t* state, int32_t nsteps,
+                        int32_t max_kernels, char* names, int32_t* launches, double* ms,
+                        int32_t* n_kernels);
+
+/* Block until all work enqueued by this dycore has finished. */
+int icon_dycore_synchronize(icon_dycore_t* dycore);
+
+/* Sizes: nlev, n_cells, n_edges, n_verts (any output pointer may be NULL). */
+int icon_dycore_sizes(const icon_dycore_t* dycore, int32_t* nlev, int32_t* n_cells,
+                      int32_t* n_edges, int32_t* n_verts);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* icon_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICON_DYCORE_H */

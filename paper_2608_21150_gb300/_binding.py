@@ -1,0 +1,236 @@
+"""Python binding of libicondycore (GB300 ICON-type nonhydrostatic dycore).
+
+Argument marshalling only: every computation of the dycore runs in the CUDA
+kernels behind the C-ABI declared in ``include/icon_dycore.h``.  The entry
+points keep the C names (``icon_grid_create``, ``icon_dycore_create``,
+``icon_dycore_step``, ``icon_nh_solve``, ``icon_nh_diff``, ...); ``Grid`` and
+``Dycore`` below only own the handles and pass tensor pointers.
+
+Fields are passed as torch tensors (device pointers, no copies) or as
+C-contiguous numpy float64 arrays (host pointers; the library copies them in
+and out around the call).  Importing this module fails if the shared library
+has not been built (``python -m paper_2608_21150_gb300.build``): there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(
+        "libicondycore.so is not built; run `python -m paper_2608_21150_gb300.build` "
+        "(or __graft_entry__.build()) first")
+
+_lib = ctypes.CDLL(LIB)
+
+ICON_OK = 0
+ICON_ERR_ARG = -1
+ICON_ERR_CUDA = -2
+ICON_ERR_GRID = -3
+ICON_ERR_NUMERIC = -4
+ICON_ERR_UNSUPPORTED = -5
+ICON_PREC_FP64 = 0
+ICON_PREC_MIXED = 1
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class icon_grid_desc_t(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("n_verts", ctypes.c_int32),
+                ("index_base", ctypes.c_int32), ("sphere_radius", ctypes.c_double),
+                ("c2v", _i32p), ("c2e", _i32p), ("e2c", _i32p), ("e2v", _i32p), ("v2e", _i32p),
+                ("v2c", _i32p), ("cell_xyz", _f64p), ("vert_xyz", _f64p), ("edge_xyz", _f64p)]
+
+
+class icon_dycore_params_t(ctypes.Structure):
+    _fields_ = [("dtime", ctypes.c_double), ("ndyn_substeps", ctypes.c_int32),
+                ("grav", ctypes.c_double), ("rd", ctypes.c_double), ("cpd", ctypes.c_double),
+                ("p00", ctypes.c_double), ("omega", ctypes.c_double),
+                ("vwind_impl_wgt", ctypes.c_double), ("wgt_nnow_vel", ctypes.c_double),
+                ("wgt_nnew_vel", ctypes.c_double), ("wgt_nnow_rth", ctypes.c_double),
+                ("wgt_nnew_rth", ctypes.c_double), ("exner_exfac", ctypes.c_double),
+                ("divdamp_fac", ctypes.c_double), ("divflux_fac", ctypes.c_double),
+                ("rayleigh_coeff", ctypes.c_double),
+                ("damp_height", ctypes.c_double), ("hdiff_smag_fac", ctypes.c_double),
+                ("hdiff_k4", ctypes.c_double), ("hdiff_w_k4", ctypes.c_double),
+                ("hdiff_temp", ctypes.c_int32), ("ref_T0", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("synchronous", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class icon_state_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("vn", "w", "rho", "exner", "theta_v", "exner_pr")]
+
+
+STATE_FIELDS = ("vn", "w", "rho", "exner", "theta_v", "exner_pr")
+
+_sig = {
+    "icon_grid_create": (ctypes.c_int, [ctypes.POINTER(icon_grid_desc_t), ctypes.POINTER(ctypes.c_void_p)]),
+    "icon_grid_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "icon_dycore_params_default": (None, [ctypes.POINTER(icon_dycore_params_t)]),
+    "icon_dycore_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _f64p,
+                                          ctypes.POINTER(icon_dycore_params_t),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "icon_dycore_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "icon_dycore_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t)]),
+    "icon_nh_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t)]),
+    "icon_nh_diff": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t)]),
+    "icon_velocity_tendencies": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
+    "icon_dycore_reference_state": (ctypes.c_int, [ctypes.c_void_p, _f64p, _f64p]),
+    "icon_dycore_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "icon_dycore_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
+    "icon_dycore_sizes": (ctypes.c_int, [ctypes.c_void_p] + [_i32p] * 4),
+    "icon_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class IconError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+def _check(rc):
+    if rc != ICON_OK:
+        raise IconError(rc, icon_last_error().decode())
+    return rc
+
+
+def default_params(**overrides):
+    p = icon_dycore_params_t()
+    icon_dycore_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or a numpy array (must be contiguous float64)."""
+    if isinstance(x, np.ndarray):
+        if not (x.flags["C_CONTIGUOUS"] and x.dtype == np.float64):
+            raise ValueError("numpy fields must be C-contiguous float64")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor fields must be contiguous")
+    return x.data_ptr()
+
+
+class Grid:
+    """Owns an icon_grid_t built from raw connectivity and coordinates."""
+
+    def __init__(self, grid, radius=6.371229e6, index_base=0):
+        keep = {}
+
+        def i32(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            keep[id(a)] = a
+            return a.ctypes.data_as(_i32p)
+
+        def f64(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep[id(a)] = a
+            return a.ctypes.data_as(_f64p)
+
+        off = index_base
+        d = icon_grid_desc_t(grid.n_cells, grid.n_edges, grid.n_verts, index_base, radius,
+                             i32(grid.c2v + off), i32(grid.c2e + off), i32(grid.e2c + off),
+                             i32(grid.e2v + off), i32(grid.v2e + off), i32(grid.v2c + off),
+                             f64(grid.cell_xyz), f64(grid.vert_xyz), f64(grid.edge_xyz))
+        h = ctypes.c_void_p()
+        _check(icon_grid_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.n_cells, self.n_edges, self.n_verts = grid.n_cells, grid.n_edges, grid.n_verts
+
+    def close(self):
+        if self.handle:
+            icon_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Dycore:
+    """Owns an icon_dycore_t.  ``params`` is an icon_dycore_params_t or a dict of overrides."""
+
+    def __init__(self, grid: Grid, z_ifc, params=None, stream=None):
+        if params is None or isinstance(params, dict):
+            params = default_params(**(params or {}))
+        if stream is not None:
+            params.stream = stream
+        z = np.ascontiguousarray(z_ifc, dtype=np.float64)
+        self.nlev = z.size - 1
+        h = ctypes.c_void_p()
+        _check(icon_dycore_create(grid.handle, self.nlev, z.ctypes.data_as(_f64p), ctypes.byref(params),
+                                  ctypes.byref(h)))
+        self.handle = h
+        self.grid = grid
+        self.params = params
+
+    @staticmethod
+    def _state(st):
+        return icon_state_t(*[_ptr(st[n]) for n in STATE_FIELDS])
+
+    def step(self, st):
+        s = self._state(st)
+        _check(icon_dycore_step(self.handle, ctypes.byref(s)))
+
+    def nh_solve(self, st):
+        s = self._state(st)
+        _check(icon_nh_solve(self.handle, ctypes.byref(s)))
+
+    def nh_diff(self, st):
+        s = self._state(st)
+        _check(icon_nh_diff(self.handle, ctypes.byref(s)))
+
+    def velocity_tendencies(self, vn, w, ddt_vn, ddt_w):
+        _check(icon_velocity_tendencies(self.handle, _ptr(vn), _ptr(w), _ptr(ddt_vn), _ptr(ddt_w)))
+
+    def reference_state(self):
+        th = np.empty(self.nlev)
+        ex = np.empty(self.nlev)
+        _check(icon_dycore_reference_state(self.handle, th.ctypes.data_as(_f64p), ex.ctypes.data_as(_f64p)))
+        return th, ex
+
+    def profile(self, st, nsteps):
+        """Per-kernel launch counts and summed device milliseconds over nsteps steps
+        (events around every launch); returns {name: (launches, ms)}."""
+        s = self._state(st)
+        cap = 64
+        names = ctypes.create_string_buffer(64 * cap)
+        launches = (ctypes.c_int32 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int32()
+        _check(icon_dycore_profile(self.handle, ctypes.byref(s), nsteps, cap, names, launches, ms,
+                                   ctypes.byref(n)))
+        return {names.raw[64 * j:64 * j + 64].split(b"\0")[0].decode(): (launches[j], ms[j])
+                for j in range(n.value)}
+
+    def synchronize(self):
+        _check(icon_dycore_synchronize(self.handle))
+
+    def close(self):
+        if self.handle:
+            icon_dycore_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

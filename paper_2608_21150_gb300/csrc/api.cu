@@ -1,0 +1,580 @@
+// C-ABI entry points of the dycore library (paper Sec. 4.3: the host model
+// gathers field pointers and calls a C function; scalars by value, arrays by
+// reference without copies, device arrays accepted directly).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+using namespace icon;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t err_ = (expr);                                                              \
+    if (err_ != cudaSuccess)                                                                \
+      return fail(ICON_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(err_));     \
+  } while (0)
+
+// Owner of a set of device allocations.
+struct DevArena {
+  std::vector<void*> ptrs;
+  cudaError_t status = cudaSuccess;
+  template <typename T>
+  T* upload(const std::vector<T>& h) {
+    T* d = alloc<T>(h.size());
+    if (d && !h.empty()) {
+      cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) status = e;
+    }
+    return d;
+  }
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (status != cudaSuccess) return nullptr;
+    cudaError_t e = cudaMalloc(&p, (n ? n : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+      status = e;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+}  // namespace
+
+struct icon_grid {
+  HostGrid host;
+  DevGrid dev{};
+  DevArena arena;
+};
+
+struct GraphEntry {
+  StateView key{};
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long last_use = 0;
+};
+
+struct icon_dycore {
+  const icon_grid* grid = nullptr;
+  icon_dycore_params_t params{};
+  Scalars sc{};
+  int nlev = 0;
+  std::vector<double> z_ifc, theta_ref, exner_ref;
+  DevVert vert{};
+  DevGrid g{};  // grid factors with the parameter-dependent edge/cell arrays filled in
+  DevWork work{};
+  DevArena arena;
+  cudaStream_t stream = nullptr;       // caller's stream (may be the default stream)
+  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  GraphEntry graphs[2];
+  unsigned long long use_counter = 0;
+  StateView staging{};                 // device copy used when the caller passes host arrays
+  bool have_staging = false;
+};
+
+extern "C" {
+
+const char* icon_last_error(void) { return g_last_error.c_str(); }
+
+void icon_dycore_params_default(icon_dycore_params_t* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->dtime = 1800.0;
+  p->ndyn_substeps = 5;
+  p->grav = 9.80665;
+  p->rd = 287.04;
+  p->cpd = 1004.64;
+  p->p00 = 1.0e5;
+  p->omega = 7.29212e-5;
+  p->vwind_impl_wgt = 0.65;
+  p->wgt_nnow_vel = 0.25;
+  p->wgt_nnew_vel = 0.75;
+  p->wgt_nnow_rth = 0.6;
+  p->wgt_nnew_rth = 0.4;
+  p->exner_exfac = 1.0 / 3.0;
+  p->divdamp_fac = 0.0025;
+  p->divflux_fac = 0.07;
+  p->rayleigh_coeff = 0.0;
+  p->damp_height = 20000.0;
+  p->hdiff_smag_fac = 0.015;
+  p->hdiff_k4 = 1.0 / 288.0;
+  p->hdiff_w_k4 = 1.0 / 288.0;
+  p->hdiff_temp = 1;
+  p->ref_T0 = 250.0;
+  p->precision = ICON_PREC_FP64;
+  p->use_graph = 1;
+  p->synchronous = 1;
+  p->stream = nullptr;
+}
+
+int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
+  if (!d || !out) return fail(ICON_ERR_ARG, "icon_grid_create: NULL argument");
+  *out = nullptr;
+  if (d->n_cells <= 0 || d->n_edges <= 0 || d->n_verts <= 0)
+    return fail(ICON_ERR_ARG, "icon_grid_create: counts must be positive");
+  if (d->index_base != 0 && d->index_base != 1)
+    return fail(ICON_ERR_ARG, "icon_grid_create: index_base must be 0 or 1");
+  if (!d->c2v || !d->c2e || !d->e2c || !d->e2v || !d->v2e || !d->v2c || !d->cell_xyz || !d->vert_xyz ||
+      !d->edge_xyz)
+    return fail(ICON_ERR_ARG, "icon_grid_create: NULL table or coordinate pointer");
+  icon_grid* g = new (std::nothrow) icon_grid();
+  if (!g) return fail(ICON_ERR_ARG, "icon_grid_create: out of host memory");
+  std::string err = build_host_grid(d, &g->host);
+  if (!err.empty()) {
+    delete g;
+    return fail(ICON_ERR_GRID, "icon_grid_create: " + err);
+  }
+  const HostGrid& h = g->host;
+  DevGrid& v = g->dev;
+  DevArena& A = g->arena;
+  v.nc = h.nc;
+  v.ne = h.ne;
+  v.nv = h.nv;
+  v.c2e = A.upload(h.c2e);
+  v.c2e2c = A.upload(h.c2e2c);
+  v.e2c = A.upload(h.e2c);
+  v.e2v = A.upload(h.e2v_t);
+  v.e2c2v = A.upload(h.e2c2v);
+  v.e2c2e = A.upload(h.e2c2e);
+  v.v2e = A.upload(h.v2e);
+  v.v2c = A.upload(h.v2c);
+  v.div_c = A.upload(h.div_c);
+  v.lap_c = A.upload(h.lap_c);
+  v.e2c_w = A.upload(h.e2c_w);
+  v.grad_c = A.upload(h.grad_c);
+  v.inv_d = A.upload(h.inv_d);
+  v.inv_l = A.upload(h.inv_l);
+  v.vt_w = A.upload(h.vt_w);
+  v.upw = A.upload(h.upw);
+  v.nt = A.upload(h.nt);
+  v.inv_dn = A.upload(h.inv_dn);
+  v.curl_v = A.upload(h.curl_v);
+  v.c2v_w = A.upload(h.c2v_w);
+  v.uv_w = A.upload(h.uv_w);
+  v.mean_area = h.mean_area;
+  if (A.status != cudaSuccess) {
+    std::string m = std::string("icon_grid_create: ") + cudaGetErrorString(A.status);
+    A.release();
+    delete g;
+    return fail(ICON_ERR_CUDA, m);
+  }
+  *out = g;
+  return ICON_OK;
+}
+
+int icon_grid_destroy(icon_grid_t* g) {
+  if (!g) return ICON_OK;
+  g->arena.release();
+  delete g;
+  return ICON_OK;
+}
+
+static void free_graphs(icon_dycore* d) {
+  for (auto& e : d->graphs) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    e = GraphEntry{};
+  }
+}
+
+int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
+                       const icon_dycore_params_t* p, icon_dycore_t** out) {
+  if (!grid || !z_ifc || !p || !out) return fail(ICON_ERR_ARG, "icon_dycore_create: NULL argument");
+  *out = nullptr;
+  if (nlev < 2) return fail(ICON_ERR_ARG, "icon_dycore_create: nlev must be >= 2");
+  for (int k = 0; k <= nlev; ++k)
+    if (!std::isfinite(z_ifc[k])) return fail(ICON_ERR_ARG, "icon_dycore_create: z_ifc not finite");
+  for (int k = 0; k < nlev; ++k)
+    if (!(z_ifc[k] > z_ifc[k + 1])) return fail(ICON_ERR_ARG, "icon_dycore_create: z_ifc must decrease");
+  if (z_ifc[nlev] != 0.0) return fail(ICON_ERR_ARG, "icon_dycore_create: z_ifc[nlev] must be 0 (flat ground)");
+  if (!(p->dtime > 0.0) || p->ndyn_substeps < 1)
+    return fail(ICON_ERR_ARG, "icon_dycore_create: dtime must be > 0 and ndyn_substeps >= 1");
+  if (p->precision != ICON_PREC_FP64)
+    return fail(ICON_ERR_UNSUPPORTED, "icon_dycore_create: only ICON_PREC_FP64 is built");
+
+  icon_dycore* d = new (std::nothrow) icon_dycore();
+  if (!d) return fail(ICON_ERR_ARG, "icon_dycore_create: out of host memory");
+  d->grid = grid;
+  d->params = *p;
+  d->nlev = nlev;
+  d->stream = static_cast<cudaStream_t>(p->stream);
+  const HostGrid& h = grid->host;
+  const int nc = h.nc, ne = h.ne, nv = h.nv;
+
+  // scalars
+  Scalars& s = d->sc;
+  s.dtime = p->dtime;
+  s.dt_s = p->dtime / p->ndyn_substeps;
+  s.grav = p->grav;
+  s.rd = p->rd;
+  s.cpd = p->cpd;
+  s.cvd = p->cpd - p->rd;
+  s.p00 = p->p00;
+  s.beta = p->vwind_impl_wgt;
+  s.wnow_vel = p->wgt_nnow_vel;
+  s.wnew_vel = p->wgt_nnew_vel;
+  s.wnow_rth = p->wgt_nnow_rth;
+  s.wnew_rth = p->wgt_nnew_rth;
+  s.exfac = p->exner_exfac;
+  s.divdamp = p->divdamp_fac;
+  s.divflux = p->divflux_fac * h.mean_area;
+  s.rd_o_cvd = p->rd / s.cvd;
+  s.cvd_o_rd = s.cvd / p->rd;
+  s.hdiff_temp = p->hdiff_temp ? 1 : 0;
+
+  // vertical metrics and reference state (row A0)
+  d->z_ifc.assign(z_ifc, z_ifc + nlev + 1);
+  std::vector<double> z_mc(nlev), dz(nlev), inv_dz(nlev), inv_dzh(nlev + 1, 0.0), wgt(nlev + 1, 0.0);
+  std::vector<double> dref(nlev + 1, 0.0), ray(nlev + 1, 1.0);
+  for (int k = 0; k < nlev; ++k) {
+    z_mc[k] = 0.5 * (z_ifc[k] + z_ifc[k + 1]);
+    dz[k] = z_ifc[k] - z_ifc[k + 1];
+    inv_dz[k] = 1.0 / dz[k];
+  }
+  for (int k = 1; k < nlev; ++k) {
+    inv_dzh[k] = 1.0 / (z_mc[k - 1] - z_mc[k]);
+    wgt[k] = (z_ifc[k] - z_mc[k]) / (z_mc[k - 1] - z_mc[k]);
+  }
+  const double T0 = p->ref_T0, H = p->cpd * T0 / p->grav;
+  d->theta_ref.resize(nlev);
+  d->exner_ref.resize(nlev);
+  for (int k = 0; k < nlev; ++k) d->theta_ref[k] = T0 * std::exp(z_mc[k] / H);
+  d->exner_ref[nlev - 1] = std::exp(-z_mc[nlev - 1] / H);
+  for (int k = nlev - 1; k >= 1; --k) {
+    double th_ic = wgt[k] * d->theta_ref[k - 1] + (1.0 - wgt[k]) * d->theta_ref[k];
+    d->exner_ref[k - 1] = d->exner_ref[k] - p->grav * (z_mc[k - 1] - z_mc[k]) / (p->cpd * th_ic);
+  }
+  for (int k = 1; k < nlev; ++k) dref[k] = (d->exner_ref[k - 1] - d->exner_ref[k]) * inv_dzh[k];
+  if (p->rayleigh_coeff > 0.0) {
+    const double top = z_ifc[0], zd = p->damp_height;
+    for (int k = 0; k <= nlev; ++k)
+      if (z_ifc[k] > zd) {
+        double sn = std::sin(0.5 * M_PI * (z_ifc[k] - zd) / (top - zd));
+        ray[k] = 1.0 / (1.0 + s.dt_s * p->rayleigh_coeff * sn * sn);
+      }
+  }
+
+  DevArena& A = d->arena;
+  DevVert& v = d->vert;
+  v.nlev = nlev;
+  v.dz = A.upload(dz);
+  v.inv_dz = A.upload(inv_dz);
+  v.inv_dzh = A.upload(inv_dzh);
+  v.wgt = A.upload(wgt);
+  v.theta_ref = A.upload(d->theta_ref);
+  v.exner_ref = A.upload(d->exner_ref);
+  v.dexner_ref_ic = A.upload(dref);
+  v.ray_fac = A.upload(ray);
+
+  // parameter-dependent grid factors
+  d->g = grid->dev;
+  {
+    std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc);
+    for (int e = 0; e < ne; ++e) {
+      fe[e] = 2.0 * p->omega * h.coriolis_z[e];
+      smag[e] = p->hdiff_smag_fac * h.edge_area[e];
+      k4[e] = p->hdiff_k4 * h.edge_area[e] * h.edge_area[e];
+    }
+    for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
+    d->g.f_e = A.upload(fe);
+    d->g.smag_a = A.upload(smag);
+    d->g.k4_a = A.upload(k4);
+    d->g.k4w_c = A.upload(k4w);
+  }
+
+  // work arrays
+  const size_t ef = (size_t)ne * nlev, eh = (size_t)ne * (nlev + 1);
+  const size_t cf = (size_t)nc * nlev, ch = (size_t)nc * (nlev + 1);
+  const size_t vf = (size_t)nv * nlev, vh = (size_t)nv * (nlev + 1);
+  DevWork& w = d->work;
+  w.vt = A.alloc<double>(ef);
+  w.ekin_e = A.alloc<double>(ef);
+  w.ddt_vn0 = A.alloc<double>(ef);
+  w.ddt_vn1 = A.alloc<double>(ef);
+  w.rho_e = A.alloc<double>(ef);
+  w.theta_e = A.alloc<double>(ef);
+  w.hpg = A.alloc<double>(ef);
+  w.vn_p = A.alloc<double>(ef);
+  w.lap_vn = A.alloc<double>(ef);
+  w.nu = A.alloc<double>(ef);
+  w.gw_e = A.alloc<double>(eh);
+  w.ekin_c = A.alloc<double>(cf);
+  w.grad4 = A.alloc<double>(4 * cf);
+  w.rho_p = A.alloc<double>(cf);
+  w.exner_p = A.alloc<double>(cf);
+  w.theta_p = A.alloc<double>(cf);
+  w.zb = A.alloc<double>(cf);
+  w.divd = A.alloc<double>(cf);
+  w.divd2 = A.alloc<double>(cf);
+  w.dtheta = A.alloc<double>(cf);
+  w.div_l = A.alloc<double>(cf);
+  w.div_vn = A.alloc<double>(cf);
+  w.ddt_w0 = A.alloc<double>(ch);
+  w.ddt_w1 = A.alloc<double>(ch);
+  w.w_p = A.alloc<double>(ch);
+  w.lap_w = A.alloc<double>(ch);
+  w.zeta = A.alloc<double>(vf);
+  w.uv3 = A.alloc<double>(3 * vf);
+  w.curl_l = A.alloc<double>(vf);
+  w.w_v = A.alloc<double>(vh);
+  w.col = A.alloc<double>(6 * ch);
+  if (A.status == cudaSuccess) {
+    cudaError_t e = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) A.status = e;
+  }
+  if (A.status != cudaSuccess) {
+    std::string m = std::string("icon_dycore_create: ") + cudaGetErrorString(A.status);
+    A.release();
+    if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+    delete d;
+    return fail(ICON_ERR_CUDA, m);
+  }
+  *out = d;
+  return ICON_OK;
+}
+
+int icon_dycore_destroy(icon_dycore_t* d) {
+  if (!d) return ICON_OK;
+  cudaStreamSynchronize(d->stream);
+  free_graphs(d);
+  if (d->have_staging) {
+    cudaFree(d->staging.vn);
+    cudaFree(d->staging.w);
+    cudaFree(d->staging.rho);
+    cudaFree(d->staging.exner);
+    cudaFree(d->staging.theta_v);
+    cudaFree(d->staging.exner_pr);
+  }
+  d->arena.release();
+  if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+  delete d;
+  return ICON_OK;
+}
+
+namespace {
+
+enum class Where { kDevice, kHost, kMixed };
+
+Where locate(const icon_state_t* s) {
+  const void* ptrs[6] = {s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr};
+  int ndev = 0;
+  for (const void* p : ptrs) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;  // unknown to CUDA: plain host memory
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ++ndev;
+  }
+  if (ndev == 6) return Where::kDevice;
+  if (ndev == 0) return Where::kHost;
+  return Where::kMixed;
+}
+
+enum class Op { kStep, kSubstep, kDiffusion };
+
+void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
+  if (op == Op::kStep || op == Op::kSubstep) {
+    int n = op == Op::kStep ? d->params.ndyn_substeps : 1;
+    for (int i = 0; i < n; ++i) launch_substep(d->g, d->vert, d->sc, st, d->work, s);
+  }
+  if (op == Op::kStep || op == Op::kDiffusion) launch_diffusion(d->g, d->vert, d->sc, st, d->work, s);
+}
+
+bool same(const StateView& a, const StateView& b) {
+  return a.vn == b.vn && a.w == b.w && a.rho == b.rho && a.exner == b.exner && a.theta_v == b.theta_v &&
+         a.exner_pr == b.exner_pr;
+}
+
+// Graph of one full step for this set of state pointers; a cache of two
+// entries covers double-buffered callers (as the paper's descriptor cache).
+int step_graph(icon_dycore* d, const StateView& st, cudaGraphExec_t* exec) {
+  ++d->use_counter;
+  for (auto& e : d->graphs)
+    if (e.exec && same(e.key, st)) {
+      e.last_use = d->use_counter;
+      *exec = e.exec;
+      return ICON_OK;
+    }
+  GraphEntry* slot = &d->graphs[0];
+  for (auto& e : d->graphs)
+    if (!e.exec || e.last_use < slot->last_use) slot = &e;
+  if (slot->exec) {
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    cudaGraphExecDestroy(slot->exec);
+    *slot = GraphEntry{};
+  }
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue(d, Op::kStep, st, d->cap_stream);
+  cudaError_t le = cudaGetLastError();
+  cudaError_t ee = cudaStreamEndCapture(d->cap_stream, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(ICON_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(le));
+  }
+  CUDA_TRY(ee);
+  cudaError_t ie = cudaGraphInstantiate(&slot->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CUDA_TRY(ie);
+  slot->key = st;
+  slot->last_use = d->use_counter;
+  *exec = slot->exec;
+  return ICON_OK;
+}
+
+int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
+  if (!d || !s) return fail(ICON_ERR_ARG, std::string(name) + ": NULL argument");
+  if (!s->vn || !s->w || !s->rho || !s->exner || !s->theta_v || !s->exner_pr)
+    return fail(ICON_ERR_ARG, std::string(name) + ": NULL state field");
+  const HostGrid& h = d->grid->host;
+  const int nlev = d->nlev;
+  const size_t ef = (size_t)h.ne * nlev, cf = (size_t)h.nc * nlev, ch = (size_t)h.nc * (nlev + 1);
+  Where where = locate(s);
+  if (where == Where::kMixed)
+    return fail(ICON_ERR_ARG, std::string(name) + ": state mixes host and device pointers");
+  StateView st{s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr};
+  cudaStream_t stream = d->stream;
+  if (where == Where::kHost) {
+    if (!d->have_staging) {
+      StateView& g = d->staging;
+      CUDA_TRY(cudaMalloc(&g.vn, ef * 8));
+      CUDA_TRY(cudaMalloc(&g.w, ch * 8));
+      CUDA_TRY(cudaMalloc(&g.rho, cf * 8));
+      CUDA_TRY(cudaMalloc(&g.exner, cf * 8));
+      CUDA_TRY(cudaMalloc(&g.theta_v, cf * 8));
+      CUDA_TRY(cudaMalloc(&g.exner_pr, cf * 8));
+      d->have_staging = true;
+    }
+    const StateView& g = d->staging;
+    CUDA_TRY(cudaMemcpyAsync(g.vn, s->vn, ef * 8, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(g.w, s->w, ch * 8, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(g.rho, s->rho, cf * 8, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(g.exner, s->exner, cf * 8, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(g.theta_v, s->theta_v, cf * 8, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(g.exner_pr, s->exner_pr, cf * 8, cudaMemcpyHostToDevice, stream));
+    st = g;
+  }
+  if (op == Op::kStep && d->params.use_graph) {
+    cudaGraphExec_t exec = nullptr;
+    int rc = step_graph(d, st, &exec);
+    if (rc != ICON_OK) return rc;
+    CUDA_TRY(cudaGraphLaunch(exec, stream));
+  } else {
+    enqueue(d, op, st, stream);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (where == Where::kHost) {
+    const StateView& g = d->staging;
+    CUDA_TRY(cudaMemcpyAsync(s->vn, g.vn, ef * 8, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(s->w, g.w, ch * 8, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(s->rho, g.rho, cf * 8, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(s->exner, g.exner, cf * 8, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(s->theta_v, g.theta_v, cf * 8, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(s->exner_pr, g.exner_pr, cf * 8, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+  } else if (d->params.synchronous) {
+    CUDA_TRY(cudaStreamSynchronize(stream));
+  }
+  return ICON_OK;
+}
+
+}  // namespace
+
+int icon_dycore_step(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op::kStep, "icon_dycore_step"); }
+int icon_nh_solve(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op::kSubstep, "icon_nh_solve"); }
+int icon_nh_diff(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op::kDiffusion, "icon_nh_diff"); }
+
+int icon_velocity_tendencies(icon_dycore_t* d, const double* vn, const double* w, double* ddt_vn, double* ddt_w) {
+  if (!d || !vn || !w || !ddt_vn || !ddt_w) return fail(ICON_ERR_ARG, "icon_velocity_tendencies: NULL argument");
+  launch_velocity_tendencies(d->g, d->vert, vn, w, d->work, ddt_vn, ddt_w, nullptr, nullptr, d->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return ICON_OK;
+}
+
+int icon_dycore_reference_state(const icon_dycore_t* d, double* theta_ref, double* exner_ref) {
+  if (!d || !theta_ref || !exner_ref) return fail(ICON_ERR_ARG, "icon_dycore_reference_state: NULL argument");
+  std::memcpy(theta_ref, d->theta_ref.data(), d->nlev * sizeof(double));
+  std::memcpy(exner_ref, d->exner_ref.data(), d->nlev * sizeof(double));
+  return ICON_OK;
+}
+
+int icon_dycore_profile(icon_dycore_t* d, const icon_state_t* s, int32_t nsteps, int32_t max_kernels, char* names,
+                        int32_t* launches, double* ms, int32_t* n_kernels) {
+  if (!d || !s || !names || !launches || !ms || !n_kernels || nsteps < 1 || max_kernels < 1)
+    return fail(ICON_ERR_ARG, "icon_dycore_profile: NULL or invalid argument");
+  if (!s->vn || !s->w || !s->rho || !s->exner || !s->theta_v || !s->exner_pr)
+    return fail(ICON_ERR_ARG, "icon_dycore_profile: NULL state field");
+  if (locate(s) != Where::kDevice) return fail(ICON_ERR_ARG, "icon_dycore_profile: state must be on the device");
+  StateView st{s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr};
+  Prof prof;
+  g_prof = &prof;
+  for (int i = 0; i < nsteps; ++i) enqueue(d, Op::kStep, st, d->stream);
+  g_prof = nullptr;
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  std::vector<std::string> nm;
+  std::vector<int> cnt;
+  std::vector<double> tot;
+  for (const auto& r : prof.recs) {
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.e0, r.e1));
+    size_t j = 0;
+    while (j < nm.size() && nm[j] != r.name) ++j;
+    if (j == nm.size()) {
+      nm.push_back(r.name);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[j] += 1;
+    tot[j] += t;
+  }
+  if ((int)nm.size() > max_kernels) return fail(ICON_ERR_ARG, "icon_dycore_profile: max_kernels too small");
+  for (size_t j = 0; j < nm.size(); ++j) {
+    std::snprintf(names + 64 * j, 64, "%s", nm[j].c_str());
+    launches[j] = cnt[j];
+    ms[j] = tot[j];
+  }
+  *n_kernels = (int32_t)nm.size();
+  return ICON_OK;
+}
+
+int icon_dycore_synchronize(icon_dycore_t* d) {
+  if (!d) return fail(ICON_ERR_ARG, "icon_dycore_synchronize: NULL argument");
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return ICON_OK;
+}
+
+int icon_dycore_sizes(const icon_dycore_t* d, int32_t* nlev, int32_t* nc, int32_t* ne, int32_t* nv) {
+  if (!d) return fail(ICON_ERR_ARG, "icon_dycore_sizes: NULL argument");
+  if (nlev) *nlev = d->nlev;
+  if (nc) *nc = d->grid->host.nc;
+  if (ne) *ne = d->grid->host.ne;
+  if (nv) *nv = d->grid->host.nv;
+  return ICON_OK;
+}
+
+}  // extern "C"
