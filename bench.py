@@ -178,9 +178,11 @@ def run_reference(args):
 
 def config_dict(prec):
     w = WORKLOAD
-    return {"workload": "R2B6 L90 (327680 cells, 491520 edges), dt=%gs, %d substeps + diffusion, %s, "
-                        "JW-type jet seed %d" % (w["dtime"], w["ndyn"], prec.upper(), w["seed"]),
-            "grid": "R2B6", "nlev": w["nlev"], "dtime_s": w["dtime"], "ndyn_substeps": w["ndyn"],
+    nc = 80 * 4 ** w["bisections"]
+    return {"workload": "R2B%d L90 (%d cells, %d edges), dt=%gs, %d substeps + diffusion, %s, "
+                        "JW-type jet seed %d" % (w["bisections"], nc, 3 * nc // 2, w["dtime"], w["ndyn"],
+                                                 prec.upper(), w["seed"]),
+            "grid": "R2B%d" % w["bisections"], "nlev": w["nlev"], "dtime_s": w["dtime"], "ndyn_substeps": w["ndyn"],
             "precision": prec, "cuda_graph": True,
             "l2": "inputs larger than L2 (FP64 state 1.5 GB, scratch ~9 GB); no flush"}
 
@@ -308,9 +310,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=WORKLOAD["bisections"],
+                    help="RnBm bisections (default 6 = R2B6); smaller grids only for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    WORKLOAD["bisections"] = args.grid
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
