@@ -275,6 +275,26 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
       }
   }
 
+  // per-level coefficients of the column solve (layout documented in DevVert)
+  std::vector<double> colc(8 * (size_t)(nlev + 1), 0.0);
+  {
+    const double dts = s.dt_s, beta = s.beta;
+    for (int k = 0; k <= nlev; ++k) {
+      double* c = &colc[8 * (size_t)k];
+      if (k < nlev) {
+        c[0] = dts * s.rd_o_cvd / dz[k];
+        c[1] = dts * (1.0 - beta) / dz[k];
+        c[2] = dts * beta / dz[k];
+      }
+      if (k >= 1 && k < nlev) {
+        c[3] = dts * p->cpd * (1.0 - beta) * inv_dzh[k];
+        c[4] = dts * p->cpd * dref[k];
+        c[5] = dts * p->cpd * beta * inv_dzh[k];
+        c[6] = wgt[k];
+        c[7] = 1.0 - wgt[k];
+      }
+    }
+  }
   DevArena& A = d->arena;
   DevVert& v = d->vert;
   v.nlev = nlev;
@@ -286,6 +306,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   v.exner_ref = A.upload(d->exner_ref);
   v.dexner_ref_ic = A.upload(dref);
   v.ray_fac = A.upload(ray);
+  v.colc = A.upload(colc);
 
   // parameter-dependent grid factors
   d->g = grid->dev;
@@ -324,8 +345,9 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   w.rho_p = A.alloc<double>(cf);
   w.exner_p = A.alloc<double>(cf);
   w.theta_p = A.alloc<double>(cf);
-  w.zb = A.alloc<double>(cf);
   w.divd = A.alloc<double>(cf);
+  w.div_m = A.alloc<double>(cf);
+  w.div_t = A.alloc<double>(cf);
   w.divd2 = A.alloc<double>(cf);
   w.dtheta = A.alloc<double>(cf);
   w.div_l = A.alloc<double>(cf);
@@ -338,9 +360,14 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   w.uv3 = A.alloc<double>(3 * vf);
   w.curl_l = A.alloc<double>(vf);
   w.w_v = A.alloc<double>(vh);
-  w.col = A.alloc<double>(6 * ch);
+  w.col = A.alloc<double>(7 * ch);
+  w.zbl = A.alloc<double>(ch);
   if (A.status == cudaSuccess) {
     cudaError_t e = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) A.status = e;
+  }
+  if (A.status == cudaSuccess) {
+    cudaError_t e = init_column_kernels();
     if (e != cudaSuccess) A.status = e;
   }
   if (A.status != cudaSuccess) {

@@ -56,6 +56,10 @@ struct DevVert {
   const double* exner_ref; // [nlev]
   const double* dexner_ref_ic;  // [nlev+1]
   const double* ray_fac;   // [nlev+1] 1/(1 + dt_s tau^-1 sin^2(..)) (1 where off)
+  // per-level coefficients of the column solve, colc[k*8 + j]:
+  // 0 dt rd/(cvd dz_k), 1 dt (1-beta)/dz_k, 2 dt beta/dz_k, 3 dt cpd (1-beta)/dzh_k,
+  // 4 dt cpd dexner_ref_ic_k, 5 dt cpd beta/dzh_k, 6 wgt_k, 7 1 - wgt_k
+  const double* colc;      // [(nlev+1)*8]
 };
 
 // Work arrays of one substep / step (device, FP64).
@@ -66,14 +70,15 @@ struct DevWork {
   // edges, half levels
   double* gw_e;
   // cells, full levels
-  double *ekin_c, *grad4, *rho_p, *exner_p, *theta_p, *zb, *divd, *divd2, *dtheta, *div_l, *div_vn;
+  double *ekin_c, *grad4, *rho_p, *exner_p, *theta_p, *divd, *div_m, *div_t, *divd2, *dtheta, *div_l, *div_vn;
   // cells, half levels
   double *ddt_w0, *ddt_w1, *w_p, *lap_w;
   // vertices
   double *zeta, *uv3, *curl_l;  // full levels (uv3: 3 fields)
   double* w_v;                  // half levels
   // column-solve scratch, level-major [k][c]
-  double* col;                  // 6 arrays of (nlev+1)*nc
+  double* col;                  // 7 planes of (nlev+1)*nc: cp, rp, rho*, pr*, rho_ic, alpha, eos
+  double* zbl;                  // level-major zb [(nlev+1)*nc], predictor -> corrector
 };
 
 struct Scalars {

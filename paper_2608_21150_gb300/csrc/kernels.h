@@ -32,20 +32,22 @@ struct Prof {
 };
 extern thread_local Prof* g_prof;
 
-#define ICON_LAUNCH(name, grid, block, stream, kernel, ...)     \
-  do {                                                          \
-    cudaEvent_t e0_ = nullptr;                                  \
-    if (g_prof) {                                               \
-      e0_ = g_prof->get();                                      \
-      cudaEventRecord(e0_, stream);                             \
-    }                                                           \
-    kernel<<<grid, block, 0, stream>>>(__VA_ARGS__);            \
-    if (g_prof) {                                               \
-      cudaEvent_t e1_ = g_prof->get();                          \
-      cudaEventRecord(e1_, stream);                             \
-      g_prof->recs.push_back({name, e0_, e1_});                 \
-    }                                                           \
+#define ICON_LAUNCH_SMEM(name, grid, block, smem, stream, kernel, ...) \
+  do {                                                                  \
+    cudaEvent_t e0_ = nullptr;                                          \
+    if (g_prof) {                                                       \
+      e0_ = g_prof->get();                                              \
+      cudaEventRecord(e0_, stream);                                     \
+    }                                                                   \
+    kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);                 \
+    if (g_prof) {                                                       \
+      cudaEvent_t e1_ = g_prof->get();                                  \
+      cudaEventRecord(e1_, stream);                                     \
+      g_prof->recs.push_back({name, e0_, e1_});                         \
+    }                                                                   \
   } while (0)
+#define ICON_LAUNCH(name, grid, block, stream, kernel, ...) \
+  ICON_LAUNCH_SMEM(name, grid, block, 0, stream, kernel, __VA_ARGS__)
 
 // Device pointers of one prognostic state (level-contiguous, FP64).
 struct StateView {
@@ -60,6 +62,14 @@ void launch_velocity_tendencies(const DevGrid& g, const DevVert& v, const double
 // Rows A5-A9: one predictor + corrector substep, state updated in place.
 void launch_substep(const DevGrid& g, const DevVert& v, const Scalars& sc, const StateView& st, DevWork& wk,
                     cudaStream_t s);
+// Row A7: vertically implicit column solve (predictor: corrector = 0 writes the
+// predicted state to wk.w_p/rho_p/exner_p/theta_p; corrector = 1 writes the new
+// state over st).  Needs wk.div_m/div_t (flux divergences) of the pass.
+void launch_column(const DevGrid& g, const DevVert& v, const Scalars& sc, int corrector, const StateView& st,
+                   DevWork& wk, cudaStream_t s);
+// One-time kernel attributes (dynamic shared memory above 48 KB).
+cudaError_t init_column_kernels();
+
 // Row A10: diffusion over dtime, state updated in place.
 void launch_diffusion(const DevGrid& g, const DevVert& v, const Scalars& sc, const StateView& st, DevWork& wk,
                       cudaStream_t s);

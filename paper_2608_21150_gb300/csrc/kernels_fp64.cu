@@ -260,178 +260,50 @@ __global__ void sn_edge_corr(DevGrid g, DevVert v, Scalars sc, double* __restric
 // divergence of vn* (fourth-order damping and flux filter of the predictor)
 // or of vn^{n+1} (flux filter of the corrector).
 // -------------------------------------------------------------------------
-__global__ void sn_cell_div(DevGrid g, DevVert v, const double* __restrict__ vn, double* __restrict__ divd) {
+// In the predictor launch it also updates the exner extrapolation history,
+// exner_pr = exner - exner_ref (sn_edge_pred, the last reader of the old
+// history, has completed).
+__global__ void sn_cell_div(DevGrid g, DevVert v, const double* __restrict__ vn, double* __restrict__ divd,
+                            const double* __restrict__ exner, double* __restrict__ exner_pr) {
   int c, k;
   const int nlev = v.nlev;
   if (!flat_index(g.nc, nlev, c, k)) return;
   const int* ce = g.c2e + 3 * (size_t)c;
   const double* dv = g.div_c + 3 * (size_t)c;
-  divd[(size_t)c * nlev + k] = dv[0] * vn[(size_t)ce[0] * nlev + k] + dv[1] * vn[(size_t)ce[1] * nlev + k] +
-                               dv[2] * vn[(size_t)ce[2] * nlev + k];
+  const size_t i = (size_t)c * nlev + k;
+  divd[i] = dv[0] * vn[(size_t)ce[0] * nlev + k] + dv[1] * vn[(size_t)ce[1] * nlev + k] +
+            dv[2] * vn[(size_t)ce[2] * nlev + k];
+  if (exner_pr) exner_pr[i] = exner[i] - v.exner_ref[k];
 }
 
 // -------------------------------------------------------------------------
-// A7: vertically implicit solve, one thread per column (see the oracle's
-// vertical_solve for the equations).  Predictor: half-level rho/theta from
-// the "now" state, writes the predicted state to (w_o, rho_o, exner_o,
-// theta_o), updates exner_pr, stores zb and the divergence of vn* for the
-// damping.  Corrector: half-level values from 0.6 now + 0.4 predicted, reuses
-// zb, writes the new state in place.  Scratch `col` holds level-major
-// [k][c] planes: cp, rp, rho*, pr*, rho_ic, alpha.
+// Divergences of the horizontal mass and theta fluxes with the flux-velocity
+// filter, per cell and level:
+//   vf_e = vn_e + divflux (D_c1 - D_c0)/d_e,  F_e = rho_e vf_e,
+//   div_m = sum s l F / A,  div_t = sum s l F theta_e / A
 // -------------------------------------------------------------------------
-// The corrector writes the new state over the "now" state of its own column
-// (w_o == w etc.), so the state pointers carry no __restrict__.
-__global__ void sn_column(DevGrid g, DevVert v, Scalars sc, int corrector,
-                          const double* w, const double* rho,
-                          const double* exner, const double* theta,
-                          double* __restrict__ exner_pr, const double* __restrict__ ddt_w0,
-                          const double* __restrict__ ddt_w1, const double* __restrict__ vn_f,
-                          const double* __restrict__ divd, const double* __restrict__ rho_e,
-                          const double* __restrict__ theta_e, const double* __restrict__ rho_p,
-                          const double* __restrict__ theta_p, double* __restrict__ zb_buf, double* w_o,
-                          double* rho_o, double* exner_o, double* theta_o, double* __restrict__ col) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nc = g.nc;
-  if (c >= nc) return;
-  const int nlev = v.nlev, nlevp = nlev + 1;
-  const double dt = sc.dt_s, beta = sc.beta, ombeta = 1.0 - beta;
-  const size_t plane = (size_t)nlevp * nc;
-  double* cp_s = col;
-  double* rp_s = col + plane;
-  double* rs_s = col + 2 * plane;
-  double* ps_s = col + 3 * plane;
-  double* ri_s = col + 4 * plane;
-  double* al_s = col + 5 * plane;
+__global__ void sn_cell_fluxdiv(DevGrid g, DevVert v, Scalars sc, const double* __restrict__ vn,
+                                const double* __restrict__ divd, const double* __restrict__ rho_e,
+                                const double* __restrict__ theta_e, double* __restrict__ div_m,
+                                double* __restrict__ div_t) {
+  int c, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.nc, nlev, c, k)) return;
   const int* ce = g.c2e + 3 * (size_t)c;
   const double* dv = g.div_c + 3 * (size_t)c;
-  const size_t e0 = (size_t)ce[0] * nlev, e1 = (size_t)ce[1] * nlev, e2 = (size_t)ce[2] * nlev;
-  const size_t cb = (size_t)c * nlev, cbh = (size_t)c * nlevp;
-  // flux velocity vn + divflux * (D_c1 - D_c0)/d_e of the three edges
-  const size_t d00 = (size_t)g.e2c[2 * ce[0]] * nlev, d01 = (size_t)g.e2c[2 * ce[0] + 1] * nlev;
-  const size_t d10 = (size_t)g.e2c[2 * ce[1]] * nlev, d11 = (size_t)g.e2c[2 * ce[1] + 1] * nlev;
-  const size_t d20 = (size_t)g.e2c[2 * ce[2]] * nlev, d21 = (size_t)g.e2c[2 * ce[2] + 1] * nlev;
-  const double kf0 = sc.divflux * g.inv_d[ce[0]], kf1 = sc.divflux * g.inv_d[ce[1]],
-               kf2 = sc.divflux * g.inv_d[ce[2]];
-
-  auto rho_at = [&](int k) -> double {
-    return corrector ? sc.wnow_rth * rho[cb + k] + sc.wnew_rth * rho_p[cb + k] : rho[cb + k];
-  };
-  auto th_at = [&](int k) -> double {
-    return corrector ? sc.wnow_rth * theta[cb + k] + sc.wnew_rth * theta_p[cb + k] : theta[cb + k];
-  };
-
-  // half-level quantities of the current interface k: rho_ic, theta_ic,
-  // theta'_ic (zero at top and ground; w = 0 there)
-  double rho_k = rho_at(0), th_k = th_at(0);
-  double ric_k = 0.0, tic_k = 0.0, tpic_k = 0.0;   // half level 0
-  double zb_km1 = 0.0, al_km1 = 0.0, ps_km1 = 0.0;  // full level k-1 values
-  double cp_km1 = 0.0, rp_km1 = 0.0;
-  double pr_km1 = 0.0;
-  for (int k = 0; k < nlev; ++k) {
-    // half level k+1 interface values
-    double ric_k1 = 0.0, tic_k1 = 0.0, tpic_k1 = 0.0, rho_k1 = 0.0, th_k1 = 0.0;
-    if (k + 1 < nlev) {
-      rho_k1 = rho_at(k + 1);
-      th_k1 = th_at(k + 1);
-      double wg = v.wgt[k + 1];
-      ric_k1 = wg * rho_k + (1.0 - wg) * rho_k1;
-      tic_k1 = wg * th_k + (1.0 - wg) * th_k1;
-      tpic_k1 = wg * (th_k - v.theta_ref[k]) + (1.0 - wg) * (th_k1 - v.theta_ref[k + 1]);
-    }
-    // full level k
-    const double pi_n = exner[cb + k];
-    const double pr_k = pi_n - v.exner_ref[k];
-    double zb;
-    if (!corrector) {
-      zb = dt * sc.rd_o_cvd * pi_n / (rho[cb + k] * theta[cb + k] * v.dz[k]);
-      zb_buf[cb + k] = zb;
-      exner_pr[cb + k] = pr_k;
-    } else {
-      zb = zb_buf[cb + k];
-    }
-    const double vf0 = vn_f[e0 + k] + kf0 * (divd[d01 + k] - divd[d00 + k]);
-    const double vf1 = vn_f[e1 + k] + kf1 * (divd[d11 + k] - divd[d10 + k]);
-    const double vf2 = vn_f[e2 + k] + kf2 * (divd[d21 + k] - divd[d20 + k]);
-    const double fm0 = rho_e[e0 + k] * vf0, fm1 = rho_e[e1 + k] * vf1, fm2 = rho_e[e2 + k] * vf2;
-    const double dm = dv[0] * fm0 + dv[1] * fm1 + dv[2] * fm2;
-    const double dtf = dv[0] * (fm0 * theta_e[e0 + k]) + dv[1] * (fm1 * theta_e[e1 + k]) +
-                       dv[2] * (fm2 * theta_e[e2 + k]);
-    const double wk = w[cbh + k], wk1 = w[cbh + k + 1];
-    const double rt_k = ric_k * tic_k, rt_k1 = ric_k1 * tic_k1;
-    const double rstar = rho[cb + k] - dt * dm - dt * ombeta * (ric_k * wk - ric_k1 * wk1) * v.inv_dz[k];
-    const double pstar = pr_k - zb * (v.dz[k] * dtf + ombeta * (rt_k * wk - rt_k1 * wk1));
-    const double al_k = beta * rt_k;
-    const double al_k1 = beta * rt_k1;
-    rs_s[(size_t)k * nc + c] = rstar;
-    ps_s[(size_t)k * nc + c] = pstar;
-    ri_s[(size_t)k * nc + c] = ric_k;
-    al_s[(size_t)k * nc + c] = al_k;
-    if (k >= 1) {
-      // tridiagonal row of half level k
-      const double ddtw = corrector ? sc.wnow_vel * ddt_w0[cbh + k] + sc.wnew_vel * ddt_w1[cbh + k]
-                                    : ddt_w0[cbh + k];
-      const double wstar = wk + dt * ddtw -
-                           dt * sc.cpd *
-                               (ombeta * tic_k * (pr_km1 - pr_k) * v.inv_dzh[k] + tpic_k * v.dexner_ref_ic[k]);
-      const double gam = dt * sc.cpd * beta * tic_k * v.inv_dzh[k];
-      const double a = -gam * zb_km1 * al_km1;
-      const double b = 1.0 + gam * al_k * (zb_km1 + zb);
-      const double cc = -gam * zb * al_k1;
-      const double r = wstar - gam * (ps_km1 - pstar);
-      double cpk, rpk;
-      if (k == 1) {
-        cpk = cc / b;
-        rpk = r / b;
-      } else {
-        const double m = 1.0 / (b - a * cp_km1);
-        cpk = cc * m;
-        rpk = (r - a * rp_km1) * m;
-      }
-      cp_s[(size_t)k * nc + c] = cpk;
-      rp_s[(size_t)k * nc + c] = rpk;
-      cp_km1 = cpk;
-      rp_km1 = rpk;
-    }
-    // shift
-    zb_km1 = zb;
-    al_km1 = al_k;
-    ps_km1 = pstar;
-    pr_km1 = pr_k;
-    rho_k = rho_k1;
-    th_k = th_k1;
-    ric_k = ric_k1;
-    tic_k = tic_k1;
-    tpic_k = tpic_k1;
+  double dm = 0.0, dt = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int e = ce[j];
+    const size_t ie = (size_t)e * nlev + k;
+    const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+    const double vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
+    const double f = rho_e[ie] * vf;
+    dm += dv[j] * f;
+    dt += dv[j] * (f * theta_e[ie]);
   }
-  ri_s[(size_t)nlev * nc + c] = 0.0;
-  al_s[(size_t)nlev * nc + c] = 0.0;
-
-  // back-substitution, bottom to top; w = 0 at the ground and the top
-  double w_und_k1 = 0.0, wd_k1 = 0.0;
-  double ric_k1 = 0.0, al_k1 = 0.0;
-  if (w_o) w_o[cbh + nlev] = 0.0;
-  for (int k = nlev - 1; k >= 0; --k) {
-    double w_und = 0.0, wd = 0.0;
-    if (k >= 1) {
-      w_und = rp_s[(size_t)k * nc + c] - cp_s[(size_t)k * nc + c] * w_und_k1;
-      wd = w_und * v.ray_fac[k];
-    }
-    const double ric = ri_s[(size_t)k * nc + c], al = al_s[(size_t)k * nc + c];
-    const double zb = zb_buf[cb + k];
-    const double rnew = rs_s[(size_t)k * nc + c] - dt * beta * (ric * wd - ric_k1 * wd_k1) * v.inv_dz[k];
-    const double prnew = ps_s[(size_t)k * nc + c] - zb * (al * wd - al_k1 * wd_k1);
-    const double rho_n = rho[cb + k], th_n = theta[cb + k], pi_n = exner[cb + k];
-    const double pr_n = pi_n - v.exner_ref[k];
-    const double thnew = th_n * (rho_n / rnew) * (1.0 + sc.cvd_o_rd * (prnew - pr_n) / pi_n);
-    w_o[cbh + k] = wd;
-    rho_o[cb + k] = rnew;
-    exner_o[cb + k] = v.exner_ref[k] + prnew;
-    theta_o[cb + k] = thnew;
-    w_und_k1 = w_und;
-    wd_k1 = wd;
-    ric_k1 = ric;
-    al_k1 = al;
-  }
+  div_m[(size_t)c * nlev + k] = dm;
+  div_t[(size_t)c * nlev + k] = dt;
 }
 
 // -------------------------------------------------------------------------
@@ -606,24 +478,23 @@ void launch_substep(const DevGrid& g, const DevVert& v, const Scalars& sc, const
                     cudaStream_t s) {
   const int nlev = v.nlev;
   const unsigned bc = blocks_for((long long)g.nc * nlev, kThreads), be = blocks_for((long long)g.ne * nlev, kThreads);
-  const int colt = 64;
   // ---------------- predictor ----------------
   launch_velocity_tendencies(g, v, st.vn, st.w, wk, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s);
   ICON_LAUNCH("sn_cell_grad", bc, kThreads, s, sn_cell_grad, g, v, st.rho, st.theta_v, wk.grad4);
   ICON_LAUNCH("sn_edge_pred", be, kThreads, s, sn_edge_pred, g, v, sc, st.vn, wk.vt, wk.ddt_vn0, st.rho, st.theta_v,
               st.exner, st.exner_pr, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p);
-  ICON_LAUNCH("sn_cell_div", bc, kThreads, s, sn_cell_div, g, v, wk.vn_p, wk.divd);
-  ICON_LAUNCH("sn_column_pred", blocks_for(g.nc, colt), colt, s, sn_column, g, v, sc, 0, st.w, st.rho, st.exner,
-              st.theta_v, st.exner_pr, wk.ddt_w0, nullptr, wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, nullptr, nullptr,
-              wk.zb, wk.w_p, wk.rho_p, wk.exner_p, wk.theta_p, wk.col);
+  ICON_LAUNCH("sn_cell_div", bc, kThreads, s, sn_cell_div, g, v, wk.vn_p, wk.divd, st.exner, st.exner_pr);
+  ICON_LAUNCH("sn_cell_fluxdiv", bc, kThreads, s, sn_cell_fluxdiv, g, v, sc, wk.vn_p, wk.divd, wk.rho_e, wk.theta_e,
+              wk.div_m, wk.div_t);
+  launch_column(g, v, sc, 0, st, wk, s);
   // ---------------- corrector ----------------
   launch_velocity_tendencies(g, v, wk.vn_p, wk.w_p, wk, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s);
   ICON_LAUNCH("sn_edge_corr", be, kThreads, s, sn_edge_corr, g, v, sc, st.vn, wk.ddt_vn0, wk.ddt_vn1, wk.hpg,
               wk.divd2);
-  ICON_LAUNCH("sn_cell_div", bc, kThreads, s, sn_cell_div, g, v, st.vn, wk.divd);
-  ICON_LAUNCH("sn_column_corr", blocks_for(g.nc, colt), colt, s, sn_column, g, v, sc, 1, st.w, st.rho, st.exner,
-              st.theta_v, nullptr, wk.ddt_w0, wk.ddt_w1, st.vn, wk.divd, wk.rho_e, wk.theta_e, wk.rho_p,
-              wk.theta_p, wk.zb, st.w, st.rho, st.exner, st.theta_v, wk.col);
+  ICON_LAUNCH("sn_cell_div", bc, kThreads, s, sn_cell_div, g, v, st.vn, wk.divd, nullptr, nullptr);
+  ICON_LAUNCH("sn_cell_fluxdiv", bc, kThreads, s, sn_cell_fluxdiv, g, v, sc, st.vn, wk.divd, wk.rho_e, wk.theta_e,
+              wk.div_m, wk.div_t);
+  launch_column(g, v, sc, 1, st, wk, s);
 }
 
 void launch_diffusion(const DevGrid& g, const DevVert& v, const Scalars& sc, const StateView& st, DevWork& wk,
