@@ -121,17 +121,20 @@ class Dycore:
 
     def grad_cell(self, X):
         """Green-Gauss cell gradient [nc, K, 3]:
-        (1/A_c) sum_e s l_e n_e X_e, projected on the tangent plane, with X_e the
-        linear interpolation along the dual edge to the edge midpoint,
-        X_e = (r1 X_c0 + r0 X_c1)/(r0 + r1), r_i = arc(x_ci, x_e)."""
+        (1/A_c) sum_e s l_e n_e (X_e - X_c), projected on the tangent plane, with X_e
+        the linear interpolation along the dual edge to the edge midpoint,
+        X_e = (r1 X_c0 + r0 X_c1)/(r0 + r1), r_i = arc(x_ci, x_e).  Subtracting X_c
+        changes nothing on a plane (sum_e s l n_e = 0 around a closed polygon) and
+        makes the gradient of a constant exactly zero on the sphere, where the
+        edge normals lie in different tangent planes."""
         g = self.g
         out = np.zeros(X.shape + (3,))
         for j in range(3):
             e = g.c2e[:, j]
             coef = g.c2e_sign[:, j] * g.edge_length[e] / g.cell_area
             w_self = np.where(g.e2c[e, 0] == np.arange(g.nc), g.e2c_lin[e, 0], g.e2c_lin[e, 1])
-            xe = w_self[:, None] * X + (1.0 - w_self)[:, None] * X[g.c2e2c[:, j]]
-            out += coef[:, None, None] * xe[:, :, None] * g.normal[e][:, None, :]
+            dxe = (1.0 - w_self)[:, None] * (X[g.c2e2c[:, j]] - X)
+            out += coef[:, None, None] * dxe[:, :, None] * g.normal[e][:, None, :]
         return project(out, g.C[:, None, :])
 
     # ------------------------------------------------------------------

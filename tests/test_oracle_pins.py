@@ -117,6 +117,16 @@ def test_operator_convergence_on_analytic_fields(dycores):
         assert min(_convergence(e)[1:]) > 1.8, (k, e)
 
 
+def test_cell_gradient_of_a_constant_vanishes(dycores):
+    """Exact for constants on the sphere (the reference profiles are horizontally
+    uniform, so the gradient of a field and of its perturbation must agree)."""
+    d = dycores[2]
+    c = np.full((d.g.nc, 2), 1.2345)
+    assert np.max(np.abs(d.grad_cell(c))) == 0.0
+    x = np.random.default_rng(9).standard_normal((d.g.nc, 2))
+    assert np.allclose(d.grad_cell(x + 300.0), d.grad_cell(x), rtol=0, atol=1e-9 * np.max(np.abs(d.grad_cell(x))))
+
+
 def test_cell_laplacian_is_symmetric_negative_and_consistent_weakly(dycores):
     weak = []
     for b in (1, 2, 3, 4):
