@@ -82,6 +82,7 @@ _sig = {
     "icon_velocity_tendencies": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
     "icon_dycore_reference_state": (ctypes.c_int, [ctypes.c_void_p, _f64p, _f64p]),
     "icon_dycore_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "icon_dycore_debug_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_int64]),
     "icon_dycore_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
     "icon_dycore_sizes": (ctypes.c_int, [ctypes.c_void_p] + [_i32p] * 4),
@@ -220,6 +221,10 @@ class Dycore:
                                    ctypes.byref(n)))
         return {names.raw[64 * j:64 * j + 64].split(b"\0")[0].decode(): (launches[j], ms[j])
                 for j in range(n.value)}
+
+    def debug_field(self, name, out):
+        """Copy the internal work field `name` into the device tensor `out`."""
+        _check(icon_dycore_debug_field(self.handle, name.encode(), _ptr(out), out.numel() * out.element_size()))
 
     def synchronize(self):
         _check(icon_dycore_synchronize(self.handle))

@@ -82,9 +82,7 @@ struct icon_dycore {
   Scalars sc{};
   int nlev = 0;
   std::vector<double> z_ifc, theta_ref, exner_ref;
-  DevVert vert{};
-  DevGrid g{};  // grid factors with the parameter-dependent edge/cell arrays filled in
-  DevWork work{};
+  Engine en;
   DevArena arena;
   cudaStream_t stream = nullptr;       // caller's stream (may be the default stream)
   cudaStream_t cap_stream = nullptr;   // private stream for graph capture
@@ -210,8 +208,8 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   if (z_ifc[nlev] != 0.0) return fail(ICON_ERR_ARG, "icon_dycore_create: z_ifc[nlev] must be 0 (flat ground)");
   if (!(p->dtime > 0.0) || p->ndyn_substeps < 1)
     return fail(ICON_ERR_ARG, "icon_dycore_create: dtime must be > 0 and ndyn_substeps >= 1");
-  if (p->precision != ICON_PREC_FP64)
-    return fail(ICON_ERR_UNSUPPORTED, "icon_dycore_create: only ICON_PREC_FP64 is built");
+  if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED)
+    return fail(ICON_ERR_ARG, "icon_dycore_create: precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
 
   icon_dycore* d = new (std::nothrow) icon_dycore();
   if (!d) return fail(ICON_ERR_ARG, "icon_dycore_create: out of host memory");
@@ -295,8 +293,15 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
       }
     }
   }
+  // reference density: the offset of the FP32 rho perturbation (mixed mode)
+  std::vector<double> rho_ref(nlev);
+  for (int k = 0; k < nlev; ++k)
+    rho_ref[k] = p->p00 * std::pow(d->exner_ref[k], s.cvd / p->rd) / (p->rd * d->theta_ref[k]);
+
   DevArena& A = d->arena;
-  DevVert& v = d->vert;
+  Engine& en = d->en;
+  en.precision = p->precision;
+  DevVert& v = en.v;
   v.nlev = nlev;
   v.dz = A.upload(dz);
   v.inv_dz = A.upload(inv_dz);
@@ -307,59 +312,127 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   v.dexner_ref_ic = A.upload(dref);
   v.ray_fac = A.upload(ray);
   v.colc = A.upload(colc);
+  en.rho_ref64 = A.upload(rho_ref);
+  en.sc = s;
 
   // parameter-dependent grid factors
-  d->g = grid->dev;
-  {
-    std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc);
-    for (int e = 0; e < ne; ++e) {
-      fe[e] = 2.0 * p->omega * h.coriolis_z[e];
-      smag[e] = p->hdiff_smag_fac * h.edge_area[e];
-      k4[e] = p->hdiff_k4 * h.edge_area[e] * h.edge_area[e];
-    }
-    for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
-    d->g.f_e = A.upload(fe);
-    d->g.smag_a = A.upload(smag);
-    d->g.k4_a = A.upload(k4);
-    d->g.k4w_c = A.upload(k4w);
+  std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc);
+  for (int e = 0; e < ne; ++e) {
+    fe[e] = 2.0 * p->omega * h.coriolis_z[e];
+    smag[e] = p->hdiff_smag_fac * h.edge_area[e];
+    k4[e] = p->hdiff_k4 * h.edge_area[e] * h.edge_area[e];
   }
+  for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
+  en.g64 = grid->dev;
+  en.g64.f_e = A.upload(fe);
+  en.g64.smag_a = A.upload(smag);
+  en.g64.k4_a = A.upload(k4);
+  en.g64.k4w_c = A.upload(k4w);
 
-  // work arrays
   const size_t ef = (size_t)ne * nlev, eh = (size_t)ne * (nlev + 1);
   const size_t cf = (size_t)nc * nlev, ch = (size_t)nc * (nlev + 1);
   const size_t vf = (size_t)nv * nlev, vh = (size_t)nv * (nlev + 1);
-  DevWork& w = d->work;
-  w.vt = A.alloc<double>(ef);
-  w.ekin_e = A.alloc<double>(ef);
-  w.ddt_vn0 = A.alloc<double>(ef);
-  w.ddt_vn1 = A.alloc<double>(ef);
-  w.rho_e = A.alloc<double>(ef);
-  w.theta_e = A.alloc<double>(ef);
-  w.hpg = A.alloc<double>(ef);
-  w.vn_p = A.alloc<double>(ef);
-  w.lap_vn = A.alloc<double>(ef);
-  w.nu = A.alloc<double>(ef);
-  w.gw_e = A.alloc<double>(eh);
-  w.ekin_c = A.alloc<double>(cf);
-  w.grad4 = A.alloc<double>(4 * cf);
+  auto build_ctx = [&](auto& x, auto tag) {
+    using T = decltype(tag);
+    auto up = [&](const std::vector<double>& src) { return A.upload(std::vector<T>(src.begin(), src.end())); };
+    GridT<T>& g = x.g;
+    const DevGrid& g0 = grid->dev;
+    g.nc = nc;
+    g.ne = ne;
+    g.nv = nv;
+    g.c2e = g0.c2e;
+    g.c2e2c = g0.c2e2c;
+    g.e2c = g0.e2c;
+    g.e2v = g0.e2v;
+    g.e2c2v = g0.e2c2v;
+    g.e2c2e = g0.e2c2e;
+    g.v2e = g0.v2e;
+    g.v2c = g0.v2c;
+    g.div_c = up(h.div_c);
+    g.lap_c = up(h.lap_c);
+    g.e2c_w = up(h.e2c_w);
+    g.grad_c = up(h.grad_c);
+    g.k4w_c = up(k4w);
+    g.inv_d = up(h.inv_d);
+    g.inv_l = up(h.inv_l);
+    g.f_e = up(fe);
+    g.vt_w = up(h.vt_w);
+    g.upw = up(h.upw);
+    g.nt = up(h.nt);
+    g.inv_dn = up(h.inv_dn);
+    g.smag_a = up(smag);
+    g.k4_a = up(k4);
+    g.curl_v = up(h.curl_v);
+    g.c2v_w = up(h.c2v_w);
+    g.uv_w = up(h.uv_w);
+    g.mean_area = (T)h.mean_area;
+    VertT<T>& vt = x.v;
+    vt.nlev = nlev;
+    vt.inv_dz = up(inv_dz);
+    vt.inv_dzh = up(inv_dzh);
+    vt.wgt = up(wgt);
+    vt.theta_ref = up(d->theta_ref);
+    vt.rho_ref = up(rho_ref);
+    vt.exner_ref = v.exner_ref;
+    ScalT<T>& st = x.s;
+    st.dt_s = (T)s.dt_s;
+    st.dtime = (T)s.dtime;
+    st.cpd = (T)s.cpd;
+    st.exfac = (T)s.exfac;
+    st.divdamp = (T)s.divdamp;
+    st.divflux = (T)s.divflux;
+    st.wnow_vel = (T)s.wnow_vel;
+    st.wnew_vel = (T)s.wnew_vel;
+    st.hdiff_temp = s.hdiff_temp;
+    WorkT<T>& w = x.w;
+    w.vt = A.template alloc<T>(ef);
+    w.ekin_e = A.template alloc<T>(ef);
+    w.ddt_vn0 = A.template alloc<T>(ef);
+    w.ddt_vn1 = A.template alloc<T>(ef);
+    w.rho_e = A.template alloc<T>(ef);
+    w.theta_e = A.template alloc<T>(ef);
+    w.hpg = A.template alloc<T>(ef);
+    w.vn_p = A.template alloc<T>(ef);
+    w.lap_vn = A.template alloc<T>(ef);
+    w.nu = A.template alloc<T>(ef);
+    w.gw_e = A.template alloc<T>(eh);
+    w.ekin_c = A.template alloc<T>(cf);
+    w.grad4 = A.template alloc<T>(4 * cf);
+    w.divd = A.template alloc<T>(cf);
+    w.divd2 = A.template alloc<T>(cf);
+    w.dtheta = A.template alloc<T>(cf);
+    w.div_l = A.template alloc<T>(cf);
+    w.div_vn = A.template alloc<T>(cf);
+    w.ddt_w0 = A.template alloc<T>(ch);
+    w.ddt_w1 = A.template alloc<T>(ch);
+    w.lap_w = A.template alloc<T>(ch);
+    w.zeta = A.template alloc<T>(vf);
+    w.uv3 = A.template alloc<T>(3 * vf);
+    w.curl_l = A.template alloc<T>(vf);
+    w.w_v = A.template alloc<T>(vh);
+  };
+  if (p->precision == ICON_PREC_FP64) {
+    build_ctx(en.c64, double{});
+    // the FP64 stencils use the grid's own FP64 factors
+    en.c64.g = en.g64;
+  } else {
+    build_ctx(en.c32, float{});
+    Mirrors& m = en.m;
+    m.vn = A.alloc<float>(ef);
+    m.w = A.alloc<float>(ch);
+    m.rho = A.alloc<float>(cf);
+    m.th = A.alloc<float>(cf);
+    m.w_p = A.alloc<float>(ch);
+  }
+
+  // FP64 work of the column solve and the predicted state
+  DevWork& w = en.wk;
+  w.div_m = A.alloc<double>(cf);
+  w.div_t = A.alloc<double>(cf);
   w.rho_p = A.alloc<double>(cf);
   w.exner_p = A.alloc<double>(cf);
   w.theta_p = A.alloc<double>(cf);
-  w.divd = A.alloc<double>(cf);
-  w.div_m = A.alloc<double>(cf);
-  w.div_t = A.alloc<double>(cf);
-  w.divd2 = A.alloc<double>(cf);
-  w.dtheta = A.alloc<double>(cf);
-  w.div_l = A.alloc<double>(cf);
-  w.div_vn = A.alloc<double>(cf);
-  w.ddt_w0 = A.alloc<double>(ch);
-  w.ddt_w1 = A.alloc<double>(ch);
   w.w_p = A.alloc<double>(ch);
-  w.lap_w = A.alloc<double>(ch);
-  w.zeta = A.alloc<double>(vf);
-  w.uv3 = A.alloc<double>(3 * vf);
-  w.curl_l = A.alloc<double>(vf);
-  w.w_v = A.alloc<double>(vh);
   w.col = A.alloc<double>(7 * ch);
   w.zbl = A.alloc<double>(ch);
   if (A.status == cudaSuccess) {
@@ -425,9 +498,23 @@ enum class Op { kStep, kSubstep, kDiffusion };
 void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
   if (op == Op::kStep || op == Op::kSubstep) {
     int n = op == Op::kStep ? d->params.ndyn_substeps : 1;
-    for (int i = 0; i < n; ++i) launch_substep(d->g, d->vert, d->sc, st, d->work, s);
+    const bool mixed = d->en.precision == ICON_PREC_MIXED;
+    if (mixed) launch_refresh_mirrors(d->en, st, s);
+    for (int i = 0; i < n; ++i) {
+      if (mixed)
+        launch_substep<float>(d->en, d->en.c32, st, s);
+      else
+        launch_substep<double>(d->en, d->en.c64, st, s);
+    }
   }
-  if (op == Op::kStep || op == Op::kDiffusion) launch_diffusion(d->g, d->vert, d->sc, st, d->work, s);
+  if (op == Op::kStep || op == Op::kDiffusion) {
+    if (d->en.precision == ICON_PREC_MIXED) {
+      if (op == Op::kDiffusion) launch_refresh_mirrors(d->en, st, s);
+      launch_diffusion<float>(d->en, d->en.c32, st, s);
+    } else {
+      launch_diffusion<double>(d->en, d->en.c64, st, s);
+    }
+  }
 }
 
 bool same(const StateView& a, const StateView& b) {
@@ -536,7 +623,9 @@ int icon_nh_diff(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op:
 
 int icon_velocity_tendencies(icon_dycore_t* d, const double* vn, const double* w, double* ddt_vn, double* ddt_w) {
   if (!d || !vn || !w || !ddt_vn || !ddt_w) return fail(ICON_ERR_ARG, "icon_velocity_tendencies: NULL argument");
-  launch_velocity_tendencies(d->g, d->vert, vn, w, d->work, ddt_vn, ddt_w, nullptr, nullptr, d->stream);
+  if (d->en.precision != ICON_PREC_FP64)
+    return fail(ICON_ERR_UNSUPPORTED, "icon_velocity_tendencies: stage output is provided in FP64 mode only");
+  launch_velocity_tendencies<double>(d->en.c64, vn, w, ddt_vn, ddt_w, nullptr, nullptr, d->stream);
   CUDA_TRY(cudaGetLastError());
   if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
   return ICON_OK;
@@ -586,6 +675,47 @@ int icon_dycore_profile(icon_dycore_t* d, const icon_state_t* s, int32_t nsteps,
     ms[j] = tot[j];
   }
   *n_kernels = (int32_t)nm.size();
+  return ICON_OK;
+}
+
+int icon_dycore_debug_field(icon_dycore_t* d, const char* name, void* dst, int64_t bytes) {
+  if (!d || !name || !dst) return fail(ICON_ERR_ARG, "icon_dycore_debug_field: NULL argument");
+  const HostGrid& h = d->grid->host;
+  const size_t nlev = d->nlev, ef = h.ne * nlev, cf = h.nc * nlev, ch = h.nc * (nlev + 1);
+  const bool mixed = d->en.precision == ICON_PREC_MIXED;
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  const void* src = nullptr;
+  size_t n = 0;
+  auto pick = [&](const char* nm, const void* p64, const void* p32, size_t count, size_t elem) {
+    if (std::strcmp(name, nm) == 0) {
+      src = mixed ? p32 : p64;
+      n = count * elem;
+    }
+  };
+  const WorkT<double>& a = d->en.c64.w;
+  const WorkT<float>& b = d->en.c32.w;
+  pick("vt", a.vt, b.vt, ef, es);
+  pick("ekin_e", a.ekin_e, b.ekin_e, ef, es);
+  pick("ddt_vn0", a.ddt_vn0, b.ddt_vn0, ef, es);
+  pick("ddt_vn1", a.ddt_vn1, b.ddt_vn1, ef, es);
+  pick("rho_e", a.rho_e, b.rho_e, ef, es);
+  pick("theta_e", a.theta_e, b.theta_e, ef, es);
+  pick("hpg", a.hpg, b.hpg, ef, es);
+  pick("vn_p", a.vn_p, b.vn_p, ef, es);
+  pick("divd", a.divd, b.divd, cf, es);
+  pick("divd2", a.divd2, b.divd2, cf, es);
+  pick("ddt_w0", a.ddt_w0, b.ddt_w0, ch, es);
+  pick("ddt_w1", a.ddt_w1, b.ddt_w1, ch, es);
+  pick("grad4", a.grad4, b.grad4, 4 * cf, es);
+  pick("div_m", d->en.wk.div_m, d->en.wk.div_m, cf, sizeof(double));
+  pick("div_t", d->en.wk.div_t, d->en.wk.div_t, cf, sizeof(double));
+  pick("w_p", d->en.wk.w_p, d->en.wk.w_p, ch, sizeof(double));
+  pick("rho_p", d->en.wk.rho_p, d->en.wk.rho_p, cf, sizeof(double));
+  pick("theta_p", d->en.wk.theta_p, d->en.wk.theta_p, cf, sizeof(double));
+  if (!src) return fail(ICON_ERR_ARG, std::string("icon_dycore_debug_field: unknown field ") + name);
+  if (bytes < (int64_t)n) return fail(ICON_ERR_ARG, "icon_dycore_debug_field: destination too small");
+  CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
   return ICON_OK;
 }
 

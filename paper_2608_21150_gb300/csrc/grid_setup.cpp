@@ -205,14 +205,13 @@ std::string build_host_grid(const icon_grid_desc_t* d, HostGrid* g) {
   g->div_c.resize(3 * (size_t)nc);
   g->lap_c.resize(3 * (size_t)nc);
   g->e2c_w.resize(3 * (size_t)nc);
-  g->grad_c.resize(8 * (size_t)nc);
+  g->grad_c.resize(6 * (size_t)nc);
   std::vector<V3> f1(nc), f2(nc);
   for (int c = 0; c < nc; ++c) {
     V3 C = at(g->cell_xyz, c);
     f1[c] = unit(tangential(at(g->edge_xyz, g->c2e[3 * c]) - C, C));
     f2[c] = cross(C, f1[c]);
     double A = g->cell_area[c], qs = 0.0, q[3];
-    double sx = 0.0, sy = 0.0;
     for (int j = 0; j < 3; ++j) {
       int e = g->c2e[3 * c + j];
       double sgn = g->e2c[2 * e] == c ? 1.0 : -1.0;
@@ -227,13 +226,10 @@ std::string build_host_grid(const icon_grid_desc_t* d, HostGrid* g) {
       double w_self = r_nbr / (r_self + r_nbr);
       V3 w = (sgn * l / A) * nrm[e];
       double wx = dot(w, f1[c]), wy = dot(w, f2[c]);
-      g->grad_c[8 * c + 2 + 2 * j] = (1.0 - w_self) * wx;
-      g->grad_c[8 * c + 3 + 2 * j] = (1.0 - w_self) * wy;
-      sx += w_self * wx;
-      sy += w_self * wy;
+      // gradient = sum_j G_j (psi_nbr_j - psi_c): exact for constants on the sphere
+      g->grad_c[6 * c + 2 * j] = (1.0 - w_self) * wx;
+      g->grad_c[6 * c + 2 * j + 1] = (1.0 - w_self) * wy;
     }
-    g->grad_c[8 * c] = sx;
-    g->grad_c[8 * c + 1] = sy;
     for (int j = 0; j < 3; ++j) g->e2c_w[3 * c + j] = q[j] / qs;
   }
 

@@ -8,10 +8,12 @@
 
 namespace icon {
 
-// Horizontal grid factors in device memory (row A0).  Index tables are
-// 0-based; pad entries of the 6-wide vertex tables point at a valid index
-// and carry a zero coefficient.
-struct DevGrid {
+// Horizontal grid factors in device memory (row A0), in the compute type T of
+// the stencil kernels (double: FP64 mode; float: mixed mode, rounded once from
+// the FP64 factors).  Index tables are 0-based; pad entries of the 6-wide
+// vertex tables point at a valid index and carry a zero coefficient.
+template <class T>
+struct GridT {
   int nc, ne, nv;
   // connectivity
   const int* c2e;    // [nc*3]
@@ -23,26 +25,46 @@ struct DevGrid {
   const int* v2e;    // [nv*6]
   const int* v2c;    // [nv*6]
   // cell coefficients
-  const double* div_c;   // [nc*3] s_{c,e} l_e / A_c
-  const double* lap_c;   // [nc*3] l_e / (d_e A_c)
-  const double* e2c_w;   // [nc*3] edge->cell interpolation weights
-  const double* grad_c;  // [nc*8] Green-Gauss gradient in the cell frame: self (x,y), 3 nbrs (x,y)
-  const double* k4w_c;   // [nc]   hdiff_w_k4 * A_c^2
+  const T* div_c;   // [nc*3] s_{c,e} l_e / A_c
+  const T* lap_c;   // [nc*3] l_e / (d_e A_c)
+  const T* e2c_w;   // [nc*3] edge->cell interpolation weights
+  const T* grad_c;  // [nc*6] Green-Gauss gradient in the cell frame, (x,y) per nbr: sum G_j (psi_j - psi_c)
+  const T* k4w_c;   // [nc]   hdiff_w_k4 * A_c^2
   // edge coefficients
-  const double* inv_d;   // [ne] 1/d_e
-  const double* inv_l;   // [ne] 1/l_e
-  const double* f_e;     // [ne] Coriolis parameter
-  const double* vt_w;    // [ne*5] tangential-wind weights: self, e2c2e[0..3]
-  const double* upw;     // [ne*12] per upwind side s: (dx, dy, nx, ny, tx, ty) in that cell's frame
-  const double* nt;      // [ne*6] normal xyz, tangent xyz
-  const double* inv_dn;  // [ne] 1/(arc between the two opposite diamond vertices)
-  const double* smag_a;  // [ne] hdiff_smag_fac * A_e
-  const double* k4_a;    // [ne] hdiff_k4 * A_e^2
+  const T* inv_d;   // [ne] 1/d_e
+  const T* inv_l;   // [ne] 1/l_e
+  const T* f_e;     // [ne] Coriolis parameter
+  const T* vt_w;    // [ne*5] tangential-wind weights: self, e2c2e[0..3]
+  const T* upw;     // [ne*12] per upwind side s: (dx, dy, nx, ny, tx, ty) in that cell's frame
+  const T* nt;      // [ne*6] normal xyz, tangent xyz
+  const T* inv_dn;  // [ne] 1/(arc between the two opposite diamond vertices)
+  const T* smag_a;  // [ne] hdiff_smag_fac * A_e
+  const T* k4_a;    // [ne] hdiff_k4 * A_e^2
   // vertex coefficients
-  const double* curl_v;  // [nv*6] t_{v,e} d_e / A_v (0 for pads)
-  const double* c2v_w;   // [nv*6] cell->vertex weights (0 for pads)
-  const double* uv_w;    // [nv*6*3] vertex velocity weights (xyz per edge)
-  double mean_area;
+  const T* curl_v;  // [nv*6] t_{v,e} d_e / A_v (0 for pads)
+  const T* c2v_w;   // [nv*6] cell->vertex weights (0 for pads)
+  const T* uv_w;    // [nv*6*3] vertex velocity weights (xyz per edge)
+  T mean_area;
+};
+using DevGrid = GridT<double>;
+
+// Vertical factors of the stencil kernels in the compute type T.
+template <class T>
+struct VertT {
+  int nlev;
+  const T* inv_dz;     // [nlev]
+  const T* inv_dzh;    // [nlev+1]
+  const T* wgt;        // [nlev+1]
+  const T* theta_ref;  // [nlev]
+  const T* rho_ref;    // [nlev] (mixed mode: offset of the rho perturbation)
+  const double* exner_ref;  // [nlev] (FP64 mode: exner perturbation)
+};
+
+// Scalars of the stencil kernels in the compute type T.
+template <class T>
+struct ScalT {
+  T dt_s, dtime, cpd, exfac, divdamp, divflux, wnow_vel, wnew_vel;
+  int hdiff_temp;
 };
 
 // Vertical metrics and reference state in device memory.
@@ -62,23 +84,36 @@ struct DevVert {
   const double* colc;      // [(nlev+1)*8]
 };
 
-// Work arrays of one substep / step (device, FP64).
-struct DevWork {
+// Work arrays of the stencil kernels, compute type T.
+template <class T>
+struct WorkT {
   // edges, full levels
-  double *vt, *ekin_e, *ddt_vn0, *ddt_vn1, *rho_e, *theta_e, *hpg, *vn_p;
-  double *lap_vn, *nu;
+  T *vt, *ekin_e, *ddt_vn0, *ddt_vn1, *rho_e, *theta_e, *hpg, *vn_p, *lap_vn, *nu;
   // edges, half levels
-  double* gw_e;
+  T* gw_e;
   // cells, full levels
-  double *ekin_c, *grad4, *rho_p, *exner_p, *theta_p, *divd, *div_m, *div_t, *divd2, *dtheta, *div_l, *div_vn;
+  T *ekin_c, *grad4, *divd, *divd2, *dtheta, *div_l, *div_vn;
   // cells, half levels
-  double *ddt_w0, *ddt_w1, *w_p, *lap_w;
+  T *ddt_w0, *ddt_w1, *lap_w;
   // vertices
-  double *zeta, *uv3, *curl_l;  // full levels (uv3: 3 fields)
-  double* w_v;                  // half levels
-  // column-solve scratch, level-major [k][c]
-  double* col;                  // 7 planes of (nlev+1)*nc: cp, rp, rho*, pr*, rho_ic, alpha, eos
-  double* zbl;                  // level-major zb [(nlev+1)*nc], predictor -> corrector
+  T *zeta, *uv3, *curl_l;  // full levels (uv3: 3 fields)
+  T* w_v;                  // half levels
+};
+
+// FP64 work of the column solve and the predicted state.
+struct DevWork {
+  double *div_m, *div_t;                  // cells: flux divergences (FP64 sums)
+  double *rho_p, *exner_p, *theta_p;      // cells: predicted state
+  double* w_p;                            // cells, half levels
+  double* col;   // level-major [k][c] scratch: 7 planes of (nlev+1)*nc: cp, rp, rho*, pr*, rho_ic, alpha, eos
+  double* zbl;   // level-major zb [(nlev+1)*nc], predictor -> corrector
+};
+
+// FP32 mirrors of the state read by the mixed-mode stencils: vn, w, the
+// perturbations rho - rho_ref and theta_v - theta_ref, and the predicted w.
+// Written by the FP64 writers.
+struct Mirrors {
+  float *vn, *w, *rho, *th, *w_p;
 };
 
 struct Scalars {

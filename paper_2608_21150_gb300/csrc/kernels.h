@@ -54,24 +54,50 @@ struct StateView {
   double *vn, *w, *rho, *exner, *theta_v, *exner_pr;
 };
 
-// Rows A1-A4 on (vn, w): writes ddt_vn [ne*nlev] and ddt_w [nc*(nlev+1)].
-// With divd2 != nullptr also the divergence-damping Laplacian of divd (A8).
-void launch_velocity_tendencies(const DevGrid& g, const DevVert& v, const double* vn, const double* w,
-                                DevWork& wk, double* ddt_vn, double* ddt_w, const double* divd,
-                                double* divd2, cudaStream_t s);
+// Everything the stencil kernels of one precision mode need.
+template <class T>
+struct Ctx {
+  GridT<T> g;
+  VertT<T> v;
+  ScalT<T> s;
+  WorkT<T> w;
+};
+
+// Device-side state of one dycore: FP64 factors and column-solve work, the
+// FP32 mirrors (mixed mode) and the stencil context of the active mode.
+struct Engine {
+  int precision = ICON_PREC_FP64;
+  DevGrid g64{};
+  DevVert v{};
+  Scalars sc{};
+  DevWork wk{};
+  Mirrors m{};
+  const double* rho_ref64 = nullptr;  // [nlev] rho offset of the mixed-mode perturbation
+  Ctx<double> c64{};
+  Ctx<float> c32{};
+};
+
+// Rows A1-A4 on (vn, w) in compute type T: writes ddt_vn [ne*nlev] and ddt_w
+// [nc*(nlev+1)].  With divd2 != nullptr also the divergence-damping Laplacian
+// of divd (A8).
+template <class T>
+void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
+                                T* divd2, cudaStream_t s);
 // Rows A5-A9: one predictor + corrector substep, state updated in place.
-void launch_substep(const DevGrid& g, const DevVert& v, const Scalars& sc, const StateView& st, DevWork& wk,
-                    cudaStream_t s);
-// Row A7: vertically implicit column solve (predictor: corrector = 0 writes the
-// predicted state to wk.w_p/rho_p/exner_p/theta_p; corrector = 1 writes the new
-// state over st).  Needs wk.div_m/div_t (flux divergences) of the pass.
-void launch_column(const DevGrid& g, const DevVert& v, const Scalars& sc, int corrector, const StateView& st,
-                   DevWork& wk, cudaStream_t s);
+template <class T>
+void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s);
+// Row A10: diffusion over dtime, state updated in place.
+template <class T>
+void launch_diffusion(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s);
+// Mixed mode: FP32 mirrors from the FP64 state.
+void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t s);
+// Row A7: vertically implicit column solve (corrector = 0: the predicted state
+// into en.wk.w_p/rho_p/exner_p/theta_p; corrector = 1: the new state over st).
+// Reads the flux divergences en.wk.div_m/div_t and ddt_w of type T.
+template <class T>
+void launch_column(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
+                   cudaStream_t s);
 // One-time kernel attributes (dynamic shared memory above 48 KB).
 cudaError_t init_column_kernels();
-
-// Row A10: diffusion over dtime, state updated in place.
-void launch_diffusion(const DevGrid& g, const DevVert& v, const Scalars& sc, const StateView& st, DevWork& wk,
-                      cudaStream_t s);
 
 }  // namespace icon

@@ -23,6 +23,8 @@
 // [k][c], coalesced for one thread per column.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace icon {
@@ -62,15 +64,22 @@ __device__ __forceinline__ void cp8(double* dst, const double* src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double* dst, const double* src) { cp8(dst, src); }
+__device__ __forceinline__ void cp_async(float* dst, const float* src) { cp4(dst, src); }
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // tile[kk][col] = X[rows[col] * ld + k0 + kk] for kk < nk (level-contiguous
 // field; consecutive threads copy consecutive levels of one row)
-__device__ __forceinline__ void tile_rows(double* tile, const double* __restrict__ X, int ld,
-                                          const int* __restrict__ rows, int k0, int nk) {
+template <class T>
+__device__ __forceinline__ void tile_rows(T* tile, const T* __restrict__ X, int ld, const int* __restrict__ rows,
+                                          int k0, int nk) {
   for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
     const int col = i / nk, kk = i - col * nk;
-    cp8(tile + kk * kLD + col, X + (size_t)rows[col] * ld + k0 + kk);
+    cp_async(tile + kk * kLD + col, X + (size_t)rows[col] * ld + k0 + kk);
   }
 }
 
@@ -90,16 +99,22 @@ __device__ __forceinline__ void store_tile(const double* __restrict__ tile, doub
   }
 }
 
+template <class T>
 struct ColArgs {
-  const double *w, *rho, *exner, *theta, *ddt_w0, *ddt_w1, *rho_p, *theta_p, *div_m, *div_t;
+  const double *w, *rho, *exner, *theta, *rho_p, *theta_p, *div_m, *div_t;
+  const T *ddt_w0, *ddt_w1;
   double *zbl, *col, *w_o, *rho_o, *exner_o, *theta_o;
+  // mixed mode: FP32 mirrors of the outputs (w; rho, theta_v perturbations)
+  float *m_w, *m_rho, *m_th;
+  const double* rho_ref;
 };
 
-__global__ void __launch_bounds__(kCW) sn_column_tiled(DevGrid g, DevVert v, Scalars sc, int corrector, ColArgs a) {
+template <class T>
+__global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
   extern __shared__ double sm[];
   __shared__ int rows_c[kCW];
   const int t = threadIdx.x;
-  const int nc = g.nc, nlev = v.nlev, nlevp = nlev + 1;
+  const int nlev = v.nlev, nlevp = nlev + 1;
   const int c0 = blockIdx.x * kCW;
   const int c = c0 + t;
   const bool active = c < nc;
@@ -110,10 +125,10 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(DevGrid g, DevVert v, Sca
   double* T_rho = sm + kTile;
   double* T_pi = sm + 2 * kTile;
   double* T_th = sm + 3 * kTile;
-  double* T_dw0 = sm + 4 * kTile;
+  T* T_dw0 = reinterpret_cast<T*>(sm + 4 * kTile);
   double* T_dm = sm + 5 * kTile;
   double* T_dt = sm + 6 * kTile;
-  double* T_dw1 = sm + 7 * kTile;
+  T* T_dw1 = reinterpret_cast<T*>(sm + 7 * kTile);
   double* T_rp = sm + 8 * kTile;
   double* T_tp = sm + 9 * kTile;
   double* T_zb = sm + 10 * kTile;
@@ -196,7 +211,8 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(DevGrid g, DevVert v, Sca
       ri_s[ik] = ric_k;
       al_s[ik] = al_k;
       if (k >= 1) {
-        const double ddtw = corrector ? sc.wnow_vel * T_dw0[o] + sc.wnew_vel * T_dw1[o] : T_dw0[o];
+        const double ddtw = corrector ? sc.wnow_vel * (double)T_dw0[o] + sc.wnew_vel * (double)T_dw1[o]
+                                      : (double)T_dw0[o];
         const double wstar = wk + dt * ddtw - (cf[CWX] * tic_k * (pr_km1 - pr_k) + cf[CB] * tpic_k);
         const double gam = cf[CGAM] * tic_k;
         const double am = -gam * zb_km1 * al_km1;
@@ -290,45 +306,77 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(DevGrid g, DevVert v, Sca
     store_tile(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
     store_tile(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
     store_tile(O_th, a.theta_o, nlev, c0, nc, k0, nk);
+    if (a.m_w) {
+      // FP32 mirrors for the mixed-mode stencils (one conversion per value)
+      for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
+        const int col = i / nk, kk = i - col * nk, k = k0 + kk;
+        if (c0 + col >= nc) continue;
+        const size_t ic = (size_t)(c0 + col) * nlev + k;
+        a.m_w[(size_t)(c0 + col) * nlevp + k] = (float)O_w[kk * kLD + col];
+        if (a.m_rho) {
+          a.m_rho[ic] = (float)(O_rho[kk * kLD + col] - a.rho_ref[k]);
+          a.m_th[ic] = (float)(O_th[kk * kLD + col] - v.theta_ref[k]);
+        }
+      }
+    }
   }
-  if (active) a.w_o[(size_t)c * nlevp + nlev] = 0.0;
+  if (active) {
+    a.w_o[(size_t)c * nlevp + nlev] = 0.0;
+    if (a.m_w) a.m_w[(size_t)c * nlevp + nlev] = 0.0f;
+  }
 }
 
 }  // namespace
 
 cudaError_t init_column_kernels() {
-  return cudaFuncSetAttribute(sn_column_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  cudaError_t e = cudaFuncSetAttribute(sn_column_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sn_column_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
 }
 
-void launch_column(const DevGrid& g, const DevVert& v, const Scalars& sc, int corrector, const StateView& st,
-                   DevWork& wk, cudaStream_t s) {
-  ColArgs a;
+template <class T>
+void launch_column(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
+                   cudaStream_t s) {
+  const DevWork& wk = en.wk;
+  ColArgs<T> a{};
   a.w = st.w;
   a.rho = st.rho;
   a.exner = st.exner;
   a.theta = st.theta_v;
-  a.ddt_w0 = wk.ddt_w0;
-  a.ddt_w1 = wk.ddt_w1;
+  a.ddt_w0 = ddt_w0;
+  a.ddt_w1 = ddt_w1;
   a.rho_p = wk.rho_p;
   a.theta_p = wk.theta_p;
   a.div_m = wk.div_m;
   a.div_t = wk.div_t;
   a.zbl = wk.zbl;
   a.col = wk.col;
+  a.rho_ref = en.rho_ref64;
+  const bool mixed = std::is_same<T, float>::value;
   if (corrector) {
     a.w_o = st.w;
     a.rho_o = st.rho;
     a.exner_o = st.exner;
     a.theta_o = st.theta_v;
+    if (mixed) {
+      a.m_w = en.m.w;
+      a.m_rho = en.m.rho;
+      a.m_th = en.m.th;
+    }
   } else {
     a.w_o = wk.w_p;
     a.rho_o = wk.rho_p;
     a.exner_o = wk.exner_p;
     a.theta_o = wk.theta_p;
+    if (mixed) a.m_w = en.m.w_p;
   }
-  const unsigned blocks = (unsigned)((g.nc + kCW - 1) / kCW);
-  ICON_LAUNCH_SMEM(corrector ? "sn_column_corr" : "sn_column_pred", blocks, kCW, kSmem, s, sn_column_tiled, g, v,
-                   sc, corrector, a);
+  const unsigned blocks = (unsigned)((en.g64.nc + kCW - 1) / kCW);
+  const char* name = mixed ? (corrector ? "sn_column_corr_mx" : "sn_column_pred_mx")
+                           : (corrector ? "sn_column_corr" : "sn_column_pred");
+  ICON_LAUNCH_SMEM(name, blocks, kCW, kSmem, s, sn_column_tiled<T>, en.g64.nc, en.v, en.sc, corrector, a);
 }
+
+template void launch_column<double>(const Engine&, int, const StateView&, const double*, const double*, cudaStream_t);
+template void launch_column<float>(const Engine&, int, const StateView&, const float*, const float*, cudaStream_t);
 
 }  // namespace icon

@@ -1,0 +1,628 @@
+// Stencil kernels of one dycore step (rows A1-A6, A8-A10), templated on the
+// compute type T: double (FP64 mode) or float (mixed mode, row A12).
+//
+// Layout: level-contiguous X[h * nk + k] (k = 0 at the model top); one thread
+// per (horizontal point, level), flattened so that the 32 lanes of a warp
+// cover consecutive levels of one or two columns.  Neighbour gathers
+// X[nbr * nk + k] are coalesced runs of consecutive levels.
+//
+// Mixed mode: the stencils read FP32 mirrors of the state (vn, w and the
+// perturbations rho - rho_ref, theta_v - theta_ref) and compute in FP32,
+// except the exner difference of the horizontal pressure gradient; prognostic updates stay FP64 (the FP64 state plus an FP32
+// increment) and rewrite the mirrors; flux divergences are summed in FP64 so
+// that every edge flux is one value shared by its two cells (mass conserved
+// to FP64 rounding).  FP64<->FP32 conversions run on the FP64 pipe on this
+// GPU, so each value is converted once by its writer, never per gather.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace icon {
+
+thread_local Prof* g_prof = nullptr;
+
+namespace {
+
+template <class T>
+constexpr bool kMixed = std::is_same<T, float>::value;
+
+__device__ __forceinline__ bool flat_index(int n_h, int nk, int& h, int& k) {
+  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)n_h * (unsigned)nk) return false;
+  h = (int)(i / (unsigned)nk);
+  k = (int)(i - (unsigned)h * (unsigned)nk);
+  return true;
+}
+
+inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+constexpr int kThreads = 256;
+
+template <class T>
+const char* kname(const char* f64, const char* f32) {
+  return kMixed<T> ? f32 : f64;
+}
+
+// -------------------------------------------------------------------------
+// A1: tangential wind and edge kinetic energy
+//   vt = sum_j vt_w[j] vn[e_j] (Perot reconstruction averaged over the two
+//   cells, projected on t_e), K_e = (vn^2 + vt^2)/2
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ vt,
+                            T* __restrict__ ekin) {
+  int e, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const T* w = g.vt_w + 5 * (size_t)e;
+  const int* q = g.e2c2e + 4 * (size_t)e;
+  const T vne = vn[(size_t)e * nlev + k];
+  T t = w[0] * vne;
+  t += w[1] * vn[(size_t)q[0] * nlev + k];
+  t += w[2] * vn[(size_t)q[1] * nlev + k];
+  t += w[3] * vn[(size_t)q[2] * nlev + k];
+  t += w[4] * vn[(size_t)q[3] * nlev + k];
+  vt[(size_t)e * nlev + k] = t;
+  ekin[(size_t)e * nlev + k] = T(0.5) * (vne * vne + t * t);
+}
+
+// -------------------------------------------------------------------------
+// A2: cells: K_c = sum q_e K_e  (and, in the corrector, the divergence-damping
+//     Laplacian dd2 = lapc(div vn*));  vertices: zeta = curl vn (full levels),
+//     w_v = sum r_c w_c (half levels).  One launch over nc*nlev + nv*(nlev+1).
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void va_cell_vert(GridT<T> g, VertT<T> v, const T* __restrict__ vn, const T* __restrict__ w,
+                             const T* __restrict__ ekin_e, T* __restrict__ ekin_c, const T* __restrict__ divd,
+                             T* __restrict__ divd2, T* __restrict__ zeta, T* __restrict__ w_v) {
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned ncell = (unsigned)g.nc * nlev;
+  if (i < ncell) {
+    int c = (int)(i / (unsigned)nlev), k = (int)(i - (unsigned)c * nlev);
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const T* q = g.e2c_w + 3 * (size_t)c;
+    T s = q[0] * ekin_e[(size_t)ce[0] * nlev + k];
+    s += q[1] * ekin_e[(size_t)ce[1] * nlev + k];
+    s += q[2] * ekin_e[(size_t)ce[2] * nlev + k];
+    ekin_c[i] = s;
+    if (divd2) {
+      const int* cc = g.c2e2c + 3 * (size_t)c;
+      const T* L = g.lap_c + 3 * (size_t)c;
+      const T dc = divd[i];
+      T r = L[0] * (divd[(size_t)cc[0] * nlev + k] - dc);
+      r += L[1] * (divd[(size_t)cc[1] * nlev + k] - dc);
+      r += L[2] * (divd[(size_t)cc[2] * nlev + k] - dc);
+      divd2[i] = r;
+    }
+    return;
+  }
+  i -= ncell;
+  if (i >= (unsigned)g.nv * nlevp) return;
+  int vx = (int)(i / (unsigned)nlevp), k = (int)(i - (unsigned)vx * nlevp);
+  const int* ve = g.v2e + 6 * (size_t)vx;
+  const int* vc = g.v2c + 6 * (size_t)vx;
+  const T* cw = g.curl_v + 6 * (size_t)vx;
+  const T* rw = g.c2v_w + 6 * (size_t)vx;
+  if (k < nlev) {
+    T z = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) z += cw[j] * vn[(size_t)ve[j] * nlev + k];
+    zeta[(size_t)vx * nlev + k] = z;
+  }
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s += rw[j] * w[(size_t)vc[j] * nlevp + k];
+  w_v[i] = s;
+}
+
+// -------------------------------------------------------------------------
+// A3: vn advective tendency (full levels) and horizontal advection of w at
+//     edges (interior half levels); one launch over ne*(nlev+1).
+//   ddt_vn = -(K_c1 - K_c0)/d + (zeta_e + f) vt - wbar (vn_ie_k - vn_ie_k+1)/dz
+//   gw_e   = vn_ie (w_c1 - w_c0)/d + vt_ie (w_vp - w_vm)/l
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, const T* __restrict__ w,
+                             const T* __restrict__ vt, const T* __restrict__ ekin_c, const T* __restrict__ zeta,
+                             const T* __restrict__ w_v, T* __restrict__ ddt_vn, T* __restrict__ gw_e) {
+  int e, k;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  if (!flat_index(g.ne, nlevp, e, k)) return;
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
+  const T inv_d = g.inv_d[e];
+  const T* vne = vn + (size_t)e * nlev;
+  const T* vte = vt + (size_t)e * nlev;
+  // vn at half levels k and k+1 (top: vn_0, ground: vn_{nlev-1})
+  auto vn_ie = [&](int kh) -> T {
+    if (kh == 0) return vne[0];
+    if (kh == nlev) return vne[nlev - 1];
+    const T wg = v.wgt[kh];
+    return wg * vne[kh - 1] + (T(1) - wg) * vne[kh];
+  };
+  const T vnie_k = vn_ie(k);
+  if (k < nlev) {
+    const T vnie_k1 = vn_ie(k + 1);
+    const T* w0 = w + (size_t)c0 * nlevp;
+    const T* w1 = w + (size_t)c1 * nlevp;
+    const T wbar = T(0.5) * (T(0.5) * (w0[k] + w0[k + 1]) + T(0.5) * (w1[k] + w1[k + 1]));
+    const T zeta_e = T(0.5) * (zeta[(size_t)vm * nlev + k] + zeta[(size_t)vp * nlev + k]);
+    const T dkdn = (ekin_c[(size_t)c1 * nlev + k] - ekin_c[(size_t)c0 * nlev + k]) * inv_d;
+    const T dvdz = (vnie_k - vnie_k1) * v.inv_dz[k];
+    ddt_vn[(size_t)e * nlev + k] = -dkdn + (zeta_e + g.f_e[e]) * vte[k] - wbar * dvdz;
+  }
+  T gw = 0;
+  if (k > 0 && k < nlev) {
+    const T wg = v.wgt[k];
+    const T vtie = wg * vte[k - 1] + (T(1) - wg) * vte[k];
+    const T dwdn = (w[(size_t)c1 * nlevp + k] - w[(size_t)c0 * nlevp + k]) * inv_d;
+    const T dwdt = (w_v[(size_t)vp * nlevp + k] - w_v[(size_t)vm * nlevp + k]) * g.inv_l[e];
+    gw = vnie_k * dwdn + vtie * dwdt;
+  }
+  gw_e[(size_t)e * nlevp + k] = gw;
+}
+
+// -------------------------------------------------------------------------
+// A4: w advective tendency at interior half levels (0 at top and ground)
+//   ddt_w = -sum q_e gw_e - w (wf_{k-1} - wf_k)/dzh,  wf full-level averages
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const T* __restrict__ gw_e,
+                          T* __restrict__ ddt_w) {
+  int c, k;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  if (!flat_index(g.nc, nlevp, c, k)) return;
+  T r = 0;
+  if (k > 0 && k < nlev) {
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const T* q = g.e2c_w + 3 * (size_t)c;
+    T h = q[0] * gw_e[(size_t)ce[0] * nlevp + k];
+    h += q[1] * gw_e[(size_t)ce[1] * nlevp + k];
+    h += q[2] * gw_e[(size_t)ce[2] * nlevp + k];
+    const T* wc = w + (size_t)c * nlevp;
+    const T wf_up = T(0.5) * (wc[k - 1] + wc[k]);
+    const T wf_dn = T(0.5) * (wc[k] + wc[k + 1]);
+    r = -h - wc[k] * (wf_up - wf_dn) * v.inv_dzh[k];
+  }
+  ddt_w[(size_t)c * nlevp + k] = r;
+}
+
+// -------------------------------------------------------------------------
+// A5 (predictor): Green-Gauss gradients of rho and theta_v (perturbations in
+// mixed mode: the reference is horizontally uniform) in each cell's local
+// frame: grad4 = (drho_x, drho_y, dth_x, dth_y) as 4 planes [4][nc*nlev].
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, const T* __restrict__ theta,
+                             T* __restrict__ grad4) {
+  int c, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.nc, nlev, c, k)) return;
+  const size_t n = (size_t)g.nc * nlev;
+  const int* cc = g.c2e2c + 3 * (size_t)c;
+  const T* G = g.grad_c + 6 * (size_t)c;
+  const size_t i = (size_t)c * nlev + k;
+  const size_t i0 = (size_t)cc[0] * nlev + k, i1 = (size_t)cc[1] * nlev + k, i2 = (size_t)cc[2] * nlev + k;
+  const T r = rho[i], t = theta[i];
+  const T r0 = rho[i0] - r, r1 = rho[i1] - r, r2 = rho[i2] - r;
+  const T t0 = theta[i0] - t, t1 = theta[i1] - t, t2 = theta[i2] - t;
+  grad4[i] = G[0] * r0 + G[2] * r1 + G[4] * r2;
+  grad4[n + i] = G[1] * r0 + G[3] * r1 + G[5] * r2;
+  grad4[2 * n + i] = G[0] * t0 + G[2] * t1 + G[4] * t2;
+  grad4[3 * n + i] = G[1] * t0 + G[3] * t1 + G[5] * t2;
+}
+
+// -------------------------------------------------------------------------
+// A6 (predictor edges): upwind rho_e/theta_e from the back trajectory over
+// dt/2, horizontal pressure gradient with the extrapolated exner perturbation,
+// and the vn predictor.  FP64 mode reads totals; mixed mode reads the
+// perturbations of rho and theta_v and adds the reference back.  The exner
+// difference between the two cells is always taken in FP64: neighbouring
+// perturbations agree to 4-5 digits, more than FP32 carries.
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ vn,
+                             const T* __restrict__ vt, const T* __restrict__ ddt_vn, const T* __restrict__ rho,
+                             const T* __restrict__ theta, const double* __restrict__ exner,
+                             const double* __restrict__ exner_pr, const double* __restrict__ inv_d64, double exfac,
+                             const T* __restrict__ grad4, T* __restrict__ rho_e, T* __restrict__ theta_e,
+                             T* __restrict__ hpg, T* __restrict__ vn_p) {
+  int e, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const size_t n = (size_t)g.nc * nlev;
+  const size_t ie = (size_t)e * nlev + k;
+  const T vne = vn[ie], vte = vt[ie];
+  const int side = vne >= T(0) ? 0 : 1;
+  const int cu = g.e2c[2 * e + side];
+  const T* u = g.upw + 12 * (size_t)e + 6 * side;
+  const T hdt = T(0.5) * sc.dt_s;
+  const T dx = u[0] - hdt * (vne * u[2] + vte * u[4]);
+  const T dy = u[1] - hdt * (vne * u[3] + vte * u[5]);
+  const size_t iu = (size_t)cu * nlev + k;
+  T ru = rho[iu], tu = theta[iu];
+  if constexpr (kMixed<T>) {
+    ru += v.rho_ref[k];
+    tu += v.theta_ref[k];
+  }
+  const T re = ru + (grad4[iu] * dx + grad4[n + iu] * dy);
+  const T te = tu + (grad4[2 * n + iu] * dx + grad4[3 * n + iu] * dy);
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  const size_t i0 = (size_t)c0 * nlev + k, i1 = (size_t)c1 * nlev + k;
+  const double pref = v.exner_ref[k];
+  const double pex0 = (1.0 + exfac) * (exner[i0] - pref) - exfac * exner_pr[i0];
+  const double pex1 = (1.0 + exfac) * (exner[i1] - pref) - exfac * exner_pr[i1];
+  const T h = sc.cpd * te * (T)((pex1 - pex0) * inv_d64[e]);
+  rho_e[ie] = re;
+  theta_e[ie] = te;
+  hpg[ie] = h;
+  vn_p[ie] = vne + sc.dt_s * (ddt_vn[ie] - h);
+}
+
+// -------------------------------------------------------------------------
+// A8 + A9 (corrector edges): vn corrector with time-weighted advective
+// tendencies, the predictor's pressure gradient and fourth-order divergence
+// damping; the increment is formed in T, the update in FP64 (in place).
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __restrict__ vn,
+                             const T* __restrict__ ddt_vn0, const T* __restrict__ ddt_vn1,
+                             const T* __restrict__ hpg, const T* __restrict__ divd2, float* __restrict__ m_vn) {
+  int e, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const size_t ie = (size_t)e * nlev + k;
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  const T dd = (divd2[(size_t)c1 * nlev + k] - divd2[(size_t)c0 * nlev + k]) * g.inv_d[e];
+  const T am = g.mean_area;
+  const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - sc.divdamp * am * am * dd;
+  const double vnn = vn[ie] + (double)inc;
+  vn[ie] = vnn;
+  if constexpr (kMixed<T>) m_vn[ie] = (float)vnn;
+}
+
+// -------------------------------------------------------------------------
+// Cell divergence D = (1/A_c) sum_e s l_e vn_e of vn* (fourth-order damping and
+// flux filter of the predictor) or vn^{n+1} (flux filter of the corrector).
+// The predictor launch also updates the exner extrapolation history,
+// exner_pr = exner - exner_ref (sn_edge_pred, its last reader, has completed).
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ divd,
+                            const double* __restrict__ exner, double* __restrict__ exner_pr) {
+  int c, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.nc, nlev, c, k)) return;
+  const int* ce = g.c2e + 3 * (size_t)c;
+  const T* dv = g.div_c + 3 * (size_t)c;
+  const size_t i = (size_t)c * nlev + k;
+  divd[i] = dv[0] * vn[(size_t)ce[0] * nlev + k] + dv[1] * vn[(size_t)ce[1] * nlev + k] +
+            dv[2] * vn[(size_t)ce[2] * nlev + k];
+  if (exner_pr) exner_pr[i] = exner[i] - v.exner_ref[k];
+}
+
+// -------------------------------------------------------------------------
+// Divergences of the horizontal mass and theta fluxes with the flux-velocity
+// filter, per cell and level, summed in FP64:
+//   vf_e = vn_e + divflux (D_c1 - D_c0)/d_e,  F_e = rho_e vf_e,
+//   div_m = sum s l F / A,  div_t = sum s l F theta_e / A
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ vn,
+                                const T* __restrict__ divd, const T* __restrict__ rho_e,
+                                const T* __restrict__ theta_e, const double* __restrict__ div_c64,
+                                double* __restrict__ div_m, double* __restrict__ div_t) {
+  int c, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.nc, nlev, c, k)) return;
+  const int* ce = g.c2e + 3 * (size_t)c;
+  const double* dv = div_c64 + 3 * (size_t)c;
+  double dm = 0.0, dt = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int e = ce[j];
+    const size_t ie = (size_t)e * nlev + k;
+    const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+    const T vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
+    const T f = rho_e[ie] * vf;
+    const T ft = f * theta_e[ie];
+    dm += dv[j] * (double)f;
+    dt += dv[j] * (double)ft;
+  }
+  div_m[(size_t)c * nlev + k] = dm;
+  div_t[(size_t)c * nlev + k] = dt;
+}
+
+// -------------------------------------------------------------------------
+// Mixed mode: FP32 mirrors of the FP64 state at the start of a call
+// (the caller may have changed the state between calls).  One launch over
+// ne*nlev + nc*(nlev+1).
+// -------------------------------------------------------------------------
+__global__ void mx_refresh(int ne, int nc, int nlev, const double* __restrict__ exner_ref,
+                           const double* __restrict__ theta_ref, const double* __restrict__ rho_ref, StateView st,
+                           Mirrors m) {
+  const int nlevp = nlev + 1;
+  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nedge = (unsigned)ne * nlev;
+  if (i < nedge) {
+    m.vn[i] = (float)st.vn[i];
+    return;
+  }
+  i -= nedge;
+  if (i >= (unsigned)nc * nlevp) return;
+  const int c = (int)(i / (unsigned)nlevp), k = (int)(i - (unsigned)c * nlevp);
+  m.w[i] = (float)st.w[i];
+  if (k < nlev) {
+    const size_t j = (size_t)c * nlev + k;
+    m.rho[j] = (float)(st.rho[j] - rho_ref[k]);
+    m.th[j] = (float)(st.theta_v[j] - theta_ref[k]);
+  }
+}
+
+// -------------------------------------------------------------------------
+// A10 diffusion
+// -------------------------------------------------------------------------
+// cells: div vn; vertices: curl vn and the vertex velocity (xyz)
+template <class T>
+__global__ void diff_div_curl_uv(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ div_vn,
+                                 T* __restrict__ zeta, T* __restrict__ uv3) {
+  const int nlev = v.nlev;
+  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned ncell = (unsigned)g.nc * nlev;
+  if (i < ncell) {
+    int c = (int)(i / (unsigned)nlev), k = (int)(i - (unsigned)c * nlev);
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const T* dv = g.div_c + 3 * (size_t)c;
+    div_vn[i] = dv[0] * vn[(size_t)ce[0] * nlev + k] + dv[1] * vn[(size_t)ce[1] * nlev + k] +
+                dv[2] * vn[(size_t)ce[2] * nlev + k];
+    return;
+  }
+  i -= ncell;
+  const size_t nvl = (size_t)g.nv * nlev;
+  if (i >= nvl) return;
+  int vx = (int)(i / (unsigned)nlev), k = (int)(i - (unsigned)vx * nlev);
+  const int* ve = g.v2e + 6 * (size_t)vx;
+  const T* cw = g.curl_v + 6 * (size_t)vx;
+  const T* U = g.uv_w + 18 * (size_t)vx;
+  T z = 0, ux = 0, uy = 0, uz = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const T x = vn[(size_t)ve[j] * nlev + k];
+    z += cw[j] * x;
+    ux += U[3 * j] * x;
+    uy += U[3 * j + 1] * x;
+    uz += U[3 * j + 2] * x;
+  }
+  zeta[i] = z;
+  uv3[i] = ux;
+  uv3[nvl + i] = uy;
+  uv3[2 * nvl + i] = uz;
+}
+
+// edges: Smagorinsky coefficient and the vector Laplacian of vn
+template <class T>
+__global__ void diff_edge_smag(GridT<T> g, VertT<T> v, const T* __restrict__ div_vn, const T* __restrict__ zeta,
+                               const T* __restrict__ uv3, T* __restrict__ nu, T* __restrict__ lap) {
+  int e, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const size_t nvl = (size_t)g.nv * nlev;
+  const int* dm = g.e2c2v + 4 * (size_t)e;
+  const size_t im = (size_t)dm[0] * nlev + k, ip = (size_t)dm[1] * nlev + k;
+  const size_t i2 = (size_t)dm[2] * nlev + k, i3 = (size_t)dm[3] * nlev + k;
+  const T* nt = g.nt + 6 * (size_t)e;
+  const T dtx = uv3[ip] - uv3[im], dty = uv3[nvl + ip] - uv3[nvl + im], dtz = uv3[2 * nvl + ip] - uv3[2 * nvl + im];
+  const T dnx = uv3[i3] - uv3[i2], dny = uv3[nvl + i3] - uv3[nvl + i2], dnz = uv3[2 * nvl + i3] - uv3[2 * nvl + i2];
+  const T il = g.inv_l[e], idn = g.inv_dn[e];
+  const T tension = (dnx * nt[0] + dny * nt[1] + dnz * nt[2]) * idn - (dtx * nt[3] + dty * nt[4] + dtz * nt[5]) * il;
+  const T shear = (dtx * nt[0] + dty * nt[1] + dtz * nt[2]) * il + (dnx * nt[3] + dny * nt[4] + dnz * nt[5]) * idn;
+  const size_t ie = (size_t)e * nlev + k;
+  nu[ie] = g.smag_a[e] * sqrt(tension * tension + shear * shear);
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  lap[ie] = (div_vn[(size_t)c1 * nlev + k] - div_vn[(size_t)c0 * nlev + k]) * g.inv_d[e] -
+            (zeta[ip] - zeta[im]) * il;
+}
+
+// cells (half-level range): div of lap vn, cell Laplacian of w, theta increment;
+// vertices: curl of lap vn
+template <class T>
+__global__ void diff_second(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ lap, const T* __restrict__ nu,
+                            const T* __restrict__ w, const T* __restrict__ theta, T* __restrict__ div_l,
+                            T* __restrict__ lap_w, T* __restrict__ dtheta, T* __restrict__ curl_l) {
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned ncell = (unsigned)g.nc * nlevp;
+  if (i < ncell) {
+    int c = (int)(i / (unsigned)nlevp), k = (int)(i - (unsigned)c * nlevp);
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const int* cc = g.c2e2c + 3 * (size_t)c;
+    const T* L = g.lap_c + 3 * (size_t)c;
+    const T wc = w[(size_t)c * nlevp + k];
+    T lw = L[0] * (w[(size_t)cc[0] * nlevp + k] - wc);
+    lw += L[1] * (w[(size_t)cc[1] * nlevp + k] - wc);
+    lw += L[2] * (w[(size_t)cc[2] * nlevp + k] - wc);
+    lap_w[i] = lw;
+    if (k < nlev) {
+      const T* dv = g.div_c + 3 * (size_t)c;
+      const size_t ic = (size_t)c * nlev + k;
+      div_l[ic] = dv[0] * lap[(size_t)ce[0] * nlev + k] + dv[1] * lap[(size_t)ce[1] * nlev + k] +
+                  dv[2] * lap[(size_t)ce[2] * nlev + k];
+      if (sc.hdiff_temp) {
+        const T tc = theta[ic];
+        T f = L[0] * nu[(size_t)ce[0] * nlev + k] * (theta[(size_t)cc[0] * nlev + k] - tc);
+        f += L[1] * nu[(size_t)ce[1] * nlev + k] * (theta[(size_t)cc[1] * nlev + k] - tc);
+        f += L[2] * nu[(size_t)ce[2] * nlev + k] * (theta[(size_t)cc[2] * nlev + k] - tc);
+        dtheta[ic] = sc.dtime * f;
+      }
+    }
+    return;
+  }
+  i -= ncell;
+  if (i >= (unsigned)g.nv * nlev) return;
+  int vx = (int)(i / (unsigned)nlev), k = (int)(i - (unsigned)vx * nlev);
+  const int* ve = g.v2e + 6 * (size_t)vx;
+  const T* cw = g.curl_v + 6 * (size_t)vx;
+  T z = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) z += cw[j] * lap[(size_t)ve[j] * nlev + k];
+  curl_l[i] = z;
+}
+
+// edges: vn update (FP64, in place)
+template <class T>
+__global__ void diff_edge_update(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __restrict__ vn,
+                                 const T* __restrict__ nu, const T* __restrict__ lap, const T* __restrict__ div_l,
+                                 const T* __restrict__ curl_l, float* __restrict__ m_vn) {
+  int e, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const size_t ie = (size_t)e * nlev + k;
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
+  const T lap2 = (div_l[(size_t)c1 * nlev + k] - div_l[(size_t)c0 * nlev + k]) * g.inv_d[e] -
+                 (curl_l[(size_t)vp * nlev + k] - curl_l[(size_t)vm * nlev + k]) * g.inv_l[e];
+  const T inc = sc.dtime * nu[ie] * lap[ie] - g.k4_a[e] * lap2;
+  const double vnn = vn[ie] + (double)inc;
+  vn[ie] = vnn;
+  if constexpr (kMixed<T>) m_vn[ie] = (float)vnn;
+}
+
+// cells (half-level range): w fourth-order diffusion, theta/exner update (FP64, in place)
+template <class T>
+__global__ void diff_cell_update(GridT<T> g, VertT<T> v, ScalT<T> sc, const double* __restrict__ theta_ref,
+                                 const double* __restrict__ exner_ref, double rd_o_cvd, StateView st,
+                                 const T* __restrict__ lap_w, const T* __restrict__ dtheta, Mirrors m) {
+  int c, k;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  if (!flat_index(g.nc, nlevp, c, k)) return;
+  if (k > 0 && k < nlev) {
+    const int* cc = g.c2e2c + 3 * (size_t)c;
+    const T* L = g.lap_c + 3 * (size_t)c;
+    const T lc = lap_w[(size_t)c * nlevp + k];
+    T l2 = L[0] * (lap_w[(size_t)cc[0] * nlevp + k] - lc);
+    l2 += L[1] * (lap_w[(size_t)cc[1] * nlevp + k] - lc);
+    l2 += L[2] * (lap_w[(size_t)cc[2] * nlevp + k] - lc);
+    const size_t iw = (size_t)c * nlevp + k;
+    const double wn = st.w[iw] - (double)(g.k4w_c[c] * l2);
+    st.w[iw] = wn;
+    if constexpr (kMixed<T>) m.w[iw] = (float)wn;
+  }
+  if (k < nlev && sc.hdiff_temp) {
+    const size_t ic = (size_t)c * nlev + k;
+    const double th = st.theta_v[ic];
+    const double thn = th + (double)dtheta[ic];
+    const double exn = st.exner[ic] * (1.0 + rd_o_cvd * (thn - th) / th);
+    st.theta_v[ic] = thn;
+    st.exner[ic] = exn;
+    if constexpr (kMixed<T>) m.th[ic] = (float)(thn - theta_ref[k]);
+  }
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------------
+// launch sequences
+// -------------------------------------------------------------------------
+template <class T>
+void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
+                                T* divd2, cudaStream_t s) {
+  const GridT<T>& g = x.g;
+  const VertT<T>& v = x.v;
+  const WorkT<T>& wk = x.w;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_for((long long)g.ne * nlev, kThreads), kThreads, s,
+              va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e);
+  const long long n2 = (long long)g.nc * nlev + (long long)g.nv * nlevp;
+  ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, kThreads), kThreads, s, va_cell_vert<T>, g,
+              v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v);
+  ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, kThreads), kThreads,
+              s, va_edge_tend<T>, g, v, vn, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e);
+  ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_for((long long)g.nc * nlevp, kThreads), kThreads, s,
+              va_cell_w<T>, g, v, w, wk.gw_e, ddt_w);
+}
+
+template <class T>
+void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
+  const GridT<T>& g = x.g;
+  const VertT<T>& v = x.v;
+  const WorkT<T>& wk = x.w;
+  const Mirrors& m = en.m;
+  const int nlev = v.nlev;
+  const unsigned bc = blocks_for((long long)g.nc * nlev, kThreads), be = blocks_for((long long)g.ne * nlev, kThreads);
+  // stencil views of the state: the FP64 state itself, or the FP32 mirrors
+  const T *s_vn, *s_w, *s_rho, *s_th, *s_wp;
+  if constexpr (kMixed<T>) {
+    s_vn = m.vn, s_w = m.w, s_rho = m.rho, s_th = m.th, s_wp = m.w_p;
+  } else {
+    s_vn = st.vn, s_w = st.w, s_rho = st.rho, s_th = st.theta_v, s_wp = en.wk.w_p;
+  }
+  // ---------------- predictor ----------------
+  launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s);
+  ICON_LAUNCH(kname<T>("sn_cell_grad", "sn_cell_grad_f32"), bc, kThreads, s, sn_cell_grad<T>, g, v, s_rho, s_th,
+              wk.grad4);
+  ICON_LAUNCH(kname<T>("sn_edge_pred", "sn_edge_pred_f32"), be, kThreads, s, sn_edge_pred<T>, g, v, x.s, s_vn, wk.vt,
+              wk.ddt_vn0, s_rho, s_th, st.exner, st.exner_pr, en.g64.inv_d, en.sc.exfac, wk.grad4, wk.rho_e,
+              wk.theta_e, wk.hpg, wk.vn_p);
+  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), bc, kThreads, s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
+              st.exner, st.exner_pr);
+  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), bc, kThreads, s, sn_cell_fluxdiv<T>, g, v, x.s,
+              wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
+  launch_column<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, s);
+  // ---------------- corrector ----------------
+  launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s);
+  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), be, kThreads, s, sn_edge_corr<T>, g, v, x.s, st.vn,
+              wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn);
+  const T* vn_new = kMixed<T> ? (const T*)m.vn : (const T*)st.vn;
+  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), bc, kThreads, s, sn_cell_div<T>, g, v, vn_new, wk.divd,
+              nullptr, nullptr);
+  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), bc, kThreads, s, sn_cell_fluxdiv<T>, g, v, x.s,
+              vn_new, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
+  launch_column<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, s);
+}
+
+template <class T>
+void launch_diffusion(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
+  const GridT<T>& g = x.g;
+  const VertT<T>& v = x.v;
+  const WorkT<T>& wk = x.w;
+  const Mirrors& m = en.m;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  const T *s_vn, *s_w, *s_th;
+  if constexpr (kMixed<T>) {
+    s_vn = m.vn, s_w = m.w, s_th = m.th;
+  } else {
+    s_vn = st.vn, s_w = st.w, s_th = st.theta_v;
+  }
+  const long long n1 = (long long)g.nc * nlev + (long long)g.nv * nlev;
+  ICON_LAUNCH(kname<T>("diff_div_curl_uv", "diff_div_curl_uv_f32"), blocks_for(n1, kThreads), kThreads, s,
+              diff_div_curl_uv<T>, g, v, s_vn, wk.div_vn, wk.zeta, wk.uv3);
+  ICON_LAUNCH(kname<T>("diff_edge_smag", "diff_edge_smag_f32"), blocks_for((long long)g.ne * nlev, kThreads),
+              kThreads, s, diff_edge_smag<T>, g, v, wk.div_vn, wk.zeta, wk.uv3, wk.nu, wk.lap_vn);
+  const long long n3 = (long long)g.nc * nlevp + (long long)g.nv * nlev;
+  ICON_LAUNCH(kname<T>("diff_second", "diff_second_f32"), blocks_for(n3, kThreads), kThreads, s, diff_second<T>, g, v,
+              x.s, wk.lap_vn, wk.nu, s_w, s_th, wk.div_l, wk.lap_w, wk.dtheta, wk.curl_l);
+  ICON_LAUNCH(kname<T>("diff_edge_update", "diff_edge_update_f32"), blocks_for((long long)g.ne * nlev, kThreads),
+              kThreads, s, diff_edge_update<T>, g, v, x.s, st.vn, wk.nu, wk.lap_vn, wk.div_l, wk.curl_l, m.vn);
+  ICON_LAUNCH(kname<T>("diff_cell_update", "diff_cell_update_f32"), blocks_for((long long)g.nc * nlevp, kThreads),
+              kThreads, s, diff_cell_update<T>, g, v, x.s, en.v.theta_ref, en.v.exner_ref, en.sc.rd_o_cvd, st,
+              wk.lap_w, wk.dtheta, m);
+}
+
+void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t s) {
+  const int nlev = en.v.nlev;
+  const long long n = (long long)en.g64.ne * nlev + (long long)en.g64.nc * (nlev + 1);
+  ICON_LAUNCH("mx_refresh", blocks_for(n, kThreads), kThreads, s, mx_refresh, en.g64.ne, en.g64.nc, nlev,
+              en.v.exner_ref, en.v.theta_ref, en.rho_ref64, st, en.m);
+}
+
+template void launch_velocity_tendencies<double>(const Ctx<double>&, const double*, const double*, double*, double*,
+                                                 const double*, double*, cudaStream_t);
+template void launch_substep<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
+template void launch_substep<float>(const Engine&, const Ctx<float>&, const StateView&, cudaStream_t);
+template void launch_diffusion<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
+template void launch_diffusion<float>(const Engine&, const Ctx<float>&, const StateView&, cudaStream_t);
+
+}  // namespace icon
