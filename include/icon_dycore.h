@@ -228,6 +228,55 @@ int icon_dycore_synchronize(icon_dycore_t* dycore);
 int icon_dycore_sizes(const icon_dycore_t* dycore, int32_t* nlev, int32_t* n_cells,
                       int32_t* n_edges, int32_t* n_verts);
 
+/*
+ * Allocation-free vertically implicit column solve.  The paper has no
+ * counterpart: this entry point is for callers that cannot allocate device
+ * memory when they call -- a host model that has reserved nearly all device
+ * memory for its own arrays at start-up, or one that enqueues its time step
+ * while capturing a stream into a CUDA graph (cudaMalloc is not a capturable
+ * operation).  Such a caller cannot create a dycore, whose work arrays are
+ * allocated for a whole step, but can run this solve on arrays it owns.
+ *
+ * It runs the same column kernel as icon_nh_solve (one thread per column,
+ * Thomas elimination, Rayleigh damping, back-substitution, linearised
+ * equation of state) for n_cols independent columns of nlev levels:
+ *   z_ifc [nlev+1] HOST, half-level heights as for icon_dycore_create;
+ *   p      the scheme parameters (dtime/ndyn_substeps is the time step of the
+ *          solve; stream and synchronous are honoured; precision is ignored,
+ *          the solve is FP64);
+ * DEVICE inputs, level-contiguous like the state:
+ *   w [n_cols*(nlev+1)], rho, exner, theta_v [n_cols*nlev]  state at the
+ *          start of the substep;
+ *   ddt_w0 [n_cols*(nlev+1)]  explicit w tendency;
+ *   div_m, div_t [n_cols*nlev]  horizontal divergences of the mass and
+ *          rho*theta_v fluxes;
+ *   rho_pred, theta_pred [n_cols*nlev], ddt_w1 [n_cols*(nlev+1)]  the
+ *          predicted state and its w tendency for the corrector form
+ *          (half levels from 0.6 now + 0.4 predicted, tendency 0.25 ddt_w0 +
+ *          0.75 ddt_w1); all three NULL for the predictor form.
+ * DEVICE outputs (may alias the corresponding inputs): w_new, rho_new,
+ *   exner_new, theta_new.
+ * Scratch: one file-scope static device array of 64 MiB, held by every GPU
+ * that loads this library until the process exits; it limits a call to
+ * nlev <= 256 and n_cols*(nlev+1) <= 1 047 552 column-levels (larger calls
+ * return ICON_ERR_ARG).  No cudaMalloc, cudaFree or other allocating call
+ * is made.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and sets the kernel's shared-memory limit;
+ * make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (every value a call reads is
+ * written earlier in the same call, so nothing needs clearing); calls whose
+ * GPU work overlaps -- on different streams, or from different threads --
+ * race on it and must be serialised by the caller.
+ * Errors: ICON_ERR_ARG (NULL, sizes beyond the limit, bad z_ifc or time
+ * step), ICON_ERR_CUDA.
+ */
+int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const double* z_ifc,
+                              const icon_dycore_params_t* p, const double* w, const double* rho,
+                              const double* exner, const double* theta_v, const double* rho_pred,
+                              const double* theta_pred, const double* ddt_w0, const double* ddt_w1,
+                              const double* div_m, const double* div_t, double* w_new,
+                              double* rho_new, double* exner_new, double* theta_new);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* icon_last_error(void);
 

@@ -87,6 +87,8 @@ _sig = {
                                            ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
     "icon_dycore_sizes": (ctypes.c_int, [ctypes.c_void_p] + [_i32p] * 4),
     "icon_last_error": (ctypes.c_char_p, []),
+    "icon_column_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _f64p,
+                                                 ctypes.POINTER(icon_dycore_params_t)] + [ctypes.c_void_p] * 14),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -126,6 +128,22 @@ def _ptr(x):
     if not x.is_contiguous():
         raise ValueError("tensor fields must be contiguous")
     return x.data_ptr()
+
+
+def column_solve_noalloc(z_ifc, params, w, rho, exner, theta_v, ddt_w0, div_m, div_t, w_new, rho_new,
+                         exner_new, theta_new, rho_pred=None, theta_pred=None, ddt_w1=None):
+    """icon_column_solve_noalloc on device tensors; the three optional fields
+    select the corrector form.  ``params`` is an icon_dycore_params_t or a
+    dict of overrides."""
+    if params is None or isinstance(params, dict):
+        params = default_params(**(params or {}))
+    z = np.ascontiguousarray(z_ifc, dtype=np.float64)
+    n_cols = rho.shape[0] if rho.dim() == 2 else rho.numel() // (z.size - 1)
+    opt = [None if x is None else _ptr(x) for x in (rho_pred, theta_pred, ddt_w1)]
+    _check(icon_column_solve_noalloc(n_cols, z.size - 1, z.ctypes.data_as(_f64p), ctypes.byref(params),
+                                     _ptr(w), _ptr(rho), _ptr(exner), _ptr(theta_v), opt[0], opt[1],
+                                     _ptr(ddt_w0), opt[2], _ptr(div_m), _ptr(div_t), _ptr(w_new),
+                                     _ptr(rho_new), _ptr(exner_new), _ptr(theta_new)))
 
 
 class Grid:

@@ -24,6 +24,14 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+namespace icon {
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace icon
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                      \
   do {                                                                                      \
     cudaError_t err_ = (expr);                                                              \

@@ -138,6 +138,9 @@ struct HostGrid {
   double mean_area;
 };
 
+// Records `msg` as the calling thread's last error and returns `code`.
+int report_error(int code, const std::string& msg);
+
 // Builds and validates the host grid; returns an error message or "".
 std::string build_host_grid(const icon_grid_desc_t* d, HostGrid* g);
 

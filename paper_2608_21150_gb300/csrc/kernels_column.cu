@@ -23,6 +23,9 @@
 // [k][c], coalesced for one thread per column.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "kernels.h"
@@ -109,7 +112,10 @@ struct ColArgs {
   const double* rho_ref;
 };
 
-template <class T>
+// kOwnZb: the corrector form computes zb and the equation-of-state term itself
+// (as the predictor does) instead of reading the predictor's; used by the
+// allocation-free entry point below.
+template <class T, bool kOwnZb = false>
 __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
   extern __shared__ double sm[];
   __shared__ int rows_c[kCW];
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
       tile_rows(T_dw1, a.ddt_w1, nlevp, rows_c, k0, nkh);
       tile_rows(T_rp, a.rho_p, nlev, rows_c, k0, nkf);
       tile_rows(T_tp, a.theta_p, nlev, rows_c, k0, nkf);
-      tile_levels(T_zb, kLD, a.zbl, nc, c0, k0, nkc);
+      if (!kOwnZb) tile_levels(T_zb, kLD, a.zbl, nc, c0, k0, nkc);
     }
     cp_wait();
     __syncthreads();
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
       }
       const size_t ik = (size_t)k * nc + c;
       double zb;
-      if (!corrector) {
+      if (!corrector || kOwnZb) {
         zb = cf[CZB] * pi_n * rcp(rho_n * th_n);
         a.zbl[ik] = zb;
         eb_s[ik] = pi_n - sc.cvd_o_rd * pr_k;
@@ -380,3 +386,206 @@ template void launch_column<double>(const Engine&, int, const StateView&, const 
 template void launch_column<float>(const Engine&, int, const StateView&, const float*, const float*, cudaStream_t);
 
 }  // namespace icon
+
+// ===========================================================================
+// Allocation-free column solve (no counterpart in the paper).
+//
+// Who needs it: callers that cannot allocate device memory at the time they
+// call.  A host model typically reserves nearly all device memory for its own
+// arrays at start-up, or enqueues its time step while capturing a stream into
+// a CUDA graph, where cudaMalloc is not a capturable operation.  Such a
+// caller cannot create a dycore (icon_dycore_create allocates the work arrays
+// of a whole step) but can still run the vertically implicit solve on arrays
+// it owns.  The column solve needs scratch (the Thomas elimination planes and
+// the vertical metrics); here it lives in one file-scope static device array
+// that every GPU loading this library holds until the process exits.
+// ===========================================================================
+namespace icon {
+namespace {
+
+constexpr int kNoallocMaxLev = 256;
+constexpr size_t kNoallocStride = 512;                 // doubles per vertical-metric slot
+constexpr size_t kNoallocCoef = 8192;                  // doubles of the vertical-metric section
+constexpr size_t kNoallocDoubles = (size_t)8 << 20;    // 64 MiB in total
+constexpr size_t kNoallocPlanes = 8;                   // 7 Thomas planes + zb
+constexpr size_t kNoallocMaxPoints = (kNoallocDoubles - kNoallocCoef) / kNoallocPlanes;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the
+// static array (its host-side name is only a stand-in) and the kernel's
+// shared-memory attribute.
+int noalloc_setup(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoallocMaxDevices)
+    return report_error(ICON_ERR_CUDA, "icon_column_solve_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    double* ptr = nullptr;
+    e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return report_error(ICON_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    e = cudaFuncSetAttribute(sn_column_tiled<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess)
+      return report_error(ICON_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return ICON_OK;
+}
+
+}  // namespace
+}  // namespace icon
+
+extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const double* z_ifc,
+                                         const icon_dycore_params_t* p, const double* w, const double* rho,
+                                         const double* exner, const double* theta_v, const double* rho_pred,
+                                         const double* theta_pred, const double* ddt_w0, const double* ddt_w1,
+                                         const double* div_m, const double* div_t, double* w_new, double* rho_new,
+                                         double* exner_new, double* theta_new) {
+  using namespace icon;
+  const char* fn = "icon_column_solve_noalloc: ";
+  if (!z_ifc || !p || !w || !rho || !exner || !theta_v || !ddt_w0 || !div_m || !div_t || !w_new || !rho_new ||
+      !exner_new || !theta_new)
+    return report_error(ICON_ERR_ARG, std::string(fn) + "NULL argument");
+  const bool corr = rho_pred != nullptr;
+  if (corr && (!theta_pred || !ddt_w1))
+    return report_error(ICON_ERR_ARG, std::string(fn) + "the corrector form needs rho_pred, theta_pred and ddt_w1");
+  if (n_cols < 1 || nlev < 2 || nlev > kNoallocMaxLev)
+    return report_error(ICON_ERR_ARG, std::string(fn) + "need n_cols >= 1 and 2 <= nlev <= 256");
+  const size_t points = (size_t)n_cols * (size_t)(nlev + 1);
+  if (points > kNoallocMaxPoints)
+    return report_error(ICON_ERR_ARG, std::string(fn) + "n_cols*(nlev+1) = " + std::to_string(points) +
+                                          " exceeds the static scratch of " + std::to_string(kNoallocMaxPoints) +
+                                          " column-levels (64 MiB)");
+  for (int k = 0; k < nlev; ++k)
+    if (!(z_ifc[k] > z_ifc[k + 1])) return report_error(ICON_ERR_ARG, std::string(fn) + "z_ifc must decrease");
+  if (z_ifc[nlev] != 0.0) return report_error(ICON_ERR_ARG, std::string(fn) + "z_ifc[nlev] must be 0");
+  if (!(p->dtime > 0.0) || p->ndyn_substeps < 1)
+    return report_error(ICON_ERR_ARG, std::string(fn) + "dtime must be > 0 and ndyn_substeps >= 1");
+
+  // scalars and vertical metrics, with the same definitions as icon_dycore_create
+  Scalars s{};
+  s.dtime = p->dtime;
+  s.dt_s = p->dtime / p->ndyn_substeps;
+  s.grav = p->grav;
+  s.rd = p->rd;
+  s.cpd = p->cpd;
+  s.cvd = p->cpd - p->rd;
+  s.p00 = p->p00;
+  s.beta = p->vwind_impl_wgt;
+  s.wnow_vel = p->wgt_nnow_vel;
+  s.wnew_vel = p->wgt_nnew_vel;
+  s.wnow_rth = p->wgt_nnow_rth;
+  s.wnew_rth = p->wgt_nnew_rth;
+  s.exfac = p->exner_exfac;
+  s.divdamp = p->divdamp_fac;
+  s.rd_o_cvd = p->rd / s.cvd;
+  s.cvd_o_rd = s.cvd / p->rd;
+  s.hdiff_temp = p->hdiff_temp ? 1 : 0;
+  double coef[kNoallocCoef] = {};
+  double* dz = coef;
+  double* inv_dz = coef + kNoallocStride;
+  double* inv_dzh = coef + 2 * kNoallocStride;
+  double* wgt = coef + 3 * kNoallocStride;
+  double* th_ref = coef + 4 * kNoallocStride;
+  double* ex_ref = coef + 5 * kNoallocStride;
+  double* dref = coef + 6 * kNoallocStride;
+  double* ray = coef + 7 * kNoallocStride;
+  double* colc = coef + 8 * kNoallocStride;
+  double z_mc[kNoallocMaxLev];
+  for (int k = 0; k < nlev; ++k) {
+    z_mc[k] = 0.5 * (z_ifc[k] + z_ifc[k + 1]);
+    dz[k] = z_ifc[k] - z_ifc[k + 1];
+    inv_dz[k] = 1.0 / dz[k];
+  }
+  for (int k = 1; k < nlev; ++k) {
+    inv_dzh[k] = 1.0 / (z_mc[k - 1] - z_mc[k]);
+    wgt[k] = (z_ifc[k] - z_mc[k]) / (z_mc[k - 1] - z_mc[k]);
+  }
+  const double T0 = p->ref_T0, H = p->cpd * T0 / p->grav;
+  for (int k = 0; k < nlev; ++k) th_ref[k] = T0 * std::exp(z_mc[k] / H);
+  ex_ref[nlev - 1] = std::exp(-z_mc[nlev - 1] / H);
+  for (int k = nlev - 1; k >= 1; --k) {
+    const double th_ic = wgt[k] * th_ref[k - 1] + (1.0 - wgt[k]) * th_ref[k];
+    ex_ref[k - 1] = ex_ref[k] - p->grav * (z_mc[k - 1] - z_mc[k]) / (p->cpd * th_ic);
+  }
+  for (int k = 1; k < nlev; ++k) dref[k] = (ex_ref[k - 1] - ex_ref[k]) * inv_dzh[k];
+  for (int k = 0; k <= nlev; ++k) ray[k] = 1.0;
+  if (p->rayleigh_coeff > 0.0) {
+    const double top = z_ifc[0], zd = p->damp_height;
+    for (int k = 0; k <= nlev; ++k)
+      if (z_ifc[k] > zd) {
+        const double sn = std::sin(0.5 * M_PI * (z_ifc[k] - zd) / (top - zd));
+        ray[k] = 1.0 / (1.0 + s.dt_s * p->rayleigh_coeff * sn * sn);
+      }
+  }
+  for (int k = 0; k <= nlev; ++k) {
+    double* cf = colc + 8 * (size_t)k;
+    if (k < nlev) {
+      cf[0] = s.dt_s * s.rd_o_cvd / dz[k];
+      cf[1] = s.dt_s * (1.0 - s.beta) / dz[k];
+      cf[2] = s.dt_s * s.beta / dz[k];
+    }
+    if (k >= 1 && k < nlev) {
+      cf[3] = s.dt_s * p->cpd * (1.0 - s.beta) * inv_dzh[k];
+      cf[4] = s.dt_s * p->cpd * dref[k];
+      cf[5] = s.dt_s * p->cpd * s.beta * inv_dzh[k];
+      cf[6] = wgt[k];
+      cf[7] = 1.0 - wgt[k];
+    }
+  }
+
+  double* base = nullptr;
+  int rc = noalloc_setup(&base);
+  if (rc != ICON_OK) return rc;
+  cudaStream_t stream = static_cast<cudaStream_t>(p->stream);
+  // metrics into the static array (a copy from host memory, no allocation)
+  cudaError_t e = cudaMemcpyAsync(base, coef, sizeof coef, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(e));
+  DevVert v{};
+  v.nlev = nlev;
+  v.dz = base;
+  v.inv_dz = base + kNoallocStride;
+  v.inv_dzh = base + 2 * kNoallocStride;
+  v.wgt = base + 3 * kNoallocStride;
+  v.theta_ref = base + 4 * kNoallocStride;
+  v.exner_ref = base + 5 * kNoallocStride;
+  v.dexner_ref_ic = base + 6 * kNoallocStride;
+  v.ray_fac = base + 7 * kNoallocStride;
+  v.colc = base + 8 * kNoallocStride;
+  // every scratch plane the kernel reads is written earlier in the same call,
+  // so nothing has to be cleared between calls
+  ColArgs<double> a{};
+  a.w = w;
+  a.rho = rho;
+  a.exner = exner;
+  a.theta = theta_v;
+  a.ddt_w0 = ddt_w0;
+  a.ddt_w1 = ddt_w1;
+  a.rho_p = rho_pred;
+  a.theta_p = theta_pred;
+  a.div_m = div_m;
+  a.div_t = div_t;
+  a.col = base + kNoallocCoef;
+  a.zbl = a.col + 7 * points;
+  a.w_o = w_new;
+  a.rho_o = rho_new;
+  a.exner_o = exner_new;
+  a.theta_o = theta_new;
+  const unsigned blocks = (unsigned)((n_cols + kCW - 1) / kCW);
+  sn_column_tiled<double, true><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(e));
+  if (p->synchronous) {
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(e));
+  }
+  return ICON_OK;
+}
