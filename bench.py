@@ -189,6 +189,60 @@ def config_dict(prec):
             "l2": "inputs larger than L2 (FP64 state 1.5 GB, scratch ~9 GB); no flush"}
 
 
+def measure(P, G, z, st0, prec, args, dev, world):
+    """Time K steps of one precision mode; returns the numbers and the final state."""
+    import torch
+    import torch.distributed as dist
+    w = WORKLOAD
+    stream = torch.cuda.current_stream(dev)
+    D = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
+                            precision=P.ICON_PREC_MIXED if prec == "mixed" else P.ICON_PREC_FP64,
+                            use_graph=1, synchronous=0, stream=stream.cuda_stream))
+    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
+    for _ in range(args.warmup):
+        D.step(t)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        D.step(t)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms = float(mt.item())
+    nc = G.n_cells
+    ps = torch.empty(nc, dtype=torch.float64, device=dev)
+    t850 = torch.empty_like(ps)
+    try:
+        D.diagnostics(t, ps, t850)
+        finite = True
+    except P.IconError:
+        finite = False
+    out = dict(ms=ms, clocks=clocks, finite=finite, ps=ps.cpu().numpy(), t850=t850.cpu().numpy())
+    nsteps_prof = min(args.steps, 3)
+    out["prof"] = D.profile(t, nsteps_prof)
+    out["nsteps_prof"] = nsteps_prof
+    D.close()
+    return out, t
+
+
+def kernel_table(prof, nsteps):
+    tot = sum(v[1] for v in prof.values()) / nsteps
+    return {k: {"launches_per_step": n // nsteps, "ms_per_step": round(m / nsteps, 3),
+                "share": round(m / nsteps / tot, 4)} for k, (n, m) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -211,55 +265,34 @@ def run_ours(args):
     nlev = w["nlev"]
     nc, ne, nv = grid.n_cells, grid.n_edges, grid.n_verts
     st0 = jw_type_state(grid, z, seed=w["seed"])
-    stream = torch.cuda.current_stream(dev)
     G = P.Grid(grid)
-    D = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
-                            use_graph=1, synchronous=0, stream=stream.cuda_stream))
-    th_ref, ex_ref = D.reference_state()
+    Dref = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"]))
+    th_ref, ex_ref = Dref.reference_state()
+    Dref.close()
     st0["exner_pr"] = st0["exner"] - ex_ref[None, :]
-    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
 
-    for _ in range(args.warmup):
-        D.step(t)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        D.step(t)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        dist.barrier()
-        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms = float(mt.item())
-    ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
+    f64, _ = measure(P, G, z, st0, "fp64", args, dev, world)
+    ms_per_step = f64["ms"] / args.steps
+    value = world * args.steps / (f64["ms"] / 1000.0)
+    prof, nsp = f64["prof"], f64["nsteps_prof"]
+    launches_per_step = sum(n for n, _ in prof.values()) // nsp
+    name, (nl, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    achieved = FLOPS_PER_UNIT[name] * units_per_launch(name, nc, ne, nv, nlev) / (tot_ms / nl / 1000.0) / 1e12
 
-    finite = all(bool(torch.isfinite(x).all()) for x in t.values())
-
-    # per-kernel device time over a few steps (events around every launch)
-    prof = D.profile(t, min(args.steps, 3))
-    nsteps_prof = min(args.steps, 3)
-    launches_per_step = sum(n for n, _ in prof.values()) // nsteps_prof
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, tot_ms) = top
-    avg_s = tot_ms / nl / 1000.0
-    achieved = FLOPS_PER_UNIT[name] * units_per_launch(name, nc, ne, nv, nlev) / avg_s / 1e12
-    prof_ms_step = sum(v[1] for v in prof.values()) / nsteps_prof
-    kernels = {k: {"launches_per_step": n // nsteps_prof, "ms_per_step": round(m / nsteps_prof, 3),
-                   "share": round(m / nsteps_prof / prof_ms_step, 4)} for k, (n, m) in
-               sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    mx = None
+    if not args.no_mixed:
+        m, _ = measure(P, G, z, st0, "mixed", args, dev, world)
+        area = G.cell_areas()
+        rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
+        mx = {"value": world * args.steps / (m["ms"] / 1000.0), "ms_per_step": m["ms"] / args.steps,
+              "speedup_vs_fp64": f64["ms"] / m["ms"], "finite": m["finite"],
+              "rms_ps_pa": rms(m["ps"] - f64["ps"]), "rms_t850_k": rms(m["t850"] - f64["t850"]),
+              "compared_after_steps": args.warmup + args.steps,
+              "reference": "FP64 GPU dycore (equal to the FP64 oracle to 1e-9 after 10 steps, GPU parity tests)",
+              "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"]}
 
     # end to end through the C-ABI with host arrays (copies inside the timed region)
+    stream = torch.cuda.current_stream(dev)
     e2e_steps = max(1, min(args.steps, 5))
     host = {k: torch.from_numpy(v.copy()).pin_memory() for k, v in st0.items()}
     D2 = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
@@ -270,6 +303,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         D2.step(host)
     e2e_s = time.perf_counter() - t0
+    D2.close()
     sb = state_bytes(nc, ne, nlev)
 
     hbm_bytes = compulsory_bytes_per_step(nc, ne, nlev, w["ndyn"])
@@ -287,18 +321,17 @@ def run_ours(args):
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "note": "FP64 algorithmic flops per launch / event-timed launch duration; peak = nominal "
                              "FP64 rate from unit counts and clock (1.2 TFLOP/s measured by a DFMA probe)"},
-        "kernels": kernels,
+        "kernels": kernel_table(prof, nsp),
+        "mixed": mx,
         "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": sb,
                 "d2h_bytes_per_step": sb},
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks, "finite": finite,
+        "clocks": f64["clocks"], "finite": f64["finite"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(nlev)
     if rank == 0:
         print(json.dumps(line))
-    D2.close()
-    D.close()
     G.close()
     if world > 1:
         dist.destroy_process_group()
@@ -312,6 +345,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["bisections"],
                     help="RnBm bisections (default 6 = R2B6); smaller grids only for profiler captures")
     args = ap.parse_args()

@@ -198,6 +198,20 @@ int icon_velocity_tendencies(icon_dycore_t* dycore, const double* vn, const doub
 int icon_dycore_reference_state(const icon_dycore_t* dycore, double* theta_ref,
                                 double* exner_ref);
 
+/* Diagnostics of a DEVICE state (outside the step):
+ *   ps   [n_cells] DEVICE or NULL: surface pressure, Pa (exner at the ground
+ *        extrapolated hydrostatically from the lowest level with its theta_v);
+ *   t850 [n_cells] DEVICE or NULL: temperature at 850 hPa, K (linear in ln p);
+ *   mass HOST scalar or NULL: total mass sum_c A_c sum_k rho dz, kg, summed in
+ *        a fixed order (bitwise reproducible).
+ * Returns ICON_ERR_NUMERIC when vn, w, rho, exner or theta_v holds a NaN or
+ * an infinity (the outputs are still written); ICON_ERR_ARG for a host state. */
+int icon_dycore_diagnostics(icon_dycore_t* dycore, const icon_state_t* state, double* ps, double* t850,
+                            double* mass);
+
+/* Cell areas in m^2 (HOST output [n_cells]), for area-weighted statistics. */
+int icon_grid_cell_areas(const icon_grid_t* grid, double* area);
+
 /* Measurement aid: run nsteps full steps on a DEVICE state (kernel by
  * kernel, not as a graph) with a CUDA event pair around every kernel launch
  * on the dycore's stream, then synchronize and report per kernel name:

@@ -87,6 +87,9 @@ _sig = {
                                            ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
     "icon_dycore_sizes": (ctypes.c_int, [ctypes.c_void_p] + [_i32p] * 4),
     "icon_last_error": (ctypes.c_char_p, []),
+    "icon_dycore_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_void_p,
+                                               ctypes.c_void_p, _f64p]),
+    "icon_grid_cell_areas": (ctypes.c_int, [ctypes.c_void_p, _f64p]),
     "icon_column_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _f64p,
                                                  ctypes.POINTER(icon_dycore_params_t)] + [ctypes.c_void_p] * 14),
 }
@@ -172,6 +175,11 @@ class Grid:
         self.handle = h
         self.n_cells, self.n_edges, self.n_verts = grid.n_cells, grid.n_edges, grid.n_verts
 
+    def cell_areas(self):
+        a = np.empty(self.n_cells)
+        _check(icon_grid_cell_areas(self.handle, a.ctypes.data_as(_f64p)))
+        return a
+
     def close(self):
         if self.handle:
             icon_grid_destroy(self.handle)
@@ -239,6 +247,15 @@ class Dycore:
                                    ctypes.byref(n)))
         return {names.raw[64 * j:64 * j + 64].split(b"\0")[0].decode(): (launches[j], ms[j])
                 for j in range(n.value)}
+
+    def diagnostics(self, st, ps=None, t850=None):
+        """Fill the device tensors ps/t850 [n_cells] (if given) and return the total
+        mass; raises IconError(ICON_ERR_NUMERIC) for a non-finite state."""
+        s = self._state({k: st[k] for k in ("vn", "w", "rho", "exner", "theta_v")} | {"exner_pr": st["rho"]})
+        m = ctypes.c_double()
+        _check(icon_dycore_diagnostics(self.handle, ctypes.byref(s), None if ps is None else _ptr(ps),
+                                       None if t850 is None else _ptr(t850), ctypes.byref(m)))
+        return m.value
 
     def debug_field(self, name, out):
         """Copy the internal work field `name` into the device tensor `out`."""

@@ -180,6 +180,7 @@ int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
   v.c2v_w = A.upload(h.c2v_w);
   v.uv_w = A.upload(h.uv_w);
   v.mean_area = h.mean_area;
+  v.cell_area = A.upload(h.cell_area);
   if (A.status != cudaSuccess) {
     std::string m = std::string("icon_grid_create: ") + cudaGetErrorString(A.status);
     A.release();
@@ -443,6 +444,8 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   w.w_p = A.alloc<double>(ch);
   w.col = A.alloc<double>(7 * ch);
   w.zbl = A.alloc<double>(ch);
+  w.diag = A.alloc<double>(diag_partials(nc));
+  w.flag = A.alloc<int>(1);
   if (A.status == cudaSuccess) {
     cudaError_t e = cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) A.status = e;
@@ -724,6 +727,43 @@ int icon_dycore_debug_field(icon_dycore_t* d, const char* name, void* dst, int64
   if (bytes < (int64_t)n) return fail(ICON_ERR_ARG, "icon_dycore_debug_field: destination too small");
   CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, d->stream));
   CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return ICON_OK;
+}
+
+int icon_dycore_diagnostics(icon_dycore_t* d, const icon_state_t* s, double* ps, double* t850, double* mass) {
+  if (!d || !s) return fail(ICON_ERR_ARG, "icon_dycore_diagnostics: NULL argument");
+  if (!s->vn || !s->w || !s->rho || !s->exner || !s->theta_v)
+    return fail(ICON_ERR_ARG, "icon_dycore_diagnostics: NULL state field");
+  const void* ptrs[5] = {s->vn, s->w, s->rho, s->exner, s->theta_v};
+  for (const void* p : ptrs) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      return fail(ICON_ERR_ARG, "icon_dycore_diagnostics: the state must be on the device");
+    }
+  }
+  StateView st{s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr};
+  const int nb = diag_partials(d->grid->host.nc);
+  CUDA_TRY(cudaMemsetAsync(d->en.wk.flag, 0, sizeof(int), d->stream));
+  launch_diagnostics(d->en, d->en.g64.cell_area, st, ps, t850, d->en.wk.diag, d->en.wk.flag, d->stream);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> part(nb);
+  int bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(part.data(), d->en.wk.diag, nb * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(&bad, d->en.wk.flag, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  if (mass) {
+    double m = 0.0;
+    for (double x : part) m += x;
+    *mass = m;
+  }
+  if (bad) return fail(ICON_ERR_NUMERIC, "icon_dycore_diagnostics: the state holds non-finite values");
+  return ICON_OK;
+}
+
+int icon_grid_cell_areas(const icon_grid_t* g, double* area) {
+  if (!g || !area) return fail(ICON_ERR_ARG, "icon_grid_cell_areas: NULL argument");
+  std::memcpy(area, g->host.cell_area.data(), g->host.nc * sizeof(double));
   return ICON_OK;
 }
 

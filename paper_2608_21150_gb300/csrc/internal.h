@@ -45,6 +45,7 @@ struct GridT {
   const T* c2v_w;   // [nv*6] cell->vertex weights (0 for pads)
   const T* uv_w;    // [nv*6*3] vertex velocity weights (xyz per edge)
   T mean_area;
+  const double* cell_area;  // [nc] (diagnostics)
 };
 using DevGrid = GridT<double>;
 
@@ -107,6 +108,8 @@ struct DevWork {
   double* w_p;                            // cells, half levels
   double* col;   // level-major [k][c] scratch: 7 planes of (nlev+1)*nc: cp, rp, rho*, pr*, rho_ic, alpha, eos
   double* zbl;   // level-major zb [(nlev+1)*nc], predictor -> corrector
+  double* diag;  // diagnostics: partial column-mass sums
+  int* flag;     // diagnostics: non-finite flag
 };
 
 // FP32 mirrors of the state read by the mixed-mode stencils: vn, w, the

@@ -97,6 +97,11 @@ void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t 
 template <class T>
 void launch_column(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
                    cudaStream_t s);
+// Diagnostics: per-cell ps and T850 (either may be null), per-block partial
+// column masses [diag_partials(nc)] and a non-finite flag (set to 1, never cleared).
+int diag_partials(int nc);
+void launch_diagnostics(const Engine& en, const double* area, const StateView& st, double* ps, double* t850,
+                        double* partial, int* bad, cudaStream_t s);
 // One-time kernel attributes (dynamic shared memory above 48 KB).
 cudaError_t init_column_kernels();
 

@@ -432,3 +432,32 @@ def test_substeps_stable_at_the_configured_courant_number():
                 st = d.step(st)
         out.append(float(np.nanmax(np.abs(st["vn"]))) if np.isfinite(st["vn"]).all() else np.inf)
     assert out[0] < 40.0 and out[1] > 100.0, out
+
+
+# ---------------------------------------------------------------- diagnostics
+def test_diagnostics_on_closed_forms():
+    """Isothermal reference atmosphere (T = T0 up to the discrete balance):
+    T850 = T0 and ps = p00 (exner = 1 at the ground); the balanced jet has
+    exner = 1 at the ground by construction, so ps = p00 there too."""
+    from oracle.diagnostics import surface_pressure, temperature_850, total_mass, area_rms
+    g = make_grid(2)
+    z = make_vct(30)
+    d = Dycore(g, z, DycoreParams())
+    th, ex = d.reference_state()
+    nc = g.n_cells
+    T = np.tile(th * ex, (nc, 1))
+    assert np.max(np.abs(T - d.p.ref_T0)) < 1.0  # discrete balance on 4 km top layers
+    t850 = temperature_850(d, np.tile(ex, (nc, 1)), np.tile(th, (nc, 1)))
+    assert np.max(np.abs(t850 - d.p.ref_T0)) < 0.05
+    ps = surface_pressure(d, np.tile(ex, (nc, 1)), np.tile(th, (nc, 1)))
+    assert np.max(np.abs(ps - d.p.p00)) < 0.5
+    st = jw_type_state(g, z, amp=0.0)
+    ps = surface_pressure(d, st["exner"], st["theta_v"])
+    assert np.max(np.abs(ps - d.p.p00)) < 2.0
+    # the jet's polar air is cold: T850 decreases poleward
+    lat = np.arcsin(g.cell_xyz[:, 2])
+    t = temperature_850(d, st["exner"], st["theta_v"])
+    assert t[np.argmin(np.abs(lat))] > t[np.argmax(np.abs(lat))] + 20
+    # mass of a uniform density column set: rho * 4 pi a^2 * top
+    assert abs(total_mass(d, np.ones((nc, 30))) / (4 * np.pi * A * A * 30000.0) - 1) < 1e-12
+    assert area_rms(d, np.full(nc, 3.0)) == pytest.approx(3.0, rel=1e-14)
