@@ -233,6 +233,7 @@ def measure(P, G, z, st0, prec, args, dev, world):
     nsteps_prof = min(args.steps, 3)
     out["prof"] = D.profile(t, nsteps_prof)
     out["nsteps_prof"] = nsteps_prof
+    out["launch_config"] = D.launch_config()
     D.close()
     return out, t
 
@@ -289,7 +290,8 @@ def run_ours(args):
               "rms_ps_pa": rms(m["ps"] - f64["ps"]), "rms_t850_k": rms(m["t850"] - f64["t850"]),
               "compared_after_steps": args.warmup + args.steps,
               "reference": "FP64 GPU dycore (equal to the FP64 oracle to 1e-9 after 10 steps, GPU parity tests)",
-              "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"]}
+              "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"],
+              "autotuned_launch_config": m["launch_config"]}
 
     # end to end through the C-ABI with host arrays (copies inside the timed region)
     stream = torch.cuda.current_stream(dev)
@@ -322,6 +324,7 @@ def run_ours(args):
                      "note": "FP64 algorithmic flops per launch / event-timed launch duration; peak = nominal "
                              "FP64 rate from unit counts and clock (1.2 TFLOP/s measured by a DFMA probe)"},
         "kernels": kernel_table(prof, nsp),
+        "autotuned_launch_config": f64["launch_config"],
         "mixed": mx,
         "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": sb,
                 "d2h_bytes_per_step": sb},

@@ -122,6 +122,7 @@ typedef struct icon_dycore_params {
   /* execution */
   int32_t precision;       /* ICON_PREC_FP64 or ICON_PREC_MIXED */
   int32_t use_graph;       /* logical: replay a captured CUDA graph per step */
+  int32_t autotune;        /* logical: pick per-kernel launch shapes at create time */
   int32_t synchronous;     /* logical: return only after the GPU work ended */
   void* stream;            /* cudaStream_t to enqueue on; NULL = default stream */
 } icon_dycore_params_t;
@@ -130,7 +131,7 @@ typedef struct icon_dycore_params {
  * weights 0.25/0.75, rho/theta weights 0.6/0.4, exner_exfac 1/3,
  * divdamp_fac 0.0025, divflux_fac 0.07, Rayleigh off (coeff 0, height 20 km), Smagorinsky
  * 0.015, k4 = k4w = 1/288, hdiff_temp 1, ref_T0 250, FP64, graph on,
- * synchronous, default stream.  NULL-safe (does nothing). */
+ * autotune on, synchronous, default stream.  NULL-safe (does nothing). */
 void icon_dycore_params_default(icon_dycore_params_t* p);
 
 /*
@@ -234,6 +235,14 @@ int icon_dycore_profile(icon_dycore_t* dycore, const icon_state_t* state, int32_
  * div_t, w_p, rho_p, theta_p.  Errors: ICON_ERR_ARG (unknown name, bytes too
  * small), ICON_ERR_CUDA. */
 int icon_dycore_debug_field(icon_dycore_t* dycore, const char* name, void* dst, int64_t bytes);
+
+/* The launch shapes in use (picked by the autotuner when params.autotune is
+ * set): writes a NUL-terminated text "name=threads,...;column_chunk=K" of at
+ * most len bytes into buf (HOST).  The autotuner runs one step of every
+ * kernel on a temporary uniform state at create time with each candidate
+ * (128, 256, 512 threads per CTA for the stencils; 4 or 8 levels per
+ * shared-memory chunk for the column solve) and keeps the fastest per kernel. */
+int icon_dycore_launch_config(const icon_dycore_t* dycore, char* buf, int32_t len);
 
 /* Block until all work enqueued by this dycore has finished. */
 int icon_dycore_synchronize(icon_dycore_t* dycore);

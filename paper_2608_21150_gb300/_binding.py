@@ -58,7 +58,7 @@ class icon_dycore_params_t(ctypes.Structure):
                 ("damp_height", ctypes.c_double), ("hdiff_smag_fac", ctypes.c_double),
                 ("hdiff_k4", ctypes.c_double), ("hdiff_w_k4", ctypes.c_double),
                 ("hdiff_temp", ctypes.c_int32), ("ref_T0", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("synchronous", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
@@ -82,6 +82,7 @@ _sig = {
     "icon_velocity_tendencies": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
     "icon_dycore_reference_state": (ctypes.c_int, [ctypes.c_void_p, _f64p, _f64p]),
     "icon_dycore_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "icon_dycore_launch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]),
     "icon_dycore_debug_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_int64]),
     "icon_dycore_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
@@ -260,6 +261,11 @@ class Dycore:
     def debug_field(self, name, out):
         """Copy the internal work field `name` into the device tensor `out`."""
         _check(icon_dycore_debug_field(self.handle, name.encode(), _ptr(out), out.numel() * out.element_size()))
+
+    def launch_config(self):
+        buf = ctypes.create_string_buffer(1024)
+        _check(icon_dycore_launch_config(self.handle, buf, 1024))
+        return buf.value.decode()
 
     def synchronize(self):
         _check(icon_dycore_synchronize(self.handle))

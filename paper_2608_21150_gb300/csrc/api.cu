@@ -131,6 +131,7 @@ void icon_dycore_params_default(icon_dycore_params_t* p) {
   p->ref_T0 = 250.0;
   p->precision = ICON_PREC_FP64;
   p->use_graph = 1;
+  p->autotune = 1;
   p->synchronous = 1;
   p->stream = nullptr;
 }
@@ -204,6 +205,84 @@ static void free_graphs(icon_dycore* d) {
     e = GraphEntry{};
   }
 }
+
+}  // extern "C"
+
+namespace {
+
+void enqueue_op(icon_dycore* d, int op, const StateView& st, cudaStream_t s);
+
+// Autotuner: time every kernel of one step on a temporary uniform state with
+// each candidate launch shape (CUDA events around every launch) and keep the
+// fastest shape per kernel.
+int autotune(icon_dycore* d) {
+  const HostGrid& h = d->grid->host;
+  const size_t nlev = d->nlev, ef = h.ne * nlev, cf = h.nc * nlev, ch = h.nc * (nlev + 1);
+  StateView st{};
+  double** fields[6] = {&st.vn, &st.w, &st.rho, &st.exner, &st.theta_v, &st.exner_pr};
+  const size_t sizes[6] = {ef, ch, cf, cf, cf, cf};
+  const double values[6] = {10.0, 0.0, 1.0, 0.9, 300.0, 0.0};
+  int rc = ICON_OK;
+  for (int i = 0; i < 6 && rc == ICON_OK; ++i) {
+    cudaError_t e = cudaMalloc(fields[i], sizes[i] * sizeof(double));
+    if (e != cudaSuccess) {
+      *fields[i] = nullptr;
+      rc = fail(ICON_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    } else {
+      launch_fill(*fields[i], sizes[i], values[i], d->stream);
+    }
+  }
+  const int cand[3] = {128, 256, 512};
+  std::vector<std::vector<double>> t(kNumStencils, std::vector<double>(3, 0.0));
+  double col_t[2] = {0.0, 0.0};  // chunk 8 (with 256 threads), chunk 4
+  auto run = [&](int ci, int kc, bool stencils) -> int {
+    for (int k = 0; k < kNumStencils; ++k) d->en.threads[k] = cand[ci];
+    d->en.col_kc = kc;
+    Prof prof;
+    g_prof = &prof;
+    enqueue_op(d, 0, st, d->stream);
+    g_prof = nullptr;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    for (const auto& r : prof.recs) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, r.e0, r.e1));
+      const std::string nm = r.name;
+      if (nm.compare(0, 9, "sn_column") == 0) {
+        col_t[kc == 8 ? 0 : 1] += ms;
+        continue;
+      }
+      if (!stencils) continue;
+      for (int k = 0; k < kNumStencils; ++k) {
+        const std::string base = kStencilNames[k];
+        if (nm == base || nm == base + "_f32") t[k][ci] += ms;
+      }
+    }
+    return ICON_OK;
+  };
+  if (rc == ICON_OK) rc = run(1, 8, false);  // warm-up (module load, first-touch)
+  if (rc == ICON_OK) col_t[0] = 0.0;
+  for (int ci = 0; ci < 3 && rc == ICON_OK; ++ci) rc = run(ci, 8, true);
+  if (rc == ICON_OK) {
+    col_t[0] /= 3.0;
+    rc = run(1, 4, false);
+  }
+  for (double* p : {st.vn, st.w, st.rho, st.exner, st.theta_v, st.exner_pr})
+    if (p) cudaFree(p);
+  if (rc != ICON_OK) return rc;
+  for (int k = 0; k < kNumStencils; ++k) {
+    int best = 1;
+    for (int ci = 0; ci < 3; ++ci)
+      if (t[k][ci] > 0.0 && t[k][ci] < t[k][best]) best = ci;
+    d->en.threads[k] = cand[best];
+  }
+  d->en.col_kc = col_t[1] < col_t[0] ? 4 : 8;
+  return ICON_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
                        const icon_dycore_params_t* p, icon_dycore_t** out) {
@@ -461,6 +540,17 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     delete d;
     return fail(ICON_ERR_CUDA, m);
   }
+  for (int k = 0; k < kNumStencils; ++k) en.threads[k] = 256;
+  en.col_kc = 8;
+  if (p->autotune) {
+    int rc = autotune(d);
+    if (rc != ICON_OK) {
+      A.release();
+      cudaStreamDestroy(d->cap_stream);
+      delete d;
+      return rc;
+    }
+  }
   *out = d;
   return ICON_OK;
 }
@@ -482,6 +572,8 @@ int icon_dycore_destroy(icon_dycore_t* d) {
   delete d;
   return ICON_OK;
 }
+
+}  // extern "C"
 
 namespace {
 
@@ -526,6 +618,10 @@ void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
       launch_diffusion<double>(d->en, d->en.c64, st, s);
     }
   }
+}
+
+void enqueue_op(icon_dycore* d, int op, const StateView& st, cudaStream_t s) {
+  enqueue(d, op == 0 ? Op::kStep : op == 1 ? Op::kSubstep : Op::kDiffusion, st, s);
 }
 
 bool same(const StateView& a, const StateView& b) {
@@ -628,6 +724,8 @@ int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
 
 }  // namespace
 
+extern "C" {
+
 int icon_dycore_step(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op::kStep, "icon_dycore_step"); }
 int icon_nh_solve(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op::kSubstep, "icon_nh_solve"); }
 int icon_nh_diff(icon_dycore_t* d, const icon_state_t* s) { return run(d, s, Op::kDiffusion, "icon_nh_diff"); }
@@ -636,7 +734,7 @@ int icon_velocity_tendencies(icon_dycore_t* d, const double* vn, const double* w
   if (!d || !vn || !w || !ddt_vn || !ddt_w) return fail(ICON_ERR_ARG, "icon_velocity_tendencies: NULL argument");
   if (d->en.precision != ICON_PREC_FP64)
     return fail(ICON_ERR_UNSUPPORTED, "icon_velocity_tendencies: stage output is provided in FP64 mode only");
-  launch_velocity_tendencies<double>(d->en.c64, vn, w, ddt_vn, ddt_w, nullptr, nullptr, d->stream);
+  launch_velocity_tendencies<double>(d->en.c64, vn, w, ddt_vn, ddt_w, nullptr, nullptr, d->stream, d->en.threads);
   CUDA_TRY(cudaGetLastError());
   if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
   return ICON_OK;
@@ -764,6 +862,18 @@ int icon_dycore_diagnostics(icon_dycore_t* d, const icon_state_t* s, double* ps,
 int icon_grid_cell_areas(const icon_grid_t* g, double* area) {
   if (!g || !area) return fail(ICON_ERR_ARG, "icon_grid_cell_areas: NULL argument");
   std::memcpy(area, g->host.cell_area.data(), g->host.nc * sizeof(double));
+  return ICON_OK;
+}
+
+int icon_dycore_launch_config(const icon_dycore_t* d, char* buf, int32_t len) {
+  if (!d || !buf || len < 1) return fail(ICON_ERR_ARG, "icon_dycore_launch_config: NULL or invalid argument");
+  std::string s;
+  for (int k = 0; k < kNumStencils; ++k) {
+    s += kStencilNames[k];
+    s += "=" + std::to_string(d->en.threads[k]) + ",";
+  }
+  s += "column_threads=64;column_chunk=" + std::to_string(d->en.col_kc);
+  std::snprintf(buf, (size_t)len, "%s", s.c_str());
   return ICON_OK;
 }
 

@@ -75,6 +75,10 @@ struct Engine {
   const double* rho_ref64 = nullptr;  // [nlev] rho offset of the mixed-mode perturbation
   Ctx<double> c64{};
   Ctx<float> c32{};
+  // launch configuration picked by the autotuner: threads per CTA of each
+  // stencil kernel (by kernel id) and the level-chunk depth of the column solve
+  int threads[32] = {};
+  int col_kc = 8;
 };
 
 // Rows A1-A4 on (vn, w) in compute type T: writes ddt_vn [ne*nlev] and ddt_w
@@ -82,7 +86,12 @@ struct Engine {
 // of divd (A8).
 template <class T>
 void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
-                                T* divd2, cudaStream_t s);
+                                T* divd2, cudaStream_t s, const int* threads = nullptr);
+// Stencil kernel ids (index of Engine::threads) and their base names.
+constexpr int kNumStencils = 14;
+extern const char* const kStencilNames[kNumStencils];
+// Fill n doubles with v (the autotuner's temporary state).
+void launch_fill(double* p, size_t n, double v, cudaStream_t s);
 // Rows A5-A9: one predictor + corrector substep, state updated in place.
 template <class T>
 void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s);

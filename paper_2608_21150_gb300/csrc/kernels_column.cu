@@ -34,16 +34,21 @@ namespace icon {
 namespace {
 
 constexpr int kCW = 64;          // columns (threads) per CTA
-constexpr int kKC = 8;           // levels per chunk
+constexpr int kKC = 8;           // default levels per chunk (the autotuner may pick 4)
 constexpr int kLD = kCW + 1;     // padded tile row for column-gathered tiles
-constexpr int kTile = (kKC + 1) * kLD;
 // forward tiles: w, rho, exner, theta, ddt_w0, div_m, div_t, ddt_w1, rho_p, theta_p, zb
 constexpr int kTilesFwd = 11;
-// backward: 8 level-major scratch chunks [kKC][kCW] + 4 output tiles
-constexpr int kBackIn = kKC * kCW;
-constexpr size_t kSmemFwd = (size_t)kTilesFwd * kTile;
-constexpr size_t kSmemBack = (size_t)8 * kBackIn + 4 * (size_t)kTile;
-constexpr size_t kSmem = (kSmemFwd > kSmemBack ? kSmemFwd : kSmemBack) * sizeof(double);
+// backward: 8 level-major scratch chunks [KC][kCW] + 4 output tiles
+template <int KC>
+__host__ __device__ constexpr int tile_doubles() { return (KC + 1) * kLD; }
+template <int KC>
+constexpr size_t smem_bytes() {
+  return (kTilesFwd * (size_t)tile_doubles<KC>() > 8 * (size_t)KC * kCW + 4 * (size_t)tile_doubles<KC>()
+              ? kTilesFwd * (size_t)tile_doubles<KC>()
+              : 8 * (size_t)KC * kCW + 4 * (size_t)tile_doubles<KC>()) *
+         sizeof(double);
+}
+constexpr size_t kSmem = smem_bytes<kKC>();
 
 enum { CZB = 0, CR = 1, CRN = 2, CWX = 3, CB = 4, CGAM = 5, WG = 6, WG2 = 7 };
 
@@ -115,8 +120,10 @@ struct ColArgs {
 // kOwnZb: the corrector form computes zb and the equation-of-state term itself
 // (as the predictor does) instead of reading the predictor's; used by the
 // allocation-free entry point below.
-template <class T, bool kOwnZb = false>
+template <class T, bool kOwnZb = false, int KC = kKC>
 __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
+  constexpr int kTile = tile_doubles<KC>();
+  constexpr int kBackIn = KC * kCW;
   extern __shared__ double sm[];
   __shared__ int rows_c[kCW];
   const int t = threadIdx.x;
@@ -155,10 +162,10 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
   double ric_k = 0.0, tic_k = 0.0, tpic_k = 0.0, rt_k = 0.0;
   double zb_km1 = 0.0, al_km1 = 0.0, ps_km1 = 0.0, pr_km1 = 0.0, cp_km1 = 0.0, rp_km1 = 0.0;
 
-  for (int k0 = 0; k0 < nlev; k0 += kKC) {
-    const int nkc = min(kKC, nlev - k0);       // levels solved in this chunk
-    const int nkf = min(kKC + 1, nlev - k0);   // full levels loaded (one lookahead)
-    const int nkh = min(kKC + 1, nlevp - k0);  // half levels loaded
+  for (int k0 = 0; k0 < nlev; k0 += KC) {
+    const int nkc = min(KC, nlev - k0);       // levels solved in this chunk
+    const int nkf = min(KC + 1, nlev - k0);   // full levels loaded (one lookahead)
+    const int nkh = min(KC + 1, nlevp - k0);  // half levels loaded
     __syncthreads();
     tile_rows(T_w, a.w, nlevp, rows_c, k0, nkh);
     tile_rows(T_rho, a.rho, nlev, rows_c, k0, nkf);
@@ -268,8 +275,8 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
   // other threads of the CTA through the asynchronous copies below
   __threadfence_block();
   double w_und_k1 = 0.0, wd_k1 = 0.0, ric_k1 = 0.0, al_k1 = 0.0;
-  for (int kend = nlev; kend > 0; kend -= kKC) {
-    const int k0 = max(0, kend - kKC), nk = kend - k0;
+  for (int kend = nlev; kend > 0; kend -= KC) {
+    const int k0 = max(0, kend - KC), nk = kend - k0;
     __syncthreads();
     tile_levels(B_cp, kCW, cp_s, nc, c0, k0, nk);
     tile_levels(B_rp, kCW, rp_s, nc, c0, k0, nk);
@@ -335,9 +342,18 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
 }  // namespace
 
 cudaError_t init_column_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(sn_column_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sn_column_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  cudaError_t e = cudaFuncSetAttribute(sn_column_tiled<double, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<8>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<8>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sn_column_tiled<double, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<4>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<4>());
+  return e;
 }
 
 template <class T>
@@ -379,7 +395,12 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
   const unsigned blocks = (unsigned)((en.g64.nc + kCW - 1) / kCW);
   const char* name = mixed ? (corrector ? "sn_column_corr_mx" : "sn_column_pred_mx")
                            : (corrector ? "sn_column_corr" : "sn_column_pred");
-  ICON_LAUNCH_SMEM(name, blocks, kCW, kSmem, s, sn_column_tiled<T>, en.g64.nc, en.v, en.sc, corrector, a);
+  if (en.col_kc == 4)
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4>), en.g64.nc, en.v, en.sc,
+                     corrector, a);
+  else
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8>), en.g64.nc, en.v, en.sc,
+                     corrector, a);
 }
 
 template void launch_column<double>(const Engine&, int, const StateView&, const double*, const double*, cudaStream_t);

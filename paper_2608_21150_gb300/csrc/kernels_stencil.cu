@@ -40,6 +40,10 @@ inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + th
 
 constexpr int kThreads = 256;
 
+// threads per CTA of stencil kernel `id` from the autotuner's table (0: default)
+inline int tuned(const int* threads, int id) { return threads && threads[id] > 0 ? threads[id] : kThreads; }
+#define TH(id) tuned(threads, id)
+
 template <class T>
 const char* kname(const char* f64, const char* f32) {
   return kMixed<T> ? f32 : f64;
@@ -528,30 +532,31 @@ __global__ void diff_cell_update(GridT<T> g, VertT<T> v, ScalT<T> sc, const doub
 // -------------------------------------------------------------------------
 template <class T>
 void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
-                                T* divd2, cudaStream_t s) {
+                                T* divd2, cudaStream_t s, const int* threads) {
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
   const int nlev = v.nlev, nlevp = nlev + 1;
-  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_for((long long)g.ne * nlev, kThreads), kThreads, s,
+  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_for((long long)g.ne * nlev, TH(0)), TH(0), s,
               va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e);
   const long long n2 = (long long)g.nc * nlev + (long long)g.nv * nlevp;
-  ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, kThreads), kThreads, s, va_cell_vert<T>, g,
+  ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, TH(1)), TH(1), s, va_cell_vert<T>, g,
               v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v);
-  ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, kThreads), kThreads,
+  ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, TH(2)), TH(2),
               s, va_edge_tend<T>, g, v, vn, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e);
-  ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_for((long long)g.nc * nlevp, kThreads), kThreads, s,
+  ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_for((long long)g.nc * nlevp, TH(3)), TH(3), s,
               va_cell_w<T>, g, v, w, wk.gw_e, ddt_w);
 }
 
 template <class T>
 void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
+  const int* threads = en.threads;
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
   const Mirrors& m = en.m;
   const int nlev = v.nlev;
-  const unsigned bc = blocks_for((long long)g.nc * nlev, kThreads), be = blocks_for((long long)g.ne * nlev, kThreads);
+  const long long nce = (long long)g.nc * nlev, nee = (long long)g.ne * nlev;
   // stencil views of the state: the FP64 state itself, or the FP32 mirrors
   const T *s_vn, *s_w, *s_rho, *s_th, *s_wp;
   if constexpr (kMixed<T>) {
@@ -560,31 +565,32 @@ void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cuda
     s_vn = st.vn, s_w = st.w, s_rho = st.rho, s_th = st.theta_v, s_wp = en.wk.w_p;
   }
   // ---------------- predictor ----------------
-  launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s);
-  ICON_LAUNCH(kname<T>("sn_cell_grad", "sn_cell_grad_f32"), bc, kThreads, s, sn_cell_grad<T>, g, v, s_rho, s_th,
+  launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s, threads);
+  ICON_LAUNCH(kname<T>("sn_cell_grad", "sn_cell_grad_f32"), blocks_for(nce, TH(4)), TH(4), s, sn_cell_grad<T>, g, v, s_rho, s_th,
               wk.grad4);
-  ICON_LAUNCH(kname<T>("sn_edge_pred", "sn_edge_pred_f32"), be, kThreads, s, sn_edge_pred<T>, g, v, x.s, s_vn, wk.vt,
+  ICON_LAUNCH(kname<T>("sn_edge_pred", "sn_edge_pred_f32"), blocks_for(nee, TH(5)), TH(5), s, sn_edge_pred<T>, g, v, x.s, s_vn, wk.vt,
               wk.ddt_vn0, s_rho, s_th, st.exner, st.exner_pr, en.g64.inv_d, en.sc.exfac, wk.grad4, wk.rho_e,
               wk.theta_e, wk.hpg, wk.vn_p);
-  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), bc, kThreads, s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
+  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_for(nce, TH(6)), TH(6), s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
               st.exner, st.exner_pr);
-  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), bc, kThreads, s, sn_cell_fluxdiv<T>, g, v, x.s,
+  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_for(nce, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
               wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
   launch_column<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, s);
   // ---------------- corrector ----------------
-  launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s);
-  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), be, kThreads, s, sn_edge_corr<T>, g, v, x.s, st.vn,
+  launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s, threads);
+  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_for(nee, TH(8)), TH(8), s, sn_edge_corr<T>, g, v, x.s, st.vn,
               wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn);
   const T* vn_new = kMixed<T> ? (const T*)m.vn : (const T*)st.vn;
-  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), bc, kThreads, s, sn_cell_div<T>, g, v, vn_new, wk.divd,
+  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_for(nce, TH(6)), TH(6), s, sn_cell_div<T>, g, v, vn_new, wk.divd,
               nullptr, nullptr);
-  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), bc, kThreads, s, sn_cell_fluxdiv<T>, g, v, x.s,
+  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_for(nce, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
               vn_new, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
   launch_column<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, s);
 }
 
 template <class T>
 void launch_diffusion(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
+  const int* threads = en.threads;
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
@@ -597,19 +603,35 @@ void launch_diffusion(const Engine& en, const Ctx<T>& x, const StateView& st, cu
     s_vn = st.vn, s_w = st.w, s_th = st.theta_v;
   }
   const long long n1 = (long long)g.nc * nlev + (long long)g.nv * nlev;
-  ICON_LAUNCH(kname<T>("diff_div_curl_uv", "diff_div_curl_uv_f32"), blocks_for(n1, kThreads), kThreads, s,
+  ICON_LAUNCH(kname<T>("diff_div_curl_uv", "diff_div_curl_uv_f32"), blocks_for(n1, TH(9)), TH(9), s,
               diff_div_curl_uv<T>, g, v, s_vn, wk.div_vn, wk.zeta, wk.uv3);
-  ICON_LAUNCH(kname<T>("diff_edge_smag", "diff_edge_smag_f32"), blocks_for((long long)g.ne * nlev, kThreads),
-              kThreads, s, diff_edge_smag<T>, g, v, wk.div_vn, wk.zeta, wk.uv3, wk.nu, wk.lap_vn);
+  ICON_LAUNCH(kname<T>("diff_edge_smag", "diff_edge_smag_f32"), blocks_for((long long)g.ne * nlev, TH(10)),
+              TH(10), s, diff_edge_smag<T>, g, v, wk.div_vn, wk.zeta, wk.uv3, wk.nu, wk.lap_vn);
   const long long n3 = (long long)g.nc * nlevp + (long long)g.nv * nlev;
-  ICON_LAUNCH(kname<T>("diff_second", "diff_second_f32"), blocks_for(n3, kThreads), kThreads, s, diff_second<T>, g, v,
+  ICON_LAUNCH(kname<T>("diff_second", "diff_second_f32"), blocks_for(n3, TH(11)), TH(11), s, diff_second<T>, g, v,
               x.s, wk.lap_vn, wk.nu, s_w, s_th, wk.div_l, wk.lap_w, wk.dtheta, wk.curl_l);
-  ICON_LAUNCH(kname<T>("diff_edge_update", "diff_edge_update_f32"), blocks_for((long long)g.ne * nlev, kThreads),
-              kThreads, s, diff_edge_update<T>, g, v, x.s, st.vn, wk.nu, wk.lap_vn, wk.div_l, wk.curl_l, m.vn);
-  ICON_LAUNCH(kname<T>("diff_cell_update", "diff_cell_update_f32"), blocks_for((long long)g.nc * nlevp, kThreads),
-              kThreads, s, diff_cell_update<T>, g, v, x.s, en.v.theta_ref, en.v.exner_ref, en.sc.rd_o_cvd, st,
+  ICON_LAUNCH(kname<T>("diff_edge_update", "diff_edge_update_f32"), blocks_for((long long)g.ne * nlev, TH(12)),
+              TH(12), s, diff_edge_update<T>, g, v, x.s, st.vn, wk.nu, wk.lap_vn, wk.div_l, wk.curl_l, m.vn);
+  ICON_LAUNCH(kname<T>("diff_cell_update", "diff_cell_update_f32"), blocks_for((long long)g.nc * nlevp, TH(13)),
+              TH(13), s, diff_cell_update<T>, g, v, x.s, en.v.theta_ref, en.v.exner_ref, en.sc.rd_o_cvd, st,
               wk.lap_w, wk.dtheta, m);
 }
+
+namespace {
+__global__ void fill_kernel(double* p, size_t n, double v) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+}  // namespace
+
+void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
+  fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+}
+
+const char* const kStencilNames[kNumStencils] = {
+    "va_edge_pre", "va_cell_vert", "va_edge_tend", "va_cell_w", "sn_cell_grad", "sn_edge_pred", "sn_cell_div",
+    "sn_cell_fluxdiv", "sn_edge_corr", "diff_div_curl_uv", "diff_edge_smag", "diff_second", "diff_edge_update",
+    "diff_cell_update"};
 
 void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t s) {
   const int nlev = en.v.nlev;
@@ -619,7 +641,7 @@ void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t 
 }
 
 template void launch_velocity_tendencies<double>(const Ctx<double>&, const double*, const double*, double*, double*,
-                                                 const double*, double*, cudaStream_t);
+                                                 const double*, double*, cudaStream_t, const int*);
 template void launch_substep<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
 template void launch_substep<float>(const Engine&, const Ctx<float>&, const StateView&, cudaStream_t);
 template void launch_diffusion<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
