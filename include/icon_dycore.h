@@ -300,6 +300,38 @@ int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const double* z_ifc,
                               const double* div_m, const double* div_t, double* w_new,
                               double* rho_new, double* exner_new, double* theta_new);
 
+/*
+ * Learned corrector network (spec extension of the paper's step; the
+ * paper has no learned component): a 3-layer MLP
+ *   y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3,  GELU(u) = u Phi(u) (erf form),
+ * BF16 weights and activations with FP32 accumulation on the tensor cores,
+ * FP32 master weights, trained on the GPU with Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on the mean squared error.  Parameters are exchanged as one FP32
+ * host array: W1 [n_hidden][n_in], b1 [n_hidden], W2 [n_hidden][n_hidden],
+ * b2, W3 [n_out][n_hidden], b3 (each W row-major, output index first).
+ * Inputs x [batch][n_in] and outputs/targets [batch][n_out] are FP32 DEVICE
+ * arrays; batch <= max_batch, and a multiple of 64 for backward/training.
+ */
+typedef struct icon_mlp icon_mlp_t;  /* opaque */
+int icon_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, icon_mlp_t** out);
+int icon_mlp_destroy(icon_mlp_t* mlp);          /* NULL-safe */
+int64_t icon_mlp_param_count(const icon_mlp_t* mlp);
+/* Set all parameters (resets the Adam moments); get parameters / the last gradients. */
+int icon_mlp_set_params(icon_mlp_t* mlp, const float* params, int64_t n);
+int icon_mlp_get_params(const icon_mlp_t* mlp, float* params, int64_t n);
+int icon_mlp_get_grads(const icon_mlp_t* mlp, float* grads, int64_t n);
+/* Forward pass (keeps the activations of the batch for a following backward). */
+int icon_mlp_forward(icon_mlp_t* mlp, const float* x, int32_t batch, float* y, void* stream);
+/* Gradients of all parameters for dL/dy [batch][n_out] (DEVICE), after a forward
+ * on the same batch; read them with icon_mlp_get_grads. */
+int icon_mlp_backward(icon_mlp_t* mlp, const float* dy, int32_t batch, void* stream);
+/* One Adam update with the last gradients. */
+int icon_mlp_adam(icon_mlp_t* mlp, float lr, float beta1, float beta2, float eps, void* stream);
+/* forward + MSE loss against target + backward + Adam; *loss (HOST, may be NULL)
+ * receives the batch's mean squared error before the update. */
+int icon_mlp_train_step(icon_mlp_t* mlp, const float* x, const float* target, int32_t batch, float lr,
+                        double* loss, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* icon_last_error(void);
 

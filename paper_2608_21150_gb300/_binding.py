@@ -91,6 +91,18 @@ _sig = {
     "icon_dycore_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_void_p,
                                                ctypes.c_void_p, _f64p]),
     "icon_grid_cell_areas": (ctypes.c_int, [ctypes.c_void_p, _f64p]),
+    "icon_mlp_create": (ctypes.c_int, [ctypes.c_int32] * 4 + [ctypes.POINTER(ctypes.c_void_p)]),
+    "icon_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "icon_mlp_param_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "icon_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "icon_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "icon_mlp_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "icon_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "icon_mlp_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "icon_mlp_adam": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_float] * 4 + [ctypes.c_void_p]),
+    "icon_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "icon_column_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _f64p,
                                                  ctypes.POINTER(icon_dycore_params_t)] + [ctypes.c_void_p] * 14),
 }
@@ -148,6 +160,57 @@ def column_solve_noalloc(z_ifc, params, w, rho, exner, theta_v, ddt_w0, div_m, d
                                      _ptr(w), _ptr(rho), _ptr(exner), _ptr(theta_v), opt[0], opt[1],
                                      _ptr(ddt_w0), opt[2], _ptr(div_m), _ptr(div_t), _ptr(w_new),
                                      _ptr(rho_new), _ptr(exner_new), _ptr(theta_new)))
+
+
+class MLP:
+    """Owns an icon_mlp_t (the learned corrector's network); tensors are float32 on the device."""
+
+    def __init__(self, n_in, n_hidden, n_out, max_batch):
+        h = ctypes.c_void_p()
+        _check(icon_mlp_create(n_in, n_hidden, n_out, max_batch, ctypes.byref(h)))
+        self.handle = h
+        self.n_in, self.n_hidden, self.n_out, self.max_batch = n_in, n_hidden, n_out, max_batch
+        self.n_params = icon_mlp_param_count(h)
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(icon_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+
+    def _get(self, fn):
+        p = np.empty(self.n_params, dtype=np.float32)
+        _check(fn(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+        return p
+
+    def params(self):
+        return self._get(icon_mlp_get_params)
+
+    def grads(self):
+        return self._get(icon_mlp_get_grads)
+
+    def forward(self, x, y, stream=None):
+        _check(icon_mlp_forward(self.handle, _ptr(x), x.shape[0], _ptr(y), stream))
+
+    def backward(self, dy, stream=None):
+        _check(icon_mlp_backward(self.handle, _ptr(dy), dy.shape[0], stream))
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(icon_mlp_adam(self.handle, lr, beta1, beta2, eps, stream))
+
+    def train_step(self, x, target, lr, stream=None):
+        loss = ctypes.c_double()
+        _check(icon_mlp_train_step(self.handle, _ptr(x), _ptr(target), x.shape[0], lr, ctypes.byref(loss), stream))
+        return loss.value
+
+    def close(self):
+        if self.handle:
+            icon_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Grid:

@@ -1,0 +1,32 @@
+// MLP building blocks of the learned corrector (internal).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace icon {
+
+// C[M x N] = A[M x K] B[N x K]^T (bf16 operands, K-major, K a multiple of 32,
+// lda/ldb multiples of 8); epilogue: + bias, then either fp32 out or GELU ->
+// bf16 out (and the fp32 pre-activation into zpre if given).
+void mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+              const float* bias, bool gelu_act, float* out_f32, __nv_bfloat16* out_bf16, float* zpre, int ldc,
+              cudaStream_t s);
+void mlp_transpose(int rows, int cols, const __nv_bfloat16* in, int ldi, __nv_bfloat16* out, int ldo,
+                   cudaStream_t s);
+void mlp_gelu_backward(int rows, int cols, const float* dh, int ldd, const float* z, int ldz, float* dz32,
+                       __nv_bfloat16* dz16, int ldo, cudaStream_t s);
+void mlp_to_bf16(int rows, int cols, const float* in, int ldi, __nv_bfloat16* out, int ldo, cudaStream_t s);
+void mlp_bias_grad(int rows, int cols, const float* dz, int ldd, float* db, cudaStream_t s);
+void mlp_adam(int n_out, int n_in, float* w, const float* g, float* m, float* v, float lr, float b1, float b2,
+              float eps, float c1, float c2, __nv_bfloat16* wt16, int ldt, __nv_bfloat16* w16, int ldw,
+              cudaStream_t s);
+void mlp_adam_bias(int n, float* b, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                   float c1, float c2, cudaStream_t s);
+// loss = sum (y - t)^2 / (B n_out) (per-row partial sums into rowloss[B]);
+// dy = 2 (y - t) / (B n_out)
+void mlp_mse(int B, int n_out, const float* y, int ldy, const float* t, int ldt, float* dy, int lddy, double* rowloss,
+             cudaStream_t s);
+
+}  // namespace icon

@@ -1,0 +1,293 @@
+// C-ABI of the learned corrector's MLP (row A13): parameters, forward,
+// backward, Adam and a fused training step, all on the GPU.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mlp.h"
+
+using namespace icon;
+
+struct icon_mlp {
+  int dims[4];   // n_in, n_hidden, n_hidden, n_out
+  int lds[4];    // padded to multiples of 64
+  int max_batch, ld_b;
+  int adam_t = 0;
+  std::vector<void*> allocs;
+  float *w[3], *b[3], *gw[3], *gb[3], *mw[3], *vw[3], *mb[3], *vb[3];
+  __nv_bfloat16 *wt16[3], *w16[3];
+  // activations (max_batch rows)
+  __nv_bfloat16 *x16, *h16[2];
+  float *z[2], *y;
+  // backward work
+  float *dy, *dh, *dz32;
+  __nv_bfloat16 *dz16, *dzT, *hT;
+  double* rowloss;
+};
+
+namespace {
+
+int pad64(int x) { return (x + 63) / 64 * 64; }
+
+int fail_m(int code, const std::string& m) { return report_error(code, m); }
+
+template <class T>
+T* alloc(icon_mlp* m, size_t n, cudaError_t& st) {
+  if (st != cudaSuccess) return nullptr;
+  void* p = nullptr;
+  st = cudaMalloc(&p, n * sizeof(T));
+  if (st == cudaSuccess) {
+    st = cudaMemset(p, 0, n * sizeof(T));
+    m->allocs.push_back(p);
+  }
+  return static_cast<T*>(p);
+}
+
+int layer_in(const icon_mlp* m, int l) { return m->dims[l]; }
+int layer_out(const icon_mlp* m, int l) { return m->dims[l + 1]; }
+
+int64_t param_count(const icon_mlp* m) {
+  int64_t n = 0;
+  for (int l = 0; l < 3; ++l) n += (int64_t)layer_out(m, l) * layer_in(m, l) + layer_out(m, l);
+  return n;
+}
+
+void forward(icon_mlp* m, const float* x, int B, cudaStream_t s) {
+  mlp_to_bf16(B, m->dims[0], x, m->dims[0], m->x16, m->lds[0], s);
+  const __nv_bfloat16* in = m->x16;
+  for (int l = 0; l < 2; ++l) {
+    mlp_gemm(B, layer_out(m, l), m->lds[l], in, m->lds[l], m->wt16[l], m->lds[l], m->b[l], true, nullptr, m->h16[l],
+             m->z[l], m->lds[l + 1], s);
+    in = m->h16[l];
+  }
+  mlp_gemm(B, layer_out(m, 2), m->lds[2], in, m->lds[2], m->wt16[2], m->lds[2], m->b[2], false, m->y, nullptr, nullptr,
+           m->lds[3], s);
+}
+
+// gradients of all parameters for dL/dy in m->dy (fp32 [B][lds[3]]), after forward()
+void backward(icon_mlp* m, int B, cudaStream_t s) {
+  // layer 3 (no activation): dz = dy
+  const int n3 = layer_out(m, 2);
+  mlp_to_bf16(B, n3, m->dy, m->lds[3], m->dz16, m->lds[3], s);
+  mlp_bias_grad(B, n3, m->dy, m->lds[3], m->gb[2], s);
+  const float* dz32 = m->dy;
+  int ldz = m->lds[3];
+  for (int l = 2; l >= 0; --l) {
+    const int nin = layer_in(m, l), nout = layer_out(m, l);
+    const __nv_bfloat16* h = l == 0 ? m->x16 : m->h16[l - 1];
+    // dW^T [nout][nin] = dZ^T H
+    mlp_transpose(B, nout, m->dz16, ldz, m->dzT, m->ld_b, s);
+    mlp_transpose(B, nin, h, m->lds[l], m->hT, m->ld_b, s);
+    mlp_gemm(nout, nin, m->ld_b, m->dzT, m->ld_b, m->hT, m->ld_b, nullptr, false, m->gw[l], nullptr, nullptr, nin, s);
+    if (l == 0) break;
+    // dH [B][nin] = dZ W (W stored [nin][lds[l+1]])
+    mlp_gemm(B, nin, m->lds[l + 1], m->dz16, ldz, m->w16[l], m->lds[l + 1], nullptr, false, m->dh, nullptr, nullptr,
+             m->lds[l], s);
+    // dZ of the previous layer through its GELU
+    mlp_gelu_backward(B, nin, m->dh, m->lds[l], m->z[l - 1], m->lds[l], m->dz32, m->dz16, m->lds[l], s);
+    mlp_bias_grad(B, nin, m->dz32, m->lds[l], m->gb[l - 1], s);
+    dz32 = m->dz32;
+    ldz = m->lds[l];
+  }
+  (void)dz32;
+}
+
+void adam(icon_mlp* m, float lr, float b1, float b2, float eps, cudaStream_t s) {
+  m->adam_t += 1;
+  const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+  for (int l = 0; l < 3; ++l) {
+    const int nin = layer_in(m, l), nout = layer_out(m, l);
+    mlp_adam(nout, nin, m->w[l], m->gw[l], m->mw[l], m->vw[l], lr, b1, b2, eps, c1, c2, m->wt16[l], m->lds[l],
+             m->w16[l], m->lds[l + 1], s);
+    mlp_adam_bias(nout, m->b[l], m->gb[l], m->mb[l], m->vb[l], lr, b1, b2, eps, c1, c2, s);
+  }
+}
+
+__global__ void refresh_bf16(int n_out, int n_in, const float* __restrict__ w, __nv_bfloat16* __restrict__ wt16,
+                             int ldt, __nv_bfloat16* __restrict__ w16, int ldw) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)n_out * n_in) return;
+  const int o = (int)(i / n_in), k = (int)(i - (size_t)o * n_in);
+  wt16[(size_t)o * ldt + k] = __float2bfloat16(w[i]);
+  w16[(size_t)k * ldw + o] = __float2bfloat16(w[i]);
+}
+
+int check_batch(const icon_mlp* m, int B, const char* fn) {
+  if (B < 1 || B > m->max_batch) return fail_m(ICON_ERR_ARG, std::string(fn) + ": batch out of range");
+  return ICON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int icon_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, icon_mlp_t** out) {
+  if (!out || n_in < 1 || n_hidden < 1 || n_out < 1 || max_batch < 64 || max_batch % 64)
+    return fail_m(ICON_ERR_ARG, "icon_mlp_create: bad sizes (max_batch must be a positive multiple of 64)");
+  *out = nullptr;
+  icon_mlp* m = new (std::nothrow) icon_mlp();
+  if (!m) return fail_m(ICON_ERR_ARG, "icon_mlp_create: out of host memory");
+  m->dims[0] = n_in;
+  m->dims[1] = m->dims[2] = n_hidden;
+  m->dims[3] = n_out;
+  for (int i = 0; i < 4; ++i) m->lds[i] = pad64(m->dims[i]);
+  m->max_batch = max_batch;
+  m->ld_b = max_batch;
+  cudaError_t st = cudaSuccess;
+  for (int l = 0; l < 3; ++l) {
+    const size_t nw = (size_t)layer_out(m, l) * layer_in(m, l), nb = layer_out(m, l);
+    m->w[l] = alloc<float>(m, nw, st);
+    m->gw[l] = alloc<float>(m, nw, st);
+    m->mw[l] = alloc<float>(m, nw, st);
+    m->vw[l] = alloc<float>(m, nw, st);
+    m->b[l] = alloc<float>(m, nb, st);
+    m->gb[l] = alloc<float>(m, nb, st);
+    m->mb[l] = alloc<float>(m, nb, st);
+    m->vb[l] = alloc<float>(m, nb, st);
+    m->wt16[l] = alloc<__nv_bfloat16>(m, (size_t)layer_out(m, l) * m->lds[l], st);
+    m->w16[l] = alloc<__nv_bfloat16>(m, (size_t)layer_in(m, l) * m->lds[l + 1], st);
+  }
+  const size_t B = max_batch;
+  int ldmax = 0;
+  for (int i = 0; i < 4; ++i) ldmax = m->lds[i] > ldmax ? m->lds[i] : ldmax;
+  m->x16 = alloc<__nv_bfloat16>(m, B * m->lds[0], st);
+  for (int l = 0; l < 2; ++l) {
+    m->h16[l] = alloc<__nv_bfloat16>(m, B * m->lds[l + 1], st);
+    m->z[l] = alloc<float>(m, B * m->lds[l + 1], st);
+  }
+  m->y = alloc<float>(m, B * m->lds[3], st);
+  m->dy = alloc<float>(m, B * m->lds[3], st);
+  m->dh = alloc<float>(m, B * ldmax, st);
+  m->dz32 = alloc<float>(m, B * ldmax, st);
+  m->dz16 = alloc<__nv_bfloat16>(m, B * ldmax, st);
+  m->dzT = alloc<__nv_bfloat16>(m, (size_t)ldmax * B, st);
+  m->hT = alloc<__nv_bfloat16>(m, (size_t)ldmax * B, st);
+  m->rowloss = alloc<double>(m, B, st);
+  if (st != cudaSuccess) {
+    for (void* p : m->allocs) cudaFree(p);
+    delete m;
+    return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_create: ") + cudaGetErrorString(st));
+  }
+  *out = m;
+  return ICON_OK;
+}
+
+int icon_mlp_destroy(icon_mlp_t* m) {
+  if (!m) return ICON_OK;
+  cudaDeviceSynchronize();
+  for (void* p : m->allocs) cudaFree(p);
+  delete m;
+  return ICON_OK;
+}
+
+int64_t icon_mlp_param_count(const icon_mlp_t* m) { return m ? param_count(m) : -1; }
+
+int icon_mlp_set_params(icon_mlp_t* m, const float* host, int64_t n) {
+  if (!m || !host || n != param_count(m)) return fail_m(ICON_ERR_ARG, "icon_mlp_set_params: NULL or wrong count");
+  int64_t off = 0;
+  for (int l = 0; l < 3; ++l) {
+    const size_t nw = (size_t)layer_out(m, l) * layer_in(m, l), nb = layer_out(m, l);
+    if (cudaMemcpy(m->w[l], host + off, nw * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->b[l], host + off + nw, nb * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail_m(ICON_ERR_CUDA, "icon_mlp_set_params: copy failed");
+    off += nw + nb;
+    cudaMemset(m->mw[l], 0, nw * 4);
+    cudaMemset(m->vw[l], 0, nw * 4);
+    cudaMemset(m->mb[l], 0, nb * 4);
+    cudaMemset(m->vb[l], 0, nb * 4);
+    refresh_bf16<<<(unsigned)((nw + 255) / 256), 256>>>(layer_out(m, l), layer_in(m, l), m->w[l], m->wt16[l],
+                                                         m->lds[l], m->w16[l], m->lds[l + 1]);
+  }
+  m->adam_t = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_set_params: ") + cudaGetErrorString(e));
+  return ICON_OK;
+}
+
+static int copy_out(const icon_mlp* m, float* host, int64_t n, bool grads, const char* fn) {
+  if (!m || !host || n != param_count(m)) return fail_m(ICON_ERR_ARG, std::string(fn) + ": NULL or wrong count");
+  cudaDeviceSynchronize();
+  int64_t off = 0;
+  for (int l = 0; l < 3; ++l) {
+    const size_t nw = (size_t)layer_out(m, l) * layer_in(m, l), nb = layer_out(m, l);
+    if (cudaMemcpy(host + off, grads ? m->gw[l] : m->w[l], nw * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host + off + nw, grads ? m->gb[l] : m->b[l], nb * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail_m(ICON_ERR_CUDA, std::string(fn) + ": copy failed");
+    off += nw + nb;
+  }
+  return ICON_OK;
+}
+
+int icon_mlp_get_params(const icon_mlp_t* m, float* host, int64_t n) {
+  return copy_out(m, host, n, false, "icon_mlp_get_params");
+}
+int icon_mlp_get_grads(const icon_mlp_t* m, float* host, int64_t n) {
+  return copy_out(m, host, n, true, "icon_mlp_get_grads");
+}
+
+int icon_mlp_forward(icon_mlp_t* m, const float* x, int32_t batch, float* y, void* stream) {
+  if (!m || !x || !y) return fail_m(ICON_ERR_ARG, "icon_mlp_forward: NULL argument");
+  int rc = check_batch(m, batch, "icon_mlp_forward");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  forward(m, x, batch, s);
+  if (cudaMemcpy2DAsync(y, m->dims[3] * 4, m->y, m->lds[3] * 4, m->dims[3] * 4, batch, cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+    return fail_m(ICON_ERR_CUDA, "icon_mlp_forward: copy failed");
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_forward: ") + cudaGetErrorString(e));
+  return ICON_OK;
+}
+
+int icon_mlp_backward(icon_mlp_t* m, const float* dy, int32_t batch, void* stream) {
+  if (!m || !dy) return fail_m(ICON_ERR_ARG, "icon_mlp_backward: NULL argument");
+  int rc = check_batch(m, batch, "icon_mlp_backward");
+  if (rc) return rc;
+  if (batch % 64) return fail_m(ICON_ERR_ARG, "icon_mlp_backward: batch must be a multiple of 64");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpy2DAsync(m->dy, m->lds[3] * 4, dy, m->dims[3] * 4, m->dims[3] * 4, batch, cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+    return fail_m(ICON_ERR_CUDA, "icon_mlp_backward: copy failed");
+  backward(m, batch, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_backward: ") + cudaGetErrorString(e));
+  return ICON_OK;
+}
+
+int icon_mlp_adam(icon_mlp_t* m, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!m) return fail_m(ICON_ERR_ARG, "icon_mlp_adam: NULL argument");
+  adam(m, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
+  return ICON_OK;
+}
+
+int icon_mlp_train_step(icon_mlp_t* m, const float* x, const float* target, int32_t batch, float lr, double* loss,
+                        void* stream) {
+  if (!m || !x || !target) return fail_m(ICON_ERR_ARG, "icon_mlp_train_step: NULL argument");
+  int rc = check_batch(m, batch, "icon_mlp_train_step");
+  if (rc) return rc;
+  if (batch % 64) return fail_m(ICON_ERR_ARG, "icon_mlp_train_step: batch must be a multiple of 64");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  forward(m, x, batch, s);
+  mlp_mse(batch, m->dims[3], m->y, m->lds[3], target, m->dims[3], m->dy, m->lds[3], m->rowloss, s);
+  backward(m, batch, s);
+  adam(m, lr, 0.9f, 0.999f, 1e-8f, s);
+  if (loss) {
+    std::vector<double> rl(batch);
+    if (cudaMemcpyAsync(rl.data(), m->rowloss, batch * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return fail_m(ICON_ERR_CUDA, "icon_mlp_train_step: copy failed");
+    cudaStreamSynchronize(s);
+    double t = 0.0;
+    for (double v : rl) t += v;
+    *loss = t / ((double)batch * m->dims[3]);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_train_step: ") + cudaGetErrorString(e));
+  return ICON_OK;
+}
+
+}  // extern "C"

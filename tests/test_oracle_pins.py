@@ -461,3 +461,50 @@ def test_diagnostics_on_closed_forms():
     # mass of a uniform density column set: rho * 4 pi a^2 * top
     assert abs(total_mass(d, np.ones((nc, 30))) / (4 * np.pi * A * A * 30000.0) - 1) < 1e-12
     assert area_rms(d, np.full(nc, 3.0)) == pytest.approx(3.0, rel=1e-14)
+
+
+# ---------------------------------------------------------------- learned corrector MLP
+def test_mlp_gradients_match_central_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(11)
+    I, H, O, B = 5, 7, 3, 4
+    n = H * I + H + H * H + H + O * H + O
+    p = rng.standard_normal(n) * 0.5
+    x = rng.standard_normal((B, I))
+    t = rng.standard_normal((B, O))
+
+    def loss(q):
+        y, _ = mlp.forward(q, x, I, H, O)
+        return mlp.mse(y, t)[0]
+
+    y, cache = mlp.forward(p, x, I, H, O)
+    _, dy = mlp.mse(y, t)
+    g = mlp.backward(p, cache, dy, I, H, O)
+    h = 1e-6
+    fd = np.array([(loss(p + h * e) - loss(p - h * e)) / (2 * h) for e in np.eye(n)])
+    assert np.max(np.abs(fd - g)) < 1e-8 * max(1.0, np.max(np.abs(g)))
+    # a planted mistake (GELU' dropped) is caught
+    saved = mlp.gelu_grad
+    try:
+        mlp.gelu_grad = lambda u: np.ones_like(u)
+        g_bad = mlp.backward(p, cache, dy, I, H, O)
+    finally:
+        mlp.gelu_grad = saved
+    assert np.max(np.abs(fd - g_bad)) > 1e-3
+
+
+def test_gelu_closed_forms():
+    from oracle import mlp
+    assert mlp.gelu(0.0) == 0.0
+    assert abs(mlp.gelu(1.0) - 0.8413447460685429) < 1e-15      # Phi(1)
+    assert abs(mlp.gelu(-1.0) + 0.15865525393145707) < 1e-15    # -Phi(-1)
+    u = np.linspace(-4, 4, 81)
+    assert np.max(np.abs(mlp.gelu_grad(u) - (mlp.gelu(u + 1e-6) - mlp.gelu(u - 1e-6)) / 2e-6)) < 1e-8
+
+
+def test_adam_first_step_moves_by_lr_times_sign():
+    from oracle import mlp
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    q, m, v = mlp.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    assert np.allclose(q, p - 0.01 * np.sign(g), rtol=0, atol=1e-7)
