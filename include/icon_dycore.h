@@ -301,8 +301,8 @@ int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const double* z_ifc,
                               double* rho_new, double* exner_new, double* theta_new);
 
 /*
- * Learned corrector network (spec extension of the paper's step; the
- * paper has no learned component): a 3-layer MLP
+ * Learned corrector network (an extension beyond the paper's step, which has
+ * no learned component): a 3-layer MLP
  *   y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3,  GELU(u) = u Phi(u) (erf form),
  * BF16 weights and activations with FP32 accumulation on the tensor cores,
  * FP32 master weights, trained on the GPU with Adam (beta1 0.9, beta2 0.999,
@@ -331,6 +331,60 @@ int icon_mlp_adam(icon_mlp_t* mlp, float lr, float beta1, float beta2, float eps
  * receives the batch's mean squared error before the update. */
 int icon_mlp_train_step(icon_mlp_t* mlp, const float* x, const float* target, int32_t batch, float lr,
                         double* loss, void* stream);
+
+/* Normalisation statistics used by icon_dycore_step_learned (HOST FP32 arrays,
+ * copied): the network's input is (x - x_mean) / x_std per feature, and an
+ * output y stands for the physical increment y y_std + y_mean. */
+int icon_mlp_set_normalization(icon_mlp_t* mlp, const float* x_mean, const float* x_std, const float* y_mean,
+                               const float* y_std);
+
+/*
+ * Learned corrector on the state after a step with fewer acoustic substeps
+ * (Sec. 3.2's substep loop with ndyn_substeps reduced).  Column features of a
+ * cell, [nc][5 nlev] (FP32, DEVICE): w at full levels (mean of the two half
+ * levels), exner - exner_ref, theta_v - theta_ref, and the cell velocity's east
+ * and north components (Perot reconstruction from vn).  Edge features
+ * [ne][11 nlev]: the column features of e2c[0] and of e2c[1], then vn.
+ * Column outputs [nc][3 nlev - 1]: increments of w at the interior half levels
+ * 1..nlev-1, of exner and of theta_v; edge outputs [ne][nlev]: increments of vn.
+ * rho and exner_pr are never changed, so the mass budget of the reduced step is
+ * kept exactly.
+ */
+/* Raw (unnormalised) features of a DEVICE state into DEVICE arrays. */
+int icon_corrector_features(icon_dycore_t* d, const icon_state_t* s, float* col_x, float* edge_x);
+/* Raw training targets plain - reduced into DEVICE arrays col_y [nc][3 nlev - 1]
+ * and edge_y [ne][nlev]; both states on the device. */
+int icon_corrector_targets(icon_dycore_t* d, const icon_state_t* reduced, const icon_state_t* plain, float* col_y,
+                           float* edge_y);
+/*
+ * One learned step of a DEVICE state, in place: keep the input, run the step of
+ * `reduced` (fewer substeps), apply col_net (5 nlev -> 3 nlev - 1) and edge_net
+ * (11 nlev -> nlev) over all cells and edges in chunks of their max_batch,
+ * then check.  The check is the larger of the two networks' RMS normalised
+ * increments; if it is not finite (a non-finite increment, corrected value or
+ * rho is found) or above max_norm, the input is restored and the step of
+ * `plain` taken instead (*used_fallback = 1).  *norm (may be NULL) receives the
+ * check value.  Both dycores share the grid and nlev; both networks must carry
+ * normalisation statistics.  Synchronises the stream once (the check's 16-byte
+ * read).  Errors: ICON_ERR_ARG for NULL, host state, mismatched dycores or
+ * network shapes; ICON_ERR_CUDA.
+ */
+int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_mlp_t* col_net,
+                             icon_mlp_t* edge_net, const icon_state_t* s, double max_norm, int32_t* used_fallback,
+                             double* norm);
+
+/*
+ * Per-kernel profile of any sequence of calls on this thread: between
+ * icon_profile_begin and icon_profile_end every kernel launch of the library is
+ * bracketed by a CUDA event pair on its stream (steps run without their graph
+ * meanwhile, so each kernel is seen).  icon_profile_end synchronises the device
+ * and fills, for up to max_kernels distinct kernels, names[64 j] (NUL-
+ * terminated), launches[j] and summed milliseconds ms[j]; *n_kernels = count.
+ * Errors: ICON_ERR_ARG when no profile (or already one) is open on this thread,
+ * for NULL outputs or too small max_kernels.
+ */
+int icon_profile_begin(void);
+int icon_profile_end(int32_t max_kernels, char* names, int32_t* launches, double* ms, int32_t* n_kernels);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* icon_last_error(void);

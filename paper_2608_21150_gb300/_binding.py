@@ -103,6 +103,15 @@ _sig = {
     "icon_mlp_adam": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_float] * 4 + [ctypes.c_void_p]),
     "icon_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "icon_mlp_set_normalization": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_float)] * 4),
+    "icon_corrector_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_void_p,
+                                               ctypes.c_void_p]),
+    "icon_corrector_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t),
+                                              ctypes.POINTER(icon_state_t), ctypes.c_void_p, ctypes.c_void_p]),
+    "icon_dycore_step_learned": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(icon_state_t), ctypes.c_double,
+                                                _i32p, _f64p]),
+    "icon_profile_begin": (ctypes.c_int, []),
+    "icon_profile_end": (ctypes.c_int, [ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
     "icon_column_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _f64p,
                                                  ctypes.POINTER(icon_dycore_params_t)] + [ctypes.c_void_p] * 14),
 }
@@ -196,6 +205,16 @@ class MLP:
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         _check(icon_mlp_adam(self.handle, lr, beta1, beta2, eps, stream))
 
+    def set_normalization(self, x_mean, x_std, y_mean, y_std):
+        """Input/output statistics (host arrays) used by the learned step."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (x_mean, x_std, y_mean, y_std)]
+        if arrs[0].size != self.n_in or arrs[1].size != self.n_in or arrs[2].size != self.n_out \
+                or arrs[3].size != self.n_out:
+            raise ValueError("normalisation sizes must be n_in, n_in, n_out, n_out")
+        _check(icon_mlp_set_normalization(self.handle, *[a.ctypes.data_as(fp) for a in arrs]))
+        self.normalization = tuple(arrs)
+
     def train_step(self, x, target, lr, stream=None):
         loss = ctypes.c_double()
         _check(icon_mlp_train_step(self.handle, _ptr(x), _ptr(target), x.shape[0], lr, ctypes.byref(loss), stream))
@@ -211,6 +230,39 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+class Profile:
+    """Context manager around icon_profile_begin/end: per-kernel launches and
+    milliseconds of every library kernel launched on this thread inside the
+    block, as ``{name: (launches, ms)}`` in ``.kernels`` on exit."""
+
+    def __enter__(self):
+        _check(icon_profile_begin())
+        self.kernels = {}
+        return self
+
+    def __exit__(self, *exc):
+        cap = 128
+        names = ctypes.create_string_buffer(64 * cap)
+        launches = (ctypes.c_int32 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int32()
+        _check(icon_profile_end(cap, names, launches, ms, ctypes.byref(n)))
+        self.kernels = {names.raw[64 * j:64 * j + 64].split(b"\0")[0].decode(): (launches[j], ms[j])
+                        for j in range(n.value)}
+        return False
+
+
+def step_learned(reduced, plain, col_net, edge_net, st, max_norm):
+    """icon_dycore_step_learned: one step of `reduced` plus the learned increments,
+    or the step of `plain` when the check fails.  Returns (used_fallback, norm)."""
+    s = Dycore._state(st)
+    fb = ctypes.c_int32()
+    nrm = ctypes.c_double()
+    _check(icon_dycore_step_learned(reduced.handle, plain.handle, col_net.handle, edge_net.handle, ctypes.byref(s),
+                                    max_norm, ctypes.byref(fb), ctypes.byref(nrm)))
+    return bool(fb.value), nrm.value
 
 
 class Grid:
@@ -291,6 +343,17 @@ class Dycore:
 
     def velocity_tendencies(self, vn, w, ddt_vn, ddt_w):
         _check(icon_velocity_tendencies(self.handle, _ptr(vn), _ptr(w), _ptr(ddt_vn), _ptr(ddt_w)))
+
+    def corrector_features(self, st, col_x, edge_x):
+        """Raw corrector features of a device state: col_x [n_cells][5 nlev],
+        edge_x [n_edges][11 nlev] (float32 device tensors)."""
+        s = self._state(st)
+        _check(icon_corrector_features(self.handle, ctypes.byref(s), _ptr(col_x), _ptr(edge_x)))
+
+    def corrector_targets(self, reduced, plain, col_y, edge_y):
+        """Raw corrector targets plain - reduced: col_y [n_cells][3 nlev - 1], edge_y [n_edges][nlev]."""
+        a, b = self._state(reduced), self._state(plain)
+        _check(icon_corrector_targets(self.handle, ctypes.byref(a), ctypes.byref(b), _ptr(col_y), _ptr(edge_y)))
 
     def reference_state(self):
         th = np.empty(self.nlev)

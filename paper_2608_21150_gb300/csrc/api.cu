@@ -3,6 +3,7 @@
 // reference without copies, device arrays accepted directly).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "mlp.h"
 
 using namespace icon;
 
@@ -98,6 +100,11 @@ struct icon_dycore {
   unsigned long long use_counter = 0;
   StateView staging{};                 // device copy used when the caller passes host arrays
   bool have_staging = false;
+  // learned corrector (allocated on first use): saved input state, features, norm partials
+  StateView saved{};
+  float *colx = nullptr, *edgex = nullptr;
+  double *partial = nullptr, *status = nullptr;
+  int partial_cap = 0;
 };
 
 extern "C" {
@@ -182,6 +189,7 @@ int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
   v.uv_w = A.upload(h.uv_w);
   v.mean_area = h.mean_area;
   v.cell_area = A.upload(h.cell_area);
+  v.uv_c = A.upload(std::vector<float>(h.uv_c.begin(), h.uv_c.end()));
   if (A.status != cudaSuccess) {
     std::string m = std::string("icon_grid_create: ") + cudaGetErrorString(A.status);
     A.release();
@@ -567,6 +575,18 @@ int icon_dycore_destroy(icon_dycore_t* d) {
     cudaFree(d->staging.theta_v);
     cudaFree(d->staging.exner_pr);
   }
+  if (d->colx) {
+    cudaFree(d->saved.vn);
+    cudaFree(d->saved.w);
+    cudaFree(d->saved.rho);
+    cudaFree(d->saved.exner);
+    cudaFree(d->saved.theta_v);
+    cudaFree(d->saved.exner_pr);
+    cudaFree(d->colx);
+    cudaFree(d->edgex);
+    cudaFree(d->status);
+  }
+  if (d->partial) cudaFree(d->partial);
   d->arena.release();
   if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
   delete d;
@@ -622,6 +642,37 @@ void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
 
 void enqueue_op(icon_dycore* d, int op, const StateView& st, cudaStream_t s) {
   enqueue(d, op == 0 ? Op::kStep : op == 1 ? Op::kSubstep : Op::kDiffusion, st, s);
+}
+
+thread_local Prof* g_user_prof = nullptr;
+
+// per-kernel launch counts and summed event times of a finished profile
+int summarise(const Prof& prof, int max_kernels, char* names, int32_t* launches, double* ms, int32_t* n_kernels,
+              const char* fn) {
+  std::vector<std::string> nm;
+  std::vector<int> cnt;
+  std::vector<double> tot;
+  for (const auto& r : prof.recs) {
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.e0, r.e1));
+    size_t j = 0;
+    while (j < nm.size() && nm[j] != r.name) ++j;
+    if (j == nm.size()) {
+      nm.push_back(r.name);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[j] += 1;
+    tot[j] += t;
+  }
+  if ((int)nm.size() > max_kernels) return fail(ICON_ERR_ARG, std::string(fn) + ": max_kernels too small");
+  for (size_t j = 0; j < nm.size(); ++j) {
+    std::snprintf(names + 64 * j, 64, "%s", nm[j].c_str());
+    launches[j] = cnt[j];
+    ms[j] = tot[j];
+  }
+  *n_kernels = (int32_t)nm.size();
+  return ICON_OK;
 }
 
 bool same(const StateView& a, const StateView& b) {
@@ -698,7 +749,7 @@ int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
     CUDA_TRY(cudaMemcpyAsync(g.exner_pr, s->exner_pr, cf * 8, cudaMemcpyHostToDevice, stream));
     st = g;
   }
-  if (op == Op::kStep && d->params.use_graph) {
+  if (op == Op::kStep && d->params.use_graph && !g_prof) {
     cudaGraphExec_t exec = nullptr;
     int rc = step_graph(d, st, &exec);
     if (rc != ICON_OK) return rc;
@@ -761,30 +812,31 @@ int icon_dycore_profile(icon_dycore_t* d, const icon_state_t* s, int32_t nsteps,
   g_prof = nullptr;
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(d->stream));
-  std::vector<std::string> nm;
-  std::vector<int> cnt;
-  std::vector<double> tot;
-  for (const auto& r : prof.recs) {
-    float t = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&t, r.e0, r.e1));
-    size_t j = 0;
-    while (j < nm.size() && nm[j] != r.name) ++j;
-    if (j == nm.size()) {
-      nm.push_back(r.name);
-      cnt.push_back(0);
-      tot.push_back(0.0);
-    }
-    cnt[j] += 1;
-    tot[j] += t;
-  }
-  if ((int)nm.size() > max_kernels) return fail(ICON_ERR_ARG, "icon_dycore_profile: max_kernels too small");
-  for (size_t j = 0; j < nm.size(); ++j) {
-    std::snprintf(names + 64 * j, 64, "%s", nm[j].c_str());
-    launches[j] = cnt[j];
-    ms[j] = tot[j];
-  }
-  *n_kernels = (int32_t)nm.size();
+  return summarise(prof, max_kernels, names, launches, ms, n_kernels, "icon_dycore_profile");
+}
+
+int icon_profile_begin(void) {
+  if (g_user_prof) return fail(ICON_ERR_ARG, "icon_profile_begin: a profile is already open on this thread");
+  g_user_prof = new (std::nothrow) Prof();
+  if (!g_user_prof) return fail(ICON_ERR_CUDA, "icon_profile_begin: out of memory");
+  g_prof = g_user_prof;
   return ICON_OK;
+}
+
+int icon_profile_end(int32_t max_kernels, char* names, int32_t* launches, double* ms, int32_t* n_kernels) {
+  if (!g_user_prof) return fail(ICON_ERR_ARG, "icon_profile_end: no profile open on this thread");
+  g_prof = nullptr;
+  Prof* prof = g_user_prof;
+  g_user_prof = nullptr;
+  int rc = ICON_OK;
+  if (!names || !launches || !ms || !n_kernels) rc = fail(ICON_ERR_ARG, "icon_profile_end: NULL argument");
+  if (rc == ICON_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = fail(ICON_ERR_CUDA, std::string("icon_profile_end: ") + cudaGetErrorString(e));
+  }
+  if (rc == ICON_OK) rc = summarise(*prof, max_kernels, names, launches, ms, n_kernels, "icon_profile_end");
+  delete prof;
+  return rc;
 }
 
 int icon_dycore_debug_field(icon_dycore_t* d, const char* name, void* dst, int64_t bytes) {
@@ -889,6 +941,185 @@ int icon_dycore_sizes(const icon_dycore_t* d, int32_t* nlev, int32_t* nc, int32_
   if (nc) *nc = d->grid->host.nc;
   if (ne) *ne = d->grid->host.ne;
   if (nv) *nv = d->grid->host.nv;
+  return ICON_OK;
+}
+
+
+}  // extern "C"
+
+namespace {
+
+bool on_device(const icon_state_t* s) {
+  const void* ptrs[6] = {s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr};
+  for (const void* p : ptrs) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+StateView view(const icon_state_t* s) { return StateView{s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr}; }
+
+int learned_buffers(icon_dycore* d, int partials) {
+  const HostGrid& h = d->grid->host;
+  const size_t nlev = d->nlev, ef = (size_t)h.ne * nlev, cf = (size_t)h.nc * nlev, ch = (size_t)h.nc * (nlev + 1);
+  if (!d->colx) {
+    StateView& g = d->saved;
+    CUDA_TRY(cudaMalloc(&g.vn, ef * 8));
+    CUDA_TRY(cudaMalloc(&g.w, ch * 8));
+    CUDA_TRY(cudaMalloc(&g.rho, cf * 8));
+    CUDA_TRY(cudaMalloc(&g.exner, cf * 8));
+    CUDA_TRY(cudaMalloc(&g.theta_v, cf * 8));
+    CUDA_TRY(cudaMalloc(&g.exner_pr, cf * 8));
+    CUDA_TRY(cudaMalloc(&d->colx, cf * 5 * 4));
+    CUDA_TRY(cudaMalloc(&d->edgex, ef * 11 * 4));
+    CUDA_TRY(cudaMalloc(&d->status, 2 * sizeof(double)));
+  }
+  if (partials > d->partial_cap) {
+    if (d->partial) cudaFree(d->partial);
+    d->partial = nullptr;
+    CUDA_TRY(cudaMalloc(&d->partial, (size_t)partials * sizeof(double)));
+    d->partial_cap = partials;
+  }
+  return ICON_OK;
+}
+
+int copy_state(const StateView& dst, const StateView& src, const icon_dycore* d, cudaStream_t s) {
+  const HostGrid& h = d->grid->host;
+  const size_t nlev = d->nlev, ef = (size_t)h.ne * nlev, cf = (size_t)h.nc * nlev, ch = (size_t)h.nc * (nlev + 1);
+  CUDA_TRY(cudaMemcpyAsync(dst.vn, src.vn, ef * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dst.w, src.w, ch * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dst.rho, src.rho, cf * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dst.exner, src.exner, cf * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dst.theta_v, src.theta_v, cf * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dst.exner_pr, src.exner_pr, cf * 8, cudaMemcpyDeviceToDevice, s));
+  return ICON_OK;
+}
+
+// checks that a network maps n_in -> n_out and carries normalisation statistics
+int check_net(const icon_mlp_t* net, int n_in, int n_out, const char* which) {
+  int ni = 0, no = 0, mb = 0;
+  mlp_dims(net, &ni, &no, &mb);
+  if (ni != n_in || no != n_out)
+    return fail(ICON_ERR_ARG, std::string("icon_dycore_step_learned: ") + which + " network must map " +
+                                  std::to_string(n_in) + " -> " + std::to_string(n_out));
+  const float *xm, *xs, *ym, *ys;
+  mlp_norm(net, &xm, &xs, &ym, &ys);
+  if (!xm) return fail(ICON_ERR_ARG, std::string("icon_dycore_step_learned: ") + which + " network has no normalisation");
+  return ICON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int icon_corrector_features(icon_dycore_t* d, const icon_state_t* s, float* col_x, float* edge_x) {
+  if (!d || !s || !col_x || !edge_x) return fail(ICON_ERR_ARG, "icon_corrector_features: NULL argument");
+  if (!on_device(s)) return fail(ICON_ERR_ARG, "icon_corrector_features: the state must be on the device");
+  const StateView st = view(s);
+  launch_col_features(d->en, st, col_x, d->stream);
+  launch_edge_features(d->en, col_x, st.vn, nullptr, nullptr, edge_x, d->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return ICON_OK;
+}
+
+int icon_corrector_targets(icon_dycore_t* d, const icon_state_t* reduced, const icon_state_t* plain, float* col_y,
+                           float* edge_y) {
+  if (!d || !reduced || !plain || !col_y || !edge_y) return fail(ICON_ERR_ARG, "icon_corrector_targets: NULL argument");
+  if (!on_device(reduced) || !on_device(plain))
+    return fail(ICON_ERR_ARG, "icon_corrector_targets: the states must be on the device");
+  launch_targets(d->en, view(reduced), view(plain), col_y, edge_y, d->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return ICON_OK;
+}
+
+int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_mlp_t* col_net, icon_mlp_t* edge_net,
+                             const icon_state_t* s, double max_norm, int32_t* used_fallback, double* norm) {
+  const char* fn = "icon_dycore_step_learned";
+  if (!reduced || !plain || !col_net || !edge_net || !s) return fail(ICON_ERR_ARG, std::string(fn) + ": NULL argument");
+  if (reduced->grid != plain->grid || reduced->nlev != plain->nlev)
+    return fail(ICON_ERR_ARG, std::string(fn) + ": the two dycores must share the grid and the levels");
+  if (!on_device(s)) return fail(ICON_ERR_ARG, std::string(fn) + ": the state must be on the device");
+  const HostGrid& h = reduced->grid->host;
+  const int nlev = reduced->nlev, nc = h.nc, ne = h.ne;
+  int rc = check_net(col_net, 5 * nlev, 3 * nlev - 1, "column");
+  if (rc != ICON_OK) return rc;
+  rc = check_net(edge_net, 11 * nlev, nlev, "edge");
+  if (rc != ICON_OK) return rc;
+  int ni, no, mbc, mbe;
+  mlp_dims(col_net, &ni, &no, &mbc);
+  mlp_dims(edge_net, &ni, &no, &mbe);
+  // partial-sum slots: one per 256 outputs of every chunk
+  int pc = 0, pe = 0;
+  for (int r0 = 0; r0 < nc; r0 += mbc) pc += apply_partials((size_t)std::min(mbc, nc - r0) * (3 * nlev - 1));
+  for (int r0 = 0; r0 < ne; r0 += mbe) pe += apply_partials((size_t)std::min(mbe, ne - r0) * nlev);
+  rc = learned_buffers(reduced, pc + pe);
+  if (rc != ICON_OK) return rc;
+  icon_dycore* d = reduced;
+  cudaStream_t stream = d->stream;
+  const StateView st = view(s);
+  // 1. keep the input state for the fallback; 2. the reduced step
+  rc = copy_state(d->saved, st, d, stream);
+  if (rc != ICON_OK) return rc;
+  const int sync = d->params.synchronous;
+  d->params.synchronous = 0;
+  rc = run(d, s, Op::kStep, fn);
+  d->params.synchronous = sync;
+  if (rc != ICON_OK) return rc;
+  // 3. features of the reduced state (edge features first: they read the raw column features)
+  const float *cxm, *cxs, *cym, *cys, *exm, *exs, *eym, *eys;
+  mlp_norm(col_net, &cxm, &cxs, &cym, &cys);
+  mlp_norm(edge_net, &exm, &exs, &eym, &eys);
+  launch_col_features(d->en, st, d->colx, stream);
+  launch_edge_features(d->en, d->colx, st.vn, exm, exs, d->edgex, stream);
+  launch_normalise((size_t)nc, 5 * nlev, d->colx, cxm, cxs, stream);
+  // 4. both networks over row chunks, increments applied as each chunk comes out
+  int off = 0;
+  for (int r0 = 0; r0 < nc; r0 += mbc) {
+    const int rows = std::min(mbc, nc - r0);
+    const float* y;
+    int ldy;
+    rc = mlp_forward_rows(col_net, d->colx + (size_t)r0 * 5 * nlev, rows, &y, &ldy, stream);
+    if (rc != ICON_OK) return rc;
+    launch_apply_col(d->en, r0, rows, y, ldy, cym, cys, st, d->partial + off, stream);
+    off += apply_partials((size_t)rows * (3 * nlev - 1));
+  }
+  for (int r0 = 0; r0 < ne; r0 += mbe) {
+    const int rows = std::min(mbe, ne - r0);
+    const float* y;
+    int ldy;
+    rc = mlp_forward_rows(edge_net, d->edgex + (size_t)r0 * 11 * nlev, rows, &y, &ldy, stream);
+    if (rc != ICON_OK) return rc;
+    launch_apply_edge(d->en, r0, rows, y, ldy, eym, eys, st.vn, d->partial + off, stream);
+    off += apply_partials((size_t)rows * nlev);
+  }
+  // 5. the check: RMS of the normalised increments of each network (NaN if anything is non-finite)
+  launch_reduce_status(d->partial, pc, pe, d->status, stream);
+  CUDA_TRY(cudaGetLastError());
+  double ss[2] = {0.0, 0.0};
+  CUDA_TRY(cudaMemcpyAsync(ss, d->status, sizeof(ss), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  const double rms = std::max(std::sqrt(ss[0] / ((double)nc * (3 * nlev - 1))), std::sqrt(ss[1] / ((double)ne * nlev)));
+  const double r = std::isnan(ss[0] + ss[1]) ? NAN : rms;
+  if (norm) *norm = r;
+  const bool reject = !(r <= max_norm);
+  if (used_fallback) *used_fallback = reject ? 1 : 0;
+  if (reject) {
+    // 6. fallback: the plain step from the saved input state
+    rc = copy_state(st, d->saved, d, stream);
+    if (rc != ICON_OK) return rc;
+    if (plain->stream != stream) CUDA_TRY(cudaStreamSynchronize(stream));
+    rc = run(plain, s, Op::kStep, fn);
+    if (rc != ICON_OK) return rc;
+    if (plain->stream != stream) CUDA_TRY(cudaStreamSynchronize(plain->stream));
+  }
+  if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(stream));
   return ICON_OK;
 }
 

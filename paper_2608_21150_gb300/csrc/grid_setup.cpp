@@ -233,6 +233,23 @@ std::string build_host_grid(const icon_grid_desc_t* d, HostGrid* g) {
     for (int j = 0; j < 3; ++j) g->e2c_w[3 * c + j] = q[j] / qs;
   }
 
+  // cell velocity (Perot reconstruction) as east/north components: u = sum_j ce_j vn_j,
+  // v = sum_j cn_j vn_j (corrector features)
+  g->uv_c.resize(6 * (size_t)nc);
+  for (int c = 0; c < nc; ++c) {
+    V3 C = at(g->cell_xyz, c);
+    V3 east = unit(cross(V3{0.0, 0.0, 1.0}, C));
+    V3 north = cross(C, east);
+    for (int j = 0; j < 3; ++j) {
+      int e = g->c2e[3 * c + j];
+      double sgn = g->e2c[2 * e] == c ? 1.0 : -1.0;
+      V3 dx = tangential(a * (at(g->edge_xyz, e) - C), C);
+      double coef = sgn * g->edge_length[e] / g->cell_area[c];
+      g->uv_c[6 * c + 2 * j] = coef * dot(dx, east);
+      g->uv_c[6 * c + 2 * j + 1] = coef * dot(dx, north);
+    }
+  }
+
   // edge coefficients
   g->inv_d.resize(ne);
   g->inv_l.resize(ne);

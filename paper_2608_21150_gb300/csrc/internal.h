@@ -46,6 +46,7 @@ struct GridT {
   const T* uv_w;    // [nv*6*3] vertex velocity weights (xyz per edge)
   T mean_area;
   const double* cell_area;  // [nc] (diagnostics)
+  const float* uv_c;        // [nc*6] east/north cell-velocity weights (corrector features)
 };
 using DevGrid = GridT<double>;
 
@@ -137,7 +138,7 @@ struct HostGrid {
   std::vector<int> c2e2c, e2c2v, e2c2e, e2v_t;
   std::vector<double> cell_area, edge_length, dual_length, dual_area;
   std::vector<double> div_c, lap_c, e2c_w, grad_c, inv_d, inv_l, vt_w, upw, nt, inv_dn;
-  std::vector<double> curl_v, c2v_w, uv_w, coriolis_z, edge_area;
+  std::vector<double> curl_v, c2v_w, uv_w, coriolis_z, edge_area, uv_c;
   double mean_area;
 };
 

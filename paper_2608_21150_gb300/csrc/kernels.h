@@ -111,6 +111,23 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
 int diag_partials(int nc);
 void launch_diagnostics(const Engine& en, const double* area, const StateView& st, double* ps, double* t850,
                         double* partial, int* bad, cudaStream_t s);
+// Learned corrector: raw column features [nc][5 nlev]; edge features [ne][11 nlev]
+// (normalised when mean/std are given); in-place normalisation; increments of
+// rows [row0, row0 + rows) applied to the state with per-block partial sums of
+// the squared normalised outputs (apply_partials(n) blocks for n outputs);
+// their two sums; training targets (plain - reduced).
+void launch_col_features(const Engine& en, const StateView& st, float* x, cudaStream_t s);
+void launch_edge_features(const Engine& en, const float* colx, const double* vn, const float* mean,
+                          const float* stdv, float* x, cudaStream_t s);
+void launch_normalise(size_t n, int nf, float* x, const float* mean, const float* stdv, cudaStream_t s);
+int apply_partials(size_t n);
+void launch_apply_col(const Engine& en, int row0, int rows, const float* y, int ldy, const float* mean,
+                      const float* stdv, const StateView& st, double* partial, cudaStream_t s);
+void launch_apply_edge(const Engine& en, int row0, int rows, const float* y, int ldy, const float* mean,
+                       const float* stdv, double* vn, double* partial, cudaStream_t s);
+void launch_reduce_status(const double* partial, int n0, int n1, double* out, cudaStream_t s);
+void launch_targets(const Engine& en, const StateView& reduced, const StateView& plain, float* col_y, float* edge_y,
+                    cudaStream_t s);
 // One-time kernel attributes (dynamic shared memory above 48 KB).
 cudaError_t init_column_kernels();
 

@@ -29,4 +29,12 @@ void mlp_adam_bias(int n, float* b, const float* g, float* m, float* v, float lr
 void mlp_mse(int B, int n_out, const float* y, int ldy, const float* t, int ldt, float* dy, int lddy, double* rowloss,
              cudaStream_t s);
 
+// Forward pass of rows [B][n_in] (normalised FP32, DEVICE) without synchronising;
+// B <= max_batch.  *y points at the network's own output rows [B][*ldy], valid
+// until its next call.
+int mlp_forward_rows(icon_mlp_t* m, const float* x, int B, const float** y, int* ldy, cudaStream_t s);
+int mlp_dims(const icon_mlp_t* m, int* n_in, int* n_out, int* max_batch);
+// normalisation statistics (DEVICE, FP32): x_mean/x_std [n_in], y_mean/y_std [n_out]; null if unset
+void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xs, const float** ym, const float** ys);
+
 }  // namespace icon

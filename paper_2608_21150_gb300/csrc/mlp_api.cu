@@ -28,6 +28,7 @@ struct icon_mlp {
   float *dy, *dh, *dz32;
   __nv_bfloat16 *dz16, *dzT, *hT;
   double* rowloss;
+  float *x_mean = nullptr, *x_std = nullptr, *y_mean = nullptr, *y_std = nullptr;
 };
 
 namespace {
@@ -124,7 +125,47 @@ int check_batch(const icon_mlp* m, int B, const char* fn) {
 
 }  // namespace
 
+namespace icon {
+int mlp_forward_rows(icon_mlp_t* m, const float* x, int B, const float** y, int* ldy, cudaStream_t s) {
+  if (B < 1 || B > m->max_batch) return fail_m(ICON_ERR_ARG, "corrector: batch out of range");
+  forward(m, x, B, s);
+  *y = m->y;
+  *ldy = m->lds[3];
+  return ICON_OK;
+}
+int mlp_dims(const icon_mlp_t* m, int* n_in, int* n_out, int* max_batch) {
+  *n_in = m->dims[0];
+  *n_out = m->dims[3];
+  *max_batch = m->max_batch;
+  return ICON_OK;
+}
+void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xs, const float** ym, const float** ys) {
+  *xm = m->x_mean;
+  *xs = m->x_std;
+  *ym = m->y_mean;
+  *ys = m->y_std;
+}
+}  // namespace icon
+
 extern "C" {
+
+int icon_mlp_set_normalization(icon_mlp_t* m, const float* x_mean, const float* x_std, const float* y_mean,
+                               const float* y_std) {
+  if (!m || !x_mean || !x_std || !y_mean || !y_std) return fail_m(ICON_ERR_ARG, "icon_mlp_set_normalization: NULL");
+  cudaError_t st = cudaSuccess;
+  if (!m->x_mean) {
+    m->x_mean = alloc<float>(m, m->dims[0], st);
+    m->x_std = alloc<float>(m, m->dims[0], st);
+    m->y_mean = alloc<float>(m, m->dims[3], st);
+    m->y_std = alloc<float>(m, m->dims[3], st);
+  }
+  if (st == cudaSuccess) st = cudaMemcpy(m->x_mean, x_mean, m->dims[0] * 4, cudaMemcpyHostToDevice);
+  if (st == cudaSuccess) st = cudaMemcpy(m->x_std, x_std, m->dims[0] * 4, cudaMemcpyHostToDevice);
+  if (st == cudaSuccess) st = cudaMemcpy(m->y_mean, y_mean, m->dims[3] * 4, cudaMemcpyHostToDevice);
+  if (st == cudaSuccess) st = cudaMemcpy(m->y_std, y_std, m->dims[3] * 4, cudaMemcpyHostToDevice);
+  if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_set_normalization: ") + cudaGetErrorString(st));
+  return ICON_OK;
+}
 
 int icon_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, icon_mlp_t** out) {
   if (!out || n_in < 1 || n_hidden < 1 || n_out < 1 || max_batch < 64 || max_batch % 64)
