@@ -11,7 +11,10 @@ A "step" is one full dycore time step.  The device-resident leg times K
 steps replayed as one CUDA graph each, with CUDA events on the stream the
 library launches on; the state (1.5 GB) is larger than L2, so no flush is
 needed.  The end-to-end leg calls the C-ABI with HOST arrays: the library
-copies the state in and out around every step.  N>1 (torchrun) runs N
+copies the state in and out around every step.  The mixed leg runs the same
+steps with FP32 stencils; the mixed + learned leg trains the corrector on the
+GPU (untimed, other seeds), then times steps with 4 substeps plus the learned
+increments, the check and any fallback to the plain step.  N>1 (torchrun) runs N
 independent replicas (ensemble members), one per GPU.
 
 ``--impl reference`` times the FP64 CPU oracle instead (on the host cores),
@@ -238,6 +241,113 @@ def measure(P, G, z, st0, prec, args, dev, world):
     return out, t
 
 
+LEARNED = dict(ndyn_reduced=4, hidden=512, max_batch=16384, train_seeds=(100, 101, 102, 103), spinup=4,
+               snapshots=8, every=3, rows=8192, adam_steps=1500, batch=4096, lr=1e-3, max_norm=3.0)
+
+
+def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
+    """Mixed precision + learned corrector: a step with ndyn_reduced substeps,
+    the column and edge networks' increments, the norm/finiteness check and the
+    plain-step fallback (icon_dycore_step_learned).  The corrector is trained
+    first on the GPU (untimed) from paired reduced/plain steps of other seeds."""
+    import numpy as np
+    import torch
+    from paper_2608_21150_gb300 import corrector as C
+    w, L = WORKLOAD, LEARNED
+    stream = torch.cuda.current_stream(dev)
+    base = dict(dtime=w["dtime"], rayleigh_coeff=w["rayleigh"], precision=P.ICON_PREC_MIXED, use_graph=1,
+                synchronous=0, stream=stream.cuda_stream)
+    R = P.Dycore(G, z, dict(base, ndyn_substeps=L["ndyn_reduced"]))
+    Pl = P.Dycore(G, z, dict(base, ndyn_substeps=w["ndyn"]))
+    ex_ref = R.reference_state()[1]
+    t0 = time.perf_counter()
+    gen = torch.Generator()
+    gen.manual_seed(0)
+    data = C.Dataset()
+    from icon_inputs import jw_type_state
+    for seed in L["train_seeds"]:
+        s0 = jw_type_state(grid, z, seed=seed)
+        s0["exner_pr"] = s0["exner"] - ex_ref[None, :]
+        st = {k: torch.from_numpy(v).to(dev) for k, v in s0.items()}
+        for _ in range(L["spinup"]):
+            Pl.step(st)
+        for _ in range(L["snapshots"]):
+            st = C.add_pair(R, Pl, st, data, rows=L["rows"], gen=gen)
+            for _ in range(L["every"] - 1):
+                Pl.step(st)
+    cx, cy, ex, ey = data.cat()
+    del data
+    cn, en = C.make_nets(w["nlev"], hidden=L["hidden"], max_batch=L["max_batch"], seed=1)
+    lc = C.fit(cn, cx, cy, w["nlev"], L["adam_steps"], batch=L["batch"], lr=L["lr"])
+    le = C.fit(en, ex, ey, w["nlev"], L["adam_steps"], batch=L["batch"], lr=L["lr"])
+    del cx, cy, ex, ey
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+
+    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
+    fallbacks_warm = 0
+    for _ in range(args.warmup):
+        fb, _ = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
+        fallbacks_warm += int(fb)
+    # held-out error of the corrector at the bench state (reduced and learned vs the plain step)
+    sp, sr, sl = C.clone_state(t), C.clone_state(t), C.clone_state(t)
+    Pl.step(sp)
+    R.step(sr)
+    P.step_learned(R, Pl, cn, en, sl, float("inf"))
+    er, el = C.field_errors(sr, sp), C.field_errors(sl, sp)
+    del sp, sr, sl
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    fallbacks, norms = 0, []
+    e0.record(stream)
+    for _ in range(args.steps):
+        fb, r = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
+        fallbacks += int(fb)
+        norms.append(r)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms = float(mt.item())
+    nc = G.n_cells
+    ps = torch.empty(nc, dtype=torch.float64, device=dev)
+    t850 = torch.empty_like(ps)
+    try:
+        Pl.diagnostics(t, ps, t850)
+        finite = True
+    except P.IconError:
+        finite = False
+    area = G.cell_areas()
+    rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
+    with P.Profile() as prof:
+        P.step_learned(R, Pl, cn, en, t, L["max_norm"])
+    out = {"value": world * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
+           "fallbacks_timed": fallbacks, "fallbacks_warmup": fallbacks_warm, "max_norm": L["max_norm"],
+           "check_norm_mean": float(np.nanmean(norms)) if norms else None, "finite": finite,
+           "rms_ps_pa_vs_fp64": rms(ps.cpu().numpy() - f64_final["ps"]),
+           "rms_t850_k_vs_fp64": rms(t850.cpu().numpy() - f64_final["t850"]),
+           "error_vs_plain_step": {"reduced": er, "learned": el,
+                                   "ratio": {k: el[k] / er[k] for k in er}},
+           "train": {"seconds": train_s, "loss_col": [float(np.mean(lc[:10])), float(np.mean(lc[-50:]))],
+                     "loss_edge": [float(np.mean(le[:10])), float(np.mean(le[-50:]))], **{
+                         k: (list(v) if isinstance(v, tuple) else v) for k, v in L.items()}},
+           "kernels": kernel_table(prof.kernels, 1), "clocks": clocks}
+    for x in (cn, en, R, Pl):
+        x.close()
+    return out
+
+
 def kernel_table(prof, nsteps):
     tot = sum(v[1] for v in prof.values()) / nsteps
     return {k: {"launches_per_step": n // nsteps, "ms_per_step": round(m / nsteps, 3),
@@ -293,6 +403,13 @@ def run_ours(args):
               "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"],
               "autotuned_launch_config": m["launch_config"]}
 
+    lrn = None
+    if not args.no_mixed and not args.no_learned:
+        lrn = learned_leg(P, G, z, grid, st0, args, dev, world, f64)
+        lrn["speedup_vs_fp64"] = lrn["value"] / value
+        if mx:
+            lrn["speedup_vs_mixed"] = lrn["value"] / mx["value"]
+
     # end to end through the C-ABI with host arrays (copies inside the timed region)
     stream = torch.cuda.current_stream(dev)
     e2e_steps = max(1, min(args.steps, 5))
@@ -326,6 +443,7 @@ def run_ours(args):
         "kernels": kernel_table(prof, nsp),
         "autotuned_launch_config": f64["launch_config"],
         "mixed": mx,
+        "mixed_learned": lrn,
         "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": sb,
                 "d2h_bytes_per_step": sb},
         "gpu_launches": launches_per_step * args.steps,
@@ -348,7 +466,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (and learned) legs")
+    ap.add_argument("--no-learned", action="store_true", help="skip the mixed + learned-corrector leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["bisections"],
                     help="RnBm bisections (default 6 = R2B6); smaller grids only for profiler captures")
     args = ap.parse_args()

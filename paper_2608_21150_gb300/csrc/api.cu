@@ -1103,8 +1103,13 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
   launch_reduce_status(d->partial, pc, pe, d->status, stream);
   CUDA_TRY(cudaGetLastError());
   double ss[2] = {0.0, 0.0};
+  int tc_err = 0;
+  const int* tc_flag = mlp_tc_error_flag();
+  if (!tc_flag) return fail(ICON_ERR_CUDA, std::string(fn) + ": cannot read the GEMM status");
   CUDA_TRY(cudaMemcpyAsync(ss, d->status, sizeof(ss), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaMemcpyAsync(&tc_err, tc_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
+  if (tc_err) return fail(ICON_ERR_CUDA, std::string(fn) + ": a tensor-core GEMM timed out waiting for its pipeline");
   const double rms = std::max(std::sqrt(ss[0] / ((double)nc * (3 * nlev - 1))), std::sqrt(ss[1] / ((double)ne * nlev)));
   const double r = std::isnan(ss[0] + ss[1]) ? NAN : rms;
   if (norm) *norm = r;

@@ -11,33 +11,16 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
+#include <mutex>
 
 #include "mlp.h"
 
 namespace icon {
 namespace {
-
-constexpr int BM = 128, BN = 128, BK = 32;
-constexpr int kGemmThreads = 256;  // 8 warps: 2 (M) x 4 (N), warp tile 64 x 32
-constexpr int SROW = BK + 8;       // padded shared row (bf16 elements): conflict-free fragment reads
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  const int bytes = pred ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
@@ -46,6 +29,24 @@ __device__ __forceinline__ float gelu_grad(float x) {
   const float pdf = 0.3989422804014327f * expf(-0.5f * x * x);
   return cdf + x * pdf;
 }
+
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM (tcgen05): one 128 x 128 output tile per CTA, K in blocks
+// of 64 (one 128-byte swizzle row of BF16) through a 3-stage TMA ring.
+// Warp 0 (one lane) issues the TMA loads, warp 1 (one lane) the MMAs into a
+// 128-column FP32 accumulator in tensor memory; then all four warps read the
+// accumulator back (warp w owns TMEM lanes 32w..32w+31 = tile rows) and apply
+// the epilogue.  96 KB of shared memory: two CTAs per SM, so one CTA's
+// epilogue overlaps the other's main loop.
+constexpr int TBM = 128, TBN = 128, TBK = 64, kStages = 3;
+constexpr int kTcThreads = 128;
+constexpr int kTileBytesA = TBM * TBK * 2, kTileBytesB = TBN * TBK * 2;
+constexpr int kTcSmem = kStages * (kTileBytesA + kTileBytesB) + 1024 /* alignment slack */ + 128 /* barriers */;
+constexpr uint32_t kTmemCols = TBN;
+// every wait gives up after this long (ns) and flags an error instead of hanging
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ int g_tc_error = 0;
 
 // Epilogue modes: 0 = fp32 out (+bias if given); 1 = bias + GELU -> bf16 out,
 // fp32 pre-activation stored if zpre != null.
@@ -58,95 +59,236 @@ struct Epi {
   int ldc;
 };
 
-__global__ void __launch_bounds__(kGemmThreads) gemm_nt(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
-                                                        int lda, const __nv_bfloat16* __restrict__ B, int ldb,
-                                                        Epi ep) {
-  __shared__ __align__(16) __nv_bfloat16 As[2][BM * SROW];
-  __shared__ __align__(16) __nv_bfloat16 Bs[2][BN * SROW];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp >> 2, wn = warp & 3;  // warp tile origin: (wm*64, wn*32)
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  float acc[4][4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-  // each thread copies 2 x 16 bytes of A and 2 x 16 bytes of B per k-tile
-  auto load = [&](int buf, int k0) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int idx = tid + r * kGemmThreads;  // 0..511: 128 rows x 4 chunks of 8 bf16
-      const int row = idx >> 2, ch = idx & 3;
-      const int gm = m0 + row, gn = n0 + row;
-      cp_async16(&As[buf][row * SROW + ch * 8], A + (size_t)(gm < M ? gm : 0) * lda + k0 + ch * 8, gm < M);
-      cp_async16(&Bs[buf][row * SROW + ch * 8], B + (size_t)(gn < N ? gn : 0) * ldb + k0 + ch * 8, gn < N);
-    }
-    cp_async_commit();
-  };
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-  const int nk = K / BK;
-  load(0, 0);
-  for (int kt = 0; kt < nk; ++kt) {
-    const int buf = kt & 1;
-    if (kt + 1 < nk) {
-      load(buf ^ 1, (kt + 1) * BK);
-      cp_async_wait_1();
-    } else {
-      cp_async_wait_0();
-    }
-    __syncthreads();
-    const __nv_bfloat16* as = As[buf];
-    const __nv_bfloat16* bs = Bs[buf];
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t af[4][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r0 = wm * 64 + i * 16 + g;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&as[r0 * SROW + kk + 2 * t]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&as[(r0 + 8) * SROW + kk + 2 * t]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&as[r0 * SROW + kk + 2 * t + 8]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&as[(r0 + 8) * SROW + kk + 2 * t + 8]);
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity.  Gives up
+// when another thread of the CTA has flagged an abort, or after kWaitLimitNs
+// (then flags the abort and the device-wide error word itself).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const unsigned long long t0 = now_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (now_ns() - t0 > kWaitLimitNs) {
+        *abort_flag = 1;
+        atomicExch(&g_tc_error, 1);
+        return false;
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c0 = wn * 32 + j * 8 + g;
-        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&bs[c0 * SROW + kk + 2 * t]);
-        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&bs[c0 * SROW + kk + 2 * t + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
     }
-    __syncthreads();
   }
+}
 
-  // epilogue
-  const int g = lane >> 2, t = lane & 3;
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile stored as rows of
+// 128 bytes with the 128-byte swizzle (as TMA writes it): start address,
+// stride between 8-row groups 1024 B, descriptor version 1, swizzle mode 2.
+// The leading-byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* tile) {
+  const uint32_t a = smem_u32(tile);
+  return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_tc(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CUtensorMap tma_a,
+                                                      const __grid_constant__ CUtensorMap tma_b, int M, int N, int K,
+                                                      Epi ep) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + kStages * kTileBytesA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kTileBytesB);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const int nk = K / TBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // TMA stages issued by the producer lane
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1, abort_flag)) break;
+      mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
+      tma_load_2d(sA + s * kTileBytesA, &tma_a, kb * TBK, m0, &full[s]);
+      tma_load_2d(sB + s * kTileBytesB, &tma_b, kb * TBK, n0, &full[s]);
+      issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(TBM, TBN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(&full[s], (kb / kStages) & 1, abort_flag)) break;
+      tc_fence_after();
+      const uint64_t da = sdesc_sw128(sA + s * kTileBytesA), db = sdesc_sw128(sB + s * kTileBytesB);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < TBK / 16; ++k)  // 16 BF16 = 32 bytes further along K: +2 in the 16-byte address field
+        mma_bf16_tc(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+      tc_commit(&empty[s]);
+    }
+    tc_commit(done);  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: thread (warp, lane) owns tile row 32 warp + lane
+  // warp-uniform decision: the tcgen05.ld below is a warp-collective instruction
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
+  tc_fence_after();
+  if (ok) {
+    const int row = m0 + 32 * warp + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int c = 0; c < TBN; c += 16) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c, v);
+      const int col0 = n0 + c;
+      if (row >= M || col0 >= N) continue;
+      const bool whole = col0 + 16 <= N;
+      const size_t o = (size_t)row * ep.ldc + col0;
+      const bool vec32 = whole && (o & 3) == 0;   // 16-byte aligned fp32 run
+      const bool vec16 = whole && (o & 7) == 0;   // 16-byte aligned bf16 run
+      if (ep.bias) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int row = m0 + wm * 64 + i * 16 + g + (r >= 2 ? 8 : 0);
-        const int col = n0 + wn * 32 + j * 8 + 2 * t + (r & 1);
-        if (row >= M || col >= N) continue;
-        float v = acc[i][j][r];
-        if (ep.bias) v += ep.bias[col];
-        const size_t o = (size_t)row * ep.ldc + col;
-        if (ep.mode == 0) {
-          ep.out_f32[o] = v;
+        for (int j = 0; j < 16; ++j)
+          if (whole || col0 + j < N) v[j] += ep.bias[col0 + j];
+      }
+      if (ep.mode == 0) {
+        if (vec32) {
+          float4* dst = reinterpret_cast<float4*>(ep.out_f32 + o);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         } else {
-          if (ep.zpre) ep.zpre[o] = v;
-          ep.out_bf16[o] = __float2bfloat16(gelu(v));
+          for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_f32[o + j] = v[j];
+        }
+      } else {
+        if (ep.zpre) {
+          if (vec32) {
+            float4* dst = reinterpret_cast<float4*>(ep.zpre + o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            for (int j = 0; j < 16 && col0 + j < N; ++j) ep.zpre[o + j] = v[j];
+          }
+        }
+        if (vec16) {
+          __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16(gelu(v[j]));
+          uint4* dst = reinterpret_cast<uint4*>(ep.out_bf16 + o);
+          dst[0] = reinterpret_cast<const uint4*>(h)[0];
+          dst[1] = reinterpret_cast<const uint4*>(h)[1];
+        } else {
+          for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_bf16[o + j] = __float2bfloat16(gelu(v[j]));
         }
       }
+    }
+  }
+
+  // teardown: the TMA copies this CTA issued have landed (bounded), then TMEM is freed
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    const int first = issued > kStages ? issued - kStages : 0;
+    for (int kb = first; kb < issued; ++kb) {
+      const unsigned long long t0 = now_ns();
+      while (!mbar_try_wait(&full[kb % kStages], (kb / kStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
 }
 
 // out[c][r] = in[r][c] for r < rows, c < cols (bf16); pads of out left untouched
@@ -234,14 +376,68 @@ __global__ void adam_update_bias(int n, float* __restrict__ b, const float* __re
 
 inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = []() -> EncodeTiled {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// 2-D tensor map of a K-major BF16 operand [rows][ld] (K of it used): boxes of
+// 64 (K) x box_rows, 128-byte swizzle; rows past `rows` read as zero.
+bool operand_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int K, int ld, int box_rows) {
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+std::mutex g_attr_mutex;
+bool g_attr_set[64] = {};
+
 }  // namespace
 
-void mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-              const float* bias, bool gelu_act, float* out_f32, __nv_bfloat16* out_bf16, float* zpre, int ldc,
-              cudaStream_t s) {
+int mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+             const float* bias, bool gelu_act, float* out_f32, __nv_bfloat16* out_bf16, float* zpre, int ldc,
+             cudaStream_t s) {
+  if (M < 1 || N < 1 || K < TBK || K % TBK || lda % 8 || ldb % 8 || ldc < N || lda < K || ldb < K ||
+      (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) % 16)
+    return report_error(ICON_ERR_ARG, "mlp_gemm: unsupported shape or alignment");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return report_error(ICON_ERR_CUDA, "mlp_gemm: device");
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mutex);
+    if (!g_attr_set[dev]) {
+      if (cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess)
+        return report_error(ICON_ERR_CUDA, "mlp_gemm: shared memory attribute");
+      g_attr_set[dev] = true;
+    }
+  }
+  CUtensorMap ta, tb;
+  if (!operand_map(&ta, A, M, K, lda, TBM) || !operand_map(&tb, B, N, K, ldb, TBN))
+    return report_error(ICON_ERR_CUDA, "mlp_gemm: tensor map encoding failed");
   Epi ep{gelu_act ? 1 : 0, bias, out_f32, out_bf16, zpre, ldc};
-  dim3 grid(cdiv(N, BN), cdiv(M, BM));
-  ICON_LAUNCH("mlp_gemm", grid, kGemmThreads, s, gemm_nt, M, N, K, A, lda, B, ldb, ep);
+  dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
+  ICON_LAUNCH_SMEM("mlp_gemm_tc", grid, kTcThreads, kTcSmem, s, gemm_tc, ta, tb, M, N, K, ep);
+  return ICON_OK;
+}
+
+const int* mlp_tc_error_flag() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) return nullptr;
+  return static_cast<const int*>(p);
 }
 
 void mlp_transpose(int rows, int cols, const __nv_bfloat16* in, int ldi, __nv_bfloat16* out, int ldo,

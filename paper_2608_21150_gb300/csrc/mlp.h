@@ -7,10 +7,12 @@
 
 namespace icon {
 
-// C[M x N] = A[M x K] B[N x K]^T (bf16 operands, K-major, K a multiple of 32,
-// lda/ldb multiples of 8); epilogue: + bias, then either fp32 out or GELU ->
-// bf16 out (and the fp32 pre-activation into zpre if given).
-void mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+// C[M x N] = A[M x K] B[N x K]^T on the tensor cores (tcgen05): bf16 operands,
+// K-major, K a multiple of 64, lda/ldb multiples of 8 (>= K), ldc >= N, 16-byte
+// aligned operand bases; epilogue: + bias, then either fp32 out or GELU ->
+// bf16 out (and the fp32 pre-activation into zpre if given).  Returns an ICON_*
+// code (shape and alignment are checked before the launch).
+int mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
               const float* bias, bool gelu_act, float* out_f32, __nv_bfloat16* out_bf16, float* zpre, int ldc,
               cudaStream_t s);
 void mlp_transpose(int rows, int cols, const __nv_bfloat16* in, int ldi, __nv_bfloat16* out, int ldo,
@@ -28,6 +30,10 @@ void mlp_adam_bias(int n, float* b, const float* g, float* m, float* v, float lr
 // dy = 2 (y - t) / (B n_out)
 void mlp_mse(int B, int n_out, const float* y, int ldy, const float* t, int ldt, float* dy, int lddy, double* rowloss,
              cudaStream_t s);
+
+// Device address of the tensor-core GEMM's error word (nonzero once a GEMM gave
+// up a bounded wait; sticky).
+const int* mlp_tc_error_flag();
 
 // Forward pass of rows [B][n_in] (normalised FP32, DEVICE) without synchronising;
 // B <= max_batch.  *y points at the network's own output rows [B][*ldy], valid

@@ -58,44 +58,48 @@ int64_t param_count(const icon_mlp* m) {
   return n;
 }
 
-void forward(icon_mlp* m, const float* x, int B, cudaStream_t s) {
+// keep_z: store the FP32 pre-activations a following backward needs
+int forward(icon_mlp* m, const float* x, int B, cudaStream_t s, bool keep_z = true) {
   mlp_to_bf16(B, m->dims[0], x, m->dims[0], m->x16, m->lds[0], s);
   const __nv_bfloat16* in = m->x16;
   for (int l = 0; l < 2; ++l) {
-    mlp_gemm(B, layer_out(m, l), m->lds[l], in, m->lds[l], m->wt16[l], m->lds[l], m->b[l], true, nullptr, m->h16[l],
-             m->z[l], m->lds[l + 1], s);
+    int rc = mlp_gemm(B, layer_out(m, l), m->lds[l], in, m->lds[l], m->wt16[l], m->lds[l], m->b[l], true, nullptr,
+                      m->h16[l], keep_z ? m->z[l] : nullptr, m->lds[l + 1], s);
+    if (rc != ICON_OK) return rc;
     in = m->h16[l];
   }
-  mlp_gemm(B, layer_out(m, 2), m->lds[2], in, m->lds[2], m->wt16[2], m->lds[2], m->b[2], false, m->y, nullptr, nullptr,
-           m->lds[3], s);
+  return mlp_gemm(B, layer_out(m, 2), m->lds[2], in, m->lds[2], m->wt16[2], m->lds[2], m->b[2], false, m->y, nullptr,
+                  nullptr, m->lds[3], s);
 }
 
-// gradients of all parameters for dL/dy in m->dy (fp32 [B][lds[3]]), after forward()
-void backward(icon_mlp* m, int B, cudaStream_t s) {
+// gradients of all parameters for dL/dy in m->dy (fp32 [B][lds[3]]), after
+// forward(); B a multiple of 64 (the K extent of the weight-gradient GEMMs)
+int backward(icon_mlp* m, int B, cudaStream_t s) {
   // layer 3 (no activation): dz = dy
   const int n3 = layer_out(m, 2);
   mlp_to_bf16(B, n3, m->dy, m->lds[3], m->dz16, m->lds[3], s);
   mlp_bias_grad(B, n3, m->dy, m->lds[3], m->gb[2], s);
-  const float* dz32 = m->dy;
   int ldz = m->lds[3];
   for (int l = 2; l >= 0; --l) {
     const int nin = layer_in(m, l), nout = layer_out(m, l);
     const __nv_bfloat16* h = l == 0 ? m->x16 : m->h16[l - 1];
-    // dW^T [nout][nin] = dZ^T H
+    // dW^T [nout][nin] = dZ^T H over the batch
     mlp_transpose(B, nout, m->dz16, ldz, m->dzT, m->ld_b, s);
     mlp_transpose(B, nin, h, m->lds[l], m->hT, m->ld_b, s);
-    mlp_gemm(nout, nin, m->ld_b, m->dzT, m->ld_b, m->hT, m->ld_b, nullptr, false, m->gw[l], nullptr, nullptr, nin, s);
+    int rc = mlp_gemm(nout, nin, B, m->dzT, m->ld_b, m->hT, m->ld_b, nullptr, false, m->gw[l], nullptr, nullptr, nin,
+                      s);
+    if (rc != ICON_OK) return rc;
     if (l == 0) break;
     // dH [B][nin] = dZ W (W stored [nin][lds[l+1]])
-    mlp_gemm(B, nin, m->lds[l + 1], m->dz16, ldz, m->w16[l], m->lds[l + 1], nullptr, false, m->dh, nullptr, nullptr,
-             m->lds[l], s);
+    rc = mlp_gemm(B, nin, m->lds[l + 1], m->dz16, ldz, m->w16[l], m->lds[l + 1], nullptr, false, m->dh, nullptr,
+                  nullptr, m->lds[l], s);
+    if (rc != ICON_OK) return rc;
     // dZ of the previous layer through its GELU
     mlp_gelu_backward(B, nin, m->dh, m->lds[l], m->z[l - 1], m->lds[l], m->dz32, m->dz16, m->lds[l], s);
     mlp_bias_grad(B, nin, m->dz32, m->lds[l], m->gb[l - 1], s);
-    dz32 = m->dz32;
     ldz = m->lds[l];
   }
-  (void)dz32;
+  return ICON_OK;
 }
 
 void adam(icon_mlp* m, float lr, float b1, float b2, float eps, cudaStream_t s) {
@@ -118,6 +122,16 @@ __global__ void refresh_bf16(int n_out, int n_in, const float* __restrict__ w, _
   w16[(size_t)k * ldw + o] = __float2bfloat16(w[i]);
 }
 
+// ICON_ERR_CUDA once a tensor-core GEMM has given up a bounded wait (synchronous read)
+int tc_status(const char* fn) {
+  const int* flag = mlp_tc_error_flag();
+  int v = 0;
+  if (!flag || cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail_m(ICON_ERR_CUDA, std::string(fn) + ": cannot read the GEMM status");
+  if (v) return fail_m(ICON_ERR_CUDA, std::string(fn) + ": a tensor-core GEMM timed out waiting for its pipeline");
+  return ICON_OK;
+}
+
 int check_batch(const icon_mlp* m, int B, const char* fn) {
   if (B < 1 || B > m->max_batch) return fail_m(ICON_ERR_ARG, std::string(fn) + ": batch out of range");
   return ICON_OK;
@@ -128,7 +142,8 @@ int check_batch(const icon_mlp* m, int B, const char* fn) {
 namespace icon {
 int mlp_forward_rows(icon_mlp_t* m, const float* x, int B, const float** y, int* ldy, cudaStream_t s) {
   if (B < 1 || B > m->max_batch) return fail_m(ICON_ERR_ARG, "corrector: batch out of range");
-  forward(m, x, B, s);
+  const int rc = forward(m, x, B, s, false);
+  if (rc != ICON_OK) return rc;
   *y = m->y;
   *ldy = m->lds[3];
   return ICON_OK;
@@ -276,13 +291,14 @@ int icon_mlp_forward(icon_mlp_t* m, const float* x, int32_t batch, float* y, voi
   int rc = check_batch(m, batch, "icon_mlp_forward");
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  forward(m, x, batch, s);
+  rc = forward(m, x, batch, s);
+  if (rc != ICON_OK) return rc;
   if (cudaMemcpy2DAsync(y, m->dims[3] * 4, m->y, m->lds[3] * 4, m->dims[3] * 4, batch, cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
     return fail_m(ICON_ERR_CUDA, "icon_mlp_forward: copy failed");
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_forward: ") + cudaGetErrorString(e));
-  return ICON_OK;
+  return tc_status("icon_mlp_forward");
 }
 
 int icon_mlp_backward(icon_mlp_t* m, const float* dy, int32_t batch, void* stream) {
@@ -294,10 +310,11 @@ int icon_mlp_backward(icon_mlp_t* m, const float* dy, int32_t batch, void* strea
   if (cudaMemcpy2DAsync(m->dy, m->lds[3] * 4, dy, m->dims[3] * 4, m->dims[3] * 4, batch, cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
     return fail_m(ICON_ERR_CUDA, "icon_mlp_backward: copy failed");
-  backward(m, batch, s);
+  rc = backward(m, batch, s);
+  if (rc != ICON_OK) return rc;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_backward: ") + cudaGetErrorString(e));
-  return ICON_OK;
+  return tc_status("icon_mlp_backward");
 }
 
 int icon_mlp_adam(icon_mlp_t* m, float lr, float beta1, float beta2, float eps, void* stream) {
@@ -313,9 +330,11 @@ int icon_mlp_train_step(icon_mlp_t* m, const float* x, const float* target, int3
   if (rc) return rc;
   if (batch % 64) return fail_m(ICON_ERR_ARG, "icon_mlp_train_step: batch must be a multiple of 64");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  forward(m, x, batch, s);
+  rc = forward(m, x, batch, s);
+  if (rc != ICON_OK) return rc;
   mlp_mse(batch, m->dims[3], m->y, m->lds[3], target, m->dims[3], m->dy, m->lds[3], m->rowloss, s);
-  backward(m, batch, s);
+  rc = backward(m, batch, s);
+  if (rc != ICON_OK) return rc;
   adam(m, lr, 0.9f, 0.999f, 1e-8f, s);
   if (loss) {
     std::vector<double> rl(batch);
@@ -325,6 +344,8 @@ int icon_mlp_train_step(icon_mlp_t* m, const float* x, const float* target, int3
     double t = 0.0;
     for (double v : rl) t += v;
     *loss = t / ((double)batch * m->dims[3]);
+    rc = tc_status("icon_mlp_train_step");
+    if (rc != ICON_OK) return rc;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_train_step: ") + cudaGetErrorString(e));
