@@ -265,8 +265,9 @@ int icon_dycore_sizes(const icon_dycore_t* dycore, int32_t* nlev, int32_t* n_cel
  * equation of state) for n_cols independent columns of nlev levels:
  *   z_ifc [nlev+1] HOST, half-level heights as for icon_dycore_create;
  *   p      the scheme parameters (dtime/ndyn_substeps is the time step of the
- *          solve; stream and synchronous are honoured; precision is ignored,
- *          the solve is FP64);
+ *          solve; stream and synchronous are honoured; precision FP64 solves
+ *          in FP64, MIXED in the mixed mode's double-word FP32 arithmetic,
+ *          about 48 significant bits, on FP64 inputs and outputs);
  * DEVICE inputs, level-contiguous like the state:
  *   w [n_cols*(nlev+1)], rho, exner, theta_v [n_cols*nlev]  state at the
  *          start of the substep;

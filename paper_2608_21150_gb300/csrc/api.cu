@@ -408,6 +408,8 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   v.dexner_ref_ic = A.upload(dref);
   v.ray_fac = A.upload(ray);
   v.colc = A.upload(colc);
+  v.lev_hl = A.upload(level_pairs(nlev, colc.data(), d->exner_ref.data(), d->theta_ref.data(), dz.data(), ray.data(),
+                                  rho_ref.data()));
   en.rho_ref64 = A.upload(rho_ref);
   en.sc = s;
 

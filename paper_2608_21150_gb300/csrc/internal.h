@@ -84,7 +84,42 @@ struct DevVert {
   // 0 dt rd/(cvd dz_k), 1 dt (1-beta)/dz_k, 2 dt beta/dz_k, 3 dt cpd (1-beta)/dzh_k,
   // 4 dt cpd dexner_ref_ic_k, 5 dt cpd beta/dzh_k, 6 wgt_k, 7 1 - wgt_k
   const double* colc;      // [(nlev+1)*8]
+  // the same per level as double-word FP32 pairs (hi, lo), 16 pairs per level
+  // k = 0..nlev: colc 0..7, then exner_ref, theta_ref, dz, ray_fac, rho_ref
+  // (zero where a quantity is not defined at that level)
+  const float* lev_hl;     // [(nlev+1)*32]
 };
+
+// double -> (hi, lo) FP32 pair with hi + lo = x to about 48 bits
+inline void split_hl(double x, float* out) {
+  const float hi = (float)x;
+  out[0] = hi;
+  out[1] = (float)(x - (double)hi);
+}
+
+// the lev_hl table of DevVert into t[32 (nlev + 1)] (rho_ref may be null)
+inline void level_pairs_into(float* t, int nlev, const double* colc, const double* exner_ref,
+                             const double* theta_ref, const double* dz, const double* ray_fac, const double* rho_ref) {
+  for (size_t i = 0; i < 32 * (size_t)(nlev + 1); ++i) t[i] = 0.0f;
+  for (int k = 0; k <= nlev; ++k) {
+    float* r = t + 32 * (size_t)k;
+    for (int j = 0; j < 8; ++j) split_hl(colc[8 * (size_t)k + j], r + 2 * j);
+    if (k < nlev) {
+      split_hl(exner_ref[k], r + 16);
+      split_hl(theta_ref[k], r + 18);
+      split_hl(dz[k], r + 20);
+      if (rho_ref) split_hl(rho_ref[k], r + 24);
+    }
+    split_hl(ray_fac[k], r + 22);
+  }
+}
+
+inline std::vector<float> level_pairs(int nlev, const double* colc, const double* exner_ref, const double* theta_ref,
+                                      const double* dz, const double* ray_fac, const double* rho_ref) {
+  std::vector<float> t(32 * (size_t)(nlev + 1));
+  level_pairs_into(t.data(), nlev, colc, exner_ref, theta_ref, dz, ray_fac, rho_ref);
+  return t;
+}
 
 // Work arrays of the stencil kernels, compute type T.
 template <class T>

@@ -28,6 +28,7 @@
 #include <string>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 
 namespace icon {
@@ -117,11 +118,65 @@ struct ColArgs {
   const double* rho_ref;
 };
 
+// Arithmetic of the solve: FP64 (R = double), or double-word FP32 (R = df,
+// mixed precision) with inputs split and outputs joined at the tile boundary.
+template <class R>
+struct Ar;
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double in(double x) { return x; }
+  static __device__ __forceinline__ double in(float x) { return (double)x; }
+  static __device__ __forceinline__ double inv(double x) { return rcp(x); }
+  static __device__ __forceinline__ double out(double x) { return x; }
+};
+template <>
+struct Ar<df> {
+  static __device__ __forceinline__ df in(double x) { return to_df(x); }
+  static __device__ __forceinline__ df in(float x) { return to_df(x); }
+  static __device__ __forceinline__ df inv(df x) { return rcp(x); }
+  static __device__ __forceinline__ double out(df x) { return to_double(x); }
+};
+
+// per-level quantities: j < 8 the column coefficients, then these
+enum { LEX = 8, LTH = 9, LDZ = 10, LRAY = 11, LRHO = 12 };
+template <class R, int J>
+__device__ __forceinline__ R lev(const DevVert& v, int k);
+template <>
+__device__ __forceinline__ double lev<double, LEX>(const DevVert& v, int k) { return v.exner_ref[k]; }
+template <>
+__device__ __forceinline__ double lev<double, LTH>(const DevVert& v, int k) { return v.theta_ref[k]; }
+template <>
+__device__ __forceinline__ double lev<double, LDZ>(const DevVert& v, int k) { return v.dz[k]; }
+template <>
+__device__ __forceinline__ double lev<double, LRAY>(const DevVert& v, int k) { return v.ray_fac[k]; }
+template <class R, int J>
+__device__ __forceinline__ R lev(const DevVert& v, int k) {
+  if constexpr (std::is_same<R, df>::value) {
+    return reinterpret_cast<const df*>(v.lev_hl)[16 * (size_t)k + J];
+  } else {
+    static_assert(J < 8, "column coefficient");
+    return v.colc[8 * (size_t)k + J];
+  }
+}
+
+// Scratch planes hold R values in 8-byte slots (a df is two floats).
+template <class R>
+__device__ __forceinline__ void put(double* p, R x) {
+  static_assert(sizeof(R) == sizeof(double), "scratch slot");
+  *reinterpret_cast<R*>(p) = x;
+}
+template <class R>
+__device__ __forceinline__ R get(const double* p) {
+  return *reinterpret_cast<const R*>(p);
+}
+
 // kOwnZb: the corrector form computes zb and the equation-of-state term itself
 // (as the predictor does) instead of reading the predictor's; used by the
 // allocation-free entry point below.
-template <class T, bool kOwnZb = false, int KC = kKC>
+template <class T, bool kOwnZb = false, int KC = kKC, class R = double>
 __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
+  using A = Ar<R>;
+  constexpr bool kDW = std::is_same<R, df>::value;
   constexpr int kTile = tile_doubles<KC>();
   constexpr int kBackIn = KC * kCW;
   extern __shared__ double sm[];
@@ -155,12 +210,16 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
   double* al_s = a.col + 5 * plane;
   double* eb_s = a.col + 6 * plane;
 
-  const double dt = sc.dt_s, beta = sc.beta, ombeta = 1.0 - beta;
-  const double wn_r = sc.wnow_rth, wnew_r = sc.wnew_rth;
+  const R zero = A::in(0.0), one = A::in(1.0);
+  const R dt = A::in(sc.dt_s), beta = A::in(sc.beta), ombeta = A::in(1.0 - sc.beta);
+  const R wn_r = A::in(sc.wnow_rth), wnew_r = A::in(sc.wnew_rth);
+  const R wn_v = A::in(sc.wnow_vel), wnew_v = A::in(sc.wnew_vel), cvd_o_rd = A::in(sc.cvd_o_rd);
 
-  // carried values: half level k (interface above full level k) and full level k-1
-  double ric_k = 0.0, tic_k = 0.0, tpic_k = 0.0, rt_k = 0.0;
-  double zb_km1 = 0.0, al_km1 = 0.0, ps_km1 = 0.0, pr_km1 = 0.0, cp_km1 = 0.0, rp_km1 = 0.0;
+  // carried values: half level k (interface above full level k), full level k-1,
+  // and full level k itself (converted and time-averaged when it was level k+1)
+  R ric_k = zero, tic_k = zero, tpic_k = zero, rt_k = zero;
+  R zb_km1 = zero, al_km1 = zero, ps_km1 = zero, pr_km1 = zero, cp_km1 = zero, rp_km1 = zero;
+  R rho_c = zero, th_c = zero, ra_c = zero, ta_c = zero, tpa_c = zero;
 
   for (int k0 = 0; k0 < nlev; k0 += KC) {
     const int nkc = min(KC, nlev - k0);       // levels solved in this chunk
@@ -186,64 +245,68 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
 #pragma unroll 1
     for (int kk = 0; kk < nkc; ++kk) {
       const int k = k0 + kk;
-      const double* cf = v.colc + 8 * (size_t)k;
       const int o = kk * kLD + t;
-      const double rho_n = T_rho[o], th_n = T_th[o], pi_n = T_pi[o];
-      const double pr_k = pi_n - v.exner_ref[k];
+      if (k == 0) {
+        rho_c = A::in(T_rho[o]);
+        th_c = A::in(T_th[o]);
+        ra_c = corrector ? wn_r * rho_c + wnew_r * A::in(T_rp[o]) : rho_c;
+        ta_c = corrector ? wn_r * th_c + wnew_r * A::in(T_tp[o]) : th_c;
+        tpa_c = ta_c - lev<R, LTH>(v, 0);
+      }
+      const R rho_n = rho_c, th_n = th_c, pi_n = A::in(T_pi[o]);
+      const R pr_k = pi_n - lev<R, LEX>(v, k);
       // interface k+1 from full levels k and k+1 (time-averaged in the corrector)
-      double ric_k1 = 0.0, tic_k1 = 0.0, tpic_k1 = 0.0;
+      R ric_k1 = zero, tic_k1 = zero, tpic_k1 = zero;
+      R rho_x = zero, th_x = zero, ra_x = zero, ta_x = zero, tpa_x = zero;
       if (k + 1 < nlev) {
-        const double* cf1 = cf + 8;
-        double ra = rho_n, ta = th_n, rb = T_rho[o + kLD], tb = T_th[o + kLD];
-        if (corrector) {
-          ra = wn_r * ra + wnew_r * T_rp[o];
-          ta = wn_r * ta + wnew_r * T_tp[o];
-          rb = wn_r * rb + wnew_r * T_rp[o + kLD];
-          tb = wn_r * tb + wnew_r * T_tp[o + kLD];
-        }
-        ric_k1 = cf1[WG] * ra + cf1[WG2] * rb;
-        tic_k1 = cf1[WG] * ta + cf1[WG2] * tb;
-        tpic_k1 = cf1[WG] * (ta - v.theta_ref[k]) + cf1[WG2] * (tb - v.theta_ref[k + 1]);
+        rho_x = A::in(T_rho[o + kLD]);
+        th_x = A::in(T_th[o + kLD]);
+        ra_x = corrector ? wn_r * rho_x + wnew_r * A::in(T_rp[o + kLD]) : rho_x;
+        ta_x = corrector ? wn_r * th_x + wnew_r * A::in(T_tp[o + kLD]) : th_x;
+        tpa_x = ta_x - lev<R, LTH>(v, k + 1);
+        const R g1 = lev<R, WG>(v, k + 1), g2 = lev<R, WG2>(v, k + 1);
+        ric_k1 = g1 * ra_c + g2 * ra_x;
+        tic_k1 = g1 * ta_c + g2 * ta_x;
+        tpic_k1 = g1 * tpa_c + g2 * tpa_x;
       }
       const size_t ik = (size_t)k * nc + c;
-      double zb;
+      R zb;
       if (!corrector || kOwnZb) {
-        zb = cf[CZB] * pi_n * rcp(rho_n * th_n);
-        a.zbl[ik] = zb;
-        eb_s[ik] = pi_n - sc.cvd_o_rd * pr_k;
+        zb = lev<R, CZB>(v, k) * pi_n * A::inv(rho_n * th_n);
+        put(a.zbl + ik, zb);
+        put(eb_s + ik, pi_n - cvd_o_rd * pr_k);
       } else {
-        zb = T_zb[o];
+        zb = get<R>(T_zb + o);
       }
-      const double wk = T_w[o], wk1 = T_w[o + kLD];
-      const double rt_k1 = ric_k1 * tic_k1;
-      const double rstar = rho_n - dt * T_dm[o] - cf[CR] * (ric_k * wk - ric_k1 * wk1);
-      const double pstar = pr_k - zb * (v.dz[k] * T_dt[o] + ombeta * (rt_k * wk - rt_k1 * wk1));
-      const double al_k = beta * rt_k, al_k1 = beta * rt_k1;
-      rs_s[ik] = rstar;
-      ps_s[ik] = pstar;
-      ri_s[ik] = ric_k;
-      al_s[ik] = al_k;
+      const R wk = A::in(T_w[o]), wk1 = A::in(T_w[o + kLD]);
+      const R rt_k1 = ric_k1 * tic_k1;
+      const R rstar = rho_n - dt * A::in(T_dm[o]) - lev<R, CR>(v, k) * (ric_k * wk - ric_k1 * wk1);
+      const R pstar = pr_k - zb * (lev<R, LDZ>(v, k) * A::in(T_dt[o]) + ombeta * (rt_k * wk - rt_k1 * wk1));
+      const R al_k = beta * rt_k, al_k1 = beta * rt_k1;
+      put(rs_s + ik, rstar);
+      put(ps_s + ik, pstar);
+      put(ri_s + ik, ric_k);
+      put(al_s + ik, al_k);
       if (k >= 1) {
-        const double ddtw = corrector ? sc.wnow_vel * (double)T_dw0[o] + sc.wnew_vel * (double)T_dw1[o]
-                                      : (double)T_dw0[o];
-        const double wstar = wk + dt * ddtw - (cf[CWX] * tic_k * (pr_km1 - pr_k) + cf[CB] * tpic_k);
-        const double gam = cf[CGAM] * tic_k;
-        const double am = -gam * zb_km1 * al_km1;
-        const double bm = 1.0 + gam * al_k * (zb_km1 + zb);
-        const double cm = -gam * zb * al_k1;
-        const double rm = wstar - gam * (ps_km1 - pstar);
-        double cpk, rpk;
+        const R ddtw = corrector ? wn_v * A::in(T_dw0[o]) + wnew_v * A::in(T_dw1[o]) : A::in(T_dw0[o]);
+        const R wstar = wk + dt * ddtw - (lev<R, CWX>(v, k) * tic_k * (pr_km1 - pr_k) + lev<R, CB>(v, k) * tpic_k);
+        const R gam = lev<R, CGAM>(v, k) * tic_k;
+        const R am = -(gam * zb_km1 * al_km1);
+        const R bm = one + gam * al_k * (zb_km1 + zb);
+        const R cm = -(gam * zb * al_k1);
+        const R rm = wstar - gam * (ps_km1 - pstar);
+        R cpk, rpk;
         if (k == 1) {
-          const double inv = rcp(bm);
+          const R inv = A::inv(bm);
           cpk = cm * inv;
           rpk = rm * inv;
         } else {
-          const double inv = rcp(bm - am * cp_km1);
+          const R inv = A::inv(bm - am * cp_km1);
           cpk = cm * inv;
           rpk = (rm - am * rp_km1) * inv;
         }
-        cp_s[ik] = cpk;
-        rp_s[ik] = rpk;
+        put(cp_s + ik, cpk);
+        put(rp_s + ik, rpk);
         cp_km1 = cpk;
         rp_km1 = rpk;
       }
@@ -255,6 +318,11 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
       tic_k = tic_k1;
       tpic_k = tpic_k1;
       rt_k = rt_k1;
+      rho_c = rho_x;
+      th_c = th_x;
+      ra_c = ra_x;
+      ta_c = ta_x;
+      tpa_c = tpa_x;
     }
   }
 
@@ -274,7 +342,7 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
   // the level-major scratch written above by this thread is read back by
   // other threads of the CTA through the asynchronous copies below
   __threadfence_block();
-  double w_und_k1 = 0.0, wd_k1 = 0.0, ric_k1 = 0.0, al_k1 = 0.0;
+  R w_und_k1 = zero, wd_k1 = zero, ric_k1 = zero, al_k1 = zero;
   for (int kend = nlev; kend > 0; kend -= KC) {
     const int k0 = max(0, kend - KC), nk = kend - k0;
     __syncthreads();
@@ -292,22 +360,29 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
 #pragma unroll 1
       for (int kk = nk - 1; kk >= 0; --kk) {
         const int k = k0 + kk;
-        const double* cf = v.colc + 8 * (size_t)k;
         const int b = kk * kCW + t;
-        double w_und = 0.0, wd = 0.0;
+        R w_und = zero, wd = zero;
         if (k >= 1) {
-          w_und = B_rp[b] - B_cp[b] * w_und_k1;
-          wd = w_und * v.ray_fac[k];
+          w_und = get<R>(B_rp + b) - get<R>(B_cp + b) * w_und_k1;
+          wd = w_und * lev<R, LRAY>(v, k);
         }
-        const double ric = B_ri[b], al = B_al[b], zb = B_zb[b];
-        const double rnew = B_rs[b] - cf[CRN] * (ric * wd - ric_k1 * wd_k1);
-        const double prnew = B_ps[b] - zb * (al * wd - al_k1 * wd_k1);
-        const double thnew = cf[CZB] * (B_eb[b] + sc.cvd_o_rd * prnew) * rcp(zb * rnew);
+        const R ric = get<R>(B_ri + b), al = get<R>(B_al + b), zb = get<R>(B_zb + b);
+        const R rnew = get<R>(B_rs + b) - lev<R, CRN>(v, k) * (ric * wd - ric_k1 * wd_k1);
+        const R prnew = get<R>(B_ps + b) - zb * (al * wd - al_k1 * wd_k1);
+        const R thnew = lev<R, CZB>(v, k) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
         const int o = kk * kLD + t;
-        O_w[o] = wd;
-        O_rho[o] = rnew;
-        O_pi[o] = v.exner_ref[k] + prnew;
-        O_th[o] = thnew;
+        O_w[o] = A::out(wd);
+        O_rho[o] = A::out(rnew);
+        O_pi[o] = A::out(lev<R, LEX>(v, k) + prnew);
+        O_th[o] = A::out(thnew);
+        if constexpr (kDW) {
+          // FP32 mirrors straight from the double-word values, into this
+          // thread's consumed scratch slots: (w, rho - rho_ref) and theta_v - theta_ref
+          float* m0 = reinterpret_cast<float*>(B_cp + b);
+          m0[0] = to_float(wd);
+          m0[1] = to_float(rnew - lev<R, LRHO>(v, k));
+          reinterpret_cast<float*>(B_rp + b)[0] = to_float(thnew - lev<R, LTH>(v, k));
+        }
         w_und_k1 = w_und;
         wd_k1 = wd;
         ric_k1 = ric;
@@ -319,16 +394,19 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
     store_tile(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
     store_tile(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
     store_tile(O_th, a.theta_o, nlev, c0, nc, k0, nk);
-    if (a.m_w) {
-      // FP32 mirrors for the mixed-mode stencils (one conversion per value)
-      for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
-        const int col = i / nk, kk = i - col * nk, k = k0 + kk;
-        if (c0 + col >= nc) continue;
-        const size_t ic = (size_t)(c0 + col) * nlev + k;
-        a.m_w[(size_t)(c0 + col) * nlevp + k] = (float)O_w[kk * kLD + col];
-        if (a.m_rho) {
-          a.m_rho[ic] = (float)(O_rho[kk * kLD + col] - a.rho_ref[k]);
-          a.m_th[ic] = (float)(O_th[kk * kLD + col] - v.theta_ref[k]);
+    if constexpr (kDW) {
+      if (a.m_w) {
+        // FP32 mirrors for the mixed-mode stencils
+        for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
+          const int col = i / nk, kk = i - col * nk, k = k0 + kk;
+          if (c0 + col >= nc) continue;
+          const size_t ic = (size_t)(c0 + col) * nlev + k;
+          const float* m0 = reinterpret_cast<const float*>(B_cp + kk * kCW + col);
+          a.m_w[(size_t)(c0 + col) * nlevp + k] = m0[0];
+          if (a.m_rho) {
+            a.m_rho[ic] = m0[1];
+            a.m_th[ic] = reinterpret_cast<const float*>(B_rp + kk * kCW + col)[0];
+          }
         }
       }
     }
@@ -341,17 +419,22 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
 
 }  // namespace
 
+// Mixed precision (FP32 stencil inputs) solves in double-word FP32 arithmetic;
+// the FP64 mode in FP64.
+template <class T>
+using ColArith = typename std::conditional<std::is_same<T, float>::value, df, double>::type;
+
 cudaError_t init_column_kernels() {
   cudaError_t e = cudaFuncSetAttribute(sn_column_tiled<double, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes<8>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 8, df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<8>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sn_column_tiled<double, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<4>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 4, df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<4>());
   return e;
 }
@@ -396,11 +479,11 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
   const char* name = mixed ? (corrector ? "sn_column_corr_mx" : "sn_column_pred_mx")
                            : (corrector ? "sn_column_corr" : "sn_column_pred");
   if (en.col_kc == 4)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4>), en.g64.nc, en.v, en.sc,
-                     corrector, a);
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4, ColArith<T>>), en.g64.nc,
+                     en.v, en.sc, corrector, a);
   else
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8>), en.g64.nc, en.v, en.sc,
-                     corrector, a);
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8, ColArith<T>>), en.g64.nc,
+                     en.v, en.sc, corrector, a);
 }
 
 template void launch_column<double>(const Engine&, int, const StateView&, const double*, const double*, cudaStream_t);
@@ -426,7 +509,8 @@ namespace {
 
 constexpr int kNoallocMaxLev = 256;
 constexpr size_t kNoallocStride = 512;                 // doubles per vertical-metric slot
-constexpr size_t kNoallocCoef = 8192;                  // doubles of the vertical-metric section
+constexpr size_t kNoallocCoef = 10752;                 // doubles of the vertical-metric section
+constexpr size_t kNoallocLevHL = 6400;                 // offset of the double-word level table
 constexpr size_t kNoallocDoubles = (size_t)8 << 20;    // 64 MiB in total
 constexpr size_t kNoallocPlanes = 8;                   // 7 Thomas planes + zb
 constexpr size_t kNoallocMaxPoints = (kNoallocDoubles - kNoallocCoef) / kNoallocPlanes;
@@ -453,6 +537,9 @@ int noalloc_setup(double** out) {
     if (e != cudaSuccess)
       return report_error(ICON_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     e = cudaFuncSetAttribute(sn_column_tiled<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(sn_column_tiled<double, true, kKC, df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmem);
     if (e != cudaSuccess)
       return report_error(ICON_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     g_noalloc_ptr[dev] = ptr;
@@ -562,6 +649,7 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
       cf[7] = 1.0 - wgt[k];
     }
   }
+  level_pairs_into(reinterpret_cast<float*>(coef + kNoallocLevHL), nlev, colc, ex_ref, th_ref, dz, ray, nullptr);
 
   double* base = nullptr;
   int rc = noalloc_setup(&base);
@@ -581,6 +669,7 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
   v.dexner_ref_ic = base + 6 * kNoallocStride;
   v.ray_fac = base + 7 * kNoallocStride;
   v.colc = base + 8 * kNoallocStride;
+  v.lev_hl = reinterpret_cast<const float*>(base + kNoallocLevHL);
   // every scratch plane the kernel reads is written earlier in the same call,
   // so nothing has to be cleared between calls
   ColArgs<double> a{};
@@ -601,7 +690,10 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
   a.exner_o = exner_new;
   a.theta_o = theta_new;
   const unsigned blocks = (unsigned)((n_cols + kCW - 1) / kCW);
-  sn_column_tiled<double, true><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
+  if (p->precision == ICON_PREC_MIXED)  // the mixed mode's double-word FP32 arithmetic
+    sn_column_tiled<double, true, kKC, df><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
+  else
+    sn_column_tiled<double, true><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(e));
   if (p->synchronous) {
