@@ -551,7 +551,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     return fail(ICON_ERR_CUDA, m);
   }
   for (int k = 0; k < kNumStencils; ++k) en.threads[k] = 256;
-  en.col_kc = 8;
+  en.col_kc = 4;
   if (p->autotune) {
     int rc = autotune(d);
     if (rc != ICON_OK) {

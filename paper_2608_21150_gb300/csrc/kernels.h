@@ -78,7 +78,7 @@ struct Engine {
   // launch configuration picked by the autotuner: threads per CTA of each
   // stencil kernel (by kernel id) and the level-chunk depth of the column solve
   int threads[32] = {};
-  int col_kc = 8;
+  int col_kc = 4;
 };
 
 // Rows A1-A4 on (vn, w) in compute type T: writes ddt_vn [ne*nlev] and ddt_w

@@ -35,7 +35,7 @@ namespace icon {
 namespace {
 
 constexpr int kCW = 64;          // columns (threads) per CTA
-constexpr int kKC = 8;           // default levels per chunk (the autotuner may pick 4)
+constexpr int kKC = 4;           // default levels per chunk (the autotuner may pick 8)
 constexpr int kLD = kCW + 1;     // padded tile row for column-gathered tiles
 // forward tiles: w, rho, exner, theta, ddt_w0, div_m, div_t, ddt_w1, rho_p, theta_p, zb
 constexpr int kTilesFwd = 11;
@@ -82,13 +82,31 @@ __device__ __forceinline__ void cp_async(float* dst, const float* src) { cp4(dst
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // tile[kk][col] = X[rows[col] * ld + k0 + kk] for kk < nk (level-contiguous
-// field; consecutive threads copy consecutive levels of one row)
-template <class T>
+// field; consecutive threads copy consecutive levels of one row).  Each of the
+// kCW threads makes exactly nk copies; with nk a compile-time constant (the
+// full chunks) the index split needs no run-time division.
+template <int NK, class T>
+__device__ __forceinline__ void tile_rows_n(T* tile, const T* __restrict__ X, int ld, const int* __restrict__ rows,
+                                            int k0) {
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const int i = threadIdx.x + j * kCW;
+    const int col = i / NK, kk = i - col * NK;
+    cp_async(tile + kk * kLD + col, X + (size_t)rows[col] * ld + k0 + kk);
+  }
+}
+template <int KC, class T>
 __device__ __forceinline__ void tile_rows(T* tile, const T* __restrict__ X, int ld, const int* __restrict__ rows,
                                           int k0, int nk) {
-  for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
-    const int col = i / nk, kk = i - col * nk;
-    cp_async(tile + kk * kLD + col, X + (size_t)rows[col] * ld + k0 + kk);
+  if (nk == KC + 1) {
+    tile_rows_n<KC + 1>(tile, X, ld, rows, k0);
+  } else if (nk == KC) {
+    tile_rows_n<KC>(tile, X, ld, rows, k0);
+  } else {
+    for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
+      const int col = i / nk, kk = i - col * nk;
+      cp_async(tile + kk * kLD + col, X + (size_t)rows[col] * ld + k0 + kk);
+    }
   }
 }
 
@@ -100,11 +118,66 @@ __device__ __forceinline__ void tile_levels(double* tile, int ldt, const double*
   for (int kk = 0; kk < nk; ++kk) cp8(tile + kk * ldt + col, X + (size_t)(k0 + kk) * nc + cc);
 }
 
+template <int NK>
+__device__ __forceinline__ void store_tile_n(const double* __restrict__ tile, double* X, int ld, int c0, int nc,
+                                             int k0) {
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const int i = threadIdx.x + j * kCW;
+    const int col = i / NK, kk = i - col * NK;
+    if (c0 + col < nc) X[(size_t)(c0 + col) * ld + k0 + kk] = tile[kk * kLD + col];
+  }
+}
+template <int KC>
 __device__ __forceinline__ void store_tile(const double* __restrict__ tile, double* X, int ld, int c0, int nc,
                                            int k0, int nk) {
-  for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
-    const int col = i / nk, kk = i - col * nk;
-    if (c0 + col < nc) X[(size_t)(c0 + col) * ld + k0 + kk] = tile[kk * kLD + col];
+  if (nk == KC) {
+    store_tile_n<KC>(tile, X, ld, c0, nc, k0);
+  } else {
+    for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
+      const int col = i / nk, kk = i - col * nk;
+      if (c0 + col < nc) X[(size_t)(c0 + col) * ld + k0 + kk] = tile[kk * kLD + col];
+    }
+  }
+}
+
+// FP32 mirrors of a finished chunk (mixed mode), from the float pairs the
+// back-substitution left in its consumed scratch slots: (w, rho - rho_ref) in
+// m01[kk][col], theta_v - theta_ref in m2[kk][col]
+template <int NK>
+__device__ __forceinline__ void mirror_chunk_n(const double* m01, const double* m2, float* m_w, float* m_rho,
+                                               float* m_th, int nlev, int c0, int nc, int k0) {
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const int i = threadIdx.x + j * kCW;
+    const int col = i / NK, kk = i - col * NK, k = k0 + kk;
+    if (c0 + col >= nc) continue;
+    const float* m = reinterpret_cast<const float*>(m01 + kk * kCW + col);
+    m_w[(size_t)(c0 + col) * (nlev + 1) + k] = m[0];
+    if (m_rho) {
+      const size_t ic = (size_t)(c0 + col) * nlev + k;
+      m_rho[ic] = m[1];
+      m_th[ic] = reinterpret_cast<const float*>(m2 + kk * kCW + col)[0];
+    }
+  }
+}
+template <int KC>
+__device__ __forceinline__ void mirror_chunk(const double* m01, const double* m2, float* m_w, float* m_rho,
+                                             float* m_th, int nlev, int c0, int nc, int k0, int nk) {
+  if (nk == KC) {
+    mirror_chunk_n<KC>(m01, m2, m_w, m_rho, m_th, nlev, c0, nc, k0);
+  } else {
+    for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
+      const int col = i / nk, kk = i - col * nk, k = k0 + kk;
+      if (c0 + col >= nc) continue;
+      const float* m = reinterpret_cast<const float*>(m01 + kk * kCW + col);
+      m_w[(size_t)(c0 + col) * (nlev + 1) + k] = m[0];
+      if (m_rho) {
+        const size_t ic = (size_t)(c0 + col) * nlev + k;
+        m_rho[ic] = m[1];
+        m_th[ic] = reinterpret_cast<const float*>(m2 + kk * kCW + col)[0];
+      }
+    }
   }
 }
 
@@ -226,17 +299,17 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
     const int nkf = min(KC + 1, nlev - k0);   // full levels loaded (one lookahead)
     const int nkh = min(KC + 1, nlevp - k0);  // half levels loaded
     __syncthreads();
-    tile_rows(T_w, a.w, nlevp, rows_c, k0, nkh);
-    tile_rows(T_rho, a.rho, nlev, rows_c, k0, nkf);
-    tile_rows(T_pi, a.exner, nlev, rows_c, k0, nkf);
-    tile_rows(T_th, a.theta, nlev, rows_c, k0, nkf);
-    tile_rows(T_dw0, a.ddt_w0, nlevp, rows_c, k0, nkh);
-    tile_rows(T_dm, a.div_m, nlev, rows_c, k0, nkc);
-    tile_rows(T_dt, a.div_t, nlev, rows_c, k0, nkc);
+    tile_rows<KC>(T_w, a.w, nlevp, rows_c, k0, nkh);
+    tile_rows<KC>(T_rho, a.rho, nlev, rows_c, k0, nkf);
+    tile_rows<KC>(T_pi, a.exner, nlev, rows_c, k0, nkf);
+    tile_rows<KC>(T_th, a.theta, nlev, rows_c, k0, nkf);
+    tile_rows<KC>(T_dw0, a.ddt_w0, nlevp, rows_c, k0, nkh);
+    tile_rows<KC>(T_dm, a.div_m, nlev, rows_c, k0, nkc);
+    tile_rows<KC>(T_dt, a.div_t, nlev, rows_c, k0, nkc);
     if (corrector) {
-      tile_rows(T_dw1, a.ddt_w1, nlevp, rows_c, k0, nkh);
-      tile_rows(T_rp, a.rho_p, nlev, rows_c, k0, nkf);
-      tile_rows(T_tp, a.theta_p, nlev, rows_c, k0, nkf);
+      tile_rows<KC>(T_dw1, a.ddt_w1, nlevp, rows_c, k0, nkh);
+      tile_rows<KC>(T_rp, a.rho_p, nlev, rows_c, k0, nkf);
+      tile_rows<KC>(T_tp, a.theta_p, nlev, rows_c, k0, nkf);
       if (!kOwnZb) tile_levels(T_zb, kLD, a.zbl, nc, c0, k0, nkc);
     }
     cp_wait();
@@ -390,25 +463,12 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
       }
     }
     __syncthreads();
-    store_tile(O_w, a.w_o, nlevp, c0, nc, k0, nk);
-    store_tile(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
-    store_tile(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
-    store_tile(O_th, a.theta_o, nlev, c0, nc, k0, nk);
+    store_tile<KC>(O_w, a.w_o, nlevp, c0, nc, k0, nk);
+    store_tile<KC>(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
+    store_tile<KC>(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
+    store_tile<KC>(O_th, a.theta_o, nlev, c0, nc, k0, nk);
     if constexpr (kDW) {
-      if (a.m_w) {
-        // FP32 mirrors for the mixed-mode stencils
-        for (int i = threadIdx.x; i < nk * kCW; i += kCW) {
-          const int col = i / nk, kk = i - col * nk, k = k0 + kk;
-          if (c0 + col >= nc) continue;
-          const size_t ic = (size_t)(c0 + col) * nlev + k;
-          const float* m0 = reinterpret_cast<const float*>(B_cp + kk * kCW + col);
-          a.m_w[(size_t)(c0 + col) * nlevp + k] = m0[0];
-          if (a.m_rho) {
-            a.m_rho[ic] = m0[1];
-            a.m_th[ic] = reinterpret_cast<const float*>(B_rp + kk * kCW + col)[0];
-          }
-        }
-      }
+      if (a.m_w) mirror_chunk<KC>(B_cp, B_rp, a.m_w, a.m_rho, a.m_th, nlev, c0, nc, k0, nk);
     }
   }
   if (active) {
