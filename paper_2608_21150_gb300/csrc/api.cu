@@ -1,6 +1,7 @@
 // C-ABI entry points of the dycore library (paper Sec. 4.3: the host model
 // gathers field pointers and calls a C function; scalars by value, arrays by
 // reference without copies, device arrays accepted directly).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,8 +103,11 @@ struct icon_dycore {
   bool have_staging = false;
   // learned corrector (allocated on first use): saved input state, features, norm partials
   StateView saved{};
-  float *colx = nullptr, *edgex = nullptr;
-  double *partial = nullptr, *status = nullptr;
+  float* colx = nullptr;                                  // raw column features [nc][5 nlev]
+  __nv_bfloat16 *col16 = nullptr, *edge16 = nullptr;     // network inputs [nc][ld_col16], [ne][ld_edge16]
+  int ld_col16 = 0, ld_edge16 = 0;
+  float* partial = nullptr;
+  double* status = nullptr;
   int partial_cap = 0;
 };
 
@@ -585,9 +589,10 @@ int icon_dycore_destroy(icon_dycore_t* d) {
     cudaFree(d->saved.theta_v);
     cudaFree(d->saved.exner_pr);
     cudaFree(d->colx);
-    cudaFree(d->edgex);
     cudaFree(d->status);
   }
+  if (d->col16) cudaFree(d->col16);
+  if (d->edge16) cudaFree(d->edge16);
   if (d->partial) cudaFree(d->partial);
   d->arena.release();
   if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
@@ -966,7 +971,7 @@ bool on_device(const icon_state_t* s) {
 
 StateView view(const icon_state_t* s) { return StateView{s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr}; }
 
-int learned_buffers(icon_dycore* d, int partials) {
+int learned_buffers(icon_dycore* d, int partials, int ldc, int lde) {
   const HostGrid& h = d->grid->host;
   const size_t nlev = d->nlev, ef = (size_t)h.ne * nlev, cf = (size_t)h.nc * nlev, ch = (size_t)h.nc * (nlev + 1);
   if (!d->colx) {
@@ -978,13 +983,27 @@ int learned_buffers(icon_dycore* d, int partials) {
     CUDA_TRY(cudaMalloc(&g.theta_v, cf * 8));
     CUDA_TRY(cudaMalloc(&g.exner_pr, cf * 8));
     CUDA_TRY(cudaMalloc(&d->colx, cf * 5 * 4));
-    CUDA_TRY(cudaMalloc(&d->edgex, ef * 11 * 4));
-    CUDA_TRY(cudaMalloc(&d->status, 2 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&d->status, (2 + (size_t)reduce_stage_doubles()) * sizeof(double)));
+  }
+  // BF16 network inputs; the pad columns stay zero (the kernels write only the features)
+  if (ldc != d->ld_col16) {
+    if (d->col16) cudaFree(d->col16);
+    d->col16 = nullptr;
+    CUDA_TRY(cudaMalloc(&d->col16, (size_t)h.nc * ldc * sizeof(__nv_bfloat16)));
+    CUDA_TRY(cudaMemset(d->col16, 0, (size_t)h.nc * ldc * sizeof(__nv_bfloat16)));
+    d->ld_col16 = ldc;
+  }
+  if (lde != d->ld_edge16) {
+    if (d->edge16) cudaFree(d->edge16);
+    d->edge16 = nullptr;
+    CUDA_TRY(cudaMalloc(&d->edge16, (size_t)h.ne * lde * sizeof(__nv_bfloat16)));
+    CUDA_TRY(cudaMemset(d->edge16, 0, (size_t)h.ne * lde * sizeof(__nv_bfloat16)));
+    d->ld_edge16 = lde;
   }
   if (partials > d->partial_cap) {
     if (d->partial) cudaFree(d->partial);
     d->partial = nullptr;
-    CUDA_TRY(cudaMalloc(&d->partial, (size_t)partials * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&d->partial, (size_t)partials * sizeof(float)));
     d->partial_cap = partials;
   }
   return ICON_OK;
@@ -1023,8 +1042,8 @@ int icon_corrector_features(icon_dycore_t* d, const icon_state_t* s, float* col_
   if (!d || !s || !col_x || !edge_x) return fail(ICON_ERR_ARG, "icon_corrector_features: NULL argument");
   if (!on_device(s)) return fail(ICON_ERR_ARG, "icon_corrector_features: the state must be on the device");
   const StateView st = view(s);
-  launch_col_features(d->en, st, col_x, d->stream);
-  launch_edge_features(d->en, col_x, st.vn, nullptr, nullptr, edge_x, d->stream);
+  launch_col_features(d->en, st, col_x, nullptr, 0, nullptr, nullptr, d->stream);
+  launch_edge_features(d->en, col_x, st.vn, edge_x, 11 * d->nlev, nullptr, nullptr, d->stream);
   CUDA_TRY(cudaGetLastError());
   if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
   return ICON_OK;
@@ -1061,7 +1080,7 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
   int pc = 0, pe = 0;
   for (int r0 = 0; r0 < nc; r0 += mbc) pc += apply_partials((size_t)std::min(mbc, nc - r0) * (3 * nlev - 1));
   for (int r0 = 0; r0 < ne; r0 += mbe) pe += apply_partials((size_t)std::min(mbe, ne - r0) * nlev);
-  rc = learned_buffers(reduced, pc + pe);
+  rc = learned_buffers(reduced, pc + pe, mlp_input_ld(col_net), mlp_input_ld(edge_net));
   if (rc != ICON_OK) return rc;
   icon_dycore* d = reduced;
   cudaStream_t stream = d->stream;
@@ -1074,20 +1093,19 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
   rc = run(d, s, Op::kStep, fn);
   d->params.synchronous = sync;
   if (rc != ICON_OK) return rc;
-  // 3. features of the reduced state (edge features first: they read the raw column features)
-  const float *cxm, *cxs, *cym, *cys, *exm, *exs, *eym, *eys;
-  mlp_norm(col_net, &cxm, &cxs, &cym, &cys);
-  mlp_norm(edge_net, &exm, &exs, &eym, &eys);
-  launch_col_features(d->en, st, d->colx, stream);
-  launch_edge_features(d->en, d->colx, st.vn, exm, exs, d->edgex, stream);
-  launch_normalise((size_t)nc, 5 * nlev, d->colx, cxm, cxs, stream);
+  // 3. features of the reduced state, normalised, as the networks' BF16 input rows
+  const float *cxm, *cxi, *cym, *cys, *exm, *exi, *eym, *eys;
+  mlp_norm(col_net, &cxm, &cxi, &cym, &cys);
+  mlp_norm(edge_net, &exm, &exi, &eym, &eys);
+  launch_col_inputs(d->en, st, d->colx, d->col16, d->ld_col16, cxm, cxi, stream);
+  launch_edge_inputs(d->en, d->colx, st.vn, d->edge16, d->ld_edge16, exm, exi, stream);
   // 4. both networks over row chunks, increments applied as each chunk comes out
   int off = 0;
   for (int r0 = 0; r0 < nc; r0 += mbc) {
     const int rows = std::min(mbc, nc - r0);
     const float* y;
     int ldy;
-    rc = mlp_forward_rows(col_net, d->colx + (size_t)r0 * 5 * nlev, rows, &y, &ldy, stream);
+    rc = mlp_forward_rows(col_net, d->col16 + (size_t)r0 * d->ld_col16, d->ld_col16, rows, &y, &ldy, stream);
     if (rc != ICON_OK) return rc;
     launch_apply_col(d->en, r0, rows, y, ldy, cym, cys, st, d->partial + off, stream);
     off += apply_partials((size_t)rows * (3 * nlev - 1));
@@ -1096,13 +1114,13 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
     const int rows = std::min(mbe, ne - r0);
     const float* y;
     int ldy;
-    rc = mlp_forward_rows(edge_net, d->edgex + (size_t)r0 * 11 * nlev, rows, &y, &ldy, stream);
+    rc = mlp_forward_rows(edge_net, d->edge16 + (size_t)r0 * d->ld_edge16, d->ld_edge16, rows, &y, &ldy, stream);
     if (rc != ICON_OK) return rc;
     launch_apply_edge(d->en, r0, rows, y, ldy, eym, eys, st.vn, d->partial + off, stream);
     off += apply_partials((size_t)rows * nlev);
   }
   // 5. the check: RMS of the normalised increments of each network (NaN if anything is non-finite)
-  launch_reduce_status(d->partial, pc, pe, d->status, stream);
+  launch_reduce_status(d->partial, pc, pe, d->status + 2, d->status, stream);
   CUDA_TRY(cudaGetLastError());
   double ss[2] = {0.0, 0.0};
   int tc_err = 0;

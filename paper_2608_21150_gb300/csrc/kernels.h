@@ -1,5 +1,6 @@
 // Kernel launch interface of the dycore library (internal).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -111,21 +112,29 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
 int diag_partials(int nc);
 void launch_diagnostics(const Engine& en, const double* area, const StateView& st, double* ps, double* t850,
                         double* partial, int* bad, cudaStream_t s);
-// Learned corrector: raw column features [nc][5 nlev]; edge features [ne][11 nlev]
-// (normalised when mean/std are given); in-place normalisation; increments of
-// rows [row0, row0 + rows) applied to the state with per-block partial sums of
-// the squared normalised outputs (apply_partials(n) blocks for n outputs);
-// their two sums; training targets (plain - reduced).
-void launch_col_features(const Engine& en, const StateView& st, float* x, cudaStream_t s);
-void launch_edge_features(const Engine& en, const float* colx, const double* vn, const float* mean,
-                          const float* stdv, float* x, cudaStream_t s);
-void launch_normalise(size_t n, int nf, float* x, const float* mean, const float* stdv, cudaStream_t s);
+// Learned corrector.  Column features (one thread per cell-level): raw FP32
+// rows [nc][5 nlev] into raw (if given) and rows [nc][ldx] into x (normalised
+// by mean/istd when given; the BF16 form always normalises: the network's
+// input).  Edge features [ne][ldx] from the raw column features and vn.
+// Increments of rows [row0, row0 + rows) applied to the state with per-block
+// FP32 partial sums of the squared normalised outputs (apply_partials(n)
+// blocks for n outputs); their two sums in FP64; training targets (plain -
+// reduced).
+void launch_col_features(const Engine& en, const StateView& st, float* raw, float* x, int ldx, const float* mean,
+                         const float* istd, cudaStream_t s);
+void launch_col_inputs(const Engine& en, const StateView& st, float* raw, __nv_bfloat16* x, int ldx,
+                       const float* mean, const float* istd, cudaStream_t s);
+void launch_edge_features(const Engine& en, const float* colx, const double* vn, float* x, int ldx,
+                          const float* mean, const float* istd, cudaStream_t s);
+void launch_edge_inputs(const Engine& en, const float* colx, const double* vn, __nv_bfloat16* x, int ldx,
+                        const float* mean, const float* istd, cudaStream_t s);
 int apply_partials(size_t n);
 void launch_apply_col(const Engine& en, int row0, int rows, const float* y, int ldy, const float* mean,
-                      const float* stdv, const StateView& st, double* partial, cudaStream_t s);
+                      const float* stdv, const StateView& st, float* partial, cudaStream_t s);
 void launch_apply_edge(const Engine& en, int row0, int rows, const float* y, int ldy, const float* mean,
-                       const float* stdv, double* vn, double* partial, cudaStream_t s);
-void launch_reduce_status(const double* partial, int n0, int n1, double* out, cudaStream_t s);
+                       const float* stdv, double* vn, float* partial, cudaStream_t s);
+int reduce_stage_doubles();  // scratch doubles of launch_reduce_status
+void launch_reduce_status(const float* partial, int n0, int n1, double* stage, double* out, cudaStream_t s);
 void launch_targets(const Engine& en, const StateView& reduced, const StateView& plain, float* col_y, float* edge_y,
                     cudaStream_t s);
 // One-time kernel attributes (dynamic shared memory above 48 KB).

@@ -30,16 +30,30 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return cdf + x * pdf;
 }
 
+// GELU for the forward epilogue, with erf from Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26 (|error| <= 1.5e-7, far below the
+// BF16 rounding of the stored activation): erf(x) = 1 - (a1 t + ... + a5 t^5)
+// exp(-x^2), t = 1/(1 + p x), x >= 0, odd extension.
+__device__ __forceinline__ float gelu_fwd(float x) {
+  const float z = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  const float e = 1.0f - poly * __expf(-z * z);
+  return 0.5f * x * (1.0f + copysignf(e, x));
+}
+
 // ---------------------------------------------------------------------------
 // Tensor-core GEMM (tcgen05): one 128 x 128 output tile per CTA, K in blocks
 // of 64 (one 128-byte swizzle row of BF16) through a 3-stage TMA ring.
 // Warp 0 (one lane) issues the TMA loads, warp 1 (one lane) the MMAs into a
-// 128-column FP32 accumulator in tensor memory; then all four warps read the
-// accumulator back (warp w owns TMEM lanes 32w..32w+31 = tile rows) and apply
-// the epilogue.  96 KB of shared memory: two CTAs per SM, so one CTA's
-// epilogue overlaps the other's main loop.
+// 128-column FP32 accumulator in tensor memory; then all eight warps read the
+// accumulator back and apply the epilogue: warp w may access TMEM lanes
+// 32 (w % 4) .. +31 (= tile rows), and warps w and w + 4 split the columns.
+// 96 KB of shared memory: two CTAs per SM, so one CTA's epilogue overlaps the
+// other's main loop.
 constexpr int TBM = 128, TBN = 128, TBK = 64, kStages = 3;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
 constexpr int kTileBytesA = TBM * TBK * 2, kTileBytesB = TBN * TBK * 2;
 constexpr int kTcSmem = kStages * (kTileBytesA + kTileBytesB) + 1024 /* alignment slack */ + 128 /* barriers */;
 constexpr uint32_t kTmemCols = TBN;
@@ -219,15 +233,17 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CU
   }
   __syncwarp();
 
-  // epilogue: thread (warp, lane) owns tile row 32 warp + lane
+  // epilogue: thread (warp, lane) owns tile row 32 (warp % 4) + lane, columns
+  // (warp / 4) TBN/2 .. +TBN/2
   // warp-uniform decision: the tcgen05.ld below is a warp-collective instruction
   const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
   tc_fence_after();
   if (ok) {
-    const int row = m0 + 32 * warp + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = m0 + 32 * quarter + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll 1
-    for (int c = 0; c < TBN; c += 16) {
+    for (int c = half * (TBN / 2); c < (half + 1) * (TBN / 2); c += 16) {
       float v[16];
       tmem_ld16(trow + (uint32_t)c, v);
       const int col0 = n0 + c;
@@ -237,9 +253,19 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CU
       const bool vec32 = whole && (o & 3) == 0;   // 16-byte aligned fp32 run
       const bool vec16 = whole && (o & 7) == 0;   // 16-byte aligned bf16 run
       if (ep.bias) {
+        if (whole) {
+          const float4* b4 = reinterpret_cast<const float4*>(ep.bias + col0);  // col0 % 16 == 0, bias 16-byte aligned
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (whole || col0 + j < N) v[j] += ep.bias[col0 + j];
+          for (int q = 0; q < 4; ++q) {
+            const float4 bq = __ldg(b4 + q);
+            v[4 * q] += bq.x;
+            v[4 * q + 1] += bq.y;
+            v[4 * q + 2] += bq.z;
+            v[4 * q + 3] += bq.w;
+          }
+        } else {
+          for (int j = 0; j < 16 && col0 + j < N; ++j) v[j] += ep.bias[col0 + j];
+        }
       }
       if (ep.mode == 0) {
         if (vec32) {
@@ -262,12 +288,12 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CU
         if (vec16) {
           __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16(gelu(v[j]));
+          for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16(gelu_fwd(v[j]));
           uint4* dst = reinterpret_cast<uint4*>(ep.out_bf16 + o);
           dst[0] = reinterpret_cast<const uint4*>(h)[0];
           dst[1] = reinterpret_cast<const uint4*>(h)[1];
         } else {
-          for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_bf16[o + j] = __float2bfloat16(gelu(v[j]));
+          for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_bf16[o + j] = __float2bfloat16(gelu_fwd(v[j]));
         }
       }
     }
@@ -413,7 +439,7 @@ int mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bf
              const float* bias, bool gelu_act, float* out_f32, __nv_bfloat16* out_bf16, float* zpre, int ldc,
              cudaStream_t s) {
   if (M < 1 || N < 1 || K < TBK || K % TBK || lda % 8 || ldb % 8 || ldc < N || lda < K || ldb < K ||
-      (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) % 16)
+      (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(bias)) % 16)
     return report_error(ICON_ERR_ARG, "mlp_gemm: unsupported shape or alignment");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return report_error(ICON_ERR_CUDA, "mlp_gemm: device");

@@ -35,12 +35,15 @@ void mlp_mse(int B, int n_out, const float* y, int ldy, const float* t, int ldt,
 // up a bounded wait; sticky).
 const int* mlp_tc_error_flag();
 
-// Forward pass of rows [B][n_in] (normalised FP32, DEVICE) without synchronising;
-// B <= max_batch.  *y points at the network's own output rows [B][*ldy], valid
-// until its next call.
-int mlp_forward_rows(icon_mlp_t* m, const float* x, int B, const float** y, int* ldy, cudaStream_t s);
+// Forward pass of normalised BF16 input rows x16 [B][ldx] (DEVICE; ldx >=
+// mlp_input_ld(m), pads zero) without synchronising; B <= max_batch.  *y points
+// at the network's own output rows [B][*ldy], valid until its next call.
+int mlp_forward_rows(icon_mlp_t* m, const __nv_bfloat16* x16, int ldx, int B, const float** y, int* ldy,
+                     cudaStream_t s);
+int mlp_input_ld(const icon_mlp_t* m);
 int mlp_dims(const icon_mlp_t* m, int* n_in, int* n_out, int* max_batch);
-// normalisation statistics (DEVICE, FP32): x_mean/x_std [n_in], y_mean/y_std [n_out]; null if unset
-void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xs, const float** ym, const float** ys);
+// normalisation statistics (DEVICE, FP32): x_mean and 1/x_std [n_in], y_mean and
+// y_std [n_out]; null if unset
+void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xis, const float** ym, const float** ys);
 
 }  // namespace icon

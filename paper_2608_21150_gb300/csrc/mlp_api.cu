@@ -28,7 +28,7 @@ struct icon_mlp {
   float *dy, *dh, *dz32;
   __nv_bfloat16 *dz16, *dzT, *hT;
   double* rowloss;
-  float *x_mean = nullptr, *x_std = nullptr, *y_mean = nullptr, *y_std = nullptr;
+  float *x_mean = nullptr, *x_istd = nullptr, *y_mean = nullptr, *y_std = nullptr;  // normalisation
 };
 
 namespace {
@@ -58,18 +58,26 @@ int64_t param_count(const icon_mlp* m) {
   return n;
 }
 
+// The three layers on BF16 input rows x16 [B][ldx] (ldx >= lds[0], pads zero);
 // keep_z: store the FP32 pre-activations a following backward needs
-int forward(icon_mlp* m, const float* x, int B, cudaStream_t s, bool keep_z = true) {
-  mlp_to_bf16(B, m->dims[0], x, m->dims[0], m->x16, m->lds[0], s);
-  const __nv_bfloat16* in = m->x16;
+int forward_from(icon_mlp* m, const __nv_bfloat16* x16, int ldx, int B, cudaStream_t s, bool keep_z) {
+  const __nv_bfloat16* in = x16;
+  int ld = ldx;
   for (int l = 0; l < 2; ++l) {
-    int rc = mlp_gemm(B, layer_out(m, l), m->lds[l], in, m->lds[l], m->wt16[l], m->lds[l], m->b[l], true, nullptr,
+    int rc = mlp_gemm(B, layer_out(m, l), m->lds[l], in, ld, m->wt16[l], m->lds[l], m->b[l], true, nullptr,
                       m->h16[l], keep_z ? m->z[l] : nullptr, m->lds[l + 1], s);
     if (rc != ICON_OK) return rc;
     in = m->h16[l];
+    ld = m->lds[l + 1];
   }
   return mlp_gemm(B, layer_out(m, 2), m->lds[2], in, m->lds[2], m->wt16[2], m->lds[2], m->b[2], false, m->y, nullptr,
                   nullptr, m->lds[3], s);
+}
+
+// FP32 input rows [B][n_in]: converted into the network's own BF16 buffer first
+int forward(icon_mlp* m, const float* x, int B, cudaStream_t s, bool keep_z = true) {
+  mlp_to_bf16(B, m->dims[0], x, m->dims[0], m->x16, m->lds[0], s);
+  return forward_from(m, m->x16, m->lds[0], B, s, keep_z);
 }
 
 // gradients of all parameters for dL/dy in m->dy (fp32 [B][lds[3]]), after
@@ -140,23 +148,26 @@ int check_batch(const icon_mlp* m, int B, const char* fn) {
 }  // namespace
 
 namespace icon {
-int mlp_forward_rows(icon_mlp_t* m, const float* x, int B, const float** y, int* ldy, cudaStream_t s) {
+int mlp_forward_rows(icon_mlp_t* m, const __nv_bfloat16* x16, int ldx, int B, const float** y, int* ldy,
+                     cudaStream_t s) {
   if (B < 1 || B > m->max_batch) return fail_m(ICON_ERR_ARG, "corrector: batch out of range");
-  const int rc = forward(m, x, B, s, false);
+  if (ldx < m->lds[0]) return fail_m(ICON_ERR_ARG, "corrector: input rows too short");
+  const int rc = forward_from(m, x16, ldx, B, s, false);
   if (rc != ICON_OK) return rc;
   *y = m->y;
   *ldy = m->lds[3];
   return ICON_OK;
 }
+int mlp_input_ld(const icon_mlp_t* m) { return m->lds[0]; }
 int mlp_dims(const icon_mlp_t* m, int* n_in, int* n_out, int* max_batch) {
   *n_in = m->dims[0];
   *n_out = m->dims[3];
   *max_batch = m->max_batch;
   return ICON_OK;
 }
-void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xs, const float** ym, const float** ys) {
+void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xis, const float** ym, const float** ys) {
   *xm = m->x_mean;
-  *xs = m->x_std;
+  *xis = m->x_istd;
   *ym = m->y_mean;
   *ys = m->y_std;
 }
@@ -167,15 +178,20 @@ extern "C" {
 int icon_mlp_set_normalization(icon_mlp_t* m, const float* x_mean, const float* x_std, const float* y_mean,
                                const float* y_std) {
   if (!m || !x_mean || !x_std || !y_mean || !y_std) return fail_m(ICON_ERR_ARG, "icon_mlp_set_normalization: NULL");
+  std::vector<float> istd(m->dims[0]);
+  for (int j = 0; j < m->dims[0]; ++j) {
+    if (!(x_std[j] > 0.0f)) return fail_m(ICON_ERR_ARG, "icon_mlp_set_normalization: x_std must be positive");
+    istd[j] = 1.0f / x_std[j];
+  }
   cudaError_t st = cudaSuccess;
   if (!m->x_mean) {
     m->x_mean = alloc<float>(m, m->dims[0], st);
-    m->x_std = alloc<float>(m, m->dims[0], st);
+    m->x_istd = alloc<float>(m, m->dims[0], st);
     m->y_mean = alloc<float>(m, m->dims[3], st);
     m->y_std = alloc<float>(m, m->dims[3], st);
   }
   if (st == cudaSuccess) st = cudaMemcpy(m->x_mean, x_mean, m->dims[0] * 4, cudaMemcpyHostToDevice);
-  if (st == cudaSuccess) st = cudaMemcpy(m->x_std, x_std, m->dims[0] * 4, cudaMemcpyHostToDevice);
+  if (st == cudaSuccess) st = cudaMemcpy(m->x_istd, istd.data(), m->dims[0] * 4, cudaMemcpyHostToDevice);
   if (st == cudaSuccess) st = cudaMemcpy(m->y_mean, y_mean, m->dims[3] * 4, cudaMemcpyHostToDevice);
   if (st == cudaSuccess) st = cudaMemcpy(m->y_std, y_std, m->dims[3] * 4, cudaMemcpyHostToDevice);
   if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_set_normalization: ") + cudaGetErrorString(st));

@@ -263,7 +263,7 @@ def test_result_does_not_depend_on_the_chunk_size(trained):
     fb, rb = P.step_learned(trained["R"], trained["Pl"], c2, e2, sb, 3.0)
     assert not fa and not fb
     assert all(torch_equal(sa[k], sb[k]) for k in sa)
-    assert ra == pytest.approx(rb, rel=1e-12)
+    assert ra == pytest.approx(rb, rel=1e-5)   # FP32 per-block partial sums follow the chunking
 
 
 def test_argument_errors(trained):
