@@ -212,10 +212,12 @@ def measure(P, G, z, st0, prec, args, dev, world):
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push(prec + "_timed")   # marks the timed steps for profiler filters
     e0.record(stream)
     for _ in range(args.steps):
         D.step(t)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
@@ -306,12 +308,14 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     fallbacks, norms = 0, []
+    torch.cuda.nvtx.range_push("learned_timed")
     e0.record(stream)
     for _ in range(args.steps):
         fb, r = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
         fallbacks += int(fb)
         norms.append(r)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
@@ -335,8 +339,8 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
     out = {"value": world * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
            "fallbacks_timed": fallbacks, "fallbacks_warmup": fallbacks_warm, "max_norm": L["max_norm"],
            "check_norm_mean": float(np.nanmean(norms)) if norms else None, "finite": finite,
-           "rms_ps_pa_vs_fp64": rms(ps.cpu().numpy() - f64_final["ps"]),
-           "rms_t850_k_vs_fp64": rms(t850.cpu().numpy() - f64_final["t850"]),
+           "rms_ps_pa_vs_fp64": rms(ps.cpu().numpy() - f64_final["ps"]) if f64_final else None,
+           "rms_t850_k_vs_fp64": rms(t850.cpu().numpy() - f64_final["t850"]) if f64_final else None,
            "error_vs_plain_step": {"reduced": er, "learned": el,
                                    "ratio": {k: el[k] / er[k] for k in er}},
            "train": {"seconds": train_s, "loss_col": [float(np.mean(lc[:10])), float(np.mean(lc[-50:]))],
@@ -346,6 +350,53 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
     for x in (cn, en, R, Pl):
         x.close()
     return out
+
+
+# The column solve's predictor and corrector launches are one kernel (one
+# function, two forms); the roofline treats them together.
+FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
+
+# DRAM bytes per launch of the FP64 column solve from an ncu capture at R2B5
+# L90 (profiles/sn_column_r2b5_l90.md), scaled to R2B6 by the column count (x4),
+# valid while the kernel source is the one captured (its SHA-256 below).
+COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
+                  "sha256": "0b1b674ce76ed82f1eee7487cdce646db86189ab47b8cf1883a4978da87de7c9",
+                  # mean of the predictor (2.077 GB) and corrector (3.235 GB) launches, FP64
+                  "bytes_per_launch_r2b5": 0.5 * (1.372084e9 + 0.704893e9 + 2.643417e9 + 0.591441e9)}
+
+
+def column_traffic(nc):
+    import hashlib
+    t = COLUMN_TRAFFIC
+    if not t["sha256"] or not t["bytes_per_launch_r2b5"]:
+        return None
+    try:
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes_per_launch_r2b5"] * nc / 81920
+
+
+def roofline(prof, nc, ne, nv, nlev):
+    """FP64-ALU roofline of the kernel family with the largest share of the step."""
+    fam = {}
+    for k, (n, ms) in prof.items():
+        f = FAMILY.get(k, k)
+        flops = FLOPS_PER_UNIT[k] * units_per_launch(k, nc, ne, nv, nlev) * n
+        a = fam.setdefault(f, [0, 0.0, 0.0])
+        a[0] += n
+        a[1] += ms
+        a[2] += flops
+    name, (n, ms, flops) = max(fam.items(), key=lambda kv: kv[1][1])
+    achieved = flops / (ms / 1000.0) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": column_traffic(nc) if name == "sn_column" else None,
+            "note": "FP64 algorithmic flops per launch / event-timed launch duration (CUDA events around every "
+                    "launch on the library's stream); peak = nominal FP64 rate from unit counts and clock "
+                    "(1.2 TFLOP/s measured by a DFMA probe); traffic = ncu DRAM bytes per launch"}
 
 
 def kernel_table(prof, nsteps):
@@ -382,72 +433,75 @@ def run_ours(args):
     Dref.close()
     st0["exner_pr"] = st0["exner"] - ex_ref[None, :]
 
-    f64, _ = measure(P, G, z, st0, "fp64", args, dev, world)
-    ms_per_step = f64["ms"] / args.steps
-    value = world * args.steps / (f64["ms"] / 1000.0)
-    prof, nsp = f64["prof"], f64["nsteps_prof"]
-    launches_per_step = sum(n for n, _ in prof.values()) // nsp
-    name, (nl, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    achieved = FLOPS_PER_UNIT[name] * units_per_launch(name, nc, ne, nv, nlev) / (tot_ms / nl / 1000.0) / 1e12
+    legs = set(args.legs.split(","))
+    f64, value, ms_per_step, roof, kernels, launches_per_step = None, None, None, None, None, 0
+    if "fp64" in legs:
+        f64, _ = measure(P, G, z, st0, "fp64", args, dev, world)
+        ms_per_step = f64["ms"] / args.steps
+        value = world * args.steps / (f64["ms"] / 1000.0)
+        prof, nsp = f64["prof"], f64["nsteps_prof"]
+        launches_per_step = sum(n for n, _ in prof.values()) // nsp
+        kernels = kernel_table(prof, nsp)
+        roof = roofline(prof, nc, ne, nv, nlev)
 
     mx = None
-    if not args.no_mixed:
+    if "mixed" in legs:
         m, _ = measure(P, G, z, st0, "mixed", args, dev, world)
         area = G.cell_areas()
         rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
         mx = {"value": world * args.steps / (m["ms"] / 1000.0), "ms_per_step": m["ms"] / args.steps,
-              "speedup_vs_fp64": f64["ms"] / m["ms"], "finite": m["finite"],
-              "rms_ps_pa": rms(m["ps"] - f64["ps"]), "rms_t850_k": rms(m["t850"] - f64["t850"]),
+              "speedup_vs_fp64": f64["ms"] / m["ms"] if f64 else None, "finite": m["finite"],
+              "rms_ps_pa": rms(m["ps"] - f64["ps"]) if f64 else None,
+              "rms_t850_k": rms(m["t850"] - f64["t850"]) if f64 else None,
               "compared_after_steps": args.warmup + args.steps,
               "reference": "FP64 GPU dycore (equal to the FP64 oracle to 1e-9 after 10 steps, GPU parity tests)",
               "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"],
               "autotuned_launch_config": m["launch_config"]}
 
     lrn = None
-    if not args.no_mixed and not args.no_learned:
+    if "learned" in legs:
         lrn = learned_leg(P, G, z, grid, st0, args, dev, world, f64)
-        lrn["speedup_vs_fp64"] = lrn["value"] / value
+        lrn["speedup_vs_fp64"] = lrn["value"] / value if value else None
         if mx:
             lrn["speedup_vs_mixed"] = lrn["value"] / mx["value"]
 
     # end to end through the C-ABI with host arrays (copies inside the timed region)
-    stream = torch.cuda.current_stream(dev)
-    e2e_steps = max(1, min(args.steps, 5))
-    host = {k: torch.from_numpy(v.copy()).pin_memory() for k, v in st0.items()}
-    D2 = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
-                             use_graph=1, synchronous=1, stream=stream.cuda_stream))
-    D2.step(host)  # warm-up: allocates the device staging copy and captures the graph
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        D2.step(host)
-    e2e_s = time.perf_counter() - t0
-    D2.close()
     sb = state_bytes(nc, ne, nlev)
+    e2e = None
+    if "fp64" in legs:
+        stream = torch.cuda.current_stream(dev)
+        e2e_steps = max(1, min(args.steps, 5))
+        host = {k: torch.from_numpy(v.copy()).pin_memory() for k, v in st0.items()}
+        D2 = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
+                                 use_graph=1, synchronous=1, stream=stream.cuda_stream))
+        D2.step(host)  # warm-up: allocates the device staging copy and captures the graph
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            D2.step(host)
+        e2e_s = time.perf_counter() - t0
+        D2.close()
+        e2e = {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb}
 
     hbm_bytes = compulsory_bytes_per_step(nc, ne, nlev, w["ndyn"])
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict("fp64"),
-        "sdpd": value / world * w["dtime"],
+        "sdpd": value / world * w["dtime"] if value else None,
         "hbm": {"compulsory_bytes_per_step": hbm_bytes,
                 "achieved_gbs": hbm_bytes / (ms_per_step / 1000.0) / 1e9,
                 "peak_gbs": 6663.9, "frac": hbm_bytes / (ms_per_step / 1000.0) / 1e9 / 6663.9,
                 "note": "compulsory (state read+write per substep and diffusion) bytes / step time; "
-                        "of measured peak"},
-        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "note": "FP64 algorithmic flops per launch / event-timed launch duration; peak = nominal "
-                             "FP64 rate from unit counts and clock (1.2 TFLOP/s measured by a DFMA probe)"},
-        "kernels": kernel_table(prof, nsp),
-        "autotuned_launch_config": f64["launch_config"],
+                        "of measured peak"} if ms_per_step else None,
+        "roofline": roof,
+        "kernels": kernels,
+        "autotuned_launch_config": f64["launch_config"] if f64 else None,
         "mixed": mx,
         "mixed_learned": lrn,
-        "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": sb,
-                "d2h_bytes_per_step": sb},
+        "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": f64["clocks"], "finite": f64["finite"],
+        "clocks": f64["clocks"] if f64 else None, "finite": f64["finite"] if f64 else None,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(nlev)
@@ -466,7 +520,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision (and learned) legs")
+    ap.add_argument("--legs", default="fp64,mixed,learned",
+                    help="comma-separated legs to run (fp64, mixed, learned); the headline value is the fp64 leg's")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision and learned legs")
     ap.add_argument("--no-learned", action="store_true", help="skip the mixed + learned-corrector leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["bisections"],
                     help="RnBm bisections (default 6 = R2B6); smaller grids only for profiler captures")
@@ -474,6 +530,14 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     WORKLOAD["bisections"] = args.grid
+    legs = [x for x in args.legs.split(",") if x]
+    if args.no_mixed:
+        legs = [x for x in legs if x not in ("mixed", "learned")]
+    if args.no_learned:
+        legs = [x for x in legs if x != "learned"]
+    if any(x not in ("fp64", "mixed", "learned") for x in legs):
+        ap.error("--legs takes fp64, mixed, learned")
+    args.legs = ",".join(legs)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
