@@ -179,6 +179,11 @@ int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
   v.v2e = A.upload(h.v2e);
   v.v2c = A.upload(h.v2c);
   v.div_c = A.upload(h.div_c);
+  {
+    std::vector<float> hl(2 * h.div_c.size());
+    for (size_t i = 0; i < h.div_c.size(); ++i) split_hl(h.div_c[i], &hl[2 * i]);
+    v.div_c_hl = A.upload(hl);
+  }
   v.lap_c = A.upload(h.lap_c);
   v.e2c_w = A.upload(h.e2c_w);
   v.grad_c = A.upload(h.grad_c);
@@ -467,6 +472,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     g.curl_v = up(h.curl_v);
     g.c2v_w = up(h.c2v_w);
     g.uv_w = up(h.uv_w);
+    g.div_c_hl = g0.div_c_hl;
     g.mean_area = (T)h.mean_area;
     VertT<T>& vt = x.v;
     vt.nlev = nlev;

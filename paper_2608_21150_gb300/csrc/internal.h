@@ -47,6 +47,7 @@ struct GridT {
   T mean_area;
   const double* cell_area;  // [nc] (diagnostics)
   const float* uv_c;        // [nc*6] east/north cell-velocity weights (corrector features)
+  const float* div_c_hl;    // [nc*3*2] div_c as double-word FP32 (hi, lo) pairs (mixed flux divergence)
 };
 using DevGrid = GridT<double>;
 

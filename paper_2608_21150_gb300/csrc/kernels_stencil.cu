@@ -17,6 +17,7 @@
 
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 
 namespace icon {
@@ -27,6 +28,12 @@ namespace {
 
 template <class T>
 constexpr bool kMixed = std::is_same<T, float>::value;
+
+// FP64 <-> FP32 without the FP64 pipe (mixed mode): exact widening, and
+// narrowing through the double-word split (round to nearest up to rare
+// double-rounding ties)
+__device__ __forceinline__ double f2d(float x) { return f2d_exact(x); }
+__device__ __forceinline__ float d2f(double x) { return to_float(to_df(x)); }
 
 __device__ __forceinline__ bool flat_index(int n_h, int nk, int& h, int& k) {
   unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,10 +263,20 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
   const T te = tu + (grad4[2 * n + iu] * dx + grad4[3 * n + iu] * dy);
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
   const size_t i0 = (size_t)c0 * nlev + k, i1 = (size_t)c1 * nlev + k;
-  const double pref = v.exner_ref[k];
-  const double pex0 = (1.0 + exfac) * (exner[i0] - pref) - exfac * exner_pr[i0];
-  const double pex1 = (1.0 + exfac) * (exner[i1] - pref) - exfac * exner_pr[i1];
-  const T h = sc.cpd * te * (T)((pex1 - pex0) * inv_d64[e]);
+  T h;
+  if constexpr (kMixed<T>) {
+    // extrapolated exner perturbations and their difference in double-word
+    // FP32: exner is near 1, the difference across an edge ~1e-5 of it
+    const df pref = to_df(v.exner_ref[k]), a = to_df(1.0 + exfac), b = to_df(exfac);
+    const df pex0 = a * (to_df(exner[i0]) - pref) - b * to_df(exner_pr[i0]);
+    const df pex1 = a * (to_df(exner[i1]) - pref) - b * to_df(exner_pr[i1]);
+    h = sc.cpd * te * (to_float(pex1 - pex0) * g.inv_d[e]);
+  } else {
+    const double pref = v.exner_ref[k];
+    const double pex0 = (1.0 + exfac) * (exner[i0] - pref) - exfac * exner_pr[i0];
+    const double pex1 = (1.0 + exfac) * (exner[i1] - pref) - exfac * exner_pr[i1];
+    h = sc.cpd * te * (T)((pex1 - pex0) * inv_d64[e]);
+  }
   rho_e[ie] = re;
   theta_e[ie] = te;
   hpg[ie] = h;
@@ -283,9 +300,13 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
   const T dd = (divd2[(size_t)c1 * nlev + k] - divd2[(size_t)c0 * nlev + k]) * g.inv_d[e];
   const T am = g.mean_area;
   const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - sc.divdamp * am * am * dd;
-  const double vnn = vn[ie] + (double)inc;
-  vn[ie] = vnn;
-  if constexpr (kMixed<T>) m_vn[ie] = (float)vnn;
+  if constexpr (kMixed<T>) {
+    const double vnn = vn[ie] + f2d(inc);
+    vn[ie] = vnn;
+    m_vn[ie] = d2f(vnn);
+  } else {
+    vn[ie] = vn[ie] + (double)inc;
+  }
 }
 
 // -------------------------------------------------------------------------
@@ -323,21 +344,42 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
   const int nlev = v.nlev;
   if (!flat_index(g.nc, nlev, c, k)) return;
   const int* ce = g.c2e + 3 * (size_t)c;
-  const double* dv = div_c64 + 3 * (size_t)c;
-  double dm = 0.0, dt = 0.0;
+  if constexpr (kMixed<T>) {
+    // FP32 fluxes, sums in double-word FP32: FP64-grade accumulation (mass
+    // conserved to about 2^-48 of the flux) without the slow FP64 pipe
+    const df* dv = reinterpret_cast<const df*>(g.div_c_hl) + 3 * (size_t)c;
+    df dm{0.f, 0.f}, dt{0.f, 0.f};
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int e = ce[j];
-    const size_t ie = (size_t)e * nlev + k;
-    const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-    const T vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
-    const T f = rho_e[ie] * vf;
-    const T ft = f * theta_e[ie];
-    dm += dv[j] * (double)f;
-    dt += dv[j] * (double)ft;
+    for (int j = 0; j < 3; ++j) {
+      const int e = ce[j];
+      const size_t ie = (size_t)e * nlev + k;
+      const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+      const T vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
+      const T f = rho_e[ie] * vf;
+      const T ft = f * theta_e[ie];
+      const df w = dv[j];
+      dm = dm + w * f;
+      dt = dt + w * ft;
+    }
+    div_m[(size_t)c * nlev + k] = to_double(dm);
+    div_t[(size_t)c * nlev + k] = to_double(dt);
+  } else {
+    const double* dv = div_c64 + 3 * (size_t)c;
+    double dm = 0.0, dt = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int e = ce[j];
+      const size_t ie = (size_t)e * nlev + k;
+      const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+      const T vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
+      const T f = rho_e[ie] * vf;
+      const T ft = f * theta_e[ie];
+      dm += dv[j] * (double)f;
+      dt += dv[j] * (double)ft;
+    }
+    div_m[(size_t)c * nlev + k] = dm;
+    div_t[(size_t)c * nlev + k] = dt;
   }
-  div_m[(size_t)c * nlev + k] = dm;
-  div_t[(size_t)c * nlev + k] = dt;
 }
 
 // -------------------------------------------------------------------------
@@ -352,17 +394,17 @@ __global__ void mx_refresh(int ne, int nc, int nlev, const double* __restrict__ 
   unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nedge = (unsigned)ne * nlev;
   if (i < nedge) {
-    m.vn[i] = (float)st.vn[i];
+    m.vn[i] = d2f(st.vn[i]);
     return;
   }
   i -= nedge;
   if (i >= (unsigned)nc * nlevp) return;
   const int c = (int)(i / (unsigned)nlevp), k = (int)(i - (unsigned)c * nlevp);
-  m.w[i] = (float)st.w[i];
+  m.w[i] = d2f(st.w[i]);
   if (k < nlev) {
     const size_t j = (size_t)c * nlev + k;
-    m.rho[j] = (float)(st.rho[j] - rho_ref[k]);
-    m.th[j] = (float)(st.theta_v[j] - theta_ref[k]);
+    m.rho[j] = d2f(st.rho[j] - rho_ref[k]);
+    m.th[j] = d2f(st.theta_v[j] - theta_ref[k]);
   }
 }
 
@@ -489,9 +531,13 @@ __global__ void diff_edge_update(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __
   const T lap2 = (div_l[(size_t)c1 * nlev + k] - div_l[(size_t)c0 * nlev + k]) * g.inv_d[e] -
                  (curl_l[(size_t)vp * nlev + k] - curl_l[(size_t)vm * nlev + k]) * g.inv_l[e];
   const T inc = sc.dtime * nu[ie] * lap[ie] - g.k4_a[e] * lap2;
-  const double vnn = vn[ie] + (double)inc;
-  vn[ie] = vnn;
-  if constexpr (kMixed<T>) m_vn[ie] = (float)vnn;
+  if constexpr (kMixed<T>) {
+    const double vnn = vn[ie] + f2d(inc);
+    vn[ie] = vnn;
+    m_vn[ie] = d2f(vnn);
+  } else {
+    vn[ie] = vn[ie] + (double)inc;
+  }
 }
 
 // cells (half-level range): w fourth-order diffusion, theta/exner update (FP64, in place)
@@ -510,18 +556,30 @@ __global__ void diff_cell_update(GridT<T> g, VertT<T> v, ScalT<T> sc, const doub
     l2 += L[1] * (lap_w[(size_t)cc[1] * nlevp + k] - lc);
     l2 += L[2] * (lap_w[(size_t)cc[2] * nlevp + k] - lc);
     const size_t iw = (size_t)c * nlevp + k;
-    const double wn = st.w[iw] - (double)(g.k4w_c[c] * l2);
-    st.w[iw] = wn;
-    if constexpr (kMixed<T>) m.w[iw] = (float)wn;
+    if constexpr (kMixed<T>) {
+      const double wn = st.w[iw] - f2d(g.k4w_c[c] * l2);
+      st.w[iw] = wn;
+      m.w[iw] = d2f(wn);
+    } else {
+      st.w[iw] = st.w[iw] - (double)(g.k4w_c[c] * l2);
+    }
   }
   if (k < nlev && sc.hdiff_temp) {
     const size_t ic = (size_t)c * nlev + k;
     const double th = st.theta_v[ic];
-    const double thn = th + (double)dtheta[ic];
-    const double exn = st.exner[ic] * (1.0 + rd_o_cvd * (thn - th) / th);
-    st.theta_v[ic] = thn;
-    st.exner[ic] = exn;
-    if constexpr (kMixed<T>) m.th[ic] = (float)(thn - theta_ref[k]);
+    if constexpr (kMixed<T>) {
+      // exner (1 + rd/cvd dtheta/theta): the FP32 increment of a value near 1
+      const float dth = dtheta[ic];
+      const double thn = th + f2d(dth);
+      st.theta_v[ic] = thn;
+      st.exner[ic] = st.exner[ic] + f2d(d2f(st.exner[ic]) * ((float)rd_o_cvd * dth / d2f(th)));
+      m.th[ic] = d2f(thn - theta_ref[k]);
+    } else {
+      const double thn = th + (double)dtheta[ic];
+      const double exn = st.exner[ic] * (1.0 + rd_o_cvd * (thn - th) / th);
+      st.theta_v[ic] = thn;
+      st.exner[ic] = exn;
+    }
   }
 }
 
