@@ -11,3 +11,4 @@ from .grid import make_grid, Grid  # noqa: F401
 from .vertical import make_vct  # noqa: F401
 from .state import (jw_type_state, gaussian_perturbation_centre,  # noqa: F401
                     sample_perturbation_centre, CONSTANTS)
+from .perturb import perturb_state  # noqa: F401
