@@ -247,7 +247,7 @@ __device__ __forceinline__ R get(const double* p) {
 // (as the predictor does) instead of reading the predictor's; used by the
 // allocation-free entry point below.
 template <class T, bool kOwnZb = false, int KC = kKC, class R = double>
-__global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
+__global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
   using A = Ar<R>;
   constexpr bool kDW = std::is_same<R, df>::value;
   constexpr int kTile = tile_doubles<KC>();
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
     cp_wait();
     __syncthreads();
     if (!active) continue;
-#pragma unroll 1
+#pragma unroll (kDW ? 1 : 2)
     for (int kk = 0; kk < nkc; ++kk) {
       const int k = k0 + kk;
       const int o = kk * kLD + t;
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kCW) sn_column_tiled(int nc, DevVert v, Scalar
     cp_wait();
     __syncthreads();
     if (active) {
-#pragma unroll 1
+#pragma unroll (kDW ? 1 : 2)
       for (int kk = nk - 1; kk >= 0; --kk) {
         const int k = k0 + kk;
         const int b = kk * kCW + t;
