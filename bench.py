@@ -360,9 +360,9 @@ FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
 # L90 (profiles/sn_column_r2b5_l90.md), scaled to R2B6 by the column count (x4),
 # valid while the kernel source is the one captured (its SHA-256 below).
 COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
-                  "sha256": "0b1b674ce76ed82f1eee7487cdce646db86189ab47b8cf1883a4978da87de7c9",
-                  # mean of the predictor (2.077 GB) and corrector (3.235 GB) launches, FP64
-                  "bytes_per_launch_r2b5": 0.5 * (1.372084e9 + 0.704893e9 + 2.643417e9 + 0.591441e9)}
+                  "sha256": "4f809caf35b942daaa3beabfe99a223ace11a9fc822d2e89cf49bce59e804c97",
+                  # mean of the predictor (2.082 GB) and corrector (3.241 GB) launches, FP64
+                  "bytes_per_launch_r2b5": 0.5 * (1.375208e9 + 0.706401e9 + 2.646195e9 + 0.594674e9)}
 
 
 def column_traffic(nc):
