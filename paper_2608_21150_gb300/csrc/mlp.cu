@@ -14,6 +14,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -44,19 +45,21 @@ __device__ __forceinline__ float gelu_fwd(float x) {
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core GEMM (tcgen05): one 128 x 128 output tile per CTA, K in blocks
-// of 64 (one 128-byte swizzle row of BF16) through a 3-stage TMA ring.
-// Warp 0 (one lane) issues the TMA loads, warp 1 (one lane) the MMAs into a
-// 128-column FP32 accumulator in tensor memory; then all eight warps read the
-// accumulator back and apply the epilogue: warp w may access TMEM lanes
-// 32 (w % 4) .. +31 (= tile rows), and warps w and w + 4 split the columns.
-// 96 KB of shared memory: two CTAs per SM, so one CTA's epilogue overlaps the
-// other's main loop.
-constexpr int TBM = 128, TBN = 128, TBK = 64, kStages = 3;
-constexpr int kTcThreads = 256;
+// Tensor-core GEMM (tcgen05), persistent and warp-specialised.  Each CTA (one
+// per SM, 170 KB of shared memory) walks output tiles of 128 x 128 (N
+// fastest, so the CTAs in flight share A rows in L2); K runs in blocks of 64
+// BF16 (one 128-byte swizzle row) through a 5-stage TMA ring that continues
+// across tiles.  Warp 0 (one lane) issues the TMA loads; warp 1 (one lane) the
+// MMAs, into one of two 128-column FP32 accumulators in tensor memory; warps
+// 2..9 drain the other accumulator meanwhile (TMEM -> registers -> bias, GELU,
+// stores): warp w may access TMEM lanes 32 (w % 4) .. +31 (= tile rows), and
+// the two warps of a lane quarter split the columns.
+constexpr int TBM = 128, TBN = 128, TBK = 64, kStages = 5;
+constexpr int kEpiWarps = 8;
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileBytesA = TBM * TBK * 2, kTileBytesB = TBN * TBK * 2;
-constexpr int kTcSmem = kStages * (kTileBytesA + kTileBytesB) + 1024 /* alignment slack */ + 128 /* barriers */;
-constexpr uint32_t kTmemCols = TBN;
+constexpr int kTcSmem = kStages * (kTileBytesA + kTileBytesB) + 1024 /* alignment slack */ + 256 /* barriers */;
+constexpr uint32_t kTmemCols = 2 * TBN;
 // every wait gives up after this long (ns) and flags an error instead of hanging
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
@@ -88,6 +91,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -170,21 +177,77 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CUtensorMap tma_a,
-                                                      const __grid_constant__ CUtensorMap tma_b, int M, int N, int K,
-                                                      Epi ep) {
+// Epilogue of one 16-column run of a tile row (thread-private values v).
+__device__ __forceinline__ void epilogue16(float (&v)[16], int row, int col0, int M, int N, const Epi& ep) {
+  if (row >= M || col0 >= N) return;
+  const bool whole = col0 + 16 <= N;
+  const size_t o = (size_t)row * ep.ldc + col0;
+  const bool vec32 = whole && (o & 3) == 0;  // 16-byte aligned fp32 run
+  const bool vec16 = whole && (o & 7) == 0;  // 16-byte aligned bf16 run
+  if (ep.bias) {
+    if (whole) {
+      const float4* b4 = reinterpret_cast<const float4*>(ep.bias + col0);  // col0 % 16 == 0, bias 16-byte aligned
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 bq = __ldg(b4 + q);
+        v[4 * q] += bq.x;
+        v[4 * q + 1] += bq.y;
+        v[4 * q + 2] += bq.z;
+        v[4 * q + 3] += bq.w;
+      }
+    } else {
+      for (int j = 0; j < 16 && col0 + j < N; ++j) v[j] += ep.bias[col0 + j];
+    }
+  }
+  if (ep.mode == 0) {
+    if (vec32) {
+      float4* dst = reinterpret_cast<float4*>(ep.out_f32 + o);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+      for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_f32[o + j] = v[j];
+    }
+  } else {
+    if (ep.zpre) {
+      if (vec32) {
+        float4* dst = reinterpret_cast<float4*>(ep.zpre + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        for (int j = 0; j < 16 && col0 + j < N; ++j) ep.zpre[o + j] = v[j];
+      }
+    }
+    if (vec16) {
+      __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16(gelu_fwd(v[j]));
+      uint4* dst = reinterpret_cast<uint4*>(ep.out_bf16 + o);
+      dst[0] = reinterpret_cast<const uint4*>(h)[0];
+      dst[1] = reinterpret_cast<const uint4*>(h)[1];
+    } else {
+      for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_bf16[o + j] = __float2bfloat16(gelu_fwd(v[j]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc(const __grid_constant__ CUtensorMap tma_a,
+                                                         const __grid_constant__ CUtensorMap tma_b, int M, int N,
+                                                         int K, Epi ep) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + kStages * kTileBytesA;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kTileBytesB);
   uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* acc_full = empty + kStages;   // [2] MMA -> epilogue
+  uint64_t* acc_empty = acc_full + 2;     // [2] epilogue -> MMA
+  uint64_t* drain = acc_empty + 2;        // MMA issuer's own completion wait
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const int tiles_n = (N + TBN - 1) / TBN;
+  const int n_tiles = ((M + TBM - 1) / TBM) * tiles_n;
   const int nk = K / TBK;
 
   if (threadIdx.x == 0) {
@@ -192,7 +255,11 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CU
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
+    }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -207,95 +274,73 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CU
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int issued = 0;  // TMA stages issued by the producer lane
+  int issued = 0;  // k-blocks whose TMA loads the producer lane issued (all tiles)
   if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) & 1) ^ 1, abort_flag)) break;
-      mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
-      tma_load_2d(sA + s * kTileBytesA, &tma_a, kb * TBK, m0, &full[s]);
-      tma_load_2d(sB + s * kTileBytesB, &tma_b, kb * TBK, n0, &full[s]);
-      issued = kb + 1;
+    int g = 0;
+    for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+      const int m0 = (tile / tiles_n) * TBM, n0 = (tile % tiles_n) * TBN;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % kStages;
+        if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) & 1) ^ 1, abort_flag)) break;
+        mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
+        tma_load_2d(sA + s * kTileBytesA, &tma_a, kb * TBK, m0, &full[s]);
+        tma_load_2d(sB + s * kTileBytesB, &tma_b, kb * TBK, n0, &full[s]);
+        issued = g + 1;
+      }
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = idesc_bf16(TBM, TBN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      if (!mbar_wait(&full[s], (kb / kStages) & 1, abort_flag)) break;
+    int g = 0, t = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++t) {
+      const int b = t & 1;
+      const uint32_t d = tmem + (uint32_t)(b * TBN);
+      if (t >= 2 && !mbar_wait(&acc_empty[b], ((t >> 1) & 1) ^ 1, abort_flag)) break;
       tc_fence_after();
-      const uint64_t da = sdesc_sw128(sA + s * kTileBytesA), db = sdesc_sw128(sB + s * kTileBytesB);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % kStages;
+        if (!mbar_wait(&full[s], (g / kStages) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t da = sdesc_sw128(sA + s * kTileBytesA), db = sdesc_sw128(sB + s * kTileBytesB);
 #pragma unroll
-      for (int k = 0; k < TBK / 16; ++k)  // 16 BF16 = 32 bytes further along K: +2 in the 16-byte address field
-        mma_bf16_tc(tmem, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-      tc_commit(&empty[s]);
+        for (int k = 0; k < TBK / 16; ++k)  // 16 BF16 = 32 bytes further along K: +2 in the 16-byte address field
+          mma_bf16_tc(d, da + 2 * k, db + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+        tc_commit(&empty[s]);
+      }
+      if (ok) tc_commit(&acc_full[b]);
     }
-    tc_commit(done);  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // epilogue: thread (warp, lane) owns tile row 32 (warp % 4) + lane, columns
-  // (warp / 4) TBN/2 .. +TBN/2
-  // warp-uniform decision: the tcgen05.ld below is a warp-collective instruction
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
-  tc_fence_after();
-  if (ok) {
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = m0 + 32 * quarter + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+    // every MMA issued above has completed before the teardown frees TMEM
+    tc_commit(drain);
+    if (!mbar_wait(drain, 0, abort_flag)) {
+      const unsigned long long t0 = now_ns();
+      while (!mbar_try_wait(drain, 0) && now_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+  } else if (warp >= 2) {
+    // epilogue: thread (warp, lane) owns tile row 32 (warp % 4) + lane and
+    // half of the columns
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    int t = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+      const int b = t & 1;
+      // warp-uniform decision: the tcgen05.ld below is a warp-collective instruction
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (t >> 1) & 1, abort_flag))) break;
+      tc_fence_after();
+      const int m0 = (tile / tiles_n) * TBM, n0 = (tile % tiles_n) * TBN;
+      const int row = m0 + 32 * quarter + lane;
+      const uint32_t trow = tmem + (uint32_t)(b * TBN) + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll 1
-    for (int c = half * (TBN / 2); c < (half + 1) * (TBN / 2); c += 16) {
-      float v[16];
-      tmem_ld16(trow + (uint32_t)c, v);
-      const int col0 = n0 + c;
-      if (row >= M || col0 >= N) continue;
-      const bool whole = col0 + 16 <= N;
-      const size_t o = (size_t)row * ep.ldc + col0;
-      const bool vec32 = whole && (o & 3) == 0;   // 16-byte aligned fp32 run
-      const bool vec16 = whole && (o & 7) == 0;   // 16-byte aligned bf16 run
-      if (ep.bias) {
-        if (whole) {
-          const float4* b4 = reinterpret_cast<const float4*>(ep.bias + col0);  // col0 % 16 == 0, bias 16-byte aligned
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 bq = __ldg(b4 + q);
-            v[4 * q] += bq.x;
-            v[4 * q + 1] += bq.y;
-            v[4 * q + 2] += bq.z;
-            v[4 * q + 3] += bq.w;
-          }
-        } else {
-          for (int j = 0; j < 16 && col0 + j < N; ++j) v[j] += ep.bias[col0 + j];
-        }
+      for (int c = half * (TBN / 2); c < (half + 1) * (TBN / 2); c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c, v);
+        epilogue16(v, row, n0 + c, M, N, ep);
       }
-      if (ep.mode == 0) {
-        if (vec32) {
-          float4* dst = reinterpret_cast<float4*>(ep.out_f32 + o);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
-          for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_f32[o + j] = v[j];
-        }
-      } else {
-        if (ep.zpre) {
-          if (vec32) {
-            float4* dst = reinterpret_cast<float4*>(ep.zpre + o);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          } else {
-            for (int j = 0; j < 16 && col0 + j < N; ++j) ep.zpre[o + j] = v[j];
-          }
-        }
-        if (vec16) {
-          __align__(16) __nv_bfloat16 h[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16(gelu_fwd(v[j]));
-          uint4* dst = reinterpret_cast<uint4*>(ep.out_bf16 + o);
-          dst[0] = reinterpret_cast<const uint4*>(h)[0];
-          dst[1] = reinterpret_cast<const uint4*>(h)[1];
-        } else {
-          for (int j = 0; j < 16 && col0 + j < N; ++j) ep.out_bf16[o + j] = __float2bfloat16(gelu_fwd(v[j]));
-        }
-      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
   }
 
@@ -304,9 +349,9 @@ __global__ void __launch_bounds__(kTcThreads) gemm_tc(const __grid_constant__ CU
   __syncthreads();
   if (warp == 0 && lane == 0 && *abort_flag) {
     const int first = issued > kStages ? issued - kStages : 0;
-    for (int kb = first; kb < issued; ++kb) {
+    for (int g = first; g < issued; ++g) {
       const unsigned long long t0 = now_ns();
-      while (!mbar_try_wait(&full[kb % kStages], (kb / kStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
+      while (!mbar_try_wait(&full[g % kStages], (g / kStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
       }
     }
   }
@@ -432,6 +477,7 @@ bool operand_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int K, in
 
 std::mutex g_attr_mutex;
 bool g_attr_set[64] = {};
+int g_sm_count[64] = {};
 
 }  // namespace
 
@@ -448,6 +494,9 @@ int mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bf
     if (!g_attr_set[dev]) {
       if (cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess)
         return report_error(ICON_ERR_CUDA, "mlp_gemm: shared memory attribute");
+      if (cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          g_sm_count[dev] < 1)
+        return report_error(ICON_ERR_CUDA, "mlp_gemm: SM count");
       g_attr_set[dev] = true;
     }
   }
@@ -455,7 +504,8 @@ int mlp_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bf
   if (!operand_map(&ta, A, M, K, lda, TBM) || !operand_map(&tb, B, N, K, ldb, TBN))
     return report_error(ICON_ERR_CUDA, "mlp_gemm: tensor map encoding failed");
   Epi ep{gelu_act ? 1 : 0, bias, out_f32, out_bf16, zpre, ldc};
-  dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
+  const long long tiles = (long long)cdiv(N, TBN) * cdiv(M, TBM);
+  const unsigned grid = (unsigned)std::min<long long>(tiles, g_sm_count[dev]);  // one persistent CTA per SM
   ICON_LAUNCH_SMEM("mlp_gemm_tc", grid, kTcThreads, kTcSmem, s, gemm_tc, ta, tb, M, N, K, ep);
   return ICON_OK;
 }
