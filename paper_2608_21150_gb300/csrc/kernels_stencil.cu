@@ -148,18 +148,18 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
   const T* vne = vn + (size_t)e * nlev;
   const T* vte = vt + (size_t)e * nlev;
   // vn at half levels k and k+1 (top: vn_0, ground: vn_{nlev-1})
+  // linear interpolation to half level kh written as x_kh + wgt (x_kh-1 - x_kh)
   auto vn_ie = [&](int kh) -> T {
     if (kh == 0) return vne[0];
     if (kh == nlev) return vne[nlev - 1];
-    const T wg = v.wgt[kh];
-    return wg * vne[kh - 1] + (T(1) - wg) * vne[kh];
+    return vne[kh] + v.wgt[kh] * (vne[kh - 1] - vne[kh]);
   };
   const T vnie_k = vn_ie(k);
   if (k < nlev) {
     const T vnie_k1 = vn_ie(k + 1);
     const T* w0 = w + (size_t)c0 * nlevp;
     const T* w1 = w + (size_t)c1 * nlevp;
-    const T wbar = T(0.5) * (T(0.5) * (w0[k] + w0[k + 1]) + T(0.5) * (w1[k] + w1[k + 1]));
+    const T wbar = T(0.25) * ((w0[k] + w0[k + 1]) + (w1[k] + w1[k + 1]));
     const T zeta_e = T(0.5) * (zeta[(size_t)vm * nlev + k] + zeta[(size_t)vp * nlev + k]);
     const T dkdn = (ekin_c[(size_t)c1 * nlev + k] - ekin_c[(size_t)c0 * nlev + k]) * inv_d;
     const T dvdz = (vnie_k - vnie_k1) * v.inv_dz[k];
@@ -167,8 +167,7 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
   }
   T gw = 0;
   if (k > 0 && k < nlev) {
-    const T wg = v.wgt[k];
-    const T vtie = wg * vte[k - 1] + (T(1) - wg) * vte[k];
+    const T vtie = vte[k] + v.wgt[k] * (vte[k - 1] - vte[k]);
     const T dwdn = (w[(size_t)c1 * nlevp + k] - w[(size_t)c0 * nlevp + k]) * inv_d;
     const T dwdt = (w_v[(size_t)vp * nlevp + k] - w_v[(size_t)vm * nlevp + k]) * g.inv_l[e];
     gw = vnie_k * dwdn + vtie * dwdt;
