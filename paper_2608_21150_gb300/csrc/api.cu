@@ -232,6 +232,26 @@ void enqueue_op(icon_dycore* d, int op, const StateView& st, cudaStream_t s);
 // Autotuner: time every kernel of one step on a temporary uniform state with
 // each candidate launch shape (CUDA events around every launch) and keep the
 // fastest shape per kernel.
+// Every coefficient and work pointer the kernels of the active precision
+// dereference must be set: a missing one is an internal error reported at
+// create, never a device fault.
+template <class T>
+bool grid_complete(const GridT<T>& g) {
+  const void* p[] = {g.c2e, g.c2e2c, g.e2c, g.e2v, g.e2c2v, g.e2c2e, g.v2e, g.v2c, g.div_c, g.lap_c, g.e2c_w,
+                     g.grad_c, g.k4w_c, g.inv_d, g.inv_l, g.f_e, g.vt_w, g.upw, g.nt, g.inv_dn, g.smag_a, g.k4_a,
+                     g.fdiv_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl};
+  for (const void* q : p)
+    if (!q) return false;
+  return true;
+}
+
+bool work_complete(const DevWork& w) {
+  const void* p[] = {w.div_m, w.div_t, w.rho_p, w.exner_p, w.theta_p, w.w_p, w.pex, w.col, w.zbl, w.diag, w.flag};
+  for (const void* q : p)
+    if (!q) return false;
+  return true;
+}
+
 int autotune(icon_dycore* d) {
   const HostGrid& h = d->grid->host;
   const size_t nlev = d->nlev, ef = h.ne * nlev, cf = h.nc * nlev, ch = h.nc * (nlev + 1);
@@ -423,11 +443,12 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   en.sc = s;
 
   // parameter-dependent grid factors
-  std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc);
+  std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc), fdiv(ne);
   for (int e = 0; e < ne; ++e) {
     fe[e] = 2.0 * p->omega * h.coriolis_z[e];
     smag[e] = p->hdiff_smag_fac * h.edge_area[e];
     k4[e] = p->hdiff_k4 * h.edge_area[e] * h.edge_area[e];
+    fdiv[e] = s.divflux * h.inv_d[e];
   }
   for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
   en.g64 = grid->dev;
@@ -435,6 +456,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   en.g64.smag_a = A.upload(smag);
   en.g64.k4_a = A.upload(k4);
   en.g64.k4w_c = A.upload(k4w);
+  en.g64.fdiv_e = A.upload(fdiv);
 
   const size_t ef = (size_t)ne * nlev, eh = (size_t)ne * (nlev + 1);
   const size_t cf = (size_t)nc * nlev, ch = (size_t)nc * (nlev + 1);
@@ -469,10 +491,13 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     g.inv_dn = up(h.inv_dn);
     g.smag_a = up(smag);
     g.k4_a = up(k4);
+    g.fdiv_e = up(fdiv);
     g.curl_v = up(h.curl_v);
     g.c2v_w = up(h.c2v_w);
     g.uv_w = up(h.uv_w);
     g.div_c_hl = g0.div_c_hl;
+    g.cell_area = g0.cell_area;
+    g.uv_c = g0.uv_c;
     g.mean_area = (T)h.mean_area;
     VertT<T>& vt = x.v;
     vt.nlev = nlev;
@@ -541,6 +566,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   w.exner_p = A.alloc<double>(cf);
   w.theta_p = A.alloc<double>(cf);
   w.w_p = A.alloc<double>(ch);
+  w.pex = A.alloc<double>(cf);
   w.col = A.alloc<double>(7 * ch);
   w.zbl = A.alloc<double>(ch);
   w.diag = A.alloc<double>(diag_partials(nc));
@@ -559,6 +585,17 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
     delete d;
     return fail(ICON_ERR_CUDA, m);
+  }
+  {
+    const bool mixed = p->precision == ICON_PREC_MIXED;
+    const bool ok = grid_complete(en.g64) && work_complete(en.wk) &&
+                    (mixed ? grid_complete(en.c32.g) : grid_complete(en.c64.g));
+    if (!ok) {
+      A.release();
+      cudaStreamDestroy(d->cap_stream);
+      delete d;
+      return fail(ICON_ERR_CUDA, "icon_dycore_create: internal error: a coefficient or work array is missing");
+    }
   }
   for (int k = 0; k < kNumStencils; ++k) en.threads[k] = 256;
   en.col_kc = 4;

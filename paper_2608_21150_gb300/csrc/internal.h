@@ -40,6 +40,7 @@ struct GridT {
   const T* inv_dn;  // [ne] 1/(arc between the two opposite diamond vertices)
   const T* smag_a;  // [ne] hdiff_smag_fac * A_e
   const T* k4_a;    // [ne] hdiff_k4 * A_e^2
+  const T* fdiv_e;  // [ne] divflux_fac * mean cell area / d_e (flux filter)
   // vertex coefficients
   const T* curl_v;  // [nv*6] t_{v,e} d_e / A_v (0 for pads)
   const T* c2v_w;   // [nv*6] cell->vertex weights (0 for pads)
@@ -143,6 +144,7 @@ struct DevWork {
   double *div_m, *div_t;                  // cells: flux divergences (FP64 sums)
   double *rho_p, *exner_p, *theta_p;      // cells: predicted state
   double* w_p;                            // cells, half levels
+  double* pex;   // cells: extrapolated exner perturbation (FP64, or double-word pairs in mixed mode)
   double* col;   // level-major [k][c] scratch: 7 planes of (nlev+1)*nc: cp, rp, rho*, pr*, rho_ic, alpha, eos
   double* zbl;   // level-major zb [(nlev+1)*nc], predictor -> corrector
   double* diag;  // diagnostics: partial column-mass sums

@@ -207,7 +207,8 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
 // -------------------------------------------------------------------------
 template <class T>
 __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, const T* __restrict__ theta,
-                             T* __restrict__ grad4) {
+                             T* __restrict__ grad4, const double* __restrict__ exner,
+                             const double* __restrict__ exner_pr, double exfac, double* __restrict__ pex) {
   int c, k;
   const int nlev = v.nlev;
   if (!flat_index(g.nc, nlev, c, k)) return;
@@ -215,6 +216,15 @@ __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, 
   const int* cc = g.c2e2c + 3 * (size_t)c;
   const T* G = g.grad_c + 6 * (size_t)c;
   const size_t i = (size_t)c * nlev + k;
+  // extrapolated exner perturbation (1 + a) pr - a pr_old of this cell, for the
+  // pressure gradient at its edges: FP64, or a double-word pair in mixed mode
+  // (exner is near 1, the difference across an edge ~1e-5 of it)
+  if constexpr (kMixed<T>) {
+    const df a = to_df(1.0 + exfac), b = to_df(exfac);
+    reinterpret_cast<df*>(pex)[i] = a * (to_df(exner[i]) - to_df(v.exner_ref[k])) - b * to_df(exner_pr[i]);
+  } else {
+    pex[i] = (1.0 + exfac) * (exner[i] - v.exner_ref[k]) - exfac * exner_pr[i];
+  }
   const size_t i0 = (size_t)cc[0] * nlev + k, i1 = (size_t)cc[1] * nlev + k, i2 = (size_t)cc[2] * nlev + k;
   const T r = rho[i], t = theta[i];
   const T r0 = rho[i0] - r, r1 = rho[i1] - r, r2 = rho[i2] - r;
@@ -229,16 +239,17 @@ __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, 
 // A6 (predictor edges): upwind rho_e/theta_e from the back trajectory over
 // dt/2, horizontal pressure gradient with the extrapolated exner perturbation,
 // and the vn predictor.  FP64 mode reads totals; mixed mode reads the
-// perturbations of rho and theta_v and adds the reference back.  The exner
-// difference between the two cells is always taken in FP64: neighbouring
-// perturbations agree to 4-5 digits, more than FP32 carries.
+// perturbations of rho and theta_v and adds the reference back.  The
+// extrapolated exner perturbations come per cell from sn_cell_grad; their
+// difference across the edge is taken in FP64 (double-word FP32 in mixed
+// mode): neighbouring perturbations agree to 4-5 digits, more than FP32 carries.
 // -------------------------------------------------------------------------
 template <class T>
 __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ vn,
                              const T* __restrict__ vt, const T* __restrict__ ddt_vn, const T* __restrict__ rho,
-                             const T* __restrict__ theta, const double* __restrict__ exner,
-                             const double* __restrict__ exner_pr, const double* __restrict__ inv_d64, double exfac,
-                             const T* __restrict__ grad4, T* __restrict__ rho_e, T* __restrict__ theta_e,
+                             const T* __restrict__ theta, const double* __restrict__ pex,
+                             const double* __restrict__ inv_d64, const T* __restrict__ grad4, T* __restrict__ rho_e,
+                             T* __restrict__ theta_e,
                              T* __restrict__ hpg, T* __restrict__ vn_p) {
   int e, k;
   const int nlev = v.nlev;
@@ -264,17 +275,10 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
   const size_t i0 = (size_t)c0 * nlev + k, i1 = (size_t)c1 * nlev + k;
   T h;
   if constexpr (kMixed<T>) {
-    // extrapolated exner perturbations and their difference in double-word
-    // FP32: exner is near 1, the difference across an edge ~1e-5 of it
-    const df pref = to_df(v.exner_ref[k]), a = to_df(1.0 + exfac), b = to_df(exfac);
-    const df pex0 = a * (to_df(exner[i0]) - pref) - b * to_df(exner_pr[i0]);
-    const df pex1 = a * (to_df(exner[i1]) - pref) - b * to_df(exner_pr[i1]);
-    h = sc.cpd * te * (to_float(pex1 - pex0) * g.inv_d[e]);
+    const df* p = reinterpret_cast<const df*>(pex);
+    h = sc.cpd * te * (to_float(p[i1] - p[i0]) * g.inv_d[e]);
   } else {
-    const double pref = v.exner_ref[k];
-    const double pex0 = (1.0 + exfac) * (exner[i0] - pref) - exfac * exner_pr[i0];
-    const double pex1 = (1.0 + exfac) * (exner[i1] - pref) - exfac * exner_pr[i1];
-    h = sc.cpd * te * (T)((pex1 - pex0) * inv_d64[e]);
+    h = sc.cpd * te * (T)((pex[i1] - pex[i0]) * inv_d64[e]);
   }
   rho_e[ie] = re;
   theta_e[ie] = te;
@@ -353,7 +357,7 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
       const int e = ce[j];
       const size_t ie = (size_t)e * nlev + k;
       const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-      const T vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
+      const T vf = vn[ie] + g.fdiv_e[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
       const T f = rho_e[ie] * vf;
       const T ft = f * theta_e[ie];
       const df w = dv[j];
@@ -370,7 +374,7 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
       const int e = ce[j];
       const size_t ie = (size_t)e * nlev + k;
       const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-      const T vf = vn[ie] + sc.divflux * g.inv_d[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
+      const T vf = vn[ie] + g.fdiv_e[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
       const T f = rho_e[ie] * vf;
       const T ft = f * theta_e[ie];
       dm += dv[j] * (double)f;
@@ -624,10 +628,9 @@ void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cuda
   // ---------------- predictor ----------------
   launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s, threads);
   ICON_LAUNCH(kname<T>("sn_cell_grad", "sn_cell_grad_f32"), blocks_for(nce, TH(4)), TH(4), s, sn_cell_grad<T>, g, v, s_rho, s_th,
-              wk.grad4);
+              wk.grad4, st.exner, st.exner_pr, en.sc.exfac, en.wk.pex);
   ICON_LAUNCH(kname<T>("sn_edge_pred", "sn_edge_pred_f32"), blocks_for(nee, TH(5)), TH(5), s, sn_edge_pred<T>, g, v, x.s, s_vn, wk.vt,
-              wk.ddt_vn0, s_rho, s_th, st.exner, st.exner_pr, en.g64.inv_d, en.sc.exfac, wk.grad4, wk.rho_e,
-              wk.theta_e, wk.hpg, wk.vn_p);
+              wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p);
   ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_for(nce, TH(6)), TH(6), s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
               st.exner, st.exner_pr);
   ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_for(nce, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
