@@ -11,11 +11,15 @@
 //   two_prod      via the fused multiply-add (exact product error)
 //   add           "AccurateDWPlusDW", Joldes, Muller & Popescu, ACM TOMS 44
 //                 (2017), Alg. 6: relative error below 3u^2 + 13u^3 (u = 2^-24)
+//   add_same_sign "SloppyDWPlusDW", ibid. Alg. 5: fewer operations, its error
+//                 bound holds when the operands have the same sign (no
+//                 cancellation)
 //   add (df, float) "DWPlusFP", ibid. Alg. 4
 //   mul           "DWTimesDW1", ibid. Alg. 10
 //   mul (df, float) "DWTimesFP1", ibid. Alg. 7
 //   rcp           one Newton-Raphson step r + r (1 - x r) in df from the
-//                 correctly rounded FP32 reciprocal of the leading word.
+//                 approximate FP32 reciprocal of the leading word (the step
+//                 doubles its ~23 correct bits).
 // The additions and subtractions use the _rn intrinsics so the compiler never
 // fuses them into multiply-adds, which would break the exact error terms.
 #pragma once
@@ -46,6 +50,11 @@ __device__ __forceinline__ df operator+(df a, df b) {
   return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
 }
 
+__device__ __forceinline__ df add_same_sign(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
 __device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 
@@ -68,7 +77,7 @@ __device__ __forceinline__ df operator*(df a, float b) {
 }
 
 __device__ __forceinline__ df rcp(df x) {
-  const float r = __frcp_rn(x.hi);
+  const float r = __fdividef(1.0f, x.hi);
   const df e = (x * (-r)) + 1.0f;  // 1 - x r, small
   return df{r, 0.0f} + e * r;      // r + r (1 - x r)
 }

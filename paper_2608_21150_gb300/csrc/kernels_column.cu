@@ -232,6 +232,12 @@ __device__ __forceinline__ R lev(const DevVert& v, int k) {
   }
 }
 
+// Sum of two non-negative values (densities, potential temperatures, positive
+// coefficients): the cheaper double-word addition is exact enough without
+// cancellation; plain addition in FP64.
+__device__ __forceinline__ double add_pos(double a, double b) { return a + b; }
+__device__ __forceinline__ df add_pos(df a, df b) { return add_same_sign(a, b); }
+
 // Scratch planes hold R values in 8-byte slots (a df is two floats).
 template <class R>
 __device__ __forceinline__ void put(double* p, R x) {
@@ -287,12 +293,13 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
   const R dt = A::in(sc.dt_s), beta = A::in(sc.beta), ombeta = A::in(1.0 - sc.beta);
   const R wn_r = A::in(sc.wnow_rth), wnew_r = A::in(sc.wnew_rth);
   const R wn_v = A::in(sc.wnow_vel), wnew_v = A::in(sc.wnew_vel), cvd_o_rd = A::in(sc.cvd_o_rd);
+  const float wn_vf = to_float(to_df(sc.wnow_vel)), wnew_vf = to_float(to_df(sc.wnew_vel));
 
   // carried values: half level k (interface above full level k), full level k-1,
   // and full level k itself (converted and time-averaged when it was level k+1)
   R ric_k = zero, tic_k = zero, tpic_k = zero, rt_k = zero;
   R zb_km1 = zero, al_km1 = zero, ps_km1 = zero, pr_km1 = zero, cp_km1 = zero, rp_km1 = zero;
-  R rho_c = zero, th_c = zero, ra_c = zero, ta_c = zero, tpa_c = zero;
+  R rho_c = zero, th_c = zero, ra_c = zero, ta_c = zero, tpa_c = zero, wk_c = zero;
 
   for (int k0 = 0; k0 < nlev; k0 += KC) {
     const int nkc = min(KC, nlev - k0);       // levels solved in this chunk
@@ -322,9 +329,10 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       if (k == 0) {
         rho_c = A::in(T_rho[o]);
         th_c = A::in(T_th[o]);
-        ra_c = corrector ? wn_r * rho_c + wnew_r * A::in(T_rp[o]) : rho_c;
-        ta_c = corrector ? wn_r * th_c + wnew_r * A::in(T_tp[o]) : th_c;
+        ra_c = corrector ? add_pos(wn_r * rho_c, wnew_r * A::in(T_rp[o])) : rho_c;
+        ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * A::in(T_tp[o])) : th_c;
         tpa_c = ta_c - lev<R, LTH>(v, 0);
+        wk_c = A::in(T_w[o]);
       }
       const R rho_n = rho_c, th_n = th_c, pi_n = A::in(T_pi[o]);
       const R pr_k = pi_n - lev<R, LEX>(v, k);
@@ -334,12 +342,12 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       if (k + 1 < nlev) {
         rho_x = A::in(T_rho[o + kLD]);
         th_x = A::in(T_th[o + kLD]);
-        ra_x = corrector ? wn_r * rho_x + wnew_r * A::in(T_rp[o + kLD]) : rho_x;
-        ta_x = corrector ? wn_r * th_x + wnew_r * A::in(T_tp[o + kLD]) : th_x;
+        ra_x = corrector ? add_pos(wn_r * rho_x, wnew_r * A::in(T_rp[o + kLD])) : rho_x;
+        ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * A::in(T_tp[o + kLD])) : th_x;
         tpa_x = ta_x - lev<R, LTH>(v, k + 1);
         const R g1 = lev<R, WG>(v, k + 1), g2 = lev<R, WG2>(v, k + 1);
-        ric_k1 = g1 * ra_c + g2 * ra_x;
-        tic_k1 = g1 * ta_c + g2 * ta_x;
+        ric_k1 = add_pos(g1 * ra_c, g2 * ra_x);
+        tic_k1 = add_pos(g1 * ta_c, g2 * ta_x);
         tpic_k1 = g1 * tpa_c + g2 * tpa_x;
       }
       const size_t ik = (size_t)k * nc + c;
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       } else {
         zb = get<R>(T_zb + o);
       }
-      const R wk = A::in(T_w[o]), wk1 = A::in(T_w[o + kLD]);
+      const R wk = wk_c, wk1 = A::in(T_w[o + kLD]);
       const R rt_k1 = ric_k1 * tic_k1;
       const R rstar = rho_n - dt * A::in(T_dm[o]) - lev<R, CR>(v, k) * (ric_k * wk - ric_k1 * wk1);
       const R pstar = pr_k - zb * (lev<R, LDZ>(v, k) * A::in(T_dt[o]) + ombeta * (rt_k * wk - rt_k1 * wk1));
@@ -361,11 +369,16 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       put(ri_s + ik, ric_k);
       put(al_s + ik, al_k);
       if (k >= 1) {
-        const R ddtw = corrector ? wn_v * A::in(T_dw0[o]) + wnew_v * A::in(T_dw1[o]) : A::in(T_dw0[o]);
+        R ddtw;
+        if constexpr (std::is_same<T, float>::value) {  // FP32 tendencies: their time average in FP32
+          ddtw = A::in(corrector ? fmaf(wn_vf, T_dw0[o], wnew_vf * T_dw1[o]) : T_dw0[o]);
+        } else {
+          ddtw = corrector ? wn_v * A::in(T_dw0[o]) + wnew_v * A::in(T_dw1[o]) : A::in(T_dw0[o]);
+        }
         const R wstar = wk + dt * ddtw - (lev<R, CWX>(v, k) * tic_k * (pr_km1 - pr_k) + lev<R, CB>(v, k) * tpic_k);
         const R gam = lev<R, CGAM>(v, k) * tic_k;
         const R am = -(gam * zb_km1 * al_km1);
-        const R bm = one + gam * al_k * (zb_km1 + zb);
+        const R bm = add_pos(one, gam * al_k * add_pos(zb_km1, zb));
         const R cm = -(gam * zb * al_k1);
         const R rm = wstar - gam * (ps_km1 - pstar);
         R cpk, rpk;
@@ -393,6 +406,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       rt_k = rt_k1;
       rho_c = rho_x;
       th_c = th_x;
+      wk_c = wk1;
       ra_c = ra_x;
       ta_c = ta_x;
       tpa_c = tpa_x;
