@@ -387,6 +387,24 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
 int icon_profile_begin(void);
 int icon_profile_end(int32_t max_kernels, char* names, int32_t* launches, double* ms, int32_t* n_kernels);
 
+/*
+ * ICON's nproma-blocked arrays (Sec. 4.3: the host model hands the dycore its
+ * own arrays).  A blocked field of n points and nlev_x levels is the Fortran
+ * array X(nproma, nlev_x, nblks), nblks = ceil(n / nproma): point h = jb*nproma
+ * + jc (0-based) at level k sits at offset jc + nproma*(k + nlev_x*jb); the
+ * pad points of the last block are neither read nor written.  The library's
+ * own layout is level-contiguous, X[h*nlev_x + k].  These calls convert all six
+ * state fields on the device (a shared-memory tiled transpose, about the cost
+ * of copying the state once each way: not zero-copy).  All arrays DEVICE;
+ * source and destination must not share an array; nproma >= 1 with at most
+ * 65535 blocks.  Errors: ICON_ERR_ARG, ICON_ERR_CUDA.
+ */
+int icon_state_from_blocked(icon_dycore_t* d, int32_t nproma, const icon_state_t* blocked, const icon_state_t* state);
+int icon_state_to_blocked(icon_dycore_t* d, int32_t nproma, const icon_state_t* state, const icon_state_t* blocked);
+/* One step (as icon_dycore_step) of a blocked state, in place: converted into
+ * the dycore's own device copy, stepped, converted back. */
+int icon_dycore_step_blocked(icon_dycore_t* d, int32_t nproma, const icon_state_t* blocked);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* icon_last_error(void);
 

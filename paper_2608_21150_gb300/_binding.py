@@ -110,6 +110,11 @@ _sig = {
                                               ctypes.POINTER(icon_state_t), ctypes.c_void_p, ctypes.c_void_p]),
     "icon_dycore_step_learned": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.POINTER(icon_state_t), ctypes.c_double,
                                                 _i32p, _f64p]),
+    "icon_state_from_blocked": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(icon_state_t),
+                                               ctypes.POINTER(icon_state_t)]),
+    "icon_state_to_blocked": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(icon_state_t),
+                                             ctypes.POINTER(icon_state_t)]),
+    "icon_dycore_step_blocked": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(icon_state_t)]),
     "icon_profile_begin": (ctypes.c_int, []),
     "icon_profile_end": (ctypes.c_int, [ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
     "icon_column_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _f64p,
@@ -343,6 +348,21 @@ class Dycore:
 
     def velocity_tendencies(self, vn, w, ddt_vn, ddt_w):
         _check(icon_velocity_tendencies(self.handle, _ptr(vn), _ptr(w), _ptr(ddt_vn), _ptr(ddt_w)))
+
+    def from_blocked(self, nproma, blocked, st):
+        """ICON nproma-blocked device state -> the library's layout (device)."""
+        a, b = self._state(blocked), self._state(st)
+        _check(icon_state_from_blocked(self.handle, nproma, ctypes.byref(a), ctypes.byref(b)))
+
+    def to_blocked(self, nproma, st, blocked):
+        """The library's layout -> ICON nproma-blocked device state."""
+        a, b = self._state(st), self._state(blocked)
+        _check(icon_state_to_blocked(self.handle, nproma, ctypes.byref(a), ctypes.byref(b)))
+
+    def step_blocked(self, nproma, blocked):
+        """One step of an ICON nproma-blocked device state, in place."""
+        a = self._state(blocked)
+        _check(icon_dycore_step_blocked(self.handle, nproma, ctypes.byref(a)))
 
     def corrector_features(self, st, col_x, edge_x):
         """Raw corrector features of a device state: col_x [n_cells][5 nlev],

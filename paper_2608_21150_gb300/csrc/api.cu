@@ -246,7 +246,7 @@ bool grid_complete(const GridT<T>& g) {
 }
 
 bool work_complete(const DevWork& w) {
-  const void* p[] = {w.div_m, w.div_t, w.rho_p, w.exner_p, w.theta_p, w.w_p, w.pex, w.col, w.zbl, w.diag, w.flag};
+  const void* p[] = {w.div_m, w.div_t, w.rho_p, w.theta_p, w.w_p, w.pex, w.col, w.zbl, w.diag, w.flag};
   for (const void* q : p)
     if (!q) return false;
   return true;
@@ -563,7 +563,6 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   w.div_m = A.alloc<double>(cf);
   w.div_t = A.alloc<double>(cf);
   w.rho_p = A.alloc<double>(cf);
-  w.exner_p = A.alloc<double>(cf);
   w.theta_p = A.alloc<double>(cf);
   w.w_p = A.alloc<double>(ch);
   w.pex = A.alloc<double>(cf);
@@ -1192,3 +1191,78 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
 }
 
 }  // extern "C"
+
+namespace {
+
+// Checks and runs the blocked <-> level-contiguous copy of all six fields.
+int blocked_copy(icon_dycore* d, int nproma, const icon_state_t* from, const icon_state_t* to, bool to_blocked,
+                 const char* fn) {
+  if (!d || !from || !to) return fail(ICON_ERR_ARG, std::string(fn) + ": NULL argument");
+  if (!on_device(from) || !on_device(to)) return fail(ICON_ERR_ARG, std::string(fn) + ": states must be on the device");
+  const HostGrid& h = d->grid->host;
+  if (nproma < 1 || (h.ne + nproma - 1) / nproma > 65535 || (h.nc + nproma - 1) / nproma > 65535)
+    return fail(ICON_ERR_ARG, std::string(fn) + ": nproma must be >= 1 with at most 65535 blocks");
+  const StateView a = view(from), b = view(to);
+  const double* fa[6] = {a.vn, a.w, a.rho, a.exner, a.theta_v, a.exner_pr};
+  const double* fb[6] = {b.vn, b.w, b.rho, b.exner, b.theta_v, b.exner_pr};
+  for (int f = 0; f < 6; ++f)
+    for (int g = 0; g < 6; ++g)
+      if (fa[f] == fb[g]) return fail(ICON_ERR_ARG, std::string(fn) + ": source and destination arrays overlap");
+  const int nlev = d->nlev;
+  launch_blocked(to_blocked, h.ne, nlev, nproma, a.vn, b.vn, d->stream);
+  launch_blocked(to_blocked, h.nc, nlev + 1, nproma, a.w, b.w, d->stream);
+  launch_blocked(to_blocked, h.nc, nlev, nproma, a.rho, b.rho, d->stream);
+  launch_blocked(to_blocked, h.nc, nlev, nproma, a.exner, b.exner, d->stream);
+  launch_blocked(to_blocked, h.nc, nlev, nproma, a.theta_v, b.theta_v, d->stream);
+  launch_blocked(to_blocked, h.nc, nlev, nproma, a.exner_pr, b.exner_pr, d->stream);
+  CUDA_TRY(cudaGetLastError());
+  return ICON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int icon_state_from_blocked(icon_dycore_t* d, int32_t nproma, const icon_state_t* blocked, const icon_state_t* state) {
+  int rc = blocked_copy(d, nproma, blocked, state, false, "icon_state_from_blocked");
+  if (rc == ICON_OK && d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return rc;
+}
+
+int icon_state_to_blocked(icon_dycore_t* d, int32_t nproma, const icon_state_t* state, const icon_state_t* blocked) {
+  int rc = blocked_copy(d, nproma, state, blocked, true, "icon_state_to_blocked");
+  if (rc == ICON_OK && d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return rc;
+}
+
+int icon_dycore_step_blocked(icon_dycore_t* d, int32_t nproma, const icon_state_t* blocked) {
+  const char* fn = "icon_dycore_step_blocked";
+  if (!d || !blocked) return fail(ICON_ERR_ARG, std::string(fn) + ": NULL argument");
+  const HostGrid& h = d->grid->host;
+  const size_t nlev = d->nlev, ef = (size_t)h.ne * nlev, cf = (size_t)h.nc * nlev, ch = (size_t)h.nc * (nlev + 1);
+  if (!d->have_staging) {
+    StateView& g = d->staging;
+    CUDA_TRY(cudaMalloc(&g.vn, ef * 8));
+    CUDA_TRY(cudaMalloc(&g.w, ch * 8));
+    CUDA_TRY(cudaMalloc(&g.rho, cf * 8));
+    CUDA_TRY(cudaMalloc(&g.exner, cf * 8));
+    CUDA_TRY(cudaMalloc(&g.theta_v, cf * 8));
+    CUDA_TRY(cudaMalloc(&g.exner_pr, cf * 8));
+    d->have_staging = true;
+  }
+  const StateView& g = d->staging;
+  const icon_state_t lib{g.vn, g.w, g.rho, g.exner, g.theta_v, g.exner_pr};
+  int rc = blocked_copy(d, nproma, blocked, &lib, false, fn);
+  if (rc != ICON_OK) return rc;
+  const int sync = d->params.synchronous;
+  d->params.synchronous = 0;
+  rc = run(d, &lib, Op::kStep, fn);
+  d->params.synchronous = sync;
+  if (rc != ICON_OK) return rc;
+  rc = blocked_copy(d, nproma, &lib, blocked, true, fn);
+  if (rc == ICON_OK && sync) CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return rc;
+}
+
+}  // extern "C"
+

@@ -142,7 +142,7 @@ struct WorkT {
 // FP64 work of the column solve and the predicted state.
 struct DevWork {
   double *div_m, *div_t;                  // cells: flux divergences (FP64 sums)
-  double *rho_p, *exner_p, *theta_p;      // cells: predicted state
+  double *rho_p, *theta_p;                // cells: predicted state (the corrector's time averages)
   double* w_p;                            // cells, half levels
   double* pex;   // cells: extrapolated exner perturbation (FP64, or double-word pairs in mixed mode)
   double* col;   // level-major [k][c] scratch: 7 planes of (nlev+1)*nc: cp, rp, rho*, pr*, rho_ic, alpha, eos

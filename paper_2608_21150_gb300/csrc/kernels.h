@@ -102,7 +102,7 @@ void launch_diffusion(const Engine& en, const Ctx<T>& x, const StateView& st, cu
 // Mixed mode: FP32 mirrors from the FP64 state.
 void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t s);
 // Row A7: vertically implicit column solve (corrector = 0: the predicted state
-// into en.wk.w_p/rho_p/exner_p/theta_p; corrector = 1: the new state over st).
+// into en.wk.w_p/rho_p/theta_p; corrector = 1: the new state over st).
 // Reads the flux divergences en.wk.div_m/div_t and ddt_w of type T.
 template <class T>
 void launch_column(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
@@ -137,6 +137,9 @@ int reduce_stage_doubles();  // scratch doubles of launch_reduce_status
 void launch_reduce_status(const float* partial, int n0, int n1, double* stage, double* out, cudaStream_t s);
 void launch_targets(const Engine& en, const StateView& reduced, const StateView& plain, float* col_y, float* edge_y,
                     cudaStream_t s);
+// nproma-blocked (ICON) <-> level-contiguous copy of one field of n points and
+// nlev_x levels (to_blocked: library -> blocked).
+void launch_blocked(bool to_blocked, int n, int nlev_x, int nproma, const double* src, double* dst, cudaStream_t s);
 // One-time kernel attributes (dynamic shared memory above 48 KB).
 cudaError_t init_column_kernels();
 

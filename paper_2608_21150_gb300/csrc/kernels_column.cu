@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         const int o = kk * kLD + t;
         O_w[o] = A::out(wd);
         O_rho[o] = A::out(rnew);
-        O_pi[o] = A::out(lev<R, LEX>(v, k) + prnew);
+        if (a.exner_o) O_pi[o] = A::out(lev<R, LEX>(v, k) + prnew);
         O_th[o] = A::out(thnew);
         if constexpr (kDW) {
           // FP32 mirrors straight from the double-word values, into this
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
     __syncthreads();
     store_tile<KC>(O_w, a.w_o, nlevp, c0, nc, k0, nk);
     store_tile<KC>(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
-    store_tile<KC>(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
+    if (a.exner_o) store_tile<KC>(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
     store_tile<KC>(O_th, a.theta_o, nlev, c0, nc, k0, nk);
     if constexpr (kDW) {
       if (a.m_w) mirror_chunk<KC>(B_cp, B_rp, a.m_w, a.m_rho, a.m_th, nlev, c0, nc, k0, nk);
@@ -545,7 +545,7 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
   } else {
     a.w_o = wk.w_p;
     a.rho_o = wk.rho_p;
-    a.exner_o = wk.exner_p;
+    a.exner_o = nullptr;  // the predicted exner has no reader
     a.theta_o = wk.theta_p;
     if (mixed) a.m_w = en.m.w_p;
   }
