@@ -243,7 +243,7 @@ def measure(P, G, z, st0, prec, args, dev, world):
     return out, t
 
 
-LEARNED = dict(ndyn_reduced=4, hidden=512, max_batch=65536, train_seeds=(100, 101, 102, 103), spinup=4,
+LEARNED = dict(ndyn_reduced=4, hidden=512, max_batch=65536, train_seeds=(100, 101, 102, 103), spinup=1,
                snapshots=8, every=3, rows=8192, adam_steps=1500, batch=4096, lr=1e-3, max_norm=3.0)
 
 
