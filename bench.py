@@ -346,6 +346,7 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
            "train": {"seconds": train_s, "loss_col": [float(np.mean(lc[:10])), float(np.mean(lc[-50:]))],
                      "loss_edge": [float(np.mean(le[:10])), float(np.mean(le[-50:]))], **{
                          k: (list(v) if isinstance(v, tuple) else v) for k, v in L.items()}},
+           "hbm_measured": dram_measured("learned", ms / args.steps),
            "kernels": kernel_table(prof.kernels, 1), "clocks": clocks}
     for x in (cn, en, R, Pl):
         x.close()
@@ -363,6 +364,39 @@ COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
                   "sha256": "4f809caf35b942daaa3beabfe99a223ace11a9fc822d2e89cf49bce59e804c97",
                   # mean of the predictor (2.082 GB) and corrector (3.241 GB) launches, FP64
                   "bytes_per_launch_r2b5": 0.5 * (1.375208e9 + 0.706401e9 + 2.646195e9 + 0.594674e9)}
+
+
+# DRAM bytes per step of every kernel in the timed steps, from one ncu capture
+# of each leg at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid while
+# the kernel sources are the ones captured (SHA-256 over csrc/*, below).
+STEP_DRAM = {"sources_sha256": "f34f0c379cbfcc18d4eca3b209285f9d8336bc8b41fdfecfdb652d6c25a61eed",
+             "bisections": 6, "bytes_per_step": {"fp64": 243.766798e9, "mixed": 194.714794e9,
+                                                 "learned": 167.084504e9}}
+
+
+def sources_sha256():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2608_21150_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_measured(leg, ms_per_step):
+    """Measured DRAM bytes per step (ncu) over the live step time: achieved HBM
+    GB/s and its fraction of the measured peak; null if the kernels changed
+    since the capture or the grid is not the captured one."""
+    t = STEP_DRAM
+    if WORKLOAD["bisections"] != t["bisections"] or sources_sha256() != t["sources_sha256"]:
+        return None
+    b = t["bytes_per_step"][leg]
+    gbs = b / (ms_per_step / 1000.0) / 1e9
+    return {"bytes_per_step": b, "achieved_gbs": gbs, "peak_gbs": 6663.9, "frac": gbs / 6663.9,
+            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all kernels of the timed steps / "
+                    "event-timed step; of measured peak"}
 
 
 def column_traffic(nc):
@@ -455,6 +489,7 @@ def run_ours(args):
               "rms_t850_k": rms(m["t850"] - f64["t850"]) if f64 else None,
               "compared_after_steps": args.warmup + args.steps,
               "reference": "FP64 GPU dycore (equal to the FP64 oracle to 1e-9 after 10 steps, GPU parity tests)",
+              "hbm_measured": dram_measured("mixed", m["ms"] / args.steps),
               "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"],
               "autotuned_launch_config": m["launch_config"]}
 
@@ -494,6 +529,7 @@ def run_ours(args):
                 "peak_gbs": 6663.9, "frac": hbm_bytes / (ms_per_step / 1000.0) / 1e9 / 6663.9,
                 "note": "compulsory (state read+write per substep and diffusion) bytes / step time; "
                         "of measured peak"} if ms_per_step else None,
+        "hbm_measured": dram_measured("fp64", ms_per_step) if ms_per_step else None,
         "roofline": roof,
         "kernels": kernels,
         "autotuned_launch_config": f64["launch_config"] if f64 else None,
