@@ -239,7 +239,7 @@ template <class T>
 bool grid_complete(const GridT<T>& g) {
   const void* p[] = {g.c2e, g.c2e2c, g.e2c, g.e2v, g.e2c2v, g.e2c2e, g.v2e, g.v2c, g.div_c, g.lap_c, g.e2c_w,
                      g.grad_c, g.k4w_c, g.inv_d, g.inv_l, g.f_e, g.vt_w, g.upw, g.nt, g.inv_dn, g.smag_a, g.k4_a,
-                     g.fdiv_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl};
+                     g.fdiv_e, g.ddamp_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl};
   for (const void* q : p)
     if (!q) return false;
   return true;
@@ -443,12 +443,13 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   en.sc = s;
 
   // parameter-dependent grid factors
-  std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc), fdiv(ne);
+  std::vector<double> fe(ne), smag(ne), k4(ne), k4w(nc), fdiv(ne), ddamp(ne);
   for (int e = 0; e < ne; ++e) {
     fe[e] = 2.0 * p->omega * h.coriolis_z[e];
     smag[e] = p->hdiff_smag_fac * h.edge_area[e];
     k4[e] = p->hdiff_k4 * h.edge_area[e] * h.edge_area[e];
     fdiv[e] = s.divflux * h.inv_d[e];
+    ddamp[e] = s.divdamp * h.mean_area * h.mean_area * h.inv_d[e];
   }
   for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
   en.g64 = grid->dev;
@@ -457,6 +458,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   en.g64.k4_a = A.upload(k4);
   en.g64.k4w_c = A.upload(k4w);
   en.g64.fdiv_e = A.upload(fdiv);
+  en.g64.ddamp_e = A.upload(ddamp);
 
   const size_t ef = (size_t)ne * nlev, eh = (size_t)ne * (nlev + 1);
   const size_t cf = (size_t)nc * nlev, ch = (size_t)nc * (nlev + 1);
@@ -492,6 +494,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     g.smag_a = up(smag);
     g.k4_a = up(k4);
     g.fdiv_e = up(fdiv);
+    g.ddamp_e = up(ddamp);
     g.curl_v = up(h.curl_v);
     g.c2v_w = up(h.c2v_w);
     g.uv_w = up(h.uv_w);
@@ -1082,6 +1085,8 @@ extern "C" {
 
 int icon_corrector_features(icon_dycore_t* d, const icon_state_t* s, float* col_x, float* edge_x) {
   if (!d || !s || !col_x || !edge_x) return fail(ICON_ERR_ARG, "icon_corrector_features: NULL argument");
+  if ((double)d->grid->host.ne * (11.0 * d->nlev) >= 4294967295.0)
+    return fail(ICON_ERR_ARG, "icon_corrector_features: grid too large for 32-bit indexing");
   if (!on_device(s)) return fail(ICON_ERR_ARG, "icon_corrector_features: the state must be on the device");
   const StateView st = view(s);
   launch_col_features(d->en, st, col_x, nullptr, 0, nullptr, nullptr, d->stream);
@@ -1094,6 +1099,8 @@ int icon_corrector_features(icon_dycore_t* d, const icon_state_t* s, float* col_
 int icon_corrector_targets(icon_dycore_t* d, const icon_state_t* reduced, const icon_state_t* plain, float* col_y,
                            float* edge_y) {
   if (!d || !reduced || !plain || !col_y || !edge_y) return fail(ICON_ERR_ARG, "icon_corrector_targets: NULL argument");
+  if ((double)d->grid->host.nc * (3.0 * d->nlev) >= 4294967295.0)
+    return fail(ICON_ERR_ARG, "icon_corrector_targets: grid too large for 32-bit indexing");
   if (!on_device(reduced) || !on_device(plain))
     return fail(ICON_ERR_ARG, "icon_corrector_targets: the states must be on the device");
   launch_targets(d->en, view(reduced), view(plain), col_y, edge_y, d->stream);
@@ -1118,6 +1125,9 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
   int ni, no, mbc, mbe;
   mlp_dims(col_net, &ni, &no, &mbc);
   mlp_dims(edge_net, &ni, &no, &mbe);
+  // the feature and increment kernels index one chunk or one field with 32 bits
+  if ((double)std::max(mbc, mbe) * (11.0 * nlev) >= 4294967295.0 || (double)ne * (11.0 * nlev) >= 4294967295.0)
+    return fail(ICON_ERR_ARG, std::string(fn) + ": grid or network batch too large for 32-bit indexing");
   // partial-sum slots: one per 256 outputs of every chunk
   int pc = 0, pe = 0;
   for (int r0 = 0; r0 < nc; r0 += mbc) pc += apply_partials((size_t)std::min(mbc, nc - r0) * (3 * nlev - 1));

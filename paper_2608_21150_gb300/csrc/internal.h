@@ -41,6 +41,7 @@ struct GridT {
   const T* smag_a;  // [ne] hdiff_smag_fac * A_e
   const T* k4_a;    // [ne] hdiff_k4 * A_e^2
   const T* fdiv_e;  // [ne] divflux_fac * mean cell area / d_e (flux filter)
+  const T* ddamp_e; // [ne] divdamp_fac * mean cell area^2 / d_e (divergence damping)
   // vertex coefficients
   const T* curl_v;  // [nv*6] t_{v,e} d_e / A_v (0 for pads)
   const T* c2v_w;   // [nv*6] cell->vertex weights (0 for pads)

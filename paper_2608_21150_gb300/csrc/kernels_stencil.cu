@@ -193,9 +193,8 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
     h += q[1] * gw_e[(size_t)ce[1] * nlevp + k];
     h += q[2] * gw_e[(size_t)ce[2] * nlevp + k];
     const T* wc = w + (size_t)c * nlevp;
-    const T wf_up = T(0.5) * (wc[k - 1] + wc[k]);
-    const T wf_dn = T(0.5) * (wc[k] + wc[k + 1]);
-    r = -h - wc[k] * (wf_up - wf_dn) * v.inv_dzh[k];
+    // the difference of the full-level means above and below, (w_k-1 - w_k+1) / 2
+    r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
   }
   ddt_w[(size_t)c * nlevp + k] = r;
 }
@@ -300,9 +299,9 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
   if (!flat_index(g.ne, nlev, e, k)) return;
   const size_t ie = (size_t)e * nlev + k;
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-  const T dd = (divd2[(size_t)c1 * nlev + k] - divd2[(size_t)c0 * nlev + k]) * g.inv_d[e];
-  const T am = g.mean_area;
-  const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - sc.divdamp * am * am * dd;
+  // fourth-order divergence damping: divdamp_fac Abar^2 grad_n(dd2), coefficient per edge
+  const T damp = g.ddamp_e[e] * (divd2[(size_t)c1 * nlev + k] - divd2[(size_t)c0 * nlev + k]);
+  const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - damp;
   if constexpr (kMixed<T>) {
     const double vnn = vn[ie] + f2d(inc);
     vn[ie] = vnn;

@@ -44,7 +44,8 @@ __global__ void col_features(int nc, int nlev, const int* __restrict__ c2e, cons
                              const float* __restrict__ mean, const float* __restrict__ istd) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)nc * nlev) return;
-  const int c = (int)(i / nlev), k = (int)(i - (size_t)c * nlev);
+  const unsigned ui = (unsigned)i;  // < 2^32 (checked by the callers)
+  const int c = (int)(ui / (unsigned)nlev), k = (int)(ui - (unsigned)c * (unsigned)nlev);
   const size_t ic = (size_t)c * nlev + k;
   const double* wc = st.w + (size_t)c * (nlev + 1);
   float f[5];
@@ -78,7 +79,8 @@ __global__ void edge_features(int ne, int nlev, const int* __restrict__ e2c, con
                               const float* __restrict__ mean, const float* __restrict__ istd) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)ne * nlev) return;
-  const int e = (int)(i / nlev), k = (int)(i - (size_t)e * nlev);
+  const unsigned ui = (unsigned)i;  // < 2^32 (checked by the callers)
+  const int e = (int)(ui / (unsigned)nlev), k = (int)(ui - (unsigned)e * (unsigned)nlev);
   O* xe = x + (size_t)e * ldx;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -122,7 +124,8 @@ __global__ void apply_col(int row0, int rows, int nlev, const float* __restrict_
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   float s = 0.f;
   if (i < (size_t)rows * no) {
-    const int r = (int)(i / no), j = (int)(i - (size_t)r * no);
+    const unsigned ui = (unsigned)i;  // < 2^32 (checked by the callers)
+    const int r = (int)(ui / (unsigned)no), j = (int)(ui - (unsigned)r * (unsigned)no);
     const size_t c = (size_t)row0 + r;
     const float yn = y[(size_t)r * ldy + j];
     s = yn * yn;
@@ -151,7 +154,8 @@ __global__ void apply_edge(int row0, int rows, int nlev, const float* __restrict
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   float s = 0.f;
   if (i < (size_t)rows * nlev) {
-    const int r = (int)(i / nlev), k = (int)(i - (size_t)r * nlev);
+    const unsigned ui = (unsigned)i;  // < 2^32 (checked by the callers)
+    const int r = (int)(ui / (unsigned)nlev), k = (int)(ui - (unsigned)r * (unsigned)nlev);
     const float yn = y[(size_t)r * ldy + k];
     s = yn * yn;
     double* p = vn + ((size_t)row0 + r) * nlev + k;
@@ -196,7 +200,8 @@ __global__ void col_targets(int nc, int nlev, StateView a, StateView b, float* _
   const int no = 3 * nlev - 1;
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)nc * no) return;
-  const int c = (int)(i / no), j = (int)(i - (size_t)c * no);
+  const unsigned ui = (unsigned)i;  // < 2^32 (checked by the callers)
+  const int c = (int)(ui / (unsigned)no), j = (int)(ui - (unsigned)c * (unsigned)no);
   double d;
   if (j < nlev - 1) {
     const size_t ih = (size_t)c * (nlev + 1) + j + 1;
