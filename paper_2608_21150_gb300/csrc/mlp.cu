@@ -4,10 +4,13 @@
 // GPU.  GELU is the erf form, 0.5 x (1 + erf(x / sqrt(2))).
 //
 // Every GEMM is C[M x N] = A[M x K] * B[N x K]^T with both operands K-major
-// ("NT"), the layout the warp-level BF16 MMA consumes directly.  Leading
-// dimensions are padded to multiples of 64 and the pads hold zeros, so K
-// needs no tail handling; ragged M and N are guarded.  The backward GEMMs
-// reuse the same kernel on transposed copies (dW^T = dZ^T H, dH = dZ W).
+// ("NT"), the layout tcgen05.mma reads from 128-byte-swizzled shared memory
+// without transposes.  Leading dimensions are padded to multiples of 64 and
+// the pads hold zeros, so K needs no tail handling; rows of A and B past M and
+// N read as zero through the TMA bounds and the epilogue stores guard them.
+// The backward GEMMs reuse the same kernel on transposed copies (dW^T = dZ^T
+// H over the batch, dH = dZ W).  The forward epilogue's GELU uses a 1.5e-7
+// erf approximation (below); the backward pass differentiates the erf form.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
