@@ -38,7 +38,7 @@ def build(verbose=False, force=False):
     """Compile the CUDA/C++ sources and link the shared library; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "icon_dycore.h"))
     newest_header = max(os.path.getmtime(h) for h in headers)
     jobs = []

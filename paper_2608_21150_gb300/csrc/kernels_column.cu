@@ -20,7 +20,12 @@
 // kCW columns stages chunks of kKC levels of every input through shared
 // memory with coalesced loads (a column's chunk is a contiguous run), and
 // stages its outputs the same way.  The Thomas scratch is level-major
-// [k][c], coalesced for one thread per column.
+// [k][c], coalesced for one thread per column; it is written as streaming
+// data and read back evict-first, while the input rows are kept (L2 policies
+// below).  The double-word form also stages each chunk's slice of the
+// per-level table in shared memory: every thread of the CTA reads the same
+// level at the same time, and from L1 those loads were a large share of the
+// kernel's stalls.  The predictor and corrector forms are separate kernels.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,12 +47,17 @@ constexpr int kTilesFwd = 11;
 // backward: 8 level-major scratch chunks [KC][kCW] + 4 output tiles
 template <int KC>
 __host__ __device__ constexpr int tile_doubles() { return (KC + 1) * kLD; }
+// doubles of the tiles; the per-level table of a chunk (16 slots per level,
+// KC + 1 levels) follows them
+template <int KC>
+__host__ __device__ constexpr int tiles_doubles() {
+  return kTilesFwd * tile_doubles<KC>() > 8 * KC * kCW + 4 * tile_doubles<KC>()
+             ? kTilesFwd * tile_doubles<KC>()
+             : 8 * KC * kCW + 4 * tile_doubles<KC>();
+}
 template <int KC>
 constexpr size_t smem_bytes() {
-  return (kTilesFwd * (size_t)tile_doubles<KC>() > 8 * (size_t)KC * kCW + 4 * (size_t)tile_doubles<KC>()
-              ? kTilesFwd * (size_t)tile_doubles<KC>()
-              : 8 * (size_t)KC * kCW + 4 * (size_t)tile_doubles<KC>()) *
-         sizeof(double);
+  return ((size_t)tiles_doubles<KC>() + 16 * (size_t)(KC + 1)) * sizeof(double);
 }
 constexpr size_t kSmem = smem_bytes<kKC>();
 
@@ -73,12 +83,26 @@ __device__ __forceinline__ void cp8(double* dst, const double* src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp4(float* dst, const float* src) {
+// The row-gathered input copies mark their lines evict-last in L2: a chunk
+// reads a few levels of every row, so the rest of a 128-byte line is used
+// by the next chunks of the same CTA, and the Thomas scratch streaming
+// through L2 meanwhile should be evicted first.
+__device__ __forceinline__ void cp_async(double* dst, const double* src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+  asm volatile(
+      "{\n.reg .b64 pol;\ncreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n"
+      "cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, pol;\n}\n" ::"r"(s),
+      "l"(src)
+      : "memory");
 }
-__device__ __forceinline__ void cp_async(double* dst, const double* src) { cp8(dst, src); }
-__device__ __forceinline__ void cp_async(float* dst, const float* src) { cp4(dst, src); }
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile(
+      "{\n.reg .b64 pol;\ncreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n"
+      "cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, pol;\n}\n" ::"r"(s),
+      "l"(src)
+      : "memory");
+}
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // tile[kk][col] = X[rows[col] * ld + k0 + kk] for kk < nk (level-contiguous
@@ -116,6 +140,26 @@ __device__ __forceinline__ void tile_levels(double* tile, int ldt, const double*
   const int col = threadIdx.x;
   const int cc = c0 + col < nc ? c0 + col : nc - 1;
   for (int kk = 0; kk < nk; ++kk) cp8(tile + kk * ldt + col, X + (size_t)(k0 + kk) * nc + cc);
+}
+
+// L2 policy for data read for the last time: its lines are the first to go,
+// so that the partly consumed input rows of the forward sweep stay resident
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+
+// tile_levels for scratch read for the last time (evict-first in L2)
+__device__ __forceinline__ void tile_levels_last(double* tile, int ldt, const double* __restrict__ X, int nc, int c0,
+                                                 int k0, int nk, unsigned long long pol) {
+  const int col = threadIdx.x;
+  const int cc = c0 + col < nc ? c0 + col : nc - 1;
+  const unsigned s = (unsigned)__cvta_generic_to_shared(tile + col);
+  for (int kk = 0; kk < nk; ++kk)
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s + kk * ldt * 8),
+                 "l"(X + (size_t)(k0 + kk) * nc + cc), "l"(pol)
+                 : "memory");
 }
 
 template <int NK>
@@ -232,18 +276,28 @@ __device__ __forceinline__ R lev(const DevVert& v, int k) {
   }
 }
 
+// Per-level quantity of level k; the double-word form reads the chunk's copy
+// of the table in shared memory (Ls: levels from k0 on, 16 slots each).
+template <class R, int J>
+__device__ __forceinline__ R levs(const DevVert& v, const double* Ls, int k, int k0) {
+  if constexpr (std::is_same<R, df>::value) {
+    return *reinterpret_cast<const df*>(Ls + 16 * (k - k0) + J);
+  } else {
+    return lev<R, J>(v, k);
+  }
+}
+
 // Sum of two non-negative values (densities, potential temperatures, positive
 // coefficients): the cheaper double-word addition is exact enough without
 // cancellation; plain addition in FP64.
 __device__ __forceinline__ double add_pos(double a, double b) { return a + b; }
 __device__ __forceinline__ df add_pos(df a, df b) { return add_same_sign(a, b); }
 
-// Scratch planes hold R values in 8-byte slots (a df is two floats).
-template <class R>
-__device__ __forceinline__ void put(double* p, R x) {
-  static_assert(sizeof(R) == sizeof(double), "scratch slot");
-  *reinterpret_cast<R*>(p) = x;
-}
+// Scratch planes hold R values in 8-byte slots (a df is two floats).  They
+// are read back only after the whole forward sweep, so they are stored as
+// streaming (evict-first) data that does not displace the input rows in L2.
+__device__ __forceinline__ void put(double* p, double x) { __stcs(p, x); }
+__device__ __forceinline__ void put(double* p, df x) { __stcs(reinterpret_cast<float2*>(p), make_float2(x.hi, x.lo)); }
 template <class R>
 __device__ __forceinline__ R get(const double* p) {
   return *reinterpret_cast<const R*>(p);
@@ -252,8 +306,13 @@ __device__ __forceinline__ R get(const double* p) {
 // kOwnZb: the corrector form computes zb and the equation-of-state term itself
 // (as the predictor does) instead of reading the predictor's; used by the
 // allocation-free entry point below.
-template <class T, bool kOwnZb = false, int KC = kKC, class R = double>
-__global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector, ColArgs<T> a) {
+// kCorr: 0 the predictor form, 1 the corrector form, -1 the form the
+// `corrector` argument names (one kernel for both; the allocation-free entry).
+// The fixed forms are separate, smaller kernels.
+template <class T, bool kOwnZb = false, int KC = kKC, class R = double, int kCorr = -1>
+__global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector_arg,
+                                                          ColArgs<T> a) {
+  const bool corrector = kCorr < 0 ? corrector_arg != 0 : kCorr == 1;
   using A = Ar<R>;
   constexpr bool kDW = std::is_same<R, df>::value;
   constexpr int kTile = tile_doubles<KC>();
@@ -279,6 +338,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
   double* T_rp = sm + 8 * kTile;
   double* T_tp = sm + 9 * kTile;
   double* T_zb = sm + 10 * kTile;
+  double* L_s = sm + tiles_doubles<KC>();
+  const double* lev_src = reinterpret_cast<const double*>(v.lev_hl);
 
   const size_t plane = (size_t)nlevp * nc;
   double* cp_s = a.col;
@@ -319,6 +380,9 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       tile_rows<KC>(T_tp, a.theta_p, nlev, rows_c, k0, nkf);
       if (!kOwnZb) tile_levels(T_zb, kLD, a.zbl, nc, c0, k0, nkc);
     }
+    if constexpr (kDW) {
+      for (int i = t; i < 16 * nkf; i += kCW) cp8(L_s + i, lev_src + 16 * (size_t)k0 + i);
+    }
     cp_wait();
     __syncthreads();
     if (!active) continue;
@@ -331,11 +395,11 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         th_c = A::in(T_th[o]);
         ra_c = corrector ? add_pos(wn_r * rho_c, wnew_r * A::in(T_rp[o])) : rho_c;
         ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * A::in(T_tp[o])) : th_c;
-        tpa_c = ta_c - lev<R, LTH>(v, 0);
+        tpa_c = ta_c - levs<R, LTH>(v, L_s, 0, k0);
         wk_c = A::in(T_w[o]);
       }
       const R rho_n = rho_c, th_n = th_c, pi_n = A::in(T_pi[o]);
-      const R pr_k = pi_n - lev<R, LEX>(v, k);
+      const R pr_k = pi_n - levs<R, LEX>(v, L_s, k, k0);
       // interface k+1 from full levels k and k+1 (time-averaged in the corrector)
       R ric_k1 = zero, tic_k1 = zero, tpic_k1 = zero;
       R rho_x = zero, th_x = zero, ra_x = zero, ta_x = zero, tpa_x = zero;
@@ -344,8 +408,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         th_x = A::in(T_th[o + kLD]);
         ra_x = corrector ? add_pos(wn_r * rho_x, wnew_r * A::in(T_rp[o + kLD])) : rho_x;
         ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * A::in(T_tp[o + kLD])) : th_x;
-        tpa_x = ta_x - lev<R, LTH>(v, k + 1);
-        const R g1 = lev<R, WG>(v, k + 1), g2 = lev<R, WG2>(v, k + 1);
+        tpa_x = ta_x - levs<R, LTH>(v, L_s, k + 1, k0);
+        const R g1 = levs<R, WG>(v, L_s, k + 1, k0), g2 = levs<R, WG2>(v, L_s, k + 1, k0);
         ric_k1 = add_pos(g1 * ra_c, g2 * ra_x);
         tic_k1 = add_pos(g1 * ta_c, g2 * ta_x);
         tpic_k1 = g1 * tpa_c + g2 * tpa_x;
@@ -353,7 +417,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       const size_t ik = (size_t)k * nc + c;
       R zb;
       if (!corrector || kOwnZb) {
-        zb = lev<R, CZB>(v, k) * pi_n * A::inv(rho_n * th_n);
+        zb = levs<R, CZB>(v, L_s, k, k0) * pi_n * A::inv(rho_n * th_n);
         put(a.zbl + ik, zb);
         put(eb_s + ik, pi_n - cvd_o_rd * pr_k);
       } else {
@@ -361,8 +425,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       }
       const R wk = wk_c, wk1 = A::in(T_w[o + kLD]);
       const R rt_k1 = ric_k1 * tic_k1;
-      const R rstar = rho_n - dt * A::in(T_dm[o]) - lev<R, CR>(v, k) * (ric_k * wk - ric_k1 * wk1);
-      const R pstar = pr_k - zb * (lev<R, LDZ>(v, k) * A::in(T_dt[o]) + ombeta * (rt_k * wk - rt_k1 * wk1));
+      const R rstar = rho_n - dt * A::in(T_dm[o]) - levs<R, CR>(v, L_s, k, k0) * (ric_k * wk - ric_k1 * wk1);
+      const R pstar = pr_k - zb * (levs<R, LDZ>(v, L_s, k, k0) * A::in(T_dt[o]) + ombeta * (rt_k * wk - rt_k1 * wk1));
       const R al_k = beta * rt_k, al_k1 = beta * rt_k1;
       put(rs_s + ik, rstar);
       put(ps_s + ik, pstar);
@@ -375,8 +439,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         } else {
           ddtw = corrector ? wn_v * A::in(T_dw0[o]) + wnew_v * A::in(T_dw1[o]) : A::in(T_dw0[o]);
         }
-        const R wstar = wk + dt * ddtw - (lev<R, CWX>(v, k) * tic_k * (pr_km1 - pr_k) + lev<R, CB>(v, k) * tpic_k);
-        const R gam = lev<R, CGAM>(v, k) * tic_k;
+        const R wstar = wk + dt * ddtw - (levs<R, CWX>(v, L_s, k, k0) * tic_k * (pr_km1 - pr_k) + levs<R, CB>(v, L_s, k, k0) * tpic_k);
+        const R gam = levs<R, CGAM>(v, L_s, k, k0) * tic_k;
         const R am = -(gam * zb_km1 * al_km1);
         const R bm = add_pos(one, gam * al_k * add_pos(zb_km1, zb));
         const R cm = -(gam * zb * al_k1);
@@ -430,17 +494,21 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
   // other threads of the CTA through the asynchronous copies below
   __threadfence_block();
   R w_und_k1 = zero, wd_k1 = zero, ric_k1 = zero, al_k1 = zero;
+  const unsigned long long pol_last = policy_evict_first();
   for (int kend = nlev; kend > 0; kend -= KC) {
     const int k0 = max(0, kend - KC), nk = kend - k0;
     __syncthreads();
-    tile_levels(B_cp, kCW, cp_s, nc, c0, k0, nk);
-    tile_levels(B_rp, kCW, rp_s, nc, c0, k0, nk);
-    tile_levels(B_rs, kCW, rs_s, nc, c0, k0, nk);
-    tile_levels(B_ps, kCW, ps_s, nc, c0, k0, nk);
-    tile_levels(B_ri, kCW, ri_s, nc, c0, k0, nk);
-    tile_levels(B_al, kCW, al_s, nc, c0, k0, nk);
-    tile_levels(B_eb, kCW, eb_s, nc, c0, k0, nk);
+    tile_levels_last(B_cp, kCW, cp_s, nc, c0, k0, nk, pol_last);
+    tile_levels_last(B_rp, kCW, rp_s, nc, c0, k0, nk, pol_last);
+    tile_levels_last(B_rs, kCW, rs_s, nc, c0, k0, nk, pol_last);
+    tile_levels_last(B_ps, kCW, ps_s, nc, c0, k0, nk, pol_last);
+    tile_levels_last(B_ri, kCW, ri_s, nc, c0, k0, nk, pol_last);
+    tile_levels_last(B_al, kCW, al_s, nc, c0, k0, nk, pol_last);
+    tile_levels_last(B_eb, kCW, eb_s, nc, c0, k0, nk, pol_last);
     tile_levels(B_zb, kCW, a.zbl, nc, c0, k0, nk);
+    if constexpr (kDW) {
+      for (int i = t; i < 16 * nk; i += kCW) cp8(L_s + i, lev_src + 16 * (size_t)k0 + i);
+    }
     cp_wait();
     __syncthreads();
     if (active) {
@@ -451,24 +519,24 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         R w_und = zero, wd = zero;
         if (k >= 1) {
           w_und = get<R>(B_rp + b) - get<R>(B_cp + b) * w_und_k1;
-          wd = w_und * lev<R, LRAY>(v, k);
+          wd = w_und * levs<R, LRAY>(v, L_s, k, k0);
         }
         const R ric = get<R>(B_ri + b), al = get<R>(B_al + b), zb = get<R>(B_zb + b);
-        const R rnew = get<R>(B_rs + b) - lev<R, CRN>(v, k) * (ric * wd - ric_k1 * wd_k1);
+        const R rnew = get<R>(B_rs + b) - levs<R, CRN>(v, L_s, k, k0) * (ric * wd - ric_k1 * wd_k1);
         const R prnew = get<R>(B_ps + b) - zb * (al * wd - al_k1 * wd_k1);
-        const R thnew = lev<R, CZB>(v, k) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
+        const R thnew = levs<R, CZB>(v, L_s, k, k0) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
         const int o = kk * kLD + t;
         O_w[o] = A::out(wd);
         O_rho[o] = A::out(rnew);
-        if (a.exner_o) O_pi[o] = A::out(lev<R, LEX>(v, k) + prnew);
+        if (a.exner_o) O_pi[o] = A::out(levs<R, LEX>(v, L_s, k, k0) + prnew);
         O_th[o] = A::out(thnew);
         if constexpr (kDW) {
           // FP32 mirrors straight from the double-word values, into this
           // thread's consumed scratch slots: (w, rho - rho_ref) and theta_v - theta_ref
           float* m0 = reinterpret_cast<float*>(B_cp + b);
           m0[0] = to_float(wd);
-          m0[1] = to_float(rnew - lev<R, LRHO>(v, k));
-          reinterpret_cast<float*>(B_rp + b)[0] = to_float(thnew - lev<R, LTH>(v, k));
+          m0[1] = to_float(rnew - levs<R, LRHO>(v, L_s, k, k0));
+          reinterpret_cast<float*>(B_rp + b)[0] = to_float(thnew - levs<R, LTH>(v, L_s, k, k0));
         }
         w_und_k1 = w_und;
         wd_k1 = wd;
@@ -499,17 +567,18 @@ template <class T>
 using ColArith = typename std::conditional<std::is_same<T, float>::value, df, double>::type;
 
 cudaError_t init_column_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(sn_column_tiled<double, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes<8>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 8, df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<8>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sn_column_tiled<double, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<4>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sn_column_tiled<float, false, 4, df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<4>());
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto kernel, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  set(sn_column_tiled<double, false, 8, double, 0>, smem_bytes<8>());
+  set(sn_column_tiled<double, false, 8, double, 1>, smem_bytes<8>());
+  set(sn_column_tiled<float, false, 8, df, 0>, smem_bytes<8>());
+  set(sn_column_tiled<float, false, 8, df, 1>, smem_bytes<8>());
+  set(sn_column_tiled<double, false, 4, double, 0>, smem_bytes<4>());
+  set(sn_column_tiled<double, false, 4, double, 1>, smem_bytes<4>());
+  set(sn_column_tiled<float, false, 4, df, 0>, smem_bytes<4>());
+  set(sn_column_tiled<float, false, 4, df, 1>, smem_bytes<4>());
   return e;
 }
 
@@ -552,12 +621,19 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
   const unsigned blocks = (unsigned)((en.g64.nc + kCW - 1) / kCW);
   const char* name = mixed ? (corrector ? "sn_column_corr_mx" : "sn_column_pred_mx")
                            : (corrector ? "sn_column_corr" : "sn_column_pred");
-  if (en.col_kc == 4)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4, ColArith<T>>), en.g64.nc,
-                     en.v, en.sc, corrector, a);
+  using RA = ColArith<T>;
+  if (en.col_kc == 4 && corrector)
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4, RA, 1>), en.g64.nc, en.v,
+                     en.sc, 1, a);
+  else if (en.col_kc == 4)
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4, RA, 0>), en.g64.nc, en.v,
+                     en.sc, 0, a);
+  else if (corrector)
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8, RA, 1>), en.g64.nc, en.v,
+                     en.sc, 1, a);
   else
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8, ColArith<T>>), en.g64.nc,
-                     en.v, en.sc, corrector, a);
+    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8, RA, 0>), en.g64.nc, en.v,
+                     en.sc, 0, a);
 }
 
 template void launch_column<double>(const Engine&, int, const StateView&, const double*, const double*, cudaStream_t);
