@@ -439,6 +439,8 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   v.colc = A.upload(colc);
   v.lev_hl = A.upload(level_pairs(nlev, colc.data(), d->exner_ref.data(), d->theta_ref.data(), dz.data(), ray.data(),
                                   rho_ref.data()));
+  v.lev64 = A.upload(level_table64(nlev, colc.data(), d->exner_ref.data(), d->theta_ref.data(), dz.data(), ray.data(),
+                                   rho_ref.data()));
   en.rho_ref64 = A.upload(rho_ref);
   en.sc = s;
 
@@ -590,7 +592,10 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   }
   {
     const bool mixed = p->precision == ICON_PREC_MIXED;
-    const bool ok = grid_complete(en.g64) && work_complete(en.wk) &&
+    const DevVert& vv = en.v;
+    const bool vert_ok = vv.dz && vv.inv_dz && vv.inv_dzh && vv.wgt && vv.theta_ref && vv.exner_ref &&
+                         vv.dexner_ref_ic && vv.ray_fac && vv.colc && vv.lev_hl && vv.lev64;
+    const bool ok = vert_ok && grid_complete(en.g64) && work_complete(en.wk) &&
                     (mixed ? grid_complete(en.c32.g) : grid_complete(en.c64.g));
     if (!ok) {
       A.release();

@@ -91,6 +91,8 @@ struct DevVert {
   // k = 0..nlev: colc 0..7, then exner_ref, theta_ref, dz, ray_fac, rho_ref
   // (zero where a quantity is not defined at that level)
   const float* lev_hl;     // [(nlev+1)*32]
+  // the same 16 quantities per level in FP64, lev64[16 k + j]
+  const double* lev64;     // [(nlev+1)*16]
 };
 
 // double -> (hi, lo) FP32 pair with hi + lo = x to about 48 bits
@@ -115,6 +117,24 @@ inline void level_pairs_into(float* t, int nlev, const double* colc, const doubl
     }
     split_hl(ray_fac[k], r + 22);
   }
+}
+
+// the lev64 table of DevVert (the slots of lev_hl, one double each)
+inline std::vector<double> level_table64(int nlev, const double* colc, const double* exner_ref, const double* theta_ref,
+                                         const double* dz, const double* ray_fac, const double* rho_ref) {
+  std::vector<double> t(16 * (size_t)(nlev + 1), 0.0);
+  for (int k = 0; k <= nlev; ++k) {
+    double* r = t.data() + 16 * (size_t)k;
+    for (int j = 0; j < 8; ++j) r[j] = colc[8 * (size_t)k + j];
+    if (k < nlev) {
+      r[8] = exner_ref[k];
+      r[9] = theta_ref[k];
+      r[10] = dz[k];
+      if (rho_ref) r[12] = rho_ref[k];
+    }
+    r[11] = ray_fac[k];
+  }
+  return t;
 }
 
 inline std::vector<float> level_pairs(int nlev, const double* colc, const double* exner_ref, const double* theta_ref,
@@ -142,7 +162,7 @@ struct WorkT {
 
 // FP64 work of the column solve and the predicted state.
 struct DevWork {
-  double *div_m, *div_t;                  // cells: flux divergences (FP64 sums)
+  double *div_m, *div_t;                  // cells: flux divergences (FP64 sums; double-word pairs in mixed mode)
   double *rho_p, *theta_p;                // cells: predicted state (the corrector's time averages)
   double* w_p;                            // cells, half levels
   double* pex;   // cells: extrapolated exner perturbation (FP64, or double-word pairs in mixed mode)

@@ -42,24 +42,34 @@ namespace {
 constexpr int kCW = 64;          // columns (threads) per CTA
 constexpr int kKC = 4;           // default levels per chunk (the autotuner may pick 8)
 constexpr int kLD = kCW + 1;     // padded tile row for column-gathered tiles
-// forward tiles: w, rho, exner, theta, ddt_w0, div_m, div_t, ddt_w1, rho_p, theta_p, zb
-constexpr int kTilesFwd = 11;
-// backward: 8 level-major scratch chunks [KC][kCW] + 4 output tiles
 template <int KC>
 __host__ __device__ constexpr int tile_doubles() { return (KC + 1) * kLD; }
-// doubles of the tiles; the per-level table of a chunk (16 slots per level,
-// KC + 1 levels) follows them
-template <int KC>
-__host__ __device__ constexpr int tiles_doubles() {
-  return kTilesFwd * tile_doubles<KC>() > 8 * KC * kCW + 4 * tile_doubles<KC>()
-             ? kTilesFwd * tile_doubles<KC>()
-             : 8 * KC * kCW + 4 * tile_doubles<KC>();
+// Shared memory of one CTA, in bytes.  Forward: the FP64 tiles w, rho,
+// exner, theta, div_m, div_t (+ rho_p, theta_p, zb in the corrector), then
+// the tendency tiles ddt_w0 (+ ddt_w1) of the stencils' type T, each
+// (KC + 1) x kLD.  Backward (reusing it): 8 level-major scratch chunks
+// [KC][kCW] and 4 output tiles [KC][kLD].  Then the per-level table of a
+// chunk: 16 slots per level, KC + 1 levels.  kCorrTiles: room for the
+// corrector's tiles.
+template <class T, int KC, bool kCorrTiles>
+__host__ __device__ constexpr int fwd_bytes() {
+  return (6 + (kCorrTiles ? 3 : 0)) * tile_doubles<KC>() * 8 + (kCorrTiles ? 2 : 1) * tile_doubles<KC>() * (int)sizeof(T);
 }
 template <int KC>
+__host__ __device__ constexpr int back_bytes() {
+  return (8 * KC * kCW + 4 * KC * kLD) * 8;
+}
+template <class T, int KC, bool kCorrTiles>
+__host__ __device__ constexpr int lev_offset_bytes() {
+  return ((fwd_bytes<T, KC, kCorrTiles>() > back_bytes<KC>() ? fwd_bytes<T, KC, kCorrTiles>() : back_bytes<KC>()) +
+          15) /
+         16 * 16;
+}
+template <class T, int KC, bool kCorrTiles>
 constexpr size_t smem_bytes() {
-  return ((size_t)tiles_doubles<KC>() + 16 * (size_t)(KC + 1)) * sizeof(double);
+  return (size_t)lev_offset_bytes<T, KC, kCorrTiles>() + 16 * (size_t)(KC + 1) * sizeof(double);
 }
-constexpr size_t kSmem = smem_bytes<kKC>();
+constexpr size_t kSmem = smem_bytes<double, kKC, true>();
 
 enum { CZB = 0, CR = 1, CRN = 2, CWX = 3, CB = 4, CGAM = 5, WG = 6, WG2 = 7 };
 
@@ -276,14 +286,26 @@ __device__ __forceinline__ R lev(const DevVert& v, int k) {
   }
 }
 
-// Per-level quantity of level k; the double-word form reads the chunk's copy
-// of the table in shared memory (Ls: levels from k0 on, 16 slots each).
-template <class R, int J>
+// Per-level quantity of level k: from the chunk's copy of the table in shared
+// memory (Ls: levels from k0 on, 16 slots each; kStaged), else from the
+// device arrays.
+template <class R, int J, bool kStaged>
 __device__ __forceinline__ R levs(const DevVert& v, const double* Ls, int k, int k0) {
-  if constexpr (std::is_same<R, df>::value) {
-    return *reinterpret_cast<const df*>(Ls + 16 * (k - k0) + J);
+  if constexpr (kStaged) {
+    return *reinterpret_cast<const R*>(Ls + 16 * (k - k0) + J);
   } else {
     return lev<R, J>(v, k);
+  }
+}
+
+// A flux divergence of the tile: FP64, or in the mixed-precision step (T =
+// float) the double-word pair the flux-divergence kernel stored.
+template <class T, class R>
+__device__ __forceinline__ R divergence(const double* p) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<R, df>::value) {
+    return *reinterpret_cast<const df*>(p);
+  } else {
+    return Ar<R>::in(*p);
   }
 }
 
@@ -310,13 +332,15 @@ __device__ __forceinline__ R get(const double* p) {
 // `corrector` argument names (one kernel for both; the allocation-free entry).
 // The fixed forms are separate, smaller kernels.
 template <class T, bool kOwnZb = false, int KC = kKC, class R = double, int kCorr = -1>
-__global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector_arg,
+__global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector_arg,
                                                           ColArgs<T> a) {
   const bool corrector = kCorr < 0 ? corrector_arg != 0 : kCorr == 1;
   using A = Ar<R>;
   constexpr bool kDW = std::is_same<R, df>::value;
   constexpr int kTile = tile_doubles<KC>();
   constexpr int kBackIn = KC * kCW;
+  constexpr int kOut = KC * kLD;
+  constexpr bool kCT = kCorr != 0;
   extern __shared__ double sm[];
   __shared__ int rows_c[kCW];
   const int t = threadIdx.x;
@@ -331,15 +355,18 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
   double* T_rho = sm + kTile;
   double* T_pi = sm + 2 * kTile;
   double* T_th = sm + 3 * kTile;
-  T* T_dw0 = reinterpret_cast<T*>(sm + 4 * kTile);
-  double* T_dm = sm + 5 * kTile;
-  double* T_dt = sm + 6 * kTile;
-  T* T_dw1 = reinterpret_cast<T*>(sm + 7 * kTile);
-  double* T_rp = sm + 8 * kTile;
-  double* T_tp = sm + 9 * kTile;
-  double* T_zb = sm + 10 * kTile;
-  double* L_s = sm + tiles_doubles<KC>();
-  const double* lev_src = reinterpret_cast<const double*>(v.lev_hl);
+  double* T_dm = sm + 4 * kTile;
+  double* T_dt = sm + 5 * kTile;
+  double* T_rp = sm + 6 * kTile;  // corrector tiles (kCT)
+  double* T_tp = sm + 7 * kTile;
+  double* T_zb = sm + 8 * kTile;
+  T* T_dw0 = reinterpret_cast<T*>(sm + (kCT ? 9 : 6) * kTile);
+  T* T_dw1 = T_dw0 + kTile;
+  // the per-level table is staged per chunk, except in the FP64 form of the
+  // allocation-free entry, which has no FP64 copy of the table
+  constexpr bool kStage = kDW || !kOwnZb;
+  double* L_s = sm + lev_offset_bytes<T, KC, kCT>() / 8;
+  const double* lev_src = kDW ? reinterpret_cast<const double*>(v.lev_hl) : v.lev64;
 
   const size_t plane = (size_t)nlevp * nc;
   double* cp_s = a.col;
@@ -361,6 +388,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
   R ric_k = zero, tic_k = zero, tpic_k = zero, rt_k = zero;
   R zb_km1 = zero, al_km1 = zero, ps_km1 = zero, pr_km1 = zero, cp_km1 = zero, rp_km1 = zero;
   R rho_c = zero, th_c = zero, ra_c = zero, ta_c = zero, tpa_c = zero, wk_c = zero;
+  // products of half level k carried from level k-1: rho_ic w, (rho theta)_ic w, beta (rho theta)_ic
+  R fr_c = zero, fg_c = zero, al_c = zero;
 
   for (int k0 = 0; k0 < nlev; k0 += KC) {
     const int nkc = min(KC, nlev - k0);       // levels solved in this chunk
@@ -380,7 +409,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       tile_rows<KC>(T_tp, a.theta_p, nlev, rows_c, k0, nkf);
       if (!kOwnZb) tile_levels(T_zb, kLD, a.zbl, nc, c0, k0, nkc);
     }
-    if constexpr (kDW) {
+    if constexpr (kStage) {
       for (int i = t; i < 16 * nkf; i += kCW) cp8(L_s + i, lev_src + 16 * (size_t)k0 + i);
     }
     cp_wait();
@@ -395,11 +424,14 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         th_c = A::in(T_th[o]);
         ra_c = corrector ? add_pos(wn_r * rho_c, wnew_r * A::in(T_rp[o])) : rho_c;
         ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * A::in(T_tp[o])) : th_c;
-        tpa_c = ta_c - levs<R, LTH>(v, L_s, 0, k0);
+        tpa_c = ta_c - levs<R, LTH, kStage>(v, L_s, 0, k0);
         wk_c = A::in(T_w[o]);
+        fr_c = ric_k * wk_c;
+        fg_c = rt_k * wk_c;
+        al_c = beta * rt_k;
       }
       const R rho_n = rho_c, th_n = th_c, pi_n = A::in(T_pi[o]);
-      const R pr_k = pi_n - levs<R, LEX>(v, L_s, k, k0);
+      const R pr_k = pi_n - levs<R, LEX, kStage>(v, L_s, k, k0);
       // interface k+1 from full levels k and k+1 (time-averaged in the corrector)
       R ric_k1 = zero, tic_k1 = zero, tpic_k1 = zero;
       R rho_x = zero, th_x = zero, ra_x = zero, ta_x = zero, tpa_x = zero;
@@ -408,8 +440,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         th_x = A::in(T_th[o + kLD]);
         ra_x = corrector ? add_pos(wn_r * rho_x, wnew_r * A::in(T_rp[o + kLD])) : rho_x;
         ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * A::in(T_tp[o + kLD])) : th_x;
-        tpa_x = ta_x - levs<R, LTH>(v, L_s, k + 1, k0);
-        const R g1 = levs<R, WG>(v, L_s, k + 1, k0), g2 = levs<R, WG2>(v, L_s, k + 1, k0);
+        tpa_x = ta_x - levs<R, LTH, kStage>(v, L_s, k + 1, k0);
+        const R g1 = levs<R, WG, kStage>(v, L_s, k + 1, k0), g2 = levs<R, WG2, kStage>(v, L_s, k + 1, k0);
         ric_k1 = add_pos(g1 * ra_c, g2 * ra_x);
         tic_k1 = add_pos(g1 * ta_c, g2 * ta_x);
         tpic_k1 = g1 * tpa_c + g2 * tpa_x;
@@ -417,7 +449,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       const size_t ik = (size_t)k * nc + c;
       R zb;
       if (!corrector || kOwnZb) {
-        zb = levs<R, CZB>(v, L_s, k, k0) * pi_n * A::inv(rho_n * th_n);
+        zb = levs<R, CZB, kStage>(v, L_s, k, k0) * pi_n * A::inv(rho_n * th_n);
         put(a.zbl + ik, zb);
         put(eb_s + ik, pi_n - cvd_o_rd * pr_k);
       } else {
@@ -425,9 +457,10 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       }
       const R wk = wk_c, wk1 = A::in(T_w[o + kLD]);
       const R rt_k1 = ric_k1 * tic_k1;
-      const R rstar = rho_n - dt * A::in(T_dm[o]) - levs<R, CR>(v, L_s, k, k0) * (ric_k * wk - ric_k1 * wk1);
-      const R pstar = pr_k - zb * (levs<R, LDZ>(v, L_s, k, k0) * A::in(T_dt[o]) + ombeta * (rt_k * wk - rt_k1 * wk1));
-      const R al_k = beta * rt_k, al_k1 = beta * rt_k1;
+      const R fr_k1 = ric_k1 * wk1, fg_k1 = rt_k1 * wk1;
+      const R rstar = rho_n - dt * divergence<T, R>(T_dm + o) - levs<R, CR, kStage>(v, L_s, k, k0) * (fr_c - fr_k1);
+      const R pstar = pr_k - zb * (levs<R, LDZ, kStage>(v, L_s, k, k0) * divergence<T, R>(T_dt + o) + ombeta * (fg_c - fg_k1));
+      const R al_k = al_c, al_k1 = beta * rt_k1;
       put(rs_s + ik, rstar);
       put(ps_s + ik, pstar);
       put(ri_s + ik, ric_k);
@@ -439,8 +472,8 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         } else {
           ddtw = corrector ? wn_v * A::in(T_dw0[o]) + wnew_v * A::in(T_dw1[o]) : A::in(T_dw0[o]);
         }
-        const R wstar = wk + dt * ddtw - (levs<R, CWX>(v, L_s, k, k0) * tic_k * (pr_km1 - pr_k) + levs<R, CB>(v, L_s, k, k0) * tpic_k);
-        const R gam = levs<R, CGAM>(v, L_s, k, k0) * tic_k;
+        const R wstar = wk + dt * ddtw - (levs<R, CWX, kStage>(v, L_s, k, k0) * tic_k * (pr_km1 - pr_k) + levs<R, CB, kStage>(v, L_s, k, k0) * tpic_k);
+        const R gam = levs<R, CGAM, kStage>(v, L_s, k, k0) * tic_k;
         const R am = -(gam * zb_km1 * al_km1);
         const R bm = add_pos(one, gam * al_k * add_pos(zb_km1, zb));
         const R cm = -(gam * zb * al_k1);
@@ -468,6 +501,9 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
       tic_k = tic_k1;
       tpic_k = tpic_k1;
       rt_k = rt_k1;
+      fr_c = fr_k1;
+      fg_c = fg_k1;
+      al_c = al_k1;
       rho_c = rho_x;
       th_c = th_x;
       wk_c = wk1;
@@ -487,13 +523,14 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
   double* B_eb = sm + 6 * kBackIn;
   double* B_zb = sm + 7 * kBackIn;
   double* O_w = sm + 8 * kBackIn;
-  double* O_rho = O_w + kTile;
-  double* O_pi = O_w + 2 * kTile;
-  double* O_th = O_w + 3 * kTile;
+  double* O_rho = O_w + kOut;
+  double* O_pi = O_w + 2 * kOut;
+  double* O_th = O_w + 3 * kOut;
   // the level-major scratch written above by this thread is read back by
   // other threads of the CTA through the asynchronous copies below
   __threadfence_block();
-  R w_und_k1 = zero, wd_k1 = zero, ric_k1 = zero, al_k1 = zero;
+  // w_und of level k+1 and the fluxes rho_ic w', beta (rho theta)_ic w' at its half level
+  R w_und_k1 = zero, fr_k1 = zero * zero, fa_k1 = zero * zero;
   const unsigned long long pol_last = policy_evict_first();
   for (int kend = nlev; kend > 0; kend -= KC) {
     const int k0 = max(0, kend - KC), nk = kend - k0;
@@ -506,7 +543,7 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
     tile_levels_last(B_al, kCW, al_s, nc, c0, k0, nk, pol_last);
     tile_levels_last(B_eb, kCW, eb_s, nc, c0, k0, nk, pol_last);
     tile_levels(B_zb, kCW, a.zbl, nc, c0, k0, nk);
-    if constexpr (kDW) {
+    if constexpr (kStage) {
       for (int i = t; i < 16 * nk; i += kCW) cp8(L_s + i, lev_src + 16 * (size_t)k0 + i);
     }
     cp_wait();
@@ -519,29 +556,29 @@ __global__ void __launch_bounds__(kCW, 7) sn_column_tiled(int nc, DevVert v, Sca
         R w_und = zero, wd = zero;
         if (k >= 1) {
           w_und = get<R>(B_rp + b) - get<R>(B_cp + b) * w_und_k1;
-          wd = w_und * levs<R, LRAY>(v, L_s, k, k0);
+          wd = w_und * levs<R, LRAY, kStage>(v, L_s, k, k0);
         }
         const R ric = get<R>(B_ri + b), al = get<R>(B_al + b), zb = get<R>(B_zb + b);
-        const R rnew = get<R>(B_rs + b) - levs<R, CRN>(v, L_s, k, k0) * (ric * wd - ric_k1 * wd_k1);
-        const R prnew = get<R>(B_ps + b) - zb * (al * wd - al_k1 * wd_k1);
-        const R thnew = levs<R, CZB>(v, L_s, k, k0) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
+        const R fr = ric * wd, fa = al * wd;
+        const R rnew = get<R>(B_rs + b) - levs<R, CRN, kStage>(v, L_s, k, k0) * (fr - fr_k1);
+        const R prnew = get<R>(B_ps + b) - zb * (fa - fa_k1);
+        const R thnew = levs<R, CZB, kStage>(v, L_s, k, k0) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
         const int o = kk * kLD + t;
         O_w[o] = A::out(wd);
         O_rho[o] = A::out(rnew);
-        if (a.exner_o) O_pi[o] = A::out(levs<R, LEX>(v, L_s, k, k0) + prnew);
+        if (a.exner_o) O_pi[o] = A::out(levs<R, LEX, kStage>(v, L_s, k, k0) + prnew);
         O_th[o] = A::out(thnew);
         if constexpr (kDW) {
           // FP32 mirrors straight from the double-word values, into this
           // thread's consumed scratch slots: (w, rho - rho_ref) and theta_v - theta_ref
           float* m0 = reinterpret_cast<float*>(B_cp + b);
           m0[0] = to_float(wd);
-          m0[1] = to_float(rnew - levs<R, LRHO>(v, L_s, k, k0));
-          reinterpret_cast<float*>(B_rp + b)[0] = to_float(thnew - levs<R, LTH>(v, L_s, k, k0));
+          m0[1] = to_float(rnew - levs<R, LRHO, kStage>(v, L_s, k, k0));
+          reinterpret_cast<float*>(B_rp + b)[0] = to_float(thnew - levs<R, LTH, kStage>(v, L_s, k, k0));
         }
         w_und_k1 = w_und;
-        wd_k1 = wd;
-        ric_k1 = ric;
-        al_k1 = al;
+        fr_k1 = fr;
+        fa_k1 = fa;
       }
     }
     __syncthreads();
@@ -571,14 +608,14 @@ cudaError_t init_column_kernels() {
   auto set = [&](auto kernel, size_t bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   };
-  set(sn_column_tiled<double, false, 8, double, 0>, smem_bytes<8>());
-  set(sn_column_tiled<double, false, 8, double, 1>, smem_bytes<8>());
-  set(sn_column_tiled<float, false, 8, df, 0>, smem_bytes<8>());
-  set(sn_column_tiled<float, false, 8, df, 1>, smem_bytes<8>());
-  set(sn_column_tiled<double, false, 4, double, 0>, smem_bytes<4>());
-  set(sn_column_tiled<double, false, 4, double, 1>, smem_bytes<4>());
-  set(sn_column_tiled<float, false, 4, df, 0>, smem_bytes<4>());
-  set(sn_column_tiled<float, false, 4, df, 1>, smem_bytes<4>());
+  set(sn_column_tiled<double, false, 8, double, 0>, smem_bytes<double, 8, false>());
+  set(sn_column_tiled<double, false, 8, double, 1>, smem_bytes<double, 8, true>());
+  set(sn_column_tiled<float, false, 8, df, 0>, smem_bytes<float, 8, false>());
+  set(sn_column_tiled<float, false, 8, df, 1>, smem_bytes<float, 8, true>());
+  set(sn_column_tiled<double, false, 4, double, 0>, smem_bytes<double, 4, false>());
+  set(sn_column_tiled<double, false, 4, double, 1>, smem_bytes<double, 4, true>());
+  set(sn_column_tiled<float, false, 4, df, 0>, smem_bytes<float, 4, false>());
+  set(sn_column_tiled<float, false, 4, df, 1>, smem_bytes<float, 4, true>());
   return e;
 }
 
@@ -622,17 +659,19 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
   const char* name = mixed ? (corrector ? "sn_column_corr_mx" : "sn_column_pred_mx")
                            : (corrector ? "sn_column_corr" : "sn_column_pred");
   using RA = ColArith<T>;
+  const size_t sm4c = smem_bytes<T, 4, true>(), sm4p = smem_bytes<T, 4, false>();
+  const size_t sm8c = smem_bytes<T, 8, true>(), sm8p = smem_bytes<T, 8, false>();
   if (en.col_kc == 4 && corrector)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4, RA, 1>), en.g64.nc, en.v,
+    ICON_LAUNCH_SMEM(name, blocks, kCW, sm4c, s, (sn_column_tiled<T, false, 4, RA, 1>), en.g64.nc, en.v,
                      en.sc, 1, a);
   else if (en.col_kc == 4)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<4>(), s, (sn_column_tiled<T, false, 4, RA, 0>), en.g64.nc, en.v,
+    ICON_LAUNCH_SMEM(name, blocks, kCW, sm4p, s, (sn_column_tiled<T, false, 4, RA, 0>), en.g64.nc, en.v,
                      en.sc, 0, a);
   else if (corrector)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8, RA, 1>), en.g64.nc, en.v,
+    ICON_LAUNCH_SMEM(name, blocks, kCW, sm8c, s, (sn_column_tiled<T, false, 8, RA, 1>), en.g64.nc, en.v,
                      en.sc, 1, a);
   else
-    ICON_LAUNCH_SMEM(name, blocks, kCW, smem_bytes<8>(), s, (sn_column_tiled<T, false, 8, RA, 0>), en.g64.nc, en.v,
+    ICON_LAUNCH_SMEM(name, blocks, kCW, sm8p, s, (sn_column_tiled<T, false, 8, RA, 0>), en.g64.nc, en.v,
                      en.sc, 0, a);
 }
 

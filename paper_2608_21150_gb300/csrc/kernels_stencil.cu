@@ -333,7 +333,8 @@ __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
 
 // -------------------------------------------------------------------------
 // Divergences of the horizontal mass and theta fluxes with the flux-velocity
-// filter, per cell and level, summed in FP64:
+// filter, per cell and level, summed in FP64 (double-word FP32 in mixed
+// mode, stored as the pair):
 //   vf_e = vn_e + divflux (D_c1 - D_c0)/d_e,  F_e = rho_e vf_e,
 //   div_m = sum s l F / A,  div_t = sum s l F theta_e / A
 // -------------------------------------------------------------------------
@@ -363,8 +364,9 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
       dm = dm + w * f;
       dt = dt + w * ft;
     }
-    div_m[(size_t)c * nlev + k] = to_double(dm);
-    div_t[(size_t)c * nlev + k] = to_double(dt);
+    // stored as the double-word pair itself (8 bytes, read by the column solve)
+    reinterpret_cast<df*>(div_m)[(size_t)c * nlev + k] = dm;
+    reinterpret_cast<df*>(div_t)[(size_t)c * nlev + k] = dt;
   } else {
     const double* dv = div_c64 + 3 * (size_t)c;
     double dm = 0.0, dt = 0.0;
