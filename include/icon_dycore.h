@@ -241,7 +241,7 @@ int icon_dycore_debug_field(icon_dycore_t* dycore, const char* name, void* dst, 
  * set): writes a NUL-terminated text "name=threads,...;column_chunk=K" of at
  * most len bytes into buf (HOST).  The autotuner runs one step of every
  * kernel on a temporary uniform state at create time with each candidate
- * (128, 256, 512 threads per CTA for the stencils; 4 or 8 levels per
+ * (128, 256, 512 threads per CTA for the stencils; 4, 6 or 8 levels per
  * shared-memory chunk for the column solve) and keeps the fastest per kernel. */
 int icon_dycore_launch_config(const icon_dycore_t* dycore, char* buf, int32_t len);
 

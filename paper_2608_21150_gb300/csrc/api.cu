@@ -271,7 +271,8 @@ int autotune(icon_dycore* d) {
   }
   const int cand[3] = {128, 256, 512};
   std::vector<std::vector<double>> t(kNumStencils, std::vector<double>(3, 0.0));
-  double col_t[2] = {0.0, 0.0};  // chunk 8 (with 256 threads), chunk 4
+  const int col_cand[3] = {8, 6, 4};   // levels per chunk of the column solve
+  double col_t[3] = {0.0, 0.0, 0.0};
   auto run = [&](int ci, int kc, bool stencils) -> int {
     for (int k = 0; k < kNumStencils; ++k) d->en.threads[k] = cand[ci];
     d->en.col_kc = kc;
@@ -286,7 +287,8 @@ int autotune(icon_dycore* d) {
       CUDA_TRY(cudaEventElapsedTime(&ms, r.e0, r.e1));
       const std::string nm = r.name;
       if (nm.compare(0, 9, "sn_column") == 0) {
-        col_t[kc == 8 ? 0 : 1] += ms;
+        for (int j = 0; j < 3; ++j)
+          if (col_cand[j] == kc) col_t[j] += ms;
         continue;
       }
       if (!stencils) continue;
@@ -302,8 +304,9 @@ int autotune(icon_dycore* d) {
   for (int ci = 0; ci < 3 && rc == ICON_OK; ++ci) rc = run(ci, 8, true);
   if (rc == ICON_OK) {
     col_t[0] /= 3.0;
-    rc = run(1, 4, false);
+    rc = run(1, 6, false);
   }
+  if (rc == ICON_OK) rc = run(1, 4, false);
   for (double* p : {st.vn, st.w, st.rho, st.exner, st.theta_v, st.exner_pr})
     if (p) cudaFree(p);
   if (rc != ICON_OK) return rc;
@@ -313,7 +316,10 @@ int autotune(icon_dycore* d) {
       if (t[k][ci] > 0.0 && t[k][ci] < t[k][best]) best = ci;
     d->en.threads[k] = cand[best];
   }
-  d->en.col_kc = col_t[1] < col_t[0] ? 4 : 8;
+  int best_kc = 0;
+  for (int j = 1; j < 3; ++j)
+    if (col_t[j] < col_t[best_kc]) best_kc = j;
+  d->en.col_kc = col_cand[best_kc];
   return ICON_OK;
 }
 

@@ -40,7 +40,7 @@ namespace icon {
 namespace {
 
 constexpr int kCW = 64;          // columns (threads) per CTA
-constexpr int kKC = 4;           // default levels per chunk (the autotuner may pick 8)
+constexpr int kKC = 4;           // default levels per chunk (the autotuner picks 4, 6 or 8)
 constexpr int kLD = kCW + 1;     // padded tile row for column-gathered tiles
 template <int KC>
 __host__ __device__ constexpr int tile_doubles() { return (KC + 1) * kLD; }
@@ -393,18 +393,19 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
 
   for (int k0 = 0; k0 < nlev; k0 += KC) {
     const int nkc = min(KC, nlev - k0);       // levels solved in this chunk
-    const int nkf = min(KC + 1, nlev - k0);   // full levels loaded (one lookahead)
-    const int nkh = min(KC + 1, nlevp - k0);  // half levels loaded
+    const int nkf = min(KC + 1, nlev - k0);   // full levels with one lookahead (rho, theta)
+    const int nkh = min(KC + 1, nlevp - k0);  // half levels with one lookahead (w); exner and
+                                              // the tendencies are read at the chunk's levels only
     __syncthreads();
     tile_rows<KC>(T_w, a.w, nlevp, rows_c, k0, nkh);
     tile_rows<KC>(T_rho, a.rho, nlev, rows_c, k0, nkf);
-    tile_rows<KC>(T_pi, a.exner, nlev, rows_c, k0, nkf);
+    tile_rows<KC>(T_pi, a.exner, nlev, rows_c, k0, nkc);
     tile_rows<KC>(T_th, a.theta, nlev, rows_c, k0, nkf);
-    tile_rows<KC>(T_dw0, a.ddt_w0, nlevp, rows_c, k0, nkh);
+    tile_rows<KC>(T_dw0, a.ddt_w0, nlevp, rows_c, k0, nkc);
     tile_rows<KC>(T_dm, a.div_m, nlev, rows_c, k0, nkc);
     tile_rows<KC>(T_dt, a.div_t, nlev, rows_c, k0, nkc);
     if (corrector) {
-      tile_rows<KC>(T_dw1, a.ddt_w1, nlevp, rows_c, k0, nkh);
+      tile_rows<KC>(T_dw1, a.ddt_w1, nlevp, rows_c, k0, nkc);
       tile_rows<KC>(T_rp, a.rho_p, nlev, rows_c, k0, nkf);
       tile_rows<KC>(T_tp, a.theta_p, nlev, rows_c, k0, nkf);
       if (!kOwnZb) tile_levels(T_zb, kLD, a.zbl, nc, c0, k0, nkc);
@@ -612,6 +613,10 @@ cudaError_t init_column_kernels() {
   set(sn_column_tiled<double, false, 8, double, 1>, smem_bytes<double, 8, true>());
   set(sn_column_tiled<float, false, 8, df, 0>, smem_bytes<float, 8, false>());
   set(sn_column_tiled<float, false, 8, df, 1>, smem_bytes<float, 8, true>());
+  set(sn_column_tiled<double, false, 6, double, 0>, smem_bytes<double, 6, false>());
+  set(sn_column_tiled<double, false, 6, double, 1>, smem_bytes<double, 6, true>());
+  set(sn_column_tiled<float, false, 6, df, 0>, smem_bytes<float, 6, false>());
+  set(sn_column_tiled<float, false, 6, df, 1>, smem_bytes<float, 6, true>());
   set(sn_column_tiled<double, false, 4, double, 0>, smem_bytes<double, 4, false>());
   set(sn_column_tiled<double, false, 4, double, 1>, smem_bytes<double, 4, true>());
   set(sn_column_tiled<float, false, 4, df, 0>, smem_bytes<float, 4, false>());
@@ -661,7 +666,12 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
   using RA = ColArith<T>;
   const size_t sm4c = smem_bytes<T, 4, true>(), sm4p = smem_bytes<T, 4, false>();
   const size_t sm8c = smem_bytes<T, 8, true>(), sm8p = smem_bytes<T, 8, false>();
-  if (en.col_kc == 4 && corrector)
+  const size_t sm6c = smem_bytes<T, 6, true>(), sm6p = smem_bytes<T, 6, false>();
+  if (en.col_kc == 6 && corrector)
+    ICON_LAUNCH_SMEM(name, blocks, kCW, sm6c, s, (sn_column_tiled<T, false, 6, RA, 1>), en.g64.nc, en.v, en.sc, 1, a);
+  else if (en.col_kc == 6)
+    ICON_LAUNCH_SMEM(name, blocks, kCW, sm6p, s, (sn_column_tiled<T, false, 6, RA, 0>), en.g64.nc, en.v, en.sc, 0, a);
+  else if (en.col_kc == 4 && corrector)
     ICON_LAUNCH_SMEM(name, blocks, kCW, sm4c, s, (sn_column_tiled<T, false, 4, RA, 1>), en.g64.nc, en.v,
                      en.sc, 1, a);
   else if (en.col_kc == 4)
