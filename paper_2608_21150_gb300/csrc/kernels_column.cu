@@ -73,17 +73,16 @@ constexpr size_t kSmem = smem_bytes<double, kKC, true>();
 
 enum { CZB = 0, CR = 1, CRN = 2, CWX = 3, CB = 4, CGAM = 5, WG = 6, WG2 = 7 };
 
-// Reciprocal by Newton-Raphson refinement (r <- r + r (1 - x r), quadratic
-// convergence) of the hardware FP64 reciprocal approximation; two steps take
-// the seed's ~20 correct bits past double precision.  Used for the pivots and
-// the equation-of-state denominator, whose operands are positive and far from
-// the subnormal range.
+// Reciprocal of a positive FP64 value far from the subnormal range (the
+// pivots and the equation-of-state denominator): a double-word FP32 seed
+// (about 44 correct bits, computed on the FP32 pipes) widened with one FP64
+// addition, then one Newton-Raphson step r + r (1 - x r) in FP64, which
+// squares the seed's relative error to far below double precision.  Three
+// operations on this GPU's slow FP64 pipe instead of the five of the
+// hardware approximation refined twice.
 __device__ __forceinline__ double rcp(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
+  const double r = to_double(icon::rcp(to_df(x)));
+  const double e = fma(-x, r, 1.0);
   return fma(r, e, r);
 }
 
@@ -416,7 +415,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
     cp_wait();
     __syncthreads();
     if (!active) continue;
-#pragma unroll (kDW ? 1 : 2)
+#pragma unroll 1
     for (int kk = 0; kk < nkc; ++kk) {
       const int k = k0 + kk;
       const int o = kk * kLD + t;
@@ -550,7 +549,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
     cp_wait();
     __syncthreads();
     if (active) {
-#pragma unroll (kDW ? 1 : 2)
+#pragma unroll 1
       for (int kk = nk - 1; kk >= 0; --kk) {
         const int k = k0 + kk;
         const int b = kk * kCW + t;
