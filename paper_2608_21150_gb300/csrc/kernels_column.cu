@@ -244,7 +244,7 @@ struct ColArgs {
   const double* rho_ref;
 };
 
-// Arithmetic of the solve: FP64 (R = double), or double-word FP32 (R = df,
+// Arithmetic of the solve: FP64 (R = double), or double-word FP32 (R = dws,
 // mixed precision) with inputs split and outputs joined at the tile boundary.
 template <class R>
 struct Ar;
@@ -256,11 +256,11 @@ struct Ar<double> {
   static __device__ __forceinline__ double out(double x) { return x; }
 };
 template <>
-struct Ar<df> {
-  static __device__ __forceinline__ df in(double x) { return to_df(x); }
-  static __device__ __forceinline__ df in(float x) { return to_df(x); }
-  static __device__ __forceinline__ df inv(df x) { return rcp(x); }
-  static __device__ __forceinline__ double out(df x) { return to_double(x); }
+struct Ar<dws> {
+  static __device__ __forceinline__ dws in(double x) { return to_dws(to_df(x)); }
+  static __device__ __forceinline__ dws in(float x) { return {x, 0.0f}; }
+  static __device__ __forceinline__ dws inv(dws x) { return rcp(x); }
+  static __device__ __forceinline__ double out(dws x) { return to_double(x); }
 };
 
 // per-level quantities: j < 8 the column coefficients, then these
@@ -277,8 +277,8 @@ template <>
 __device__ __forceinline__ double lev<double, LRAY>(const DevVert& v, int k) { return v.ray_fac[k]; }
 template <class R, int J>
 __device__ __forceinline__ R lev(const DevVert& v, int k) {
-  if constexpr (std::is_same<R, df>::value) {
-    return reinterpret_cast<const df*>(v.lev_hl)[16 * (size_t)k + J];
+  if constexpr (!std::is_same<R, double>::value) {
+    return reinterpret_cast<const R*>(v.lev_hl)[16 * (size_t)k + J];
   } else {
     static_assert(J < 8, "column coefficient");
     return v.colc[8 * (size_t)k + J];
@@ -301,8 +301,8 @@ __device__ __forceinline__ R levs(const DevVert& v, const double* Ls, int k, int
 // float) the double-word pair the flux-divergence kernel stored.
 template <class T, class R>
 __device__ __forceinline__ R divergence(const double* p) {
-  if constexpr (std::is_same<T, float>::value && std::is_same<R, df>::value) {
-    return *reinterpret_cast<const df*>(p);
+  if constexpr (std::is_same<T, float>::value && !std::is_same<R, double>::value) {
+    return *reinterpret_cast<const R*>(p);
   } else {
     return Ar<R>::in(*p);
   }
@@ -312,13 +312,13 @@ __device__ __forceinline__ R divergence(const double* p) {
 // coefficients): the cheaper double-word addition is exact enough without
 // cancellation; plain addition in FP64.
 __device__ __forceinline__ double add_pos(double a, double b) { return a + b; }
-__device__ __forceinline__ df add_pos(df a, df b) { return add_same_sign(a, b); }
+__device__ __forceinline__ dws add_pos(dws a, dws b) { return a + b; }
 
-// Scratch planes hold R values in 8-byte slots (a df is two floats).  They
+// Scratch planes hold R values in 8-byte slots (a double-word value is two floats).  They
 // are read back only after the whole forward sweep, so they are stored as
 // streaming (evict-first) data that does not displace the input rows in L2.
 __device__ __forceinline__ void put(double* p, double x) { __stcs(p, x); }
-__device__ __forceinline__ void put(double* p, df x) { __stcs(reinterpret_cast<float2*>(p), make_float2(x.hi, x.lo)); }
+__device__ __forceinline__ void put(double* p, dws x) { __stcs(reinterpret_cast<float2*>(p), make_float2(x.hi, x.lo)); }
 template <class R>
 __device__ __forceinline__ R get(const double* p) {
   return *reinterpret_cast<const R*>(p);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
                                                           ColArgs<T> a) {
   const bool corrector = kCorr < 0 ? corrector_arg != 0 : kCorr == 1;
   using A = Ar<R>;
-  constexpr bool kDW = std::is_same<R, df>::value;
+  constexpr bool kDW = !std::is_same<R, double>::value;
   constexpr int kTile = tile_doubles<KC>();
   constexpr int kBackIn = KC * kCW;
   constexpr int kOut = KC * kLD;
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
 // Mixed precision (FP32 stencil inputs) solves in double-word FP32 arithmetic;
 // the FP64 mode in FP64.
 template <class T>
-using ColArith = typename std::conditional<std::is_same<T, float>::value, df, double>::type;
+using ColArith = typename std::conditional<std::is_same<T, float>::value, dws, double>::type;
 
 cudaError_t init_column_kernels() {
   cudaError_t e = cudaSuccess;
@@ -610,16 +610,16 @@ cudaError_t init_column_kernels() {
   };
   set(sn_column_tiled<double, false, 8, double, 0>, smem_bytes<double, 8, false>());
   set(sn_column_tiled<double, false, 8, double, 1>, smem_bytes<double, 8, true>());
-  set(sn_column_tiled<float, false, 8, df, 0>, smem_bytes<float, 8, false>());
-  set(sn_column_tiled<float, false, 8, df, 1>, smem_bytes<float, 8, true>());
+  set(sn_column_tiled<float, false, 8, dws, 0>, smem_bytes<float, 8, false>());
+  set(sn_column_tiled<float, false, 8, dws, 1>, smem_bytes<float, 8, true>());
   set(sn_column_tiled<double, false, 6, double, 0>, smem_bytes<double, 6, false>());
   set(sn_column_tiled<double, false, 6, double, 1>, smem_bytes<double, 6, true>());
-  set(sn_column_tiled<float, false, 6, df, 0>, smem_bytes<float, 6, false>());
-  set(sn_column_tiled<float, false, 6, df, 1>, smem_bytes<float, 6, true>());
+  set(sn_column_tiled<float, false, 6, dws, 0>, smem_bytes<float, 6, false>());
+  set(sn_column_tiled<float, false, 6, dws, 1>, smem_bytes<float, 6, true>());
   set(sn_column_tiled<double, false, 4, double, 0>, smem_bytes<double, 4, false>());
   set(sn_column_tiled<double, false, 4, double, 1>, smem_bytes<double, 4, true>());
-  set(sn_column_tiled<float, false, 4, df, 0>, smem_bytes<float, 4, false>());
-  set(sn_column_tiled<float, false, 4, df, 1>, smem_bytes<float, 4, true>());
+  set(sn_column_tiled<float, false, 4, dws, 0>, smem_bytes<float, 4, false>());
+  set(sn_column_tiled<float, false, 4, dws, 1>, smem_bytes<float, 4, true>());
   return e;
 }
 
@@ -736,7 +736,7 @@ int noalloc_setup(double** out) {
       return report_error(ICON_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     e = cudaFuncSetAttribute(sn_column_tiled<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(sn_column_tiled<double, true, kKC, df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(sn_column_tiled<double, true, kKC, dws>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kSmem);
     if (e != cudaSuccess)
       return report_error(ICON_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -889,7 +889,7 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
   a.theta_o = theta_new;
   const unsigned blocks = (unsigned)((n_cols + kCW - 1) / kCW);
   if (p->precision == ICON_PREC_MIXED)  // the mixed mode's double-word FP32 arithmetic
-    sn_column_tiled<double, true, kKC, df><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
+    sn_column_tiled<double, true, kKC, dws><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
   else
     sn_column_tiled<double, true><<<blocks, kCW, kSmem, stream>>>(n_cols, v, s, corr ? 1 : 0, a);
   e = cudaGetLastError();
