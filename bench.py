@@ -357,21 +357,21 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
 # function, two forms); the roofline treats them together.
 FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
 
-# DRAM bytes per launch of the FP64 column solve from an ncu capture at R2B5
-# L90 (profiles/sn_column_r2b5_l90.md), scaled to R2B6 by the column count (x4),
-# valid while the kernel source is the one captured (its SHA-256 below).
+# DRAM bytes per launch of the FP64 column solve (the mean of its predictor
+# and corrector launches, 6.38 and 8.46 GB) from the ncu capture of the FP64
+# step at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid for that grid
+# while the kernel source is the one captured (its SHA-256 below).
 COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
-                  "sha256": "4f809caf35b942daaa3beabfe99a223ace11a9fc822d2e89cf49bce59e804c97",
-                  # mean of the predictor (2.082 GB) and corrector (3.241 GB) launches, FP64
-                  "bytes_per_launch_r2b5": 0.5 * (1.375208e9 + 0.706401e9 + 2.646195e9 + 0.594674e9)}
+                  "sha256": "3910f6ac71b23e56f1f3cdbd9eb632dad583279b5ee3e02d3bbe6f755cc4faca",
+                  "bisections": 6, "bytes_per_launch": 7.419006707e9}
 
 
 # DRAM bytes per step of every kernel in the timed steps, from one ncu capture
 # of each leg at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid while
 # the kernel sources are the ones captured (SHA-256 over csrc/*, below).
-STEP_DRAM = {"sources_sha256": "f34f0c379cbfcc18d4eca3b209285f9d8336bc8b41fdfecfdb652d6c25a61eed",
-             "bisections": 6, "bytes_per_step": {"fp64": 243.766798e9, "mixed": 194.714794e9,
-                                                 "learned": 167.084504e9}}
+STEP_DRAM = {"sources_sha256": "d9ca370fb3b54528d8294b30b41f74d62de55ec850ebf1b5da1b3b84eb618b92",
+             "bisections": 6, "bytes_per_step": {"fp64": 207.187e9, "mixed": 156.7245e9,
+                                                 "learned": 136.637e9}}
 
 
 def sources_sha256():
@@ -399,10 +399,10 @@ def dram_measured(leg, ms_per_step):
                     "event-timed step; of measured peak"}
 
 
-def column_traffic(nc):
+def column_traffic():
     import hashlib
     t = COLUMN_TRAFFIC
-    if not t["sha256"] or not t["bytes_per_launch_r2b5"]:
+    if WORKLOAD["bisections"] != t["bisections"]:
         return None
     try:
         with open(os.path.join(ROOT, t["source"]), "rb") as f:
@@ -410,7 +410,7 @@ def column_traffic(nc):
                 return None
     except OSError:
         return None
-    return t["bytes_per_launch_r2b5"] * nc / 81920
+    return t["bytes_per_launch"]
 
 
 def roofline(prof, nc, ne, nv, nlev):
@@ -427,7 +427,7 @@ def roofline(prof, nc, ne, nv, nlev):
     achieved = flops / (ms / 1000.0) / 1e12
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": column_traffic(nc) if name == "sn_column" else None,
+            "traffic": column_traffic() if name == "sn_column" else None,
             "note": "FP64 algorithmic flops per launch / event-timed launch duration (CUDA events around every "
                     "launch on the library's stream); peak = nominal FP64 rate from unit counts and clock "
                     "(1.2 TFLOP/s measured by a DFMA probe); traffic = ncu DRAM bytes per launch"}
