@@ -32,6 +32,7 @@ module icon_dycore
     real(c_double) :: ref_T0
     integer(c_int32_t) :: precision, use_graph, autotune, synchronous
     type(c_ptr) :: stream
+    integer(c_int32_t) :: column_chunk
   end type
 
   type, bind(c), public :: icon_state_t

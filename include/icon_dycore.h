@@ -125,6 +125,8 @@ typedef struct icon_dycore_params {
   int32_t autotune;        /* logical: pick per-kernel launch shapes at create time */
   int32_t synchronous;     /* logical: return only after the GPU work ended */
   void* stream;            /* cudaStream_t to enqueue on; NULL = default stream */
+  int32_t column_chunk;    /* levels per shared-memory chunk of the column solve: 4, 6 or 8;
+                              0 = 4, or the autotuner's choice when autotune is set */
 } icon_dycore_params_t;
 
 /* Writes the defaults: dtime 1800, ndyn_substeps 5, beta 0.65, tendency

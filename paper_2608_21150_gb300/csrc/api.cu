@@ -145,6 +145,7 @@ void icon_dycore_params_default(icon_dycore_params_t* p) {
   p->autotune = 1;
   p->synchronous = 1;
   p->stream = nullptr;
+  p->column_chunk = 0;
 }
 
 int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
@@ -341,6 +342,8 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     return fail(ICON_ERR_ARG, "icon_dycore_create: dtime must be > 0 and ndyn_substeps >= 1");
   if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED)
     return fail(ICON_ERR_ARG, "icon_dycore_create: precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
+  if (p->column_chunk != 0 && p->column_chunk != 4 && p->column_chunk != 6 && p->column_chunk != 8)
+    return fail(ICON_ERR_ARG, "icon_dycore_create: column_chunk must be 0, 4, 6 or 8");
 
   icon_dycore* d = new (std::nothrow) icon_dycore();
   if (!d) return fail(ICON_ERR_ARG, "icon_dycore_create: out of host memory");
@@ -621,6 +624,7 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
       return rc;
     }
   }
+  if (p->column_chunk) en.col_kc = p->column_chunk;
   *out = d;
   return ICON_OK;
 }
