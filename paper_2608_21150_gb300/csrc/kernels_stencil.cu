@@ -45,6 +45,24 @@ __device__ __forceinline__ bool flat_index(int n_h, int nk, int& h, int& k) {
 
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Second launch shape, used by the FP32 forms of the kernels whose per-point
+// gathers dominate (va_edge_pre, va_cell_w, sn_cell_div, sn_cell_fluxdiv,
+// sn_edge_corr): one warp per horizontal point, its lanes striding over the
+// levels, so the point's neighbour indices and weights are loaded once per
+// warp.  Not used for FP64, where 90 levels fill only 90 of 96 lane slots of
+// the saturated FP64 pipe, nor for the kernels that measured slower with it.
+__device__ __forceinline__ int warp_point() { return (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); }
+__device__ __forceinline__ int lane_id() { return (int)(threadIdx.x & 31u); }
+inline unsigned blocks_for_points(long long n_points, int threads) {
+  const int warps = threads / 32;
+  return (unsigned)((n_points + warps - 1) / warps);
+}
+// CTAs of a kernel over n_h points and nk levels in the shape of its type
+template <class T>
+unsigned blocks_by_point(long long n_h, int nk, int threads) {
+  return kMixed<T> ? blocks_for_points(n_h, threads) : blocks_for(n_h * nk, threads);
+}
+
 constexpr int kThreads = 256;
 
 // threads per CTA of stencil kernel `id` from the autotuner's table (0: default)
@@ -64,8 +82,31 @@ const char* kname(const char* f64, const char* f32) {
 template <class T>
 __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ vt,
                             T* __restrict__ ekin) {
-  int e, k;
   const int nlev = v.nlev;
+  if constexpr (kMixed<T>) {
+    const int e = warp_point();
+    if (e >= g.ne) return;
+    const T* w = g.vt_w + 5 * (size_t)e;
+    const int* q = g.e2c2e + 4 * (size_t)e;
+    const T w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+    const T* x0 = vn + (size_t)e * nlev;
+    const T* x1 = vn + (size_t)q[0] * nlev;
+    const T* x2 = vn + (size_t)q[1] * nlev;
+    const T* x3 = vn + (size_t)q[2] * nlev;
+    const T* x4 = vn + (size_t)q[3] * nlev;
+    for (int k = lane_id(); k < nlev; k += 32) {
+      const T vne = x0[k];
+      T t = w0 * vne;
+      t += w1 * x1[k];
+      t += w2 * x2[k];
+      t += w3 * x3[k];
+      t += w4 * x4[k];
+      vt[(size_t)e * nlev + k] = t;
+      ekin[(size_t)e * nlev + k] = T(0.5) * (vne * vne + t * t);
+    }
+    return;
+  }
+  int e, k;
   if (!flat_index(g.ne, nlev, e, k)) return;
   const T* w = g.vt_w + 5 * (size_t)e;
   const int* q = g.e2c2e + 4 * (size_t)e;
@@ -182,8 +223,30 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
 template <class T>
 __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const T* __restrict__ gw_e,
                           T* __restrict__ ddt_w) {
-  int c, k;
   const int nlev = v.nlev, nlevp = nlev + 1;
+  if constexpr (kMixed<T>) {
+    const int c = warp_point();
+    if (c >= g.nc) return;
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const T* q = g.e2c_w + 3 * (size_t)c;
+    const T q0 = q[0], q1 = q[1], q2 = q[2];
+    const T* g0 = gw_e + (size_t)ce[0] * nlevp;
+    const T* g1 = gw_e + (size_t)ce[1] * nlevp;
+    const T* g2 = gw_e + (size_t)ce[2] * nlevp;
+    const T* wc = w + (size_t)c * nlevp;
+    for (int k = lane_id(); k < nlevp; k += 32) {
+      T r = 0;
+      if (k > 0 && k < nlev) {
+        T h = q0 * g0[k];
+        h += q1 * g1[k];
+        h += q2 * g2[k];
+        r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+      }
+      ddt_w[(size_t)c * nlevp + k] = r;
+    }
+    return;
+  }
+  int c, k;
   if (!flat_index(g.nc, nlevp, c, k)) return;
   T r = 0;
   if (k > 0 && k < nlev) {
@@ -294,8 +357,25 @@ template <class T>
 __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __restrict__ vn,
                              const T* __restrict__ ddt_vn0, const T* __restrict__ ddt_vn1,
                              const T* __restrict__ hpg, const T* __restrict__ divd2, float* __restrict__ m_vn) {
-  int e, k;
   const int nlev = v.nlev;
+  if constexpr (kMixed<T>) {
+    const int e = warp_point();
+    if (e >= g.ne) return;
+    const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+    const T ddamp = g.ddamp_e[e];
+    const T* d0 = divd2 + (size_t)c0 * nlev;
+    const T* d1 = divd2 + (size_t)c1 * nlev;
+    for (int k = lane_id(); k < nlev; k += 32) {
+      const size_t ie = (size_t)e * nlev + k;
+      const T damp = ddamp * (d1[k] - d0[k]);
+      const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - damp;
+      const double vnn = vn[ie] + f2d(inc);
+      vn[ie] = vnn;
+      m_vn[ie] = d2f(vnn);
+    }
+    return;
+  }
+  int e, k;
   if (!flat_index(g.ne, nlev, e, k)) return;
   const size_t ie = (size_t)e * nlev + k;
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
@@ -320,8 +400,24 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
 template <class T>
 __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ divd,
                             const double* __restrict__ exner, double* __restrict__ exner_pr) {
-  int c, k;
   const int nlev = v.nlev;
+  if constexpr (kMixed<T>) {
+    const int c = warp_point();
+    if (c >= g.nc) return;
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const T* dvp = g.div_c + 3 * (size_t)c;
+    const T dv0 = dvp[0], dv1 = dvp[1], dv2 = dvp[2];
+    const T* x0 = vn + (size_t)ce[0] * nlev;
+    const T* x1 = vn + (size_t)ce[1] * nlev;
+    const T* x2 = vn + (size_t)ce[2] * nlev;
+    for (int k = lane_id(); k < nlev; k += 32) {
+      const size_t i = (size_t)c * nlev + k;
+      divd[i] = dv0 * x0[k] + dv1 * x1[k] + dv2 * x2[k];
+      if (exner_pr) exner_pr[i] = exner[i] - v.exner_ref[k];
+    }
+    return;
+  }
+  int c, k;
   if (!flat_index(g.nc, nlev, c, k)) return;
   const int* ce = g.c2e + 3 * (size_t)c;
   const T* dv = g.div_c + 3 * (size_t)c;
@@ -343,31 +439,47 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
                                 const T* __restrict__ divd, const T* __restrict__ rho_e,
                                 const T* __restrict__ theta_e, const double* __restrict__ div_c64,
                                 double* __restrict__ div_m, double* __restrict__ div_t) {
-  int c, k;
   const int nlev = v.nlev;
-  if (!flat_index(g.nc, nlev, c, k)) return;
-  const int* ce = g.c2e + 3 * (size_t)c;
   if constexpr (kMixed<T>) {
     // FP32 fluxes, sums in double-word FP32: FP64-grade accumulation (mass
-    // conserved to about 2^-48 of the flux) without the slow FP64 pipe
-    const df* dv = reinterpret_cast<const df*>(g.div_c_hl) + 3 * (size_t)c;
-    df dm{0.f, 0.f}, dt{0.f, 0.f};
+    // conserved to about 2^-48 of the flux) without the slow FP64 pipe.  One
+    // warp per cell: the cell's three edges, their filter coefficients and
+    // the divergence rows of their cells are loaded once.
+    const int c = warp_point();
+    if (c >= g.nc) return;
+    const int* ce = g.c2e + 3 * (size_t)c;
+    size_t be[3], bd0[3], bd1[3];
+    T fd[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int e = ce[j];
-      const size_t ie = (size_t)e * nlev + k;
-      const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-      const T vf = vn[ie] + g.fdiv_e[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
-      const T f = rho_e[ie] * vf;
-      const T ft = f * theta_e[ie];
-      const df w = dv[j];
-      dm = dm + w * f;
-      dt = dt + w * ft;
+      be[j] = (size_t)e * nlev;
+      bd0[j] = (size_t)g.e2c[2 * e] * nlev;
+      bd1[j] = (size_t)g.e2c[2 * e + 1] * nlev;
+      fd[j] = g.fdiv_e[e];
     }
-    // stored as the double-word pair itself (8 bytes, read by the column solve)
-    reinterpret_cast<df*>(div_m)[(size_t)c * nlev + k] = dm;
-    reinterpret_cast<df*>(div_t)[(size_t)c * nlev + k] = dt;
+    const df* dvp = reinterpret_cast<const df*>(g.div_c_hl) + 3 * (size_t)c;
+    const df dv[3] = {dvp[0], dvp[1], dvp[2]};
+    for (int k = lane_id(); k < nlev; k += 32) {
+      df dm{0.f, 0.f}, dt{0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const size_t ie = be[j] + k;
+        const T vf = vn[ie] + fd[j] * (divd[bd1[j] + k] - divd[bd0[j] + k]);
+        const T f = rho_e[ie] * vf;
+        const T ft = f * theta_e[ie];
+        const df w = dv[j];
+        dm = dm + w * f;
+        dt = dt + w * ft;
+      }
+      // stored as the double-word pair itself (8 bytes, read by the column solve)
+      reinterpret_cast<df*>(div_m)[(size_t)c * nlev + k] = dm;
+      reinterpret_cast<df*>(div_t)[(size_t)c * nlev + k] = dt;
+    }
   } else {
+    int c, k;
+    if (!flat_index(g.nc, nlev, c, k)) return;
+    const int* ce = g.c2e + 3 * (size_t)c;
     const double* dv = div_c64 + 3 * (size_t)c;
     double dm = 0.0, dt = 0.0;
 #pragma unroll
@@ -599,14 +711,14 @@ void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
   const int nlev = v.nlev, nlevp = nlev + 1;
-  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_for((long long)g.ne * nlev, TH(0)), TH(0), s,
+  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_by_point<T>(g.ne, nlev, TH(0)), TH(0), s,
               va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e);
   const long long n2 = (long long)g.nc * nlev + (long long)g.nv * nlevp;
   ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, TH(1)), TH(1), s, va_cell_vert<T>, g,
               v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v);
   ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, TH(2)), TH(2),
               s, va_edge_tend<T>, g, v, vn, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e);
-  ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_for((long long)g.nc * nlevp, TH(3)), TH(3), s,
+  ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_by_point<T>(g.nc, nlevp, TH(3)), TH(3), s,
               va_cell_w<T>, g, v, w, wk.gw_e, ddt_w);
 }
 
@@ -632,19 +744,19 @@ void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cuda
               wk.grad4, st.exner, st.exner_pr, en.sc.exfac, en.wk.pex);
   ICON_LAUNCH(kname<T>("sn_edge_pred", "sn_edge_pred_f32"), blocks_for(nee, TH(5)), TH(5), s, sn_edge_pred<T>, g, v, x.s, s_vn, wk.vt,
               wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p);
-  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_for(nce, TH(6)), TH(6), s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
+  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
               st.exner, st.exner_pr);
-  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_for(nce, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
+  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
               wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
   launch_column<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, s);
   // ---------------- corrector ----------------
   launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s, threads);
-  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_for(nee, TH(8)), TH(8), s, sn_edge_corr<T>, g, v, x.s, st.vn,
+  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_by_point<T>(g.ne, nlev, TH(8)), TH(8), s, sn_edge_corr<T>, g, v, x.s, st.vn,
               wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn);
   const T* vn_new = kMixed<T> ? (const T*)m.vn : (const T*)st.vn;
-  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_for(nce, TH(6)), TH(6), s, sn_cell_div<T>, g, v, vn_new, wk.divd,
+  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, sn_cell_div<T>, g, v, vn_new, wk.divd,
               nullptr, nullptr);
-  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_for(nce, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
+  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
               vn_new, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
   launch_column<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, s);
 }
