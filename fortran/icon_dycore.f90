@@ -41,7 +41,8 @@ module icon_dycore
 
   public :: icon_grid_create, icon_grid_destroy, icon_dycore_params_default, icon_dycore_create, &
        icon_dycore_destroy, icon_dycore_step, icon_nh_solve, icon_nh_diff, icon_dycore_diagnostics, &
-       icon_state_from_blocked, icon_state_to_blocked, icon_dycore_step_blocked, icon_last_error_string
+       icon_state_from_blocked, icon_state_to_blocked, icon_dycore_step_blocked, icon_last_error_string, &
+       icon_dycore_save, icon_dycore_load
 
   interface
     integer(c_int) function icon_grid_create(desc, grid) bind(c, name="icon_grid_create")
@@ -73,6 +74,19 @@ module icon_dycore
       import :: c_int, c_ptr, icon_state_t
       type(c_ptr), value :: dycore
       type(icon_state_t), intent(in) :: state
+    end function
+    ! checkpoint / restart; path is a NUL-terminated character array (trim(name)//c_null_char)
+    integer(c_int) function icon_dycore_save(dycore, state, path) bind(c, name="icon_dycore_save")
+      import :: c_int, c_ptr, c_char, icon_state_t
+      type(c_ptr), value :: dycore
+      type(icon_state_t), intent(in) :: state
+      character(kind=c_char), dimension(*), intent(in) :: path
+    end function
+    integer(c_int) function icon_dycore_load(dycore, state, path) bind(c, name="icon_dycore_load")
+      import :: c_int, c_ptr, c_char, icon_state_t
+      type(c_ptr), value :: dycore
+      type(icon_state_t), intent(in) :: state
+      character(kind=c_char), dimension(*), intent(in) :: path
     end function
     integer(c_int) function icon_nh_solve(dycore, state) bind(c, name="icon_nh_solve")
       import :: c_int, c_ptr, icon_state_t

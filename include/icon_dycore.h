@@ -50,7 +50,7 @@ extern "C" {
 #define ICON_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement */
 
 #define ICON_PREC_FP64 0           /* every stencil and update in FP64 */
-#define ICON_PREC_MIXED 1          /* FP32 stencils, FP64 column solve and updates */
+#define ICON_PREC_MIXED 1          /* FP32 stencils, double-word FP32 column solve, FP64 state updates */
 
 typedef struct icon_grid icon_grid_t;      /* opaque */
 typedef struct icon_dycore icon_dycore_t;  /* opaque */
@@ -249,6 +249,22 @@ int icon_dycore_launch_config(const icon_dycore_t* dycore, char* buf, int32_t le
 
 /* Block until all work enqueued by this dycore has finished. */
 int icon_dycore_synchronize(icon_dycore_t* dycore);
+
+/* Checkpoint and restart of a state (DEVICE or HOST pointers, as for
+ * icon_dycore_step; not mixed).  icon_dycore_save waits for the dycore's
+ * enqueued work, then writes the file `path`: a 64-byte header (magic
+ * "ICONDYCK", format version 1, nlev, n_cells, n_edges, payload size, FNV-1a
+ * checksum of the payload's 64-bit words) followed by vn, w, rho, exner,
+ * theta_v and exner_pr as FP64 in the state's layout, host byte order
+ * (little-endian).  icon_dycore_load reads such a file into the state; it
+ * checks the magic, the version, the sizes against this dycore's and the
+ * checksum over the whole payload before it writes any field, so a refused
+ * file leaves the state as it was.  A step from a loaded state equals the
+ * step from the saved one bit for bit.  Errors: ICON_ERR_ARG (NULL argument,
+ * NULL field, mixed pointers, a file that cannot be opened, written or read,
+ * of another grid or damaged), ICON_ERR_CUDA. */
+int icon_dycore_save(icon_dycore_t* dycore, const icon_state_t* state, const char* path);
+int icon_dycore_load(icon_dycore_t* dycore, const icon_state_t* state, const char* path);
 
 /* Sizes: nlev, n_cells, n_edges, n_verts (any output pointer may be NULL). */
 int icon_dycore_sizes(const icon_dycore_t* dycore, int32_t* nlev, int32_t* n_cells,

@@ -87,6 +87,8 @@ _sig = {
     "icon_dycore_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_char_p, _i32p, _f64p, _i32p]),
     "icon_dycore_sizes": (ctypes.c_int, [ctypes.c_void_p] + [_i32p] * 4),
+    "icon_dycore_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p]),
+    "icon_dycore_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p]),
     "icon_last_error": (ctypes.c_char_p, []),
     "icon_dycore_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_void_p,
                                                ctypes.c_void_p, _f64p]),
@@ -407,6 +409,16 @@ class Dycore:
     def debug_field(self, name, out):
         """Copy the internal work field `name` into the device tensor `out`."""
         _check(icon_dycore_debug_field(self.handle, name.encode(), _ptr(out), out.numel() * out.element_size()))
+
+    def save(self, st, path):
+        """Write the state (device tensors or host arrays) to the checkpoint file `path`."""
+        s = self._state(st)
+        _check(icon_dycore_save(self.handle, ctypes.byref(s), os.fsencode(path)))
+
+    def load(self, st, path):
+        """Read the checkpoint file `path` into the state (device tensors or host arrays)."""
+        s = self._state(st)
+        _check(icon_dycore_load(self.handle, ctypes.byref(s), os.fsencode(path)))
 
     def launch_config(self):
         buf = ctypes.create_string_buffer(1024)

@@ -840,6 +840,154 @@ int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
   return ICON_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint files of a state: a 64-byte header, then vn, w, rho, exner,
+// theta_v and exner_pr as FP64 in the state's layout and the host's byte
+// order (little-endian on the x86-64 and AArch64 hosts this library builds
+// for).  The header carries a magic, a format version, the sizes and a
+// checksum (FNV-1a over the payload's 64-bit words), so that a file of
+// another grid or a damaged file is refused before the state is touched.
+// ---------------------------------------------------------------------------
+struct CheckpointHeader {
+  char magic[8];
+  uint32_t version, nlev;
+  int64_t n_cells, n_edges;
+  uint64_t payload_bytes, checksum;
+  uint8_t reserved[16];
+};
+static_assert(sizeof(CheckpointHeader) == 64, "checkpoint header size");
+constexpr char kCheckpointMagic[8] = {'I', 'C', 'O', 'N', 'D', 'Y', 'C', 'K'};
+constexpr uint32_t kCheckpointVersion = 1;
+
+uint64_t fnv1a_words(uint64_t h, const double* p, size_t n) {
+  uint64_t w;
+  for (size_t i = 0; i < n; ++i) {
+    std::memcpy(&w, p + i, 8);
+    h = (h ^ w) * 0x100000001b3ull;
+  }
+  return h;
+}
+
+struct FieldRef {
+  double* p;
+  size_t n;
+};
+
+int checkpoint_fields(icon_dycore* d, const icon_state_t* s, const char* fn, FieldRef (&f)[6], bool& device) {
+  if (!d || !s) return fail(ICON_ERR_ARG, std::string(fn) + ": NULL argument");
+  if (!s->vn || !s->w || !s->rho || !s->exner || !s->theta_v || !s->exner_pr)
+    return fail(ICON_ERR_ARG, std::string(fn) + ": NULL state field");
+  const HostGrid& h = d->grid->host;
+  const size_t ef = (size_t)h.ne * d->nlev, cf = (size_t)h.nc * d->nlev, ch = (size_t)h.nc * (d->nlev + 1);
+  const Where where = locate(s);
+  if (where == Where::kMixed) return fail(ICON_ERR_ARG, std::string(fn) + ": state mixes host and device pointers");
+  device = where == Where::kDevice;
+  f[0] = {s->vn, ef};
+  f[1] = {s->w, ch};
+  f[2] = {s->rho, cf};
+  f[3] = {s->exner, cf};
+  f[4] = {s->theta_v, cf};
+  f[5] = {s->exner_pr, cf};
+  return ICON_OK;
+}
+
+int checkpoint_save(icon_dycore* d, const icon_state_t* s, const char* path) {
+  const char* fn = "icon_dycore_save";
+  FieldRef f[6];
+  bool device = false;
+  int rc = checkpoint_fields(d, s, fn, f, device);
+  if (rc != ICON_OK) return rc;
+  if (!path) return fail(ICON_ERR_ARG, std::string(fn) + ": NULL path");
+  CUDA_TRY(cudaStreamSynchronize(d->stream));  // the state as the last enqueued step left it
+  CheckpointHeader hd{};
+  std::memcpy(hd.magic, kCheckpointMagic, 8);
+  hd.version = kCheckpointVersion;
+  hd.nlev = (uint32_t)d->nlev;
+  hd.n_cells = d->grid->host.nc;
+  hd.n_edges = d->grid->host.ne;
+  for (const FieldRef& x : f) hd.payload_bytes += x.n * 8;
+  hd.checksum = 0xcbf29ce484222325ull;
+  FILE* out = std::fopen(path, "wb");
+  if (!out) return fail(ICON_ERR_ARG, std::string(fn) + ": cannot open " + path + " for writing");
+  bool ok = std::fwrite(&hd, sizeof hd, 1, out) == 1;
+  std::vector<double> buf;
+  for (int i = 0; i < 6 && ok; ++i) {
+    const double* src = f[i].p;
+    if (device) {
+      buf.resize(f[i].n);
+      const cudaError_t e = cudaMemcpy(buf.data(), f[i].p, f[i].n * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        std::fclose(out);
+        return fail(ICON_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(e));
+      }
+      src = buf.data();
+    }
+    hd.checksum = fnv1a_words(hd.checksum, src, f[i].n);
+    ok = std::fwrite(src, 8, f[i].n, out) == f[i].n;
+  }
+  ok = ok && std::fseek(out, 0, SEEK_SET) == 0 && std::fwrite(&hd, sizeof hd, 1, out) == 1;
+  ok = (std::fclose(out) == 0) && ok;
+  if (!ok) return fail(ICON_ERR_ARG, std::string(fn) + ": writing " + path + " failed");
+  return ICON_OK;
+}
+
+int checkpoint_load(icon_dycore* d, const icon_state_t* s, const char* path) {
+  const char* fn = "icon_dycore_load";
+  FieldRef f[6];
+  bool device = false;
+  int rc = checkpoint_fields(d, s, fn, f, device);
+  if (rc != ICON_OK) return rc;
+  if (!path) return fail(ICON_ERR_ARG, std::string(fn) + ": NULL path");
+  FILE* in = std::fopen(path, "rb");
+  if (!in) return fail(ICON_ERR_ARG, std::string(fn) + ": cannot open " + path);
+  CheckpointHeader hd{};
+  size_t payload = 0;
+  for (const FieldRef& x : f) payload += x.n * 8;
+  std::string why;
+  if (std::fread(&hd, sizeof hd, 1, in) != 1) why = "no header";
+  else if (std::memcmp(hd.magic, kCheckpointMagic, 8) != 0) why = "not a dycore checkpoint";
+  else if (hd.version != kCheckpointVersion) why = "format version " + std::to_string(hd.version);
+  else if (hd.nlev != (uint32_t)d->nlev || hd.n_cells != d->grid->host.nc || hd.n_edges != d->grid->host.ne ||
+           hd.payload_bytes != payload)
+    why = "sizes differ from this dycore's";
+  std::vector<double> buf;
+  // first pass: the checksum over the whole payload, before the state is touched
+  uint64_t sum = 0xcbf29ce484222325ull;
+  for (int i = 0; i < 6 && why.empty(); ++i) {
+    buf.resize(f[i].n);
+    if (std::fread(buf.data(), 8, f[i].n, in) != f[i].n) why = "file truncated";
+    else sum = fnv1a_words(sum, buf.data(), f[i].n);
+  }
+  if (why.empty() && sum != hd.checksum) why = "checksum mismatch";
+  // second pass: into the state
+  if (why.empty() && std::fseek(in, (long)sizeof hd, SEEK_SET) != 0) why = "cannot rewind";
+  if (why.empty()) {
+    const cudaError_t e0 = cudaStreamSynchronize(d->stream);
+    if (e0 != cudaSuccess) {
+      std::fclose(in);
+      return fail(ICON_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(e0));
+    }
+  }
+  for (int i = 0; i < 6 && why.empty(); ++i) {
+    double* dst = device ? nullptr : f[i].p;
+    if (device) buf.resize(f[i].n);
+    if (std::fread(device ? buf.data() : dst, 8, f[i].n, in) != f[i].n) {
+      why = "file changed while reading";
+      break;
+    }
+    if (device) {
+      const cudaError_t e = cudaMemcpy(f[i].p, buf.data(), f[i].n * 8, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        std::fclose(in);
+        return fail(ICON_ERR_CUDA, std::string(fn) + ": " + cudaGetErrorString(e));
+      }
+    }
+  }
+  std::fclose(in);
+  if (!why.empty()) return fail(ICON_ERR_ARG, std::string(fn) + ": " + path + ": " + why);
+  return ICON_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1009,6 +1157,14 @@ int icon_dycore_sizes(const icon_dycore_t* d, int32_t* nlev, int32_t* nc, int32_
   if (ne) *ne = d->grid->host.ne;
   if (nv) *nv = d->grid->host.nv;
   return ICON_OK;
+}
+
+int icon_dycore_save(icon_dycore_t* d, const icon_state_t* s, const char* path) {
+  return checkpoint_save(d, s, path);
+}
+
+int icon_dycore_load(icon_dycore_t* d, const icon_state_t* s, const char* path) {
+  return checkpoint_load(d, s, path);
 }
 
 
