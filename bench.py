@@ -561,11 +561,14 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision and learned legs")
     ap.add_argument("--no-learned", action="store_true", help="skip the mixed + learned-corrector leg")
     ap.add_argument("--grid", type=int, default=WORKLOAD["bisections"],
-                    help="RnBm bisections (default 6 = R2B6); smaller grids only for profiler captures")
+                    help="RnBm bisections (default 6 = R2B6); other grids for profiler captures and scaling runs")
+    ap.add_argument("--dtime", type=float, default=WORKLOAD["dtime"],
+                    help="time step in s (default 360, the R2B6 step; 180 at R2B7)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     WORKLOAD["bisections"] = args.grid
+    WORKLOAD["dtime"] = args.dtime
     legs = [x for x in args.legs.split(",") if x]
     if args.no_mixed:
         legs = [x for x in legs if x not in ("mixed", "learned")]
