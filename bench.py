@@ -369,9 +369,9 @@ COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
 # DRAM bytes per step of every kernel in the timed steps, from one ncu capture
 # of each leg at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid while
 # the kernel sources are the ones captured (SHA-256 over csrc/*, below).
-STEP_DRAM = {"sources_sha256": "3d58c28d5beb88806ca9e4e5a5f47c2518f84190e3a8733dad0412cf0a4a05cf",
-             "bisections": 6, "bytes_per_step": {"fp64": 207.196e9, "mixed": 156.610e9,
-                                                 "learned": 136.526e9}}
+STEP_DRAM = {"sources_sha256": "3cdb769be49ecfd4b481dae6f607bae8fcc10071ecdba6a0e7df08f87cdd54b9",
+             "bisections": 6, "bytes_per_step": {"fp64": 207.168e9, "mixed": 156.647e9,
+                                                 "learned": 136.601e9}}
 
 
 def sources_sha256():
