@@ -1085,7 +1085,7 @@ int icon_dycore_debug_field(icon_dycore_t* d, const char* name, void* dst, int64
   pick("grad4", a.grad4, b.grad4, 4 * cf, es);
   pick("div_m", d->en.wk.div_m, d->en.wk.div_m, cf, sizeof(double));
   pick("div_t", d->en.wk.div_t, d->en.wk.div_t, cf, sizeof(double));
-  pick("w_p", d->en.wk.w_p, d->en.wk.w_p, ch, sizeof(double));
+  pick("w_p", d->en.wk.w_p, d->en.m.w_p, ch, es);
   pick("rho_p", d->en.wk.rho_p, d->en.wk.rho_p, cf, sizeof(double));
   pick("theta_p", d->en.wk.theta_p, d->en.wk.theta_p, cf, sizeof(double));
   if (!src) return fail(ICON_ERR_ARG, std::string("icon_dycore_debug_field: unknown field ") + name);

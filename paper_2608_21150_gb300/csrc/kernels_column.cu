@@ -297,10 +297,11 @@ __device__ __forceinline__ R levs(const DevVert& v, const double* Ls, int k, int
   }
 }
 
-// A flux divergence of the tile: FP64, or in the mixed-precision step (T =
-// float) the double-word pair the flux-divergence kernel stored.
+// A value the mixed-precision step (T = float) keeps as a double-word pair in
+// an 8-byte slot -- the flux divergences and the predictor's rho and theta_v
+// -- read as the pair; otherwise an FP64 value, converted.
 template <class T, class R>
-__device__ __forceinline__ R divergence(const double* p) {
+__device__ __forceinline__ R stored_in(const double* p) {
   if constexpr (std::is_same<T, float>::value && !std::is_same<R, double>::value) {
     return *reinterpret_cast<const R*>(p);
   } else {
@@ -336,6 +337,8 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
   const bool corrector = kCorr < 0 ? corrector_arg != 0 : kCorr == 1;
   using A = Ar<R>;
   constexpr bool kDW = !std::is_same<R, double>::value;
+  // the mixed step's engine path (FP32 stencil inputs, double-word solve)
+  constexpr bool kPairs = std::is_same<T, float>::value && kDW;
   constexpr int kTile = tile_doubles<KC>();
   constexpr int kBackIn = KC * kCW;
   constexpr int kOut = KC * kLD;
@@ -422,8 +425,8 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       if (k == 0) {
         rho_c = A::in(T_rho[o]);
         th_c = A::in(T_th[o]);
-        ra_c = corrector ? add_pos(wn_r * rho_c, wnew_r * A::in(T_rp[o])) : rho_c;
-        ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * A::in(T_tp[o])) : th_c;
+        ra_c = corrector ? add_pos(wn_r * rho_c, wnew_r * stored_in<T, R>(T_rp + o)) : rho_c;
+        ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * stored_in<T, R>(T_tp + o)) : th_c;
         tpa_c = ta_c - levs<R, LTH, kStage>(v, L_s, 0, k0);
         wk_c = A::in(T_w[o]);
         fr_c = ric_k * wk_c;
@@ -438,8 +441,8 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       if (k + 1 < nlev) {
         rho_x = A::in(T_rho[o + kLD]);
         th_x = A::in(T_th[o + kLD]);
-        ra_x = corrector ? add_pos(wn_r * rho_x, wnew_r * A::in(T_rp[o + kLD])) : rho_x;
-        ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * A::in(T_tp[o + kLD])) : th_x;
+        ra_x = corrector ? add_pos(wn_r * rho_x, wnew_r * stored_in<T, R>(T_rp + o + kLD)) : rho_x;
+        ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * stored_in<T, R>(T_tp + o + kLD)) : th_x;
         tpa_x = ta_x - levs<R, LTH, kStage>(v, L_s, k + 1, k0);
         const R g1 = levs<R, WG, kStage>(v, L_s, k + 1, k0), g2 = levs<R, WG2, kStage>(v, L_s, k + 1, k0);
         ric_k1 = add_pos(g1 * ra_c, g2 * ra_x);
@@ -458,8 +461,8 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       const R wk = wk_c, wk1 = A::in(T_w[o + kLD]);
       const R rt_k1 = ric_k1 * tic_k1;
       const R fr_k1 = ric_k1 * wk1, fg_k1 = rt_k1 * wk1;
-      const R rstar = rho_n - dt * divergence<T, R>(T_dm + o) - levs<R, CR, kStage>(v, L_s, k, k0) * (fr_c - fr_k1);
-      const R pstar = pr_k - zb * (levs<R, LDZ, kStage>(v, L_s, k, k0) * divergence<T, R>(T_dt + o) + ombeta * (fg_c - fg_k1));
+      const R rstar = rho_n - dt * stored_in<T, R>(T_dm + o) - levs<R, CR, kStage>(v, L_s, k, k0) * (fr_c - fr_k1);
+      const R pstar = pr_k - zb * (levs<R, LDZ, kStage>(v, L_s, k, k0) * stored_in<T, R>(T_dt + o) + ombeta * (fg_c - fg_k1));
       const R al_k = al_c, al_k1 = beta * rt_k1;
       put(rs_s + ik, rstar);
       put(ps_s + ik, pstar);
@@ -564,10 +567,16 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
         const R prnew = get<R>(B_ps + b) - zb * (fa - fa_k1);
         const R thnew = levs<R, CZB, kStage>(v, L_s, k, k0) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
         const int o = kk * kLD + t;
-        O_w[o] = A::out(wd);
-        O_rho[o] = A::out(rnew);
+        if (a.w_o) O_w[o] = A::out(wd);
+        if (kPairs && !corrector) {
+          // the mixed predictor's rho and theta_v stay double-word pairs (read by the corrector)
+          *reinterpret_cast<R*>(O_rho + o) = rnew;
+          *reinterpret_cast<R*>(O_th + o) = thnew;
+        } else {
+          O_rho[o] = A::out(rnew);
+          O_th[o] = A::out(thnew);
+        }
         if (a.exner_o) O_pi[o] = A::out(levs<R, LEX, kStage>(v, L_s, k, k0) + prnew);
-        O_th[o] = A::out(thnew);
         if constexpr (kDW) {
           // FP32 mirrors straight from the double-word values, into this
           // thread's consumed scratch slots: (w, rho - rho_ref) and theta_v - theta_ref
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       }
     }
     __syncthreads();
-    store_tile<KC>(O_w, a.w_o, nlevp, c0, nc, k0, nk);
+    if (a.w_o) store_tile<KC>(O_w, a.w_o, nlevp, c0, nc, k0, nk);
     store_tile<KC>(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
     if (a.exner_o) store_tile<KC>(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
     store_tile<KC>(O_th, a.theta_o, nlev, c0, nc, k0, nk);
@@ -591,7 +600,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
     }
   }
   if (active) {
-    a.w_o[(size_t)c * nlevp + nlev] = 0.0;
+    if (a.w_o) a.w_o[(size_t)c * nlevp + nlev] = 0.0;
     if (a.m_w) a.m_w[(size_t)c * nlevp + nlev] = 0.0f;
   }
 }
@@ -653,7 +662,7 @@ void launch_column(const Engine& en, int corrector, const StateView& st, const T
       a.m_th = en.m.th;
     }
   } else {
-    a.w_o = wk.w_p;
+    a.w_o = mixed ? nullptr : wk.w_p;  // mixed: the predicted w is read only as its FP32 mirror
     a.rho_o = wk.rho_p;
     a.exner_o = nullptr;  // the predicted exner has no reader
     a.theta_o = wk.theta_p;
