@@ -362,16 +362,16 @@ FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
 # step at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid for that grid
 # while the kernel source is the one captured (its SHA-256 below).
 COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
-                  "sha256": "3910f6ac71b23e56f1f3cdbd9eb632dad583279b5ee3e02d3bbe6f755cc4faca",
-                  "bisections": 6, "bytes_per_launch": 7.419006707e9}
+                  "sha256": "65803cf84dd8fb1a006740f0e0dce6e2892a81b01d18fd9f2bb4403acdaa30dd",
+                  "bisections": 6, "bytes_per_launch": 7.42e9}
 
 
 # DRAM bytes per step of every kernel in the timed steps, from one ncu capture
 # of each leg at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid while
 # the kernel sources are the ones captured (SHA-256 over csrc/*, below).
-STEP_DRAM = {"sources_sha256": "3cdb769be49ecfd4b481dae6f607bae8fcc10071ecdba6a0e7df08f87cdd54b9",
-             "bisections": 6, "bytes_per_step": {"fp64": 207.168e9, "mixed": 156.647e9,
-                                                 "learned": 136.601e9}}
+STEP_DRAM = {"sources_sha256": "625bffad32b74614d20a005f9a24d7fcbbb676b96f1b13d8749de50c7a9bcf1e",
+             "bisections": 6, "bytes_per_step": {"fp64": 207.191e9, "mixed": 154.254e9,
+                                                 "learned": 134.686e9}}
 
 
 def sources_sha256():
