@@ -17,13 +17,14 @@
 //
 // Memory: the state is level-contiguous, so a thread walking its own column
 // would read every 32-byte sector for 8 useful bytes.  Instead each CTA of
-// kCW columns stages chunks of kKC levels of every input through shared
-// memory with coalesced loads (a column's chunk is a contiguous run), and
-// stages its outputs the same way.  The Thomas scratch is level-major
+// kCW columns stages chunks of KC levels (4, 6 or 8, picked by the
+// autotuner) of every input through shared memory with coalesced loads (a
+// column's chunk is a contiguous run), and stages its outputs the same way.
+// The Thomas scratch is level-major
 // [k][c], coalesced for one thread per column; it is written as streaming
 // data and read back evict-first, while the input rows are kept (L2 policies
-// below).  The double-word form also stages each chunk's slice of the
-// per-level table in shared memory: every thread of the CTA reads the same
+// below).  Each chunk's slice of the per-level table is staged in shared
+// memory as well (FP64 or double-word): every thread of the CTA reads the same
 // level at the same time, and from L1 those loads were a large share of the
 // kernel's stalls.  The predictor and corrector forms are separate kernels.
 #include <cuda_runtime.h>

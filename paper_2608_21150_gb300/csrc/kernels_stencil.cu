@@ -3,16 +3,19 @@
 //
 // Layout: level-contiguous X[h * nk + k] (k = 0 at the model top); one thread
 // per (horizontal point, level), flattened so that the 32 lanes of a warp
-// cover consecutive levels of one or two columns.  Neighbour gathers
-// X[nbr * nk + k] are coalesced runs of consecutive levels.
+// cover consecutive levels of one or two columns (the FP32 forms of five
+// gather-heavy kernels: one warp per point instead, see blocks_by_point).
+// Neighbour gathers X[nbr * nk + k] are coalesced runs of consecutive levels.
 //
 // Mixed mode: the stencils read FP32 mirrors of the state (vn, w and the
 // perturbations rho - rho_ref, theta_v - theta_ref) and compute in FP32,
-// except the exner difference of the horizontal pressure gradient; prognostic updates stay FP64 (the FP64 state plus an FP32
-// increment) and rewrite the mirrors; flux divergences are summed in FP64 so
+// except the exner difference of the horizontal pressure gradient (double-
+// word); prognostic updates stay FP64 (the FP64 state plus an FP32 increment)
+// and rewrite the mirrors; flux divergences are summed in double-word FP32 so
 // that every edge flux is one value shared by its two cells (mass conserved
-// to FP64 rounding).  FP64<->FP32 conversions run on the FP64 pipe on this
-// GPU, so each value is converted once by its writer, never per gather.
+// to about 2^-48), and stored as the pair for the column solve.  FP64<->FP32
+// conversions run on the FP64 pipe on this GPU, so they are done with integer
+// operations, once per value by its writer, never per gather.
 #include <cuda_runtime.h>
 
 #include <type_traits>
