@@ -388,20 +388,20 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
 FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
 
 # DRAM bytes per launch of the FP64 column solve (the mean of its predictor
-# and corrector launches, 6.38 and 8.46 GB) from the ncu capture of the FP64
+# and corrector launches, 6.39 and 8.47 GB) from the ncu capture of the FP64
 # step at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid for that grid
 # while the kernel source is the one captured (its SHA-256 below).
 COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
-                  "sha256": "65803cf84dd8fb1a006740f0e0dce6e2892a81b01d18fd9f2bb4403acdaa30dd",
-                  "bisections": 6, "bytes_per_launch": 7.42e9}
+                  "sha256": "1fc4e7a652e5d510c7db7dfe44654c9b8fd3a81b01462c4eac418754c02a58ea",
+                  "bisections": 6, "bytes_per_launch": 7.427e9}
 
 
 # DRAM bytes per step of every kernel in the timed steps, from one ncu capture
 # of each leg at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid while
 # the kernel sources are the ones captured (SHA-256 over csrc/*, below).
-STEP_DRAM = {"sources_sha256": "625bffad32b74614d20a005f9a24d7fcbbb676b96f1b13d8749de50c7a9bcf1e",
-             "bisections": 6, "bytes_per_step": {"fp64": 207.191e9, "mixed": 154.254e9,
-                                                 "learned": 134.686e9}}
+STEP_DRAM = {"sources_sha256": "bb89d434b15ae2f57f5e3ce4e070b62bd2962f886547159bd38476f8b0782b0e",
+             "bisections": 6, "bytes_per_step": {"fp64": 207.265e9, "mixed": 154.345e9,
+                                                 "learned": 134.728e9}}
 
 
 def sources_sha256():
