@@ -146,6 +146,32 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def init_ranks(world, backend="nccl"):
+    """One process per GPU (replicas): join the process group when world > 1
+    (NCCL on the GPUs; gloo in the CPU tests of this logic)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend, init_method="env://")
+
+
+def max_over_ranks(ms, world, device):
+    """The longest of the ranks' timed regions: the job ends with its slowest
+    rank, so the whole-job throughput is measured against that time."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms):
+    """Whole-job steps/s: every rank advances its own replica by `steps` in at
+    most `ms` milliseconds (weak scaling: the work per GPU is fixed)."""
+    return world * steps / (ms / 1000.0)
+
+
 def oracle_sample(bisections, nlev, reps):
     """Time the oracle (as it stands) on one substep and one diffusion call of
     the given grid, in a fresh single-threaded process; returns seconds."""
@@ -253,9 +279,7 @@ def measure(P, G, z, st0, prec, args, dev, world):
     ms = e0.elapsed_time(e1)
     if world > 1:
         dist.barrier()
-        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms = float(mt.item())
+    ms = max_over_ranks(ms, world, dev)
     nc = G.n_cells
     ps = torch.empty(nc, dtype=torch.float64, device=dev)
     t850 = torch.empty_like(ps)
@@ -348,12 +372,7 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        mt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms = float(mt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     nc = G.n_cells
     ps = torch.empty(nc, dtype=torch.float64, device=dev)
     t850 = torch.empty_like(ps)
@@ -366,7 +385,7 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
     rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
     with P.Profile() as prof:
         P.step_learned(R, Pl, cn, en, t, L["max_norm"])
-    out = {"value": world * args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
+    out = {"value": job_throughput(world, args.steps, ms), "ms_per_step": ms / args.steps,
            "fallbacks_timed": fallbacks, "fallbacks_warmup": fallbacks_warm, "max_norm": L["max_norm"],
            "check_norm_mean": float(np.nanmean(norms)) if norms else None, "finite": finite,
            "rms_ps_pa_vs_fp64": rms(ps.cpu().numpy() - f64_final["ps"]) if f64_final else None,
@@ -480,8 +499,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
+    init_ranks(world, "nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -507,7 +525,7 @@ def run_ours(args):
     if "fp64" in legs:
         f64, _ = measure(P, G, z, st0, "fp64", args, dev, world)
         ms_per_step = f64["ms"] / args.steps
-        value = world * args.steps / (f64["ms"] / 1000.0)
+        value = job_throughput(world, args.steps, f64["ms"])
         prof, nsp = f64["prof"], f64["nsteps_prof"]
         launches_per_step = sum(n for n, _ in prof.values()) // nsp
         kernels = kernel_table(prof, nsp)
@@ -518,7 +536,7 @@ def run_ours(args):
         m, _ = measure(P, G, z, st0, "mixed", args, dev, world)
         area = G.cell_areas()
         rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
-        mx = {"value": world * args.steps / (m["ms"] / 1000.0), "ms_per_step": m["ms"] / args.steps,
+        mx = {"value": job_throughput(world, args.steps, m["ms"]), "ms_per_step": m["ms"] / args.steps,
               "speedup_vs_fp64": f64["ms"] / m["ms"] if f64 else None, "finite": m["finite"],
               "rms_ps_pa": rms(m["ps"] - f64["ps"]) if f64 else None,
               "rms_t850_k": rms(m["t850"] - f64["t850"]) if f64 else None,
