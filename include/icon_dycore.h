@@ -47,7 +47,7 @@ extern "C" {
 #define ICON_ERR_CUDA (-2)         /* a CUDA runtime call failed */
 #define ICON_ERR_GRID (-3)         /* grid tables or coordinates inconsistent */
 #define ICON_ERR_NUMERIC (-4)      /* non-finite or out-of-range state detected */
-#define ICON_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement */
+#define ICON_ERR_UNSUPPORTED (-5)  /* valid request the library does not implement */
 
 #define ICON_PREC_FP64 0           /* every stencil and update in FP64 */
 #define ICON_PREC_MIXED 1          /* FP32 stencils, double-word FP32 column solve, FP64 state updates */

@@ -1,4 +1,4 @@
-"""Diagnostics of a state (outside the step; SURVEY-listed, the paper has none):
+"""Diagnostics of a state (outside the step; the paper defines none):
 surface pressure, 850 hPa temperature, total mass, area-weighted RMS.
 
 Readings:

@@ -1,7 +1,8 @@
 """Build libicondycore.so in-tree with nvcc for sm_103a (GB300).
 
 Each translation unit is compiled in parallel; the CUDA runtime is linked
-statically so the library only needs the driver at run time.
+statically so the library only needs the NVIDIA kernel-mode driver (libcuda)
+at run time.
 """
 import os
 import subprocess

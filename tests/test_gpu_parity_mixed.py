@@ -1,6 +1,7 @@
 """Mixed precision (FP32 stencils, FP64 column solve and prognostic updates)
 against the FP64 oracle.  Tolerances come from FP32 rounding (6e-8)
-amplified by the cancellation in the stencils, see the design doc."""
+amplified by the cancellation of reference and perturbation parts in the
+stencils."""
 import numpy as np
 import pytest
 
