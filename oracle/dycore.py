@@ -273,6 +273,31 @@ class Dycore:
         return vn + p.divflux_fac * am * self.grad_n(self.div(vn))
 
     # ------------------------------------------------------------------
+    # predictor pieces (rows A5, A6)
+    # ------------------------------------------------------------------
+    def extrapolate_exner(self, pr, pr_old):
+        """Exner perturbation extrapolated linearly in time from the substeps
+        n-1 and n to n + gamma, gamma = exner_exfac:
+        (1 + gamma) pr - gamma pr_old."""
+        gam = self.p.exner_exfac
+        return (1.0 + gam) * pr - gam * pr_old
+
+    def upwind_edge_values(self, X, vn, vt, dt):
+        """Edge values [ne, K] of the cell field X taken from the upwind cell
+        (c0 where vn >= 0, else c1) at the back-trajectory point of the edge
+        midpoint over dt/2: X_up + grad X_up . (a x_e - (dt/2) v_e - a x_up),
+        v_e = vn n + vt t, grad the Green-Gauss cell gradient."""
+        g = self.g
+        c0, c1 = g.e2c[:, 0], g.e2c[:, 1]
+        grad = self.grad_cell(X)
+        up = np.where(vn >= 0.0, c0[:, None], c1[:, None])         # [ne, K]
+        disp = (g.a * (g.E[:, None, :] - g.C[up])
+                - 0.5 * dt * (vn[:, :, None] * g.normal[:, None, :]
+                              + vt[:, :, None] * g.tangent[:, None, :]))
+        kidx = np.arange(X.shape[1])[None, :]
+        return X[up, kidx] + np.sum(grad[up, kidx] * disp, axis=-1)
+
+    # ------------------------------------------------------------------
     # one dynamical substep: predictor + corrector (rows A5-A9, A7)
     # ------------------------------------------------------------------
     def substep(self, st):
@@ -280,8 +305,6 @@ class Dycore:
         Returns the new state (vn, w, rho, exner, theta_v, exner_pr)."""
         p, g, v = self.p, self.g, self.v
         dt = p.dtime / p.ndyn_substeps
-        nlev = v.nlev
-        c0, c1 = g.e2c[:, 0], g.e2c[:, 1]
         vn, w = st["vn"], st["w"]
         rho, exner, theta = st["rho"], st["exner"], st["theta_v"]
 
@@ -289,18 +312,11 @@ class Dycore:
         ddt_vn_now, ddt_w_now, vt = self.velocity_tendencies(vn, w)
         # A5: exner perturbation, extrapolated in time; history update
         pr = exner - v.exner_ref[None, :]
-        pr_ex = (1.0 + p.exner_exfac) * pr - p.exner_exfac * st["exner_pr"]
+        pr_ex = self.extrapolate_exner(pr, st["exner_pr"])
         exner_pr_new = pr.copy()
         # A6: upwind rho and theta_v at edges from a back trajectory over dt/2
-        grad_rho = self.grad_cell(rho)
-        grad_th = self.grad_cell(theta)
-        up = np.where(vn >= 0.0, c0[:, None], c1[:, None])         # [ne, nlev]
-        disp = (g.a * (g.E[:, None, :] - g.C[up])
-                - 0.5 * dt * (vn[:, :, None] * g.normal[:, None, :]
-                              + vt[:, :, None] * g.tangent[:, None, :]))
-        kidx = np.arange(nlev)[None, :]
-        rho_e = rho[up, kidx] + np.sum(grad_rho[up, kidx] * disp, axis=-1)
-        theta_e = theta[up, kidx] + np.sum(grad_th[up, kidx] * disp, axis=-1)
+        rho_e = self.upwind_edge_values(rho, vn, vt, dt)
+        theta_e = self.upwind_edge_values(theta, vn, vt, dt)
         # horizontal pressure gradient term, kept for the corrector
         hpg = p.cpd * theta_e * self.grad_n(pr_ex)
         vn_pred = vn + dt * (ddt_vn_now - hpg)

@@ -1,0 +1,435 @@
+"""Closed-form pins of the oracle's advective tendencies (rows A1-A4), vector
+Laplacian and Smagorinsky deformation (row A10), and Rayleigh damping of the
+column solve (row A7), on the sphere of radius a.
+
+The continuum values are those of the vector-invariant momentum equation
+(Sec. 4.1 names velocity advection and the horizontal diffusion but prints no
+discretisation):
+
+* Zonal solid-body flow u = U cos(lat) e_east, w = 0: the advective tendency
+  -(zeta + f) k x u - grad K is -U cos(lat) sin(lat) (U/a + 2 Omega) e_north
+  (zeta = 2 U sin(lat)/a, K = U^2 cos^2(lat)/2).
+* -w dvn/dz and -w dw/dz of profiles linear in z: exact in the discretisation,
+  so checked to rounding.
+* -u . grad w of w = W0 x (x, y, z the unit position vector) under the
+  rotation u = U z x r: W0 U y / a.
+* Degree-1 fields (the gradient of sin(lat) and the rotation) are
+  eigenfunctions of the vector Laplacian grad div - curl curl with eigenvalue
+  -2/a^2.
+* Rigid rotation and the gradient of a degree-1 harmonic have zero
+  deformation; u = grad chi and u = k x grad chi for chi = U a x y (a
+  degree-2 harmonic) have |D| = lambda_1 - lambda_2 of the tangential Hessian
+  of chi, independent of the frame.
+
+Horizontal derivatives of reconstructed quantities on the triangular C-grid
+are consistent only to zeroth order in the maximum norm on this
+(non-optimised) icosahedral grid, so those pins use area-RMS errors with
+tolerances set a factor 2-3 above the error measured at R2B3; a wrong sign or
+a dropped term changes the result by 4-200 % of the reference and fails them."""
+import numpy as np
+import pytest
+
+from icon_inputs import make_grid, make_vct, jw_type_state
+from oracle import Dycore, DycoreParams
+
+A = 6.371229e6
+U = 20.0
+
+
+@pytest.fixture(scope="module")
+def d3():
+    return Dycore(make_grid(3), make_vct(30), DycoreParams())
+
+
+def north(x):
+    n = np.array([0.0, 0.0, 1.0]) - x[:, 2:3] * x
+    return n / np.linalg.norm(n, axis=1, keepdims=True)
+
+
+def east(x):
+    e = np.cross([0.0, 0.0, 1.0], x)
+    return e / np.linalg.norm(e, axis=1, keepdims=True)
+
+
+def rms_rel(err, ref):
+    return float(np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(ref ** 2)))
+
+
+def rotation_vn(g, u0=U):
+    """Edge-normal component of the rigid rotation u0 z x r (eastward u0 cos(lat))."""
+    return np.sum(u0 * np.cross([0.0, 0.0, 1.0], g.E) * g.normal, 1)
+
+
+def zonal_reference(g, omega):
+    s = g.E[:, 2]
+    c = np.sqrt(1.0 - s * s)
+    return -U * c * s * (U / A + 2.0 * omega) * np.sum(north(g.E) * g.normal, 1)
+
+
+# ---------------------------------------------------------------- A1-A4
+def test_zonal_flow_tendency_with_and_without_rotation():
+    """With Omega, the Coriolis term dominates (error 0.6 % RMS); without it the
+    tendency is the residue of the vorticity term (-2 U^2 cs/a) and the kinetic
+    energy gradient (+U^2 cs/a), and the known zeroth-order inconsistency of
+    the C-grid kinetic-energy gradient leaves 25 % RMS."""
+    for omega, tol in ((None, 0.012), (0.0, 0.35)):
+        prm = DycoreParams() if omega is None else DycoreParams(omega=omega)
+        d = Dycore(make_grid(3), make_vct(30), prm)
+        g, nlev = d.g, d.v.nlev
+        vn = np.repeat(rotation_vn(g)[:, None], nlev, 1)
+        ddt_vn, ddt_w, vt = d.velocity_tendencies(vn, np.zeros((g.nc, nlev + 1)))
+        assert ddt_vn.shape == (g.ne, nlev) and ddt_w.shape == (g.nc, nlev + 1)
+        ref = zonal_reference(g, d.p.omega)
+        for k in (0, nlev // 2, nlev - 1):      # no vertical shear: every level alike
+            assert rms_rel(ddt_vn[:, k] - ref, ref) < tol, (omega, k, rms_rel(ddt_vn[:, k] - ref, ref))
+        assert np.max(np.abs(ddt_w)) < 1e-20
+
+
+def test_vertical_advection_of_vn_is_exact_for_linear_shear(d3):
+    """vn = (1 + c z) vn_rot, w = W at every half level: the part of ddt_vn that
+    w adds is -W c vn_rot at every level away from the top and the ground,
+    where vn at half levels is interpolated linearly in z (exact) rather than
+    extrapolated."""
+    d, g, v = d3, d3.g, d3.v
+    nlev, c, W = v.nlev, 1e-3, 0.3
+    rot = rotation_vn(g)
+    vn = rot[:, None] * (1.0 + c * v.z_mc)[None, :]
+    with_w, _, _ = d.velocity_tendencies(vn, np.full((g.nc, nlev + 1), W))
+    without, _, _ = d.velocity_tendencies(vn, np.zeros((g.nc, nlev + 1)))
+    diff = (with_w - without)[:, 1:nlev - 1]
+    ref = -W * c * rot[:, None]
+    assert np.max(np.abs(diff - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_vertical_advection_of_w_is_exact_for_linear_w(d3):
+    """w = alpha + beta z, vn = 0: ddt_w = -w beta at interior half levels and 0
+    at the top and the ground."""
+    d, g, v = d3, d3.g, d3.v
+    nlev, al, be = v.nlev, 0.2, 1e-4
+    w = np.repeat((al + be * v.z_ifc)[None, :], g.nc, 0)
+    _, ddt_w, _ = d.velocity_tendencies(np.zeros((g.ne, nlev)), w)
+    ref = -(al + be * v.z_ifc[1:nlev]) * be
+    assert np.max(np.abs(ddt_w[:, 1:nlev] - ref[None, :])) < 1e-14 * np.max(np.abs(ref))
+    assert np.all(ddt_w[:, 0] == 0.0) and np.all(ddt_w[:, nlev] == 0.0)
+
+
+def test_horizontal_advection_of_w(d3):
+    """w = W0 x/a (uniform in z, so no vertical part), u = U z x r: ddt_w =
+    -u . grad w = W0 U y / a at cell centres (measured 1.8 % RMS at R2B3,
+    1.3 % at R2B4)."""
+    d, g, v = d3, d3.g, d3.v
+    nlev, W0 = v.nlev, 0.5
+    vn = np.repeat(rotation_vn(g)[:, None], nlev, 1)
+    w = np.repeat((W0 * g.C[:, 0])[:, None], nlev + 1, 1)
+    _, ddt_w, _ = d.velocity_tendencies(vn, w)
+    ref = W0 * U * g.C[:, 1] / A
+    for k in (1, nlev // 2, nlev - 1):
+        assert rms_rel(ddt_w[:, k] - ref, ref) < 0.04, (k, rms_rel(ddt_w[:, k] - ref, ref))
+
+
+# ---------------------------------------------------------------- A10
+def test_vector_laplacian_of_degree_one_fields(d3):
+    """grad div - curl curl of the gradient of sin(lat) and of the rotation:
+    -2/a^2 times the field (measured 17 % and 4.7 % RMS at R2B3; grad_n of the
+    triangle divergence is zeroth-order consistent)."""
+    d, g = d3, d3.g
+    for vn, tol in (((U * g.normal[:, 2])[:, None], 0.25), (rotation_vn(g)[:, None], 0.08)):
+        ref = -2.0 * vn / A ** 2
+        assert rms_rel(d.lap_vec(vn) - ref, ref) < tol
+
+
+def _deformation(d, vn):
+    return d.smagorinsky(vn)[:, 0] / (d.p.hdiff_smag_fac * d.g.edge_area)
+
+
+def test_smagorinsky_vanishes_for_rigid_rotation_and_conformal_flow(d3):
+    """|D| = 0 for the rotation (a Killing field) and for the gradient of sin(lat)
+    (a conformal field: pure divergence, no deformation); measured 5.7 % of
+    U/a RMS."""
+    d, g = d3, d3.g
+    for vn in (rotation_vn(g)[:, None], (U * g.normal[:, 2])[:, None]):
+        D = _deformation(d, vn)
+        assert np.sqrt(np.mean(D ** 2)) < 0.1 * U / A
+
+
+def test_smagorinsky_of_degree_two_strain(d3):
+    """u = grad chi and u = k x grad chi, chi = U a x y: |D| is the difference of
+    the eigenvalues of the tangential Hessian of chi (U/a) [[0,1,0],[1,0,0],
+    [0,0,0]], evaluated in the east/north frame (measured 4.4 % RMS)."""
+    d, g = d3, d3.g
+    E, n = g.E, g.normal
+    grad_chi = np.stack([E[:, 1], E[:, 0], np.zeros(g.ne)], 1)        # (U a x y) gradient / U
+    M = np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    el, no = east(E), north(E)
+    h = lambda x, y: np.einsum("ei,ij,ej->e", x, M, y)   # noqa: E731
+    ref = (U / A) * np.sqrt((h(el, el) - h(no, no)) ** 2 + 4.0 * h(el, no) ** 2)
+    for field in (grad_chi, np.cross(E, grad_chi)):
+        vn = U * np.sum(n * field, 1)[:, None]
+        assert rms_rel(_deformation(d, vn) - ref, ref) < 0.1
+
+
+# ---------------------------------------------------------------- A7 damping
+def test_rayleigh_profile_closed_form():
+    """dt tau^-1 sin^2(pi/2 (z - z_d)/(z_top - z_d)) above z_d: 0 at and below
+    z_d, sin^2(pi/8) = (2 - sqrt 2)/4 a quarter of the way up the layer, one
+    half in its middle, dt/tau at the top; 0 when off.  (z_d = 18 km below a
+    30 km top: no shift of the phase by a multiple of pi leaves these values
+    unchanged at all three points.)"""
+    z = np.linspace(30000.0, 0.0, 31)
+    dt, coeff = 120.0, 1.0 / 3600.0
+    d = Dycore(make_grid(0), z, DycoreParams(rayleigh_coeff=coeff, damp_height=18000.0))
+    f = d.v.rayleigh_factor(dt, d.p)
+    assert f[0] == dt * coeff
+    assert abs(f[6] - 0.5 * dt * coeff) < 1e-15 * dt * coeff                 # z = 24 km
+    assert abs(f[9] - (2.0 - np.sqrt(2.0)) / 4.0 * dt * coeff) < 1e-15 * dt * coeff   # z = 21 km
+    assert np.all(f[12:] == 0.0)                                           # z <= 18 km
+    assert np.all(np.diff(f[:13]) < 0.0)                                   # decreasing downward
+    off = Dycore(make_grid(0), z, DycoreParams()).v.rayleigh_factor(dt, DycoreParams())
+    assert np.all(off == 0.0)
+
+
+def test_rayleigh_damping_scales_the_solved_w_before_back_substitution():
+    """Same column inputs with damping off and on: the damped w is the undamped
+    w divided by 1 + rf at every half level, and rho and exner follow from the
+    damped w by the back-substitution equations."""
+    grid, z = make_grid(1), make_vct(30)
+    st = jw_type_state(grid, z, amp=0.0)
+    coeff = 1.0 / 600.0
+    off = Dycore(grid, z, DycoreParams(dtime=900.0))
+    on = Dycore(grid, z, DycoreParams(dtime=900.0, rayleigh_coeff=coeff, damp_height=10000.0))
+    v, p = on.v, on.p
+    nc, nlev = st["rho"].shape
+    rng = np.random.default_rng(5)
+    st["w"] = 0.1 * rng.standard_normal((nc, nlev + 1))
+    st["w"][:, 0] = st["w"][:, -1] = 0
+    dt, beta = 180.0, p.vwind_impl_wgt
+    rho_ic, th_ic = v.interp_ic(st["rho"]), v.interp_ic(st["theta_v"])
+    thp_ic = v.interp_ic(st["theta_v"] - v.theta_ref)
+    div_m = 1e-6 * rng.standard_normal((nc, nlev))
+    div_t = 300 * div_m
+    ddt_w = 1e-3 * rng.standard_normal((nc, nlev + 1))
+    args = (st, rho_ic, th_ic, thp_ic, div_m, div_t, ddt_w, dt)
+    a, b = off.vertical_solve(*args), on.vertical_solve(*args)
+    rf = v.rayleigh_factor(dt, p)
+    assert np.max(rf) > 0.2 and np.sum(rf > 0) >= 5
+    assert np.max(np.abs(b["w"] * (1.0 + rf) - a["w"])) < 1e-15 * np.max(np.abs(a["w"])) * 4
+    damped = rf > 0
+    assert np.max(np.abs(b["w"][:, damped] - a["w"][:, damped])) > 1e-3 * np.max(np.abs(a["w"]))
+    # back-substitution with the damped w (written out independently)
+    pr = st["exner"] - v.exner_ref
+    zb = dt * (p.rd / p.cvd) * st["exner"] / (st["rho"] * st["theta_v"] * v.dz)
+    ric, rtic = np.nan_to_num(rho_ic), np.nan_to_num(rho_ic * th_ic)
+    w, wn = st["w"], b["w"]
+    for k in range(nlev):
+        gk = rtic[:, k] * w[:, k] - rtic[:, k + 1] * w[:, k + 1]
+        gkn = rtic[:, k] * wn[:, k] - rtic[:, k + 1] * wn[:, k + 1]
+        prs = pr[:, k] - zb[:, k] * (v.dz[k] * div_t[:, k] + (1 - beta) * gk)
+        assert np.max(np.abs(b["exner"][:, k] - v.exner_ref[k] - (prs - zb[:, k] * beta * gkn))) < 1e-15
+        fk = ric[:, k] * w[:, k] - ric[:, k + 1] * w[:, k + 1]
+        fkn = ric[:, k] * wn[:, k] - ric[:, k + 1] * wn[:, k + 1]
+        rs = st["rho"][:, k] - dt * div_m[:, k] - dt * (1 - beta) * fk / v.dz[k]
+        assert np.max(np.abs(b["rho"][:, k] - (rs - dt * beta * fkn / v.dz[k]))) < 1e-15
+
+
+# ---------------------------------------------------------------- A0 geometry
+def test_cell_to_vertex_kites_tile_cells_and_dual_cells():
+    """The cell->vertex weights are kite areas (vertex, edge midpoint, cell
+    centre, edge midpoint) normalised per vertex.  The kites around a vertex
+    tile its dual cell and the three kites of a cell tile the triangle (the
+    circumcentres of an edge's two cells and the edge midpoint lie on one great
+    circle), so weight x dual area summed over a cell's vertices is the cell's
+    area, to rounding."""
+    g = Dycore(make_grid(3), make_vct(4), DycoreParams()).g
+    cells = np.where(g.v2c_mask, g.v2c, 0)
+    contrib = np.where(g.v2c_mask, g.v2c_weight * g.dual_area[:, None], 0.0)
+    acc = np.zeros(g.nc)
+    np.add.at(acc, cells.ravel(), contrib.ravel())
+    assert np.max(np.abs(acc - g.cell_area) / g.cell_area) < 1e-12
+
+
+# ---------------------------------------------------------------- A10 diffusion terms
+def test_fourth_order_diffusion_is_a_scale_selective_filter():
+    """Smagorinsky part off: one application of the fourth-order operators of
+    vn and w removes about a quarter of the energy of white noise (measured
+    74-76 % kept at R2B2 and R2B3) and leaves smooth degree-1 fields unchanged
+    to 1e-4.  (The biharmonic of a smooth field is not compared with its
+    continuum value: the zeroth-order error of the first Laplacian, amplified by
+    1/h^2, dominates it on this grid.)"""
+    grid, z = make_grid(3), make_vct(30)
+    st = jw_type_state(grid, z, amp=0.0)
+    d = Dycore(grid, z, DycoreParams(hdiff_smag_fac=0.0, hdiff_temp=False))
+    g = d.g
+    rng = np.random.default_rng(11)
+    s = dict(st)
+    s["vn"] = rng.standard_normal((g.ne, 30))
+    s["w"] = rng.standard_normal((g.nc, 31))
+    s["w"][:, 0] = s["w"][:, 30] = 0.0
+    out = d.diffusion(s)
+    ev = lambda x: np.sum(g.edge_area[:, None] * x ** 2)   # noqa: E731
+    ec = lambda x: np.sum(g.cell_area[:, None] * x ** 2)   # noqa: E731
+    assert 0.6 < ev(out["vn"]) / ev(s["vn"]) < 0.9
+    assert 0.6 < ec(out["w"][:, 1:30]) / ec(s["w"][:, 1:30]) < 0.9
+    assert np.all(out["w"][:, 0] == 0.0) and np.all(out["w"][:, 30] == 0.0)
+    s["vn"] = np.repeat(rotation_vn(g)[:, None], 30, 1)
+    s["w"] = np.repeat((0.5 * g.C[:, 2])[:, None], 31, 1)
+    out = d.diffusion(s)
+    assert np.max(np.abs(out["vn"] - s["vn"])) < 1e-4 * U
+    assert np.max(np.abs(out["w"][:, 1:30] - s["w"][:, 1:30])) < 1e-4 * 0.5
+
+
+def test_smagorinsky_diffusion_of_degree_two_strain():
+    """Fourth-order part off: vn changes by dtime nu lap(vn) with nu =
+    c_s A_e |D|.  For the degree-2 strain fields |D| is known (above) and
+    lap(vn) = -6/a^2 vn, so the change is -dtime c_s A_e |D| 6/a^2 vn
+    (measured 10-18 % RMS, the error of the vector Laplacian on these fields)."""
+    grid, z = make_grid(3), make_vct(30)
+    st = jw_type_state(grid, z, amp=0.0)
+    d = Dycore(grid, z, DycoreParams(hdiff_k4=0.0, hdiff_w_k4=0.0, hdiff_temp=False))
+    g = d.g
+    E, n = g.E, g.normal
+    grad_chi = np.stack([E[:, 1], E[:, 0], np.zeros(g.ne)], 1)
+    M = np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    el, no = east(E), north(E)
+    h = lambda x, y: np.einsum("ei,ij,ej->e", x, M, y)   # noqa: E731
+    Dex = (U / A) * np.sqrt((h(el, el) - h(no, no)) ** 2 + 4.0 * h(el, no) ** 2)
+    for field in (grad_chi, np.cross(E, grad_chi)):
+        vn = U * np.sum(n * field, 1)
+        s = dict(st)
+        s["vn"] = np.repeat(vn[:, None], 30, 1)
+        out = d.diffusion(s)
+        ref = -d.p.dtime * d.p.hdiff_smag_fac * g.edge_area * Dex * 6.0 / A ** 2 * vn
+        assert rms_rel((out["vn"] - s["vn"])[:, 5] - ref, ref) < 0.3
+
+
+# ---------------------------------------------------------------- A5 history, diagnostics
+def test_initial_exner_history_is_the_perturbation_from_the_reference():
+    """A cold start takes the extrapolation history to be the present exner
+    perturbation: zero for the reference atmosphere, the added perturbation
+    otherwise."""
+    d = Dycore(make_grid(1), make_vct(30), DycoreParams())
+    nc = d.g.nc
+    ex_ref = np.tile(d.v.exner_ref, (nc, 1))
+    assert np.all(d.initial_exner_pr(ex_ref) == 0.0)
+    dp = 1e-3 * np.random.default_rng(2).standard_normal((nc, 30))
+    assert np.max(np.abs(d.initial_exner_pr(ex_ref + dp) - dp)) < 1e-15
+
+
+def test_t850_interpolates_linearly_in_log_pressure():
+    """T linear in ln p: interpolation in ln p to 850 hPa is exact, T850 =
+    T0 + G ln(0.85).  Where the whole column lies above 850 hPa (ground
+    pressure below it) the lowest level's temperature is returned."""
+    from oracle.diagnostics import temperature_850
+    d = Dycore(make_grid(0), make_vct(30), DycoreParams())
+    p = d.p
+    rng = np.random.default_rng(4)
+    nc, nlev = 6, 30
+    pres = np.sort(rng.uniform(2e4, 1.02e5, (nc, nlev)), axis=1)    # increasing downward
+    pres[:, -1] = np.linspace(1.0e5, 1.02e5, nc)
+    T0, G = 288.0, 40.0
+    temp = T0 + G * np.log(pres / p.p00)
+    exner = (pres / p.p00) ** (p.rd / p.cpd)
+    t850 = temperature_850(d, exner, temp / exner)
+    assert np.max(np.abs(t850 - (T0 + G * np.log(0.85)))) < 1e-9
+    high = pres * 0.8                                                 # ground at 800-816 hPa
+    ex_h = (high / p.p00) ** (p.rd / p.cpd)
+    t_h = T0 + G * np.log(high / p.p00)
+    assert np.allclose(temperature_850(d, ex_h, t_h / ex_h), t_h[:, -1], rtol=1e-14, atol=0)
+
+
+# ---------------------------------------------------------------- training loss
+def test_mse_value_and_gradient():
+    """Mean squared error by hand on a small case, zero at the target, and its
+    gradient against central differences."""
+    from oracle import mlp as omlp
+    val, grad = omlp.mse(np.array([[1.0, 2.0]]), np.array([[0.0, 4.0]]))
+    assert val == 2.5 and np.array_equal(grad, np.array([[1.0, -2.0]]))
+    rng = np.random.default_rng(8)
+    y, t = rng.standard_normal((4, 3)), rng.standard_normal((4, 3))
+    assert omlp.mse(t, t)[0] == 0.0
+    _, grad = omlp.mse(y, t)
+    h = 1e-6
+    for i in range(4):
+        for j in range(3):
+            yp, ym = y.copy(), y.copy()
+            yp[i, j] += h
+            ym[i, j] -= h
+            fd = (omlp.mse(yp, t)[0] - omlp.mse(ym, t)[0]) / (2 * h)
+            assert abs(fd - grad[i, j]) < 1e-8
+
+
+def test_adam_zero_gradient_and_constant_gradient_steps():
+    """Adam (Kingma & Ba 2015): a component whose gradient is zero does not move
+    (the epsilon in the denominator keeps 0/0 away); under a constant gradient
+    the bias-corrected moments equal g and g^2 at every step, so each step
+    moves every parameter by lr sign(g)."""
+    from oracle import mlp as omlp
+    p = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.3, -4.0, 1e-3, 0.0])
+    m, v = np.zeros(4), np.zeros(4)
+    q = p
+    for t in (1, 2, 3):
+        q, m, v = omlp.adam_step(q, g, m, v, t, lr=0.01)
+        assert np.all(np.isfinite(q)) and q[3] == 3.0
+        assert np.allclose(q[:3], p[:3] - 0.01 * t * np.sign(g[:3]), rtol=0, atol=1e-6)
+
+
+# ---------------------------------------------------------------- A5, A6, A9 (substep)
+def test_exner_extrapolation_is_exact_for_data_linear_in_time():
+    """pr at substeps n-1 and n, p0 and p0 + delta, extrapolated linearly to
+    n + gamma: p0 + (1 + gamma) delta; a steady pr stays itself."""
+    d = Dycore(make_grid(0), make_vct(10), DycoreParams())
+    gam = d.p.exner_exfac
+    rng = np.random.default_rng(12)
+    p0, delta = rng.standard_normal((80, 10)), 1e-3 * rng.standard_normal((80, 10))
+    got = d.extrapolate_exner(p0 + delta, p0)
+    assert np.max(np.abs(got - (p0 + (1.0 + gam) * delta))) < 1e-15
+    assert np.max(np.abs(d.extrapolate_exner(p0, p0) - p0)) < 1e-15
+
+
+def test_upwind_edge_value_is_the_field_at_the_back_trajectory_point(d3):
+    """For a field linear in space, X(x) = 1 + s x_1, the reconstruction from
+    the upwind cell with its gradient returns X at the point half a substep
+    upstream of the edge midpoint, a x_e - (dt/2)(vn n + vt t).  The velocities
+    are random in sign and size (every upwind choice occurs) and dt is long
+    enough that the displacement moves X by far more than the reconstruction
+    error on the sphere (measured 1.05 % of the displacement's effect at R2B3,
+    0.52 % at R2B4)."""
+    d, g = d3, d3.g
+    rng = np.random.default_rng(6)
+    K, dt, s = 4, 4000.0, 1e-3
+    vn = rng.uniform(-50.0, 50.0, (g.ne, K))
+    vt = rng.uniform(-50.0, 50.0, (g.ne, K))
+    X = 1.0 + s * A * np.repeat(g.C[:, 0:1], K, 1)
+    got = d.upwind_edge_values(X, vn, vt, dt)
+    dep = A * g.E[:, None, :] - 0.5 * dt * (vn[:, :, None] * g.normal[:, None, :]
+                                          + vt[:, :, None] * g.tangent[:, None, :])
+    exact = 1.0 + s * dep[:, :, 0]
+    effect = exact - (1.0 + s * A * g.E[:, 0:1])
+    assert rms_rel(got - exact, effect) < 0.05
+
+
+def test_substep_of_a_small_rotation_at_rest_is_an_inertial_oscillation():
+    """Resting reference atmosphere, a rigid rotation of 1 cm/s, a 3000 s
+    substep, no divergence damping: the pressure gradient is exactly zero and
+    the advective terms are second order in the amplitude, so vn evolves by the
+    Coriolis term alone.  Forward predictor vn* = vn + dt f vt, corrector
+    weights (1/4, 3/4) of the now and predicted tendencies: vn_new = vn +
+    dt f vt - (3/4)(dt f)^2 vn with the continuum vt (measured 1.1 % of the
+    second-order term at R2B3, 0.4 % at R2B4)."""
+    prm = DycoreParams(dtime=15000.0, ndyn_substeps=5, divdamp_fac=0.0)
+    d = Dycore(make_grid(3), make_vct(30), prm)
+    g = d.g
+    th, ex = d.reference_state()
+    exner, theta = np.tile(ex, (g.nc, 1)), np.tile(th, (g.nc, 1))
+    rho = prm.p00 * exner ** (prm.cvd / prm.rd) / (prm.rd * theta)
+    u = 0.01 * np.cross([0.0, 0.0, 1.0], g.E)
+    vn0, vt0 = np.sum(u * g.normal, 1), np.sum(u * g.tangent, 1)
+    st = dict(vn=np.repeat(vn0[:, None], 30, 1), w=np.zeros((g.nc, 31)), rho=rho, exner=exner,
+              theta_v=theta, exner_pr=d.initial_exner_pr(exner))
+    out = d.substep(st)
+    dtf = prm.dtime / prm.ndyn_substeps * d.f_e
+    assert abs(prm.wgt_nnow_vel + prm.wgt_nnew_vel - 1.0) < 1e-15
+    second = -prm.wgt_nnew_vel * dtf ** 2 * vn0
+    expect = vn0 + dtf * vt0 + second
+    for k in (0, 15, 29):
+        assert rms_rel(out["vn"][:, k] - expect, second) < 0.1, k
