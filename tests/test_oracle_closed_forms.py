@@ -433,3 +433,72 @@ def test_substep_of_a_small_rotation_at_rest_is_an_inertial_oscillation():
     expect = vn0 + dtf * vt0 + second
     for k in (0, 15, 29):
         assert rms_rel(out["vn"][:, k] - expect, second) < 0.1, k
+
+
+def _resting_state(d):
+    th, ex = d.reference_state()
+    g, p = d.g, d.p
+    exner, theta = np.tile(ex, (g.nc, 1)), np.tile(th, (g.nc, 1))
+    rho = p.p00 * exner ** (p.cvd / p.rd) / (p.rd * theta)
+    nlev = exner.shape[1]
+    return dict(vn=np.zeros((g.ne, nlev)), w=np.zeros((g.nc, nlev + 1)), rho=rho, exner=exner,
+                theta_v=theta, exner_pr=d.initial_exner_pr(exner))
+
+
+def test_corrector_time_averages_are_consistent():
+    """The corrector combines "now" and predicted values with weights that sum
+    to one, so a quantity that is the same at both times passes through
+    unchanged.  The velocity advection is replaced by one returning the same w
+    tendency C at both calls: the corrector's column solve receives C.  The
+    predictor's column solve is replaced by one that leaves rho and theta_v as
+    they are: the corrector's half-level rho and theta_v are those of "now"."""
+    d = Dycore(make_grid(1), make_vct(10), DycoreParams())
+    g, v = d.g, d.v
+    st = _resting_state(d)
+    C = 1e-3 * np.random.default_rng(13).standard_normal((g.nc, 11))
+    d.velocity_tendencies = lambda vn, w: (np.zeros_like(vn), C.copy(), np.zeros_like(vn))
+    calls = []
+    real_solve = Dycore.vertical_solve
+
+    def solve(now, rho_ic, theta_ic, thp_ic, div_m, div_t, ddt_w_expl, dt):
+        calls.append(dict(rho_ic=rho_ic, theta_ic=theta_ic, thp_ic=thp_ic, ddt_w=ddt_w_expl))
+        out = real_solve(d, now, rho_ic, theta_ic, thp_ic, div_m, div_t, ddt_w_expl, dt)
+        if len(calls) == 1:
+            out = dict(out, rho=now["rho"].copy(), theta_v=now["theta_v"].copy())
+        return out
+
+    d.vertical_solve = solve
+    d.substep(st)
+    assert len(calls) == 2
+    pred, corr = calls
+    k = slice(1, 10)
+    assert np.max(np.abs(corr["ddt_w"][:, k] - C[:, k])) < 1e-15 * np.max(np.abs(C))
+    for key in ("rho_ic", "theta_ic"):
+        assert np.max(np.abs(corr[key][:, k] - pred[key][:, k]) / np.abs(pred[key][:, k])) < 1e-15
+    assert np.max(np.abs(corr["thp_ic"][:, k])) < 1e-12 * np.max(v.theta_ref)
+
+
+def test_exner_history_carried_by_a_substep_is_the_cold_start_value():
+    """The history a substep hands to the next one is the exner perturbation at
+    its start, the same quantity a cold start takes."""
+    d = Dycore(make_grid(1), make_vct(10), DycoreParams())
+    st = _resting_state(d)
+    st["vn"] = np.random.default_rng(14).standard_normal(st["vn"].shape)
+    st["exner"] = st["exner"] * (1.0 + 1e-4 * np.random.default_rng(15).standard_normal(st["exner"].shape))
+    out = d.substep(st)
+    assert np.array_equal(out["exner_pr"], d.initial_exner_pr(st["exner"]))
+
+
+def test_divergence_damping_removes_divergence_from_noise():
+    """Fourth-order divergence damping in the corrector: one substep of white
+    noise in vn over a resting atmosphere ends with a smaller divergence than
+    the same substep without it (measured 85 % of the RMS divergence at R2B2
+    and R2B3)."""
+    rms = {}
+    for fac in (DycoreParams().divdamp_fac, 0.0):
+        d = Dycore(make_grid(2), make_vct(10), DycoreParams(divdamp_fac=fac))
+        st = _resting_state(d)
+        st["vn"] = np.random.default_rng(3).standard_normal(st["vn"].shape)
+        rms[fac] = np.sqrt(np.mean(d.div(d.substep(st)["vn"]) ** 2))
+    ratio = rms[DycoreParams().divdamp_fac] / rms[0.0]
+    assert 0.5 < ratio < 0.95, ratio
