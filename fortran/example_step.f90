@@ -4,7 +4,8 @@
 ! The grid and state are read from unformatted stream files written by the
 ! caller: grid.bin (n_cells, n_edges, n_verts, nlev as int32, then c2v, c2e,
 ! e2c, e2v, v2e, v2c as int32 and cell, vertex, edge coordinates as float64),
-! z_ifc.bin and state.bin (vn, w, rho, exner, theta_v, exner_pr).
+! z_ifc.bin and state.bin (vn, w, rho, exner, theta_v, exner_pr).  The state
+! after two steps is written to out.bin in the same layout as state.bin.
 program example_step
   use, intrinsic :: iso_c_binding
   use icon_dycore
@@ -41,6 +42,7 @@ program example_step
   call icon_dycore_params_default(params)
   params%dtime = 1800.0d0
   params%synchronous = 1
+  params%autotune = 0
   rc = icon_dycore_create(grid, nlev, z_ifc, params, dycore)
   if (rc /= ICON_OK) then
     print *, icon_last_error_string()
@@ -52,6 +54,9 @@ program example_step
     if (rc /= ICON_OK) stop 3
   end do
   print *, "stepped; vn(1, 1) =", vn(1, 1)
+  open(newunit=u, file="out.bin", access="stream", form="unformatted", status="replace")
+  write(u) vn, w, rho, exner, theta, exner_pr
+  close(u)
   rc = icon_dycore_destroy(dycore)
   rc = icon_grid_destroy(grid)
 end program example_step
