@@ -32,10 +32,10 @@ import sys
 from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PIN_SUITES = ["tests/test_probtest_cpu.py", "tests/test_oracle_closed_forms.py",
+PIN_SUITES = ["tests/test_probtest_cpu.py", "tests/test_oracle_closed_forms.py", "tests/test_oracle_terrain.py",
               "tests/test_oracle_corrector.py", "tests/test_oracle_pins.py"]
 ORACLE_FILES = ["oracle/dycore.py", "oracle/vertical.py", "oracle/geometry.py", "oracle/diagnostics.py",
-                "oracle/corrector.py", "oracle/mlp.py", "oracle/probtest.py"]
+                "oracle/corrector.py", "oracle/mlp.py", "oracle/probtest.py", "oracle/terrain.py"]
 
 
 def _is_site(node):
