@@ -87,10 +87,12 @@ typedef struct icon_grid_desc {
 } icon_grid_desc_t;
 
 /* Validate the tables (ranges, cell/edge/vertex consistency, unit vectors)
- * and build the grid.  Errors: ICON_ERR_ARG (NULL pointer, bad counts or
+ * and build the grid (Sec. 5.1: the RnBm grid; Sec. 4.3: the host model hands
+ * over its own tables, as ICON does with its grid).  Errors: ICON_ERR_ARG (NULL pointer, bad counts or
  * index_base), ICON_ERR_GRID (inconsistent tables), ICON_ERR_CUDA. */
 int icon_grid_create(const icon_grid_desc_t* desc, icon_grid_t** out);
-/* NULL-safe.  A grid must outlive every dycore created on it. */
+/* NULL-safe.  A grid must outlive every dycore created on it (Sec. 4.3: the
+ * host model owns the lifetime of what it creates through the interface). */
 int icon_grid_destroy(icon_grid_t* grid);
 
 /*
@@ -129,7 +131,8 @@ typedef struct icon_dycore_params {
                               0 = 4, or the autotuner's choice when autotune is set */
 } icon_dycore_params_t;
 
-/* Writes the defaults: dtime 1800, ndyn_substeps 5, beta 0.65, tendency
+/* Writes the defaults (Sec. 4.1 names the scheme's parts, not its values;
+ * these are ICON-like): dtime 1800, ndyn_substeps 5, beta 0.65, tendency
  * weights 0.25/0.75, rho/theta weights 0.6/0.4, exner_exfac 1/3,
  * divdamp_fac 0.0025, divflux_fac 0.07, Rayleigh off (coeff 0, height 20 km), Smagorinsky
  * 0.015, k4 = k4w = 1/288, hdiff_temp 1, ref_T0 250, FP64, graph on,
@@ -137,7 +140,9 @@ typedef struct icon_dycore_params {
 void icon_dycore_params_default(icon_dycore_params_t* p);
 
 /*
- * Create a dycore on a grid with nlev flat height levels.
+ * Create a dycore on a grid with nlev flat height levels (Sec. 4.1: the
+ * nonhydrostatic dynamical core; Sec. 4.3: created once at model set-up and
+ * stepped from the time loop).
  *   z_ifc [nlev+1]: HOST pointer, half-level heights in m, top first,
  *                   strictly decreasing, z_ifc[nlev] = 0 (flat ground).
  * Derives the vertical metrics and the reference state, uploads all
@@ -147,7 +152,8 @@ void icon_dycore_params_default(icon_dycore_params_t* p);
  */
 int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
                        const icon_dycore_params_t* params, icon_dycore_t** out);
-/* NULL-safe; frees library-owned memory only. */
+/* NULL-safe; frees library-owned memory only (Sec. 4.3: the state arrays
+ * stay the caller's). */
 int icon_dycore_destroy(icon_dycore_t* dycore);
 
 /*
@@ -395,7 +401,8 @@ int icon_dycore_step_learned(icon_dycore_t* reduced, icon_dycore_t* plain, icon_
                              double* norm);
 
 /*
- * Per-kernel profile of any sequence of calls on this thread: between
+ * Per-kernel profile of any sequence of calls on this thread (Sec. 4.3's
+ * execution profile of a substep, Sec. 5.1's synchronised timers): between
  * icon_profile_begin and icon_profile_end every kernel launch of the library is
  * bracketed by a CUDA event pair on its stream (steps run without their graph
  * meanwhile, so each kernel is seen).  icon_profile_end synchronises the device
