@@ -15,12 +15,16 @@ import numpy as np
 
 
 def surface_pressure(dycore, exner, theta_v):
+    """Diagnostics outside the step; a reading, the paper defines none (its results, Sec. 5, are ICON
+    runs)."""
     p, v = dycore.p, dycore.v
     ex_sfc = exner[:, -1] + p.grav * v.z_mc[-1] / (p.cpd * theta_v[:, -1])
     return p.p00 * ex_sfc ** (p.cpd / p.rd)
 
 
 def temperature_850(dycore, exner, theta_v, p_target=85000.0):
+    """Diagnostics outside the step; a reading, the paper defines none (its results, Sec. 5, are ICON
+    runs)."""
     p = dycore.p
     pres = p.p00 * exner ** (p.cpd / p.rd)
     temp = theta_v * exner
@@ -37,9 +41,13 @@ def temperature_850(dycore, exner, theta_v, p_target=85000.0):
 
 
 def total_mass(dycore, rho):
+    """Diagnostics outside the step; a reading, the paper defines none (its results, Sec. 5, are ICON
+    runs)."""
     return float(np.sum(dycore.g.cell_area[:, None] * rho * dycore.v.dz[None, :]))
 
 
 def area_rms(dycore, diff):
+    """Diagnostics outside the step; a reading, the paper defines none (its results, Sec. 5, are ICON
+    runs)."""
     a = dycore.g.cell_area
     return float(np.sqrt(np.sum(a * diff ** 2) / np.sum(a)))

@@ -25,7 +25,9 @@ from .vertical import VerticalGrid
 
 
 class Dycore:
+    """The dycore step of Sec. 4.1 (rows A0-A10) as an ICON-type reading."""
     def __init__(self, grid, z_ifc, params: DycoreParams = None):
+        """Row A0 set-up: geometry, vertical metrics, Coriolis parameter."""
         self.p = params if params is not None else DycoreParams()
         self.g = Geometry(grid, self.p.radius)
         self.v = VerticalGrid(z_ifc, self.p)
@@ -35,7 +37,8 @@ class Dycore:
     # discrete operators (row A0 readings, see geometry.py)
     # ------------------------------------------------------------------
     def div(self, F):
-        """Cell divergence (1/A_c) sum_e s_{c,e} l_e F_e of an edge field [ne, K]."""
+        """Cell divergence (1/A_c) sum_e s_{c,e} l_e F_e of an edge field [ne, K].
+        Row A0 operator, a reading of the ICON discretisation Sec. 4.1 cites."""
         g = self.g
         out = np.zeros((g.nc, F.shape[1]))
         for j in range(3):
@@ -44,7 +47,8 @@ class Dycore:
         return out / g.cell_area[:, None]
 
     def curl(self, F):
-        """Vertex circulation (1/A_v) sum_e t_{v,e} d_e F_e of an edge field."""
+        """Vertex circulation (1/A_v) sum_e t_{v,e} d_e F_e of an edge field.
+        Row A0 operator, a reading of the ICON discretisation Sec. 4.1 cites."""
         g = self.g
         out = np.zeros((g.nv, F.shape[1]))
         for j in range(6):
@@ -53,19 +57,22 @@ class Dycore:
         return out / g.dual_area[:, None]
 
     def grad_n(self, X):
-        """Edge-normal gradient (X_c1 - X_c0) / d_e of a cell field."""
+        """Edge-normal gradient (X_c1 - X_c0) / d_e of a cell field.
+        Row A0 operator, a reading of the ICON discretisation Sec. 4.1 cites."""
         g = self.g
         return (X[g.e2c[:, 1]] - X[g.e2c[:, 0]]) / g.dual_length[:, None]
 
     def grad_t(self, Y):
         """Edge-tangential gradient of a vertex field: (Y at the vertex t_e points to
-        minus Y at the other) / l_e."""
+        minus Y at the other) / l_e.
+        Row A0 operator, a reading of the ICON discretisation Sec. 4.1 cites."""
         g = self.g
         return (g.e2v_sign[:, 0:1] * Y[g.e2v[:, 0]] + g.e2v_sign[:, 1:2] * Y[g.e2v[:, 1]]) \
             / g.edge_length[:, None]
 
     def edge_to_cell(self, F):
-        """sum_e q_{c,e} F_e (area-weighted edge->cell average)."""
+        """sum_e q_{c,e} F_e (area-weighted edge->cell average).
+        Row A0 operator, a reading of the ICON discretisation Sec. 4.1 cites."""
         g = self.g
         out = np.zeros((g.nc, F.shape[1]))
         for j in range(3):
@@ -73,6 +80,8 @@ class Dycore:
         return out
 
     def cell_to_vert(self, X):
+        """Kite-area weighted cell->vertex average; row A0 operator, a reading of the ICON
+        discretisation Sec. 4.1 cites."""
         g = self.g
         out = np.zeros((g.nv, X.shape[1]))
         for j in range(6):
@@ -81,7 +90,8 @@ class Dycore:
         return out
 
     def lap_cell(self, X):
-        """Cell Laplacian (1/A_c) sum_e l_e (X_nbr - X_c) / d_e."""
+        """Cell Laplacian (1/A_c) sum_e l_e (X_nbr - X_c) / d_e.
+        Row A0 operator, a reading of the ICON discretisation Sec. 4.1 cites."""
         g = self.g
         out = np.zeros_like(X)
         for j in range(3):
@@ -90,12 +100,14 @@ class Dycore:
         return out / g.cell_area[:, None]
 
     def lap_vec(self, F):
-        """Vector Laplacian of an edge-normal field: grad_n(div F) - grad_t(curl F)."""
+        """Vector Laplacian of an edge-normal field: grad_n(div F) - grad_t(curl F).
+        Rows A8/A10 (diffusion), a reading of the ICON discretisation Sec. 4.1 cites."""
         return self.grad_n(self.div(F)) - self.grad_t(self.curl(F))
 
     def perot_cell(self, vn):
         """Cell velocity vector [nc, K, 3]: (1/A_c) sum_e s l_e vn_e (x_e - x_c),
-        projected on the tangent plane at the cell centre (Perot reconstruction)."""
+        projected on the tangent plane at the cell centre (Perot reconstruction).
+        Row A1 reconstruction, a reading (ICON's own is not given, Sec. 4.1)."""
         g = self.g
         u = np.zeros((g.nc, vn.shape[1], 3))
         for j in range(3):
@@ -108,7 +120,8 @@ class Dycore:
     def vertex_velocity(self, vn):
         """Vertex velocity vector [nv, K, 3] from the dual-cell circulation:
         u_v = r_v x (1/A_v) sum_e t_{v,e} d_e vn_e (m_e - x_v), m_e the dual-edge
-        midpoint; exact for uniform flow on a plane."""
+        midpoint; exact for uniform flow on a plane.
+        Row A10 (Smagorinsky deformation), a reading (Sec. 4.1)."""
         g = self.g
         s = np.zeros((g.nv, vn.shape[1], 3))
         for j in range(6):
@@ -126,7 +139,8 @@ class Dycore:
         X_e = (r1 X_c0 + r0 X_c1)/(r0 + r1), r_i = arc(x_ci, x_e).  Subtracting X_c
         changes nothing on a plane (sum_e s l n_e = 0 around a closed polygon) and
         makes the gradient of a constant exactly zero on the sphere, where the
-        edge normals lie in different tangent planes."""
+        edge normals lie in different tangent planes.
+        Row A5/A6 (upwind reconstruction), a reading (Sec. 4.1)."""
         g = self.g
         out = np.zeros(X.shape + (3,))
         for j in range(3):
@@ -205,7 +219,7 @@ class Dycore:
         rho and pr follow by back-substitution.  theta_v comes from the
         linearised equation of state,
           theta_new = theta (rho / rho_new) (1 + (c_vd/R_d)(pr_new - pr) / exner).
-        """
+        Row A7, Sec. 4.1: the vertically implicit solver of solve_nonhydro."""
         p, v = self.p, self.v
         nlev = v.nlev
         beta = p.vwind_impl_wgt
@@ -278,7 +292,8 @@ class Dycore:
     def extrapolate_exner(self, pr, pr_old):
         """Exner perturbation extrapolated linearly in time from the substeps
         n-1 and n to n + gamma, gamma = exner_exfac:
-        (1 + gamma) pr - gamma pr_old."""
+        (1 + gamma) pr - gamma pr_old.
+        Row A5, a reading of the predictor in Sec. 4.1."""
         gam = self.p.exner_exfac
         return (1.0 + gam) * pr - gam * pr_old
 
@@ -286,7 +301,8 @@ class Dycore:
         """Edge values [ne, K] of the cell field X taken from the upwind cell
         (c0 where vn >= 0, else c1) at the back-trajectory point of the edge
         midpoint over dt/2: X_up + grad X_up . (a x_e - (dt/2) v_e - a x_up),
-        v_e = vn n + vt t, grad the Green-Gauss cell gradient."""
+        v_e = vn n + vt t, grad the Green-Gauss cell gradient.
+        Row A6, a reading of the predictor in Sec. 4.1."""
         g = self.g
         c0, c1 = g.e2c[:, 0], g.e2c[:, 1]
         grad = self.grad_cell(X)
@@ -302,7 +318,8 @@ class Dycore:
     # ------------------------------------------------------------------
     def substep(self, st):
         """Advance the state dict by one substep dt_s = dtime / ndyn_substeps.
-        Returns the new state (vn, w, rho, exner, theta_v, exner_pr)."""
+        Returns the new state (vn, w, rho, exner, theta_v, exner_pr).
+        Rows A5-A9 and A7, Sec. 4.1: one predictor-corrector substep."""
         p, g, v = self.p, self.g, self.v
         dt = p.dtime / p.ndyn_substeps
         vn, w = st["vn"], st["w"]
@@ -357,7 +374,8 @@ class Dycore:
     # ------------------------------------------------------------------
     def smagorinsky(self, vn):
         """nu_e = c_s A_e |D|, |D| = sqrt(tension^2 + shear^2) from the velocity
-        vectors at the four vertices of the edge's diamond."""
+        vectors at the four vertices of the edge's diamond.
+        Row A10, Sec. 4.1 (horizontal diffusion), a reading."""
         g = self.g
         uv = self.vertex_velocity(vn)
         sgn0 = g.e2v_sign[:, 0]
@@ -379,7 +397,7 @@ class Dycore:
           w  <- w - k4w A_c^2 lapc(lapc(w))          (interior half levels)
           theta <- theta + dt (1/A_c) sum_e l_e nu_e (theta_nbr - theta_c)/d_e
           exner <- exner (1 + (R_d/c_vd)(theta_new - theta)/theta)
-        """
+        Row A10, Sec. 4.1 (nh_diffusion), a reading."""
         p, g, v = self.p, self.g, self.v
         dt = p.dtime
         vn, w, theta, exner = st["vn"], st["w"], st["theta_v"], st["exner"]
@@ -407,22 +425,26 @@ class Dycore:
 
     # ------------------------------------------------------------------
     def step(self, st):
-        """One full time step: ndyn_substeps substeps, then diffusion."""
+        """One full time step: ndyn_substeps substeps, then diffusion.
+        Sec. 4.1 and Sec. 5.1: ndyn_substeps substeps per diffusion call."""
         for _ in range(self.p.ndyn_substeps):
             st = self.substep(st)
         return self.diffusion(st)
 
     def initial_exner_pr(self, exner):
-        """exner - exner_ref: the extrapolation history at a cold start."""
+        """exner - exner_ref: the extrapolation history at a cold start.
+        Row A5, a reading."""
         return exner - self.v.exner_ref[None, :]
 
     def reference_state(self):
+        """Row A0: the reference profiles (theta_ref, exner_ref), a reading."""
         return self.v.theta_ref.copy(), self.v.exner_ref.copy()
 
 
 def thomas(a, b, c, r):
     """Solve a_k x_{k-1} + b_k x_k + c_k x_{k+1} = r_k (k = 0..n-1, a_0 and c_{n-1}
-    unused) per row, forward elimination then back-substitution, no pivoting."""
+    unused) per row, forward elimination then back-substitution, no pivoting.
+    Row A7: the tridiagonal solve of the vertically implicit scheme (Sec. 4.1), Thomas algorithm."""
     n = b.shape[1]
     cp = np.zeros_like(b)
     rp = np.zeros_like(b)

@@ -11,14 +11,20 @@ from scipy.special import erf
 
 
 def gelu(u):
+    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     return 0.5 * u * (1.0 + erf(u / np.sqrt(2.0)))
 
 
 def gelu_grad(u):
+    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     return 0.5 * (1.0 + erf(u / np.sqrt(2.0))) + u * np.exp(-0.5 * u * u) / np.sqrt(2.0 * np.pi)
 
 
 def unpack(params, n_in, n_hid, n_out):
+    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     shapes = [(n_hid, n_in), (n_hid,), (n_hid, n_hid), (n_hid,), (n_out, n_hid), (n_out,)]
     out, off = [], 0
     for s in shapes:
@@ -29,6 +35,8 @@ def unpack(params, n_in, n_hid, n_out):
 
 
 def forward(params, x, n_in, n_hid, n_out):
+    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     W1, b1, W2, b2, W3, b3 = unpack(params, n_in, n_hid, n_out)
     z1 = x @ W1.T + b1
     h1 = gelu(z1)
@@ -39,7 +47,9 @@ def forward(params, x, n_in, n_hid, n_out):
 
 
 def backward(params, cache, dy, n_in, n_hid, n_out):
-    """Gradients of all parameters (flat, library layout) for dL/dy."""
+    """Gradients of all parameters (flat, library layout) for dL/dy.
+    Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     W1, b1, W2, b2, W3, b3 = unpack(params, n_in, n_hid, n_out)
     x, z1, h1, z2, h2 = cache
     gW3 = dy.T @ h2
@@ -54,13 +64,17 @@ def backward(params, cache, dy, n_in, n_hid, n_out):
 
 
 def mse(y, t):
-    """Mean squared error and its gradient with respect to y."""
+    """Mean squared error and its gradient with respect to y.
+    Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     d = y - t
     return float(np.mean(d * d)), 2.0 * d / d.size
 
 
 def adam_step(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
-    """One Adam update (step number t >= 1); returns new params, m, v."""
+    """One Adam update (step number t >= 1); returns new params, m, v.
+    Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
+    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
     m = b1 * m + (1 - b1) * grads
     v = b2 * v + (1 - b2) * grads * grads
     mh = m / (1 - b1 ** t)

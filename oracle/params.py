@@ -12,6 +12,7 @@ from dataclasses import dataclass
 
 @dataclass
 class DycoreParams:
+    """Parameters of the step (Sec. 4.1 names their roles, not their values; ICON-like readings)."""
     dtime: float = 1800.0
     ndyn_substeps: int = 5
     # physical constants (dry, shallow atmosphere)
@@ -44,4 +45,5 @@ class DycoreParams:
 
     @property
     def cvd(self):
+        """Parameters of the step (Sec. 4.1 names their roles, not their values; ICON-like readings)."""
         return self.cpd - self.rd

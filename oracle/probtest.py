@@ -27,7 +27,8 @@ FIELDS = ("vn", "w", "rho", "exner", "theta_v")
 
 
 def differences(a, b, dycore):
-    """Per-field relative max-norm difference of state a from the control b."""
+    """Per-field relative max-norm difference of state a from the control b.
+    Sec. 4.4: probtest-style ensemble verification, a reading."""
     th_ref, ex_ref = dycore.reference_state()
     out = {}
     for k in FIELDS:
@@ -42,7 +43,8 @@ def differences(a, b, dycore):
 
 
 def control_run(dycore, st0, nsteps):
-    """States after 1..nsteps steps of the unperturbed run."""
+    """States after 1..nsteps steps of the unperturbed run.
+    Sec. 4.4: probtest-style ensemble verification, a reading."""
     out, st = [], st0
     for _ in range(nsteps):
         st = dycore.step(st)
@@ -51,7 +53,8 @@ def control_run(dycore, st0, nsteps):
 
 
 def ensemble_spread(dycore, st0, eps, seeds, nsteps, control=None):
-    """spread[field][n] = max over members of differences(member_n, control_n)."""
+    """spread[field][n] = max over members of differences(member_n, control_n).
+    Sec. 4.4: probtest-style ensemble verification, a reading."""
     if control is None:
         control = control_run(dycore, st0, nsteps)
     spread = {k: [0.0] * nsteps for k in FIELDS}

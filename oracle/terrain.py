@@ -53,6 +53,7 @@ class TerrainColumns:
     cell arrays [nc, ...], edge arrays [ne, ...]."""
 
     def __init__(self, z_ifc, g: Geometry, p: DycoreParams):
+        """Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         z = np.ascontiguousarray(z_ifc, dtype=np.float64)
         nc = z.shape[0]
         self.nlev = nlev = z.shape[1] - 1
@@ -89,21 +90,24 @@ class TerrainColumns:
         self.ddxn_mc = (self.z_mc[c1] - self.z_mc[c0]) / g.dual_length[:, None]
 
     def interp_ic(self, x):
-        """Interior half-level values [nc, nlev+1] of a cell field; ends NaN."""
+        """Interior half-level values [nc, nlev+1] of a cell field; ends NaN.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         out = np.full((x.shape[0], self.nlev + 1), np.nan)
         for k in range(1, self.nlev):
             out[:, k] = self.wgt[:, k] * x[:, k - 1] + (1.0 - self.wgt[:, k]) * x[:, k]
         return out
 
     def interp_ic_e(self, x):
-        """Interior half-level values [ne, nlev+1] of an edge field; ends NaN."""
+        """Interior half-level values [ne, nlev+1] of an edge field; ends NaN.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         out = np.full((x.shape[0], self.nlev + 1), np.nan)
         for k in range(1, self.nlev):
             out[:, k] = self.wgt_e[:, k] * x[:, k - 1] + (1.0 - self.wgt_e[:, k]) * x[:, k]
         return out
 
     def rayleigh_factor(self, dt, p):
-        """dt tau^-1 sin^2(pi/2 (z - z_d)/(z_top - z_d)) at every column's half levels."""
+        """dt tau^-1 sin^2(pi/2 (z - z_d)/(z_top - z_d)) at every column's half levels.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         z = self.z_ifc
         f = np.zeros_like(z)
         if p.rayleigh_coeff > 0.0:
@@ -114,9 +118,11 @@ class TerrainColumns:
 
 
 class TerrainDycore(Dycore):
-    """The oracle dycore over half-level heights z_ifc [nc, nlev+1]."""
+    """The oracle dycore over half-level heights z_ifc [nc, nlev+1].
+    Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
 
     def __init__(self, grid, z_ifc, params: DycoreParams = None):
+        """Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         self.p = params if params is not None else DycoreParams()
         self.g = Geometry(grid, self.p.radius)
         self.v = TerrainColumns(z_ifc, self.g, self.p)
@@ -135,7 +141,8 @@ class TerrainDycore(Dycore):
     # ---------------------------------------------------------------- A1-A4
     def half_level_winds(self, vn, vt):
         """vn and vt at half levels [ne, nlev+1]: interpolated inside, the top
-        and lowest full-level values at the top and the ground."""
+        and lowest full-level values at the top and the ground.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         nlev = self.v.nlev
         vn_ie, vt_ie = self.v.interp_ic_e(vn), self.v.interp_ic_e(vt)
         vn_ie[:, 0], vn_ie[:, nlev] = vn[:, 0], vn[:, nlev - 1]
@@ -143,19 +150,22 @@ class TerrainDycore(Dycore):
         return vn_ie, vt_ie
 
     def tangential_wind(self, vn):
+        """Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         g = self.g
         uc = self.perot_cell(vn)
         return 0.5 * np.einsum("ekx,ex->ek", uc[g.e2c[:, 0]] + uc[g.e2c[:, 1]], g.tangent)
 
     def w_concorr(self, vn):
         """Contravariant correction [nc, nlev+1] of the winds vn: the vertical
-        velocity of a parcel that follows the coordinate surface."""
+        velocity of a parcel that follows the coordinate surface.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         vn_ie, vt_ie = self.half_level_winds(vn, self.tangential_wind(vn))
         return self.edge_to_cell(vn_ie * self.v.ddxn_ifc + vt_ie * self.ddxt_ifc)
 
     def velocity_tendencies(self, vn, w):
         """As the flat oracle, with the contravariant velocity w - w_concorr as
-        the advecting vertical velocity and edge layer thicknesses."""
+        the advecting vertical velocity and edge layer thicknesses.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         g, v = self.g, self.v
         nlev = v.nlev
         c0, c1 = g.e2c[:, 0], g.e2c[:, 1]
@@ -186,7 +196,8 @@ class TerrainDycore(Dycore):
 
     # ---------------------------------------------------------------- A6
     def horizontal_pressure_gradient(self, pr_ex, theta_e):
-        """cpd theta_e [d pr/dn - (dz_mc/dn) (d pr/dz)_e] along the true horizontal."""
+        """cpd theta_e [d pr/dn - (dz_mc/dn) (d pr/dz)_e] along the true horizontal.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         g, v = self.g, self.v
         zm = v.z_mc
         dpdz = np.empty_like(pr_ex)
@@ -197,13 +208,15 @@ class TerrainDycore(Dycore):
         return self.p.cpd * theta_e * (self.grad_n(pr_ex) - v.ddxn_mc * dpdz_e)
 
     def layer_div(self, F):
-        """Flux divergence per unit volume of a layer: (1/dz_c) div(F dz_e)."""
+        """Flux divergence per unit volume of a layer: (1/dz_c) div(F dz_e).
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         return self.div(F * self.v.dz_e) / self.v.dz
 
     # ---------------------------------------------------------------- A7
     def vertical_solve(self, now, rho_ic, theta_ic, thp_ic, div_m, div_t, ddt_w_expl, dt, w_concorr=None):
         """The flat column solve in the contravariant velocity w_con = w - w_concorr
-        (zero at the top and the ground), with per-column metrics."""
+        (zero at the top and the ground), with per-column metrics.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         p, v = self.p, self.v
         nlev = v.nlev
         beta = p.vwind_impl_wgt
@@ -251,7 +264,8 @@ class TerrainDycore(Dycore):
 
     # ---------------------------------------------------------------- substep
     def substep(self, st):
-        """The flat substep (predictor, corrector) with the terrain terms above."""
+        """The flat substep (predictor, corrector) with the terrain terms above.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         p, v = self.p, self.v
         dt = p.dtime / p.ndyn_substeps
         vn, w = st["vn"], st["w"]
@@ -297,17 +311,21 @@ class TerrainDycore(Dycore):
     # ---------------------------------------------------------------- A10
     def diffusion(self, st):
         """The flat diffusion along model levels; the ground value of w (the
-        kinematic condition) is left as it is."""
+        kinematic condition) is left as it is.
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         out = super().diffusion(st)
         out["w"][:, self.v.nlev] = st["w"][:, self.v.nlev]
         return out
 
     def initial_exner_pr(self, exner):
+        """Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         return exner - self.v.exner_ref
 
     def reference_state(self):
-        """Per-column reference profiles (theta_ref, exner_ref) [nc, nlev]."""
+        """Per-column reference profiles (theta_ref, exner_ref) [nc, nlev].
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         return self.v.theta_ref.copy(), self.v.exner_ref.copy()
 
     def total_mass(self, rho):
+        """Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         return float(np.sum(self.g.cell_area[:, None] * rho * self.v.dz))

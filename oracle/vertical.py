@@ -24,7 +24,9 @@ import numpy as np
 
 
 class VerticalGrid:
+    """Row A0: vertical metrics and reference state, readings stated in this module's docstring."""
     def __init__(self, z_ifc, params):
+        """Row A0: vertical metrics and reference state, readings stated in this module's docstring."""
         z_ifc = np.asarray(z_ifc, dtype=np.float64)
         self.nlev = nlev = z_ifc.size - 1
         self.z_ifc = z_ifc
@@ -50,14 +52,16 @@ class VerticalGrid:
             self.dexner_ref_ic[k] = (self.exner_ref[k - 1] - self.exner_ref[k]) / self.dzh[k]
 
     def interp_ic(self, x):
-        """Interior half-level values [..., nlev+1] of full-level x [..., nlev]; ends NaN."""
+        """Interior half-level values [..., nlev+1] of full-level x [..., nlev]; ends NaN.
+        Row A0: vertical metrics and reference state, readings stated in this module's docstring."""
         out = np.full(x.shape[:-1] + (self.nlev + 1,), np.nan)
         for k in range(1, self.nlev):
             out[..., k] = self.wgt[k] * x[..., k - 1] + (1.0 - self.wgt[k]) * x[..., k]
         return out
 
     def rayleigh_factor(self, dt, params):
-        """dt * tau^-1 * sin^2(...) at half levels (0 below damp_height and when off)."""
+        """dt * tau^-1 * sin^2(...) at half levels (0 below damp_height and when off).
+        Row A0: vertical metrics and reference state, readings stated in this module's docstring."""
         p = params
         z = self.z_ifc
         top = z[0]
