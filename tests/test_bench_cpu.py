@@ -43,3 +43,69 @@ def test_traffic_constants_only_for_the_captured_grid():
     finally:
         B.WORKLOAD.clear()
         B.WORKLOAD.update(saved)
+
+
+def test_roofline_takes_the_longest_family_and_counts_its_flops():
+    """The column solve's predictor and corrector form one family; with the
+    longest summed time it is the one reported, at (86 + 94 flops per
+    column-level) x columns x levels x launches over its summed time."""
+    B = _bench()
+    nc, ne, nv = _sizes(6)
+    nlev = 90
+    prof = {"sn_column_pred": (5, 10.0), "sn_column_corr": (5, 12.0), "va_edge_tend": (10, 15.0)}
+    r = B.roofline(prof, nc, ne, nv, nlev)
+    flops = (86 + 94) * nc * nlev * 5
+    assert r["kernel"] == "sn_column" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - flops / 0.022 / 1e12) < 1e-12 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / B.FP64_PEAK_TFLOPS) < 1e-15
+    # a larger edge-tendency time moves the report to that kernel: 38 flops per edge-half-level
+    prof["va_edge_tend"] = (10, 30.0)
+    r = B.roofline(prof, nc, ne, nv, nlev)
+    assert r["kernel"] == "va_edge_tend" and r["traffic"] is None
+    assert abs(r["achieved"] - 38 * ne * (nlev + 1) * 10 / 0.030 / 1e12) < 1e-12 * r["achieved"]
+
+
+def test_kernel_table_per_step_and_shares():
+    B = _bench()
+    t = B.kernel_table({"a": (10, 30.0), "b": (4, 10.0)}, 2)
+    assert list(t) == ["a", "b"]
+    assert t["a"] == {"launches_per_step": 5, "ms_per_step": 15.0, "share": 0.75}
+    assert t["b"] == {"launches_per_step": 2, "ms_per_step": 5.0, "share": 0.25}
+
+
+def test_cpu_sample_scaled_to_a_full_step():
+    """A sample of one substep and one diffusion on 1/16 of the columns: a
+    full step is 16 x (ndyn substeps + diffusion)."""
+    B = _bench()
+    assert abs(B.sample_to_steps_per_s(1.6, 0.4, 16) - 1.0 / (16 * (5 * 1.6 + 0.4))) < 1e-15
+
+
+def test_dram_arithmetic_on_the_captured_grid():
+    B = _bench()
+    if B.sources_sha256() != B.STEP_DRAM["sources_sha256"]:
+        import pytest
+        pytest.skip("kernel sources changed since the DRAM capture")
+    r = B.dram_measured("fp64", 100.0)
+    b = B.STEP_DRAM["bytes_per_step"]["fp64"]
+    assert abs(r["achieved_gbs"] - b / 0.1 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved_gbs"] / 6663.9) < 1e-15
+    nc, ne, nv = _sizes(6)
+    stage = B.stage_bytes_per_step("fp64", nc, ne, nv, 90, 5)
+    assert r["stage_bytes_per_step"] == stage and abs(r["amplification"] - b / stage) < 1e-15
+    assert B.column_traffic() == B.COLUMN_TRAFFIC["bytes_per_launch"]
+
+
+def test_state_and_compulsory_bytes_are_those_of_the_state_arrays():
+    """The six prognostic arrays (vn, w, rho, exner, theta_v, exner_pr) as the
+    inputs give them: state_bytes is their total size, and the compulsory
+    traffic reads and writes them once per substep and once for diffusion."""
+    B = _bench()
+    import numpy as np
+    from icon_inputs import make_grid, make_vct, jw_type_state
+    grid, z = make_grid(1), make_vct(12)
+    st = jw_type_state(grid, z)
+    st["exner_pr"] = np.zeros_like(st["exner"])
+    total = sum(np.ascontiguousarray(st[k], dtype=np.float64).nbytes
+                for k in ("vn", "w", "rho", "exner", "theta_v", "exner_pr"))
+    assert B.state_bytes(grid.n_cells, grid.n_edges, 12) == total
+    assert B.compulsory_bytes_per_step(grid.n_cells, grid.n_edges, 12, 5) == 2 * 6 * total
