@@ -106,6 +106,14 @@ std::string build_host_grid(const icon_grid_desc_t* d, HostGrid* g) {
       if (g->e2c[2 * e] != c && g->e2c[2 * e + 1] != c)
         return fmt("cell %ld lists edge %ld which does not list it back", c, e);
     }
+  // vertex degrees from the edges' own vertex lists: every vertex row must
+  // hold each of its edges exactly once (a repeated entry would drop another
+  // edge from the vertex's circulation and average)
+  std::vector<int> degree(nv, 0);
+  for (int e = 0; e < ne; ++e) {
+    ++degree[g->e2v[2 * e]];
+    ++degree[g->e2v[2 * e + 1]];
+  }
   for (int v = 0; v < nv; ++v) {
     int ne_v = 0, nc_v = 0;
     for (int j = 0; j < 6; ++j) {
@@ -114,16 +122,21 @@ std::string build_host_grid(const icon_grid_desc_t* d, HostGrid* g) {
         if (!in(e, ne)) return fmt("v2e[%ld][%ld] out of range", v, j);
         if (g->e2v[2 * e] != v && g->e2v[2 * e + 1] != v)
           return fmt("vertex %ld lists edge %ld which does not list it back", v, e);
+        for (int i = 0; i < j; ++i)
+          if (g->v2e[6 * v + i] == e) return fmt("vertex %ld lists edge %ld twice", v, e);
         ++ne_v;
       }
       if (c != -1) {
         if (!in(c, nc)) return fmt("v2c[%ld][%ld] out of range", v, j);
         if (g->c2v[3 * c] != v && g->c2v[3 * c + 1] != v && g->c2v[3 * c + 2] != v)
           return fmt("vertex %ld lists cell %ld which does not list it back", v, c);
+        for (int i = 0; i < j; ++i)
+          if (g->v2c[6 * v + i] == c) return fmt("vertex %ld lists cell %ld twice", v, c);
         ++nc_v;
       }
     }
     if (ne_v < 3 || nc_v != ne_v) return fmt("vertex %ld has %ld edges and %ld cells", v, ne_v, nc_v);
+    if (ne_v != degree[v]) return fmt("vertex %ld lists %ld edges but %ld edges end at it", v, ne_v, degree[v]);
   }
   auto unit_ok = [](const std::vector<double>& xyz) {
     for (size_t i = 0; i < xyz.size() / 3; ++i) {

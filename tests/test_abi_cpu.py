@@ -92,3 +92,46 @@ def test_null_arguments(built_lib):
     assert P.icon_dycore_destroy(None) == P.ICON_OK
     assert P.icon_dycore_step(None, None) == P.ICON_ERR_ARG
     assert P.icon_dycore_synchronize(None) == P.ICON_ERR_ARG
+
+
+def test_grid_validation_refuses_random_single_corruptions(built_lib):
+    """Seeded sweep: one entry of one connectivity table set to another value
+    (an in-range index, the pad value, or an out-of-range index), or one
+    coordinate moved off the unit sphere.  Every such grid is refused on the
+    host (ICON_ERR_GRID or ICON_ERR_ARG): none passes validation, which on this
+    machine would surface as ICON_ERR_CUDA when the device is needed.  (A
+    vertex row listing one of its edges or cells twice, dropping another, once
+    passed: rows are now checked for repeats and against the vertex degree.)"""
+    import paper_2608_21150_gb300 as P
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only sweep")
+    rng = np.random.default_rng(2024)
+    base = make_grid(1)
+    counts = {"c2v": base.n_verts, "c2e": base.n_edges, "e2c": base.n_cells, "e2v": base.n_verts,
+              "v2e": base.n_edges, "v2c": base.n_cells}
+    refused = 0
+    for trial in range(600):
+        g = make_grid(1)
+        if trial % 8 == 7:
+            arr = (g.cell_xyz, g.vert_xyz, g.edge_xyz)[trial % 3]
+            arr[rng.integers(arr.shape[0])] *= 1.0 + rng.uniform(0.01, 0.5)
+        else:
+            name = list(counts)[trial % 6]
+            tab = getattr(g, name)
+            i, j = rng.integers(tab.shape[0]), rng.integers(tab.shape[1])
+            old = int(tab[i, j])
+            kind = rng.integers(3)
+            if kind == 0:
+                new = int(rng.integers(counts[name]))
+                if new == old:
+                    new = (new + 1) % counts[name]
+            elif kind == 1:
+                new = -1 if old != -1 else 0
+            else:
+                new = counts[name] + int(rng.integers(1, 1000))
+            tab[i, j] = new
+        code, msg = _grid_err(P, g)
+        assert code in (P.ICON_ERR_GRID, P.ICON_ERR_ARG), (trial, code, msg)
+        refused += 1
+    assert refused == 600
