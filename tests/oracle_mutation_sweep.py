@@ -15,6 +15,7 @@ _build/oracle_mutants/ (git-ignored) with `pytest -x`, several in parallel.
 
     python tests/oracle_mutation_sweep.py [--files oracle/dycore.py,...]
         [--jobs 8] [--out _build/oracle_mutants.jsonl] [--rerun previous.jsonl]
+        [--suites tests/test_a.py,tests/test_b.py]
 
 Writes one JSON line per mutant (file, kind, line, function, killed, first
 failing test) and prints the survivors.  --rerun takes only the survivors of an
@@ -119,7 +120,9 @@ def main():
     ap.add_argument("--jobs", type=int, default=8)
     ap.add_argument("--out", default=os.path.join(ROOT, "_build", "oracle_mutants.jsonl"))
     ap.add_argument("--rerun", default=None, help="only the survivors of this earlier output")
+    ap.add_argument("--suites", default=",".join(PIN_SUITES), help="test files run against each mutant")
     args = ap.parse_args()
+    suites = args.suites.split(",")
     workdir = os.path.join(ROOT, "_build", "oracle_mutants")
     trees, jobs = {}, []
     for rel in args.files.split(","):
@@ -134,7 +137,7 @@ def main():
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     killed = 0
     with open(args.out, "w") as out, ThreadPoolExecutor(args.jobs) as ex:
-        futs = [ex.submit(_run_one, i, rel, trees[rel], site, workdir, PIN_SUITES) for i, (rel, site) in enumerate(jobs)]
+        futs = [ex.submit(_run_one, i, rel, trees[rel], site, workdir, suites) for i, (rel, site) in enumerate(jobs)]
         for f in futs:
             r = f.result()
             out.write(json.dumps(r) + "\n")

@@ -85,3 +85,31 @@ def test_perturbation_centre_is_seeded():
     s0, s1 = jw_type_state(g, z, seed=0), jw_type_state(g, z, seed=0, amp=0.0)
     du = s0["vn"] - s1["vn"]
     assert 0.5 < np.max(np.abs(du)) <= 1.0
+
+
+def test_edge_normals_are_unit_tangents_from_the_first_cell_to_the_second():
+    from icon_inputs.state import edge_normals
+    g = make_grid(2)
+    n = edge_normals(g)
+    assert np.max(np.abs(np.linalg.norm(n, axis=1) - 1.0)) < 1e-14
+    assert np.max(np.abs(np.einsum("ij,ij->i", n, g.edge_xyz))) < 1e-14
+    d = g.cell_xyz[g.e2c[:, 1]] - g.cell_xyz[g.e2c[:, 0]]
+    assert np.all(np.einsum("ij,ij->i", n, d) > 0)
+
+
+def test_perturbation_is_an_eastward_bump_of_the_given_amplitude():
+    """The seeded bump adds amp exp(-(r/(a/10))^2) to the zonal wind: eastward,
+    about amp at the edges nearest its centre, negligible far away."""
+    from icon_inputs.state import edge_normals, gaussian_perturbation_centre
+    g, z = make_grid(3), make_vct(10)
+    dvn = jw_type_state(g, z, seed=4, amp=2.0)["vn"] - jw_type_state(g, z, seed=4, amp=0.0)["vn"]
+    east = np.cross([0.0, 0.0, 1.0], g.edge_xyz)
+    east /= np.linalg.norm(east, axis=1, keepdims=True)
+    proj = np.einsum("ij,ij->i", east, edge_normals(g))
+    du = dvn[:, 0] / np.where(np.abs(proj) > 0.5, proj, np.nan)      # zonal change where vn sees it
+    xc = gaussian_perturbation_centre(4)
+    r = np.arccos(np.clip(g.edge_xyz @ xc, -1.0, 1.0))
+    near = (r < 0.02) & np.isfinite(du)
+    assert near.any() and np.all(du[near] > 1.9) and np.all(du[near] <= 2.0 + 1e-12)
+    far = r > 0.5
+    assert np.max(np.abs(dvn[far])) < 1e-6
