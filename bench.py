@@ -408,7 +408,7 @@ FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
 
 # DRAM bytes per launch of the FP64 column solve (the mean of its predictor
 # and corrector launches, 6.39 and 8.47 GB) from the ncu capture of the FP64
-# step at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid for that grid
+# step at R2B6 L90, valid for that grid
 # while the kernel source is the one captured (its SHA-256 below).
 COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
                   "sha256": "1fc4e7a652e5d510c7db7dfe44654c9b8fd3a81b01462c4eac418754c02a58ea",
@@ -416,7 +416,7 @@ COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
 
 
 # DRAM bytes per step of every kernel in the timed steps, from one ncu capture
-# of each leg at R2B6 L90 (profiles/dram_per_step_r2b6_l90.md), valid while
+# of each leg at R2B6 L90, valid while
 # the kernel sources are the ones captured (SHA-256 over csrc/* except the
 # host-only set-up code, below).
 STEP_DRAM = {"sources_sha256": "987083fa96c2d1d9b02eead4bb1f78ece04babebba2a12334617df53cb029a45",

@@ -280,20 +280,21 @@ int icon_dycore_sizes(const icon_dycore_t* dycore, int32_t* nlev, int32_t* n_cel
 /*
  * Allocation-free vertically implicit column solve.  The paper has no
  * counterpart: this entry point is for callers that cannot allocate device
- * memory when they call -- a host model that has reserved nearly all device
- * memory for its own arrays at start-up, or one that enqueues its time step
- * while capturing a stream into a CUDA graph (cudaMalloc is not a capturable
- * operation).  Such a caller cannot create a dycore, whose work arrays are
- * allocated for a whole step, but can run this solve on arrays it owns.
+ * memory when they call -- typically a host model that reserved nearly all
+ * device memory for its own arrays at start-up, so that the work arrays of a
+ * whole step, which icon_dycore_create allocates, no longer fit.  Such a
+ * caller can still run this solve on arrays it owns.
  *
  * It runs the same column kernel as icon_nh_solve (one thread per column,
  * Thomas elimination, Rayleigh damping, back-substitution, linearised
  * equation of state) for n_cols independent columns of nlev levels:
- *   z_ifc [nlev+1] HOST, half-level heights as for icon_dycore_create;
+ *   z_ifc [nlev+1] HOST, half-level heights as for icon_dycore_create; read
+ *          during the call only (it is passed to the GPU by value);
  *   p      the scheme parameters (dtime/ndyn_substeps is the time step of the
  *          solve; stream and synchronous are honoured; precision FP64 solves
  *          in FP64, MIXED in the mixed mode's double-word FP32 arithmetic,
- *          about 48 significant bits, on FP64 inputs and outputs);
+ *          about 48 significant bits, on FP64 inputs and outputs; any other
+ *          precision is refused);
  * DEVICE inputs, level-contiguous like the state:
  *   w [n_cols*(nlev+1)], rho, exner, theta_v [n_cols*nlev]  state at the
  *          start of the substep;
@@ -308,17 +309,19 @@ int icon_dycore_sizes(const icon_dycore_t* dycore, int32_t* nlev, int32_t* n_cel
  *   exner_new, theta_new.
  * Scratch: one file-scope static device array of 64 MiB, held by every GPU
  * that loads this library until the process exits; it limits a call to
- * nlev <= 256 and n_cols*(nlev+1) <= 1 047 552 column-levels (larger calls
- * return ICON_ERR_ARG).  No cudaMalloc, cudaFree or other allocating call
- * is made.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) and sets the kernel's shared-memory limit;
- * make that first call before any stream capture.  All calls share the
- * array and it keeps the last call's contents (every value a call reads is
- * written earlier in the same call, so nothing needs clearing); calls whose
- * GPU work overlaps -- on different streams, or from different threads --
- * race on it and must be serialised by the caller.
- * Errors: ICON_ERR_ARG (NULL, sizes beyond the limit, bad z_ifc or time
- * step), ICON_ERR_CUDA.
+ * nlev <= 256 and n_cols*(nlev+1) <= 1 047 232 column-levels (at nlev = 90:
+ * 11 508 columns); larger calls return ICON_ERR_ARG before any GPU work.
+ * No cudaMalloc, cudaFree or other allocating call is made.  The vertical
+ * metrics are computed on the device, by a one-thread kernel on the same
+ * stream, from z_ifc and the scalars passed by value.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress)
+ * and sets the kernel's shared-memory limit.  All calls share the array and
+ * it keeps the last call's contents (every value a call reads is written
+ * earlier in the same call, so nothing needs clearing); calls whose GPU work
+ * overlaps -- on different streams, or from different threads -- race on it
+ * and must be serialised by the caller.
+ * Errors: ICON_ERR_ARG (NULL, sizes beyond the limit, bad z_ifc, time step
+ * or precision), ICON_ERR_CUDA.
  */
 int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const double* z_ifc,
                               const icon_dycore_params_t* p, const double* w, const double* rho,

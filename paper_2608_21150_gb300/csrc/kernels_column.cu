@@ -704,13 +704,14 @@ template void launch_column<float>(const Engine&, int, const StateView&, const f
 //
 // Who needs it: callers that cannot allocate device memory at the time they
 // call.  A host model typically reserves nearly all device memory for its own
-// arrays at start-up, or enqueues its time step while capturing a stream into
-// a CUDA graph, where cudaMalloc is not a capturable operation.  Such a
-// caller cannot create a dycore (icon_dycore_create allocates the work arrays
-// of a whole step) but can still run the vertically implicit solve on arrays
-// it owns.  The column solve needs scratch (the Thomas elimination planes and
-// the vertical metrics); here it lives in one file-scope static device array
-// that every GPU loading this library holds until the process exits.
+// arrays at start-up and leaves too little for a dycore's work arrays
+// (icon_dycore_create allocates those of a whole step); it can still run the
+// vertically implicit solve on arrays it owns.  The column solve needs scratch
+// (the Thomas elimination planes and the vertical metrics); here it lives in
+// one file-scope static device array that every GPU loading this library
+// holds until the process exits.  The vertical metrics are computed on the
+// device from the half-level heights and scalars passed by value as kernel
+// parameters, so the call's stream work reads no host memory.
 // ===========================================================================
 namespace icon {
 namespace {
@@ -722,8 +723,105 @@ constexpr size_t kNoallocLevHL = 6400;                 // offset of the double-w
 constexpr size_t kNoallocDoubles = (size_t)8 << 20;    // 64 MiB in total
 constexpr size_t kNoallocPlanes = 8;                   // 7 Thomas planes + zb
 constexpr size_t kNoallocMaxPoints = (kNoallocDoubles - kNoallocCoef) / kNoallocPlanes;
+static_assert(kNoallocMaxPoints == 1047232, "the limit stated in icon_dycore.h");
+static_assert(8 * kNoallocStride + 8 * (kNoallocMaxLev + 1) <= kNoallocLevHL, "column coefficients fit");
+static_assert(kNoallocLevHL + 16 * (kNoallocMaxLev + 1) <= kNoallocCoef, "level table fits");
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+// Everything the vertical metrics are derived from, passed by value (about
+// 2.1 KB of kernel parameters).
+struct NoallocSetup {
+  int nlev;
+  double dt_s, beta, rd_o_cvd, cpd, grav, ref_T0, rayleigh_coeff, damp_height;
+  double z_ifc[kNoallocMaxLev + 1];
+};
+
+// double -> (hi, lo) FP32 pair, as split_hl on the host
+__device__ __forceinline__ void split_pair(double x, float* out) {
+  const float hi = __double2float_rn(x);
+  out[0] = hi;
+  out[1] = __double2float_rn(x - (double)hi);
+}
+
+// The vertical metrics, reference state, Rayleigh factors, column
+// coefficients and double-word level table of icon_dycore_create, written
+// into the metric section of the static array (every slot the column kernel
+// reads, zeros included, so nothing is left from an earlier call).  One
+// thread: about nlev sequential levels of scalar work.
+__global__ void noalloc_metrics(NoallocSetup q, double* base) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int nlev = q.nlev;
+  double* dz = base;
+  double* inv_dz = base + kNoallocStride;
+  double* inv_dzh = base + 2 * kNoallocStride;
+  double* wgt = base + 3 * kNoallocStride;
+  double* th_ref = base + 4 * kNoallocStride;
+  double* ex_ref = base + 5 * kNoallocStride;
+  double* dref = base + 6 * kNoallocStride;
+  double* ray = base + 7 * kNoallocStride;
+  double* colc = base + 8 * kNoallocStride;
+  float* lev = reinterpret_cast<float*>(base + kNoallocLevHL);
+  const double* z = q.z_ifc;
+  const double H = q.cpd * q.ref_T0 / q.grav;
+  for (int k = 0; k < nlev; ++k) {
+    const double zm = 0.5 * (z[k] + z[k + 1]);
+    dz[k] = z[k] - z[k + 1];
+    inv_dz[k] = 1.0 / dz[k];
+    th_ref[k] = q.ref_T0 * exp(zm / H);
+  }
+  for (int k = 0; k <= nlev; ++k) {
+    inv_dzh[k] = 0.0;
+    wgt[k] = 0.0;
+    dref[k] = 0.0;
+  }
+  for (int k = 1; k < nlev; ++k) {
+    const double zu = 0.5 * (z[k - 1] + z[k]), zl = 0.5 * (z[k] + z[k + 1]);
+    inv_dzh[k] = 1.0 / (zu - zl);
+    wgt[k] = (z[k] - zl) / (zu - zl);
+  }
+  ex_ref[nlev - 1] = exp(-0.5 * (z[nlev - 1] + z[nlev]) / H);
+  for (int k = nlev - 1; k >= 1; --k) {
+    const double zu = 0.5 * (z[k - 1] + z[k]), zl = 0.5 * (z[k] + z[k + 1]);
+    const double th_ic = wgt[k] * th_ref[k - 1] + (1.0 - wgt[k]) * th_ref[k];
+    ex_ref[k - 1] = ex_ref[k] - q.grav * (zu - zl) / (q.cpd * th_ic);
+  }
+  for (int k = 1; k < nlev; ++k) dref[k] = (ex_ref[k - 1] - ex_ref[k]) * inv_dzh[k];
+  for (int k = 0; k <= nlev; ++k) {
+    ray[k] = 1.0;
+    if (q.rayleigh_coeff > 0.0 && z[k] > q.damp_height) {
+      const double sn = sin(0.5 * 3.141592653589793 * (z[k] - q.damp_height) / (z[0] - q.damp_height));
+      ray[k] = 1.0 / (1.0 + q.dt_s * q.rayleigh_coeff * sn * sn);
+    }
+  }
+  for (int k = 0; k <= nlev; ++k) {
+    double* cf = colc + 8 * (size_t)k;
+    for (int j = 0; j < 8; ++j) cf[j] = 0.0;
+    if (k < nlev) {
+      cf[0] = q.dt_s * q.rd_o_cvd / dz[k];
+      cf[1] = q.dt_s * (1.0 - q.beta) / dz[k];
+      cf[2] = q.dt_s * q.beta / dz[k];
+    }
+    if (k >= 1 && k < nlev) {
+      cf[3] = q.dt_s * q.cpd * (1.0 - q.beta) * inv_dzh[k];
+      cf[4] = q.dt_s * q.cpd * dref[k];
+      cf[5] = q.dt_s * q.cpd * q.beta * inv_dzh[k];
+      cf[6] = wgt[k];
+      cf[7] = 1.0 - wgt[k];
+    }
+    // the double-word table: colc, then exner_ref, theta_ref, dz, ray_fac
+    // (no rho offset: this entry point's inputs are FP64)
+    float* r = lev + 32 * (size_t)k;
+    for (int j = 0; j < 32; ++j) r[j] = 0.0f;
+    for (int j = 0; j < 8; ++j) split_pair(cf[j], r + 2 * j);
+    if (k < nlev) {
+      split_pair(ex_ref[k], r + 16);
+      split_pair(th_ref[k], r + 18);
+      split_pair(dz[k], r + 20);
+    }
+    split_pair(ray[k], r + 22);
+  }
+}
 
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
@@ -780,13 +878,17 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
     return report_error(ICON_ERR_ARG, std::string(fn) + "n_cols*(nlev+1) = " + std::to_string(points) +
                                           " exceeds the static scratch of " + std::to_string(kNoallocMaxPoints) +
                                           " column-levels (64 MiB)");
+  for (int k = 0; k <= nlev; ++k)
+    if (!std::isfinite(z_ifc[k])) return report_error(ICON_ERR_ARG, std::string(fn) + "z_ifc not finite");
   for (int k = 0; k < nlev; ++k)
     if (!(z_ifc[k] > z_ifc[k + 1])) return report_error(ICON_ERR_ARG, std::string(fn) + "z_ifc must decrease");
   if (z_ifc[nlev] != 0.0) return report_error(ICON_ERR_ARG, std::string(fn) + "z_ifc[nlev] must be 0");
   if (!(p->dtime > 0.0) || p->ndyn_substeps < 1)
     return report_error(ICON_ERR_ARG, std::string(fn) + "dtime must be > 0 and ndyn_substeps >= 1");
+  if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED)
+    return report_error(ICON_ERR_ARG, std::string(fn) + "precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
 
-  // scalars and vertical metrics, with the same definitions as icon_dycore_create
+  // scalars with the same definitions as icon_dycore_create
   Scalars s{};
   s.dtime = p->dtime;
   s.dt_s = p->dtime / p->ndyn_substeps;
@@ -805,66 +907,25 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
   s.rd_o_cvd = p->rd / s.cvd;
   s.cvd_o_rd = s.cvd / p->rd;
   s.hdiff_temp = p->hdiff_temp ? 1 : 0;
-  double coef[kNoallocCoef] = {};
-  double* dz = coef;
-  double* inv_dz = coef + kNoallocStride;
-  double* inv_dzh = coef + 2 * kNoallocStride;
-  double* wgt = coef + 3 * kNoallocStride;
-  double* th_ref = coef + 4 * kNoallocStride;
-  double* ex_ref = coef + 5 * kNoallocStride;
-  double* dref = coef + 6 * kNoallocStride;
-  double* ray = coef + 7 * kNoallocStride;
-  double* colc = coef + 8 * kNoallocStride;
-  double z_mc[kNoallocMaxLev];
-  for (int k = 0; k < nlev; ++k) {
-    z_mc[k] = 0.5 * (z_ifc[k] + z_ifc[k + 1]);
-    dz[k] = z_ifc[k] - z_ifc[k + 1];
-    inv_dz[k] = 1.0 / dz[k];
-  }
-  for (int k = 1; k < nlev; ++k) {
-    inv_dzh[k] = 1.0 / (z_mc[k - 1] - z_mc[k]);
-    wgt[k] = (z_ifc[k] - z_mc[k]) / (z_mc[k - 1] - z_mc[k]);
-  }
-  const double T0 = p->ref_T0, H = p->cpd * T0 / p->grav;
-  for (int k = 0; k < nlev; ++k) th_ref[k] = T0 * std::exp(z_mc[k] / H);
-  ex_ref[nlev - 1] = std::exp(-z_mc[nlev - 1] / H);
-  for (int k = nlev - 1; k >= 1; --k) {
-    const double th_ic = wgt[k] * th_ref[k - 1] + (1.0 - wgt[k]) * th_ref[k];
-    ex_ref[k - 1] = ex_ref[k] - p->grav * (z_mc[k - 1] - z_mc[k]) / (p->cpd * th_ic);
-  }
-  for (int k = 1; k < nlev; ++k) dref[k] = (ex_ref[k - 1] - ex_ref[k]) * inv_dzh[k];
-  for (int k = 0; k <= nlev; ++k) ray[k] = 1.0;
-  if (p->rayleigh_coeff > 0.0) {
-    const double top = z_ifc[0], zd = p->damp_height;
-    for (int k = 0; k <= nlev; ++k)
-      if (z_ifc[k] > zd) {
-        const double sn = std::sin(0.5 * M_PI * (z_ifc[k] - zd) / (top - zd));
-        ray[k] = 1.0 / (1.0 + s.dt_s * p->rayleigh_coeff * sn * sn);
-      }
-  }
-  for (int k = 0; k <= nlev; ++k) {
-    double* cf = colc + 8 * (size_t)k;
-    if (k < nlev) {
-      cf[0] = s.dt_s * s.rd_o_cvd / dz[k];
-      cf[1] = s.dt_s * (1.0 - s.beta) / dz[k];
-      cf[2] = s.dt_s * s.beta / dz[k];
-    }
-    if (k >= 1 && k < nlev) {
-      cf[3] = s.dt_s * p->cpd * (1.0 - s.beta) * inv_dzh[k];
-      cf[4] = s.dt_s * p->cpd * dref[k];
-      cf[5] = s.dt_s * p->cpd * s.beta * inv_dzh[k];
-      cf[6] = wgt[k];
-      cf[7] = 1.0 - wgt[k];
-    }
-  }
-  level_pairs_into(reinterpret_cast<float*>(coef + kNoallocLevHL), nlev, colc, ex_ref, th_ref, dz, ray, nullptr);
+  NoallocSetup q{};
+  q.nlev = nlev;
+  q.dt_s = s.dt_s;
+  q.beta = s.beta;
+  q.rd_o_cvd = s.rd_o_cvd;
+  q.cpd = p->cpd;
+  q.grav = p->grav;
+  q.ref_T0 = p->ref_T0;
+  q.rayleigh_coeff = p->rayleigh_coeff;
+  q.damp_height = p->damp_height;
+  for (int k = 0; k <= nlev; ++k) q.z_ifc[k] = z_ifc[k];
 
   double* base = nullptr;
   int rc = noalloc_setup(&base);
   if (rc != ICON_OK) return rc;
   cudaStream_t stream = static_cast<cudaStream_t>(p->stream);
-  // metrics into the static array (a copy from host memory, no allocation)
-  cudaError_t e = cudaMemcpyAsync(base, coef, sizeof coef, cudaMemcpyHostToDevice, stream);
+  // the metrics into the static array, on the device, from the by-value block
+  noalloc_metrics<<<1, 32, 0, stream>>>(q, base);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(e));
   DevVert v{};
   v.nlev = nlev;

@@ -1,0 +1,63 @@
+"""The R2B4 L65 configuration (20 480 cells, 65 levels to 30 km, dt 720 s,
+5 substeps, Rayleigh damping above 20 km, seed 1) on the GPU in FP64:
+whole-step parity with the oracle after 1 step (1e-12) and 10 steps (1e-9),
+and conservation of the total mass over 100 steps (|dM/M| <= 1e-13).
+
+The oracle's 10 steps take a few minutes on the host cores; they are run
+once per module."""
+import numpy as np
+import pytest
+
+from parity import setup, gpu_params, to_torch, to_numpy, rel_err
+
+pytestmark = pytest.mark.gpu
+
+BIS, NLEV, DT, SEED = 4, 65, 720.0, 1
+
+
+@pytest.fixture(scope="module")
+def oracle_run():
+    grid, z, op, od, st = setup(BIS, NLEV, DT, seed=SEED, rayleigh=0.05)
+    states = [st]
+    for _ in range(10):
+        states.append(od.step(states[-1]))
+    return grid, z, op, od, states
+
+
+@pytest.mark.parametrize("use_graph", [1, 0], ids=["graph", "direct"])
+def test_r2b4_l65_steps_match_the_oracle(built_lib, cuda, oracle_run, use_graph):
+    import paper_2608_21150_gb300 as P
+    grid, z, op, od, states = oracle_run
+    g = P.Grid(grid, radius=op.radius)
+    d = P.Dycore(g, z, gpu_params(op, use_graph=use_graph))
+    t = to_torch(states[0], cuda)
+    errs = {}
+    for n in range(1, 11):
+        d.step(t)
+        if n in (1, 10):
+            errs[n] = rel_err(to_numpy(t), states[n], od)
+    d.close()
+    g.close()
+    assert all(e < 1e-12 for e in errs[1].values()), errs[1]
+    assert all(e < 1e-9 for e in errs[10].values()), errs[10]
+    # the state has developed: the steps are not a trivial balance
+    assert np.max(np.abs(states[10]["w"])) > 1e-3
+
+
+def test_r2b4_l65_mass_conserved_over_100_steps(built_lib, cuda):
+    import paper_2608_21150_gb300 as P
+    grid, z, op, od, st = setup(BIS, NLEV, DT, seed=SEED, rayleigh=0.05)
+    g = P.Grid(grid, radius=op.radius)
+    d = P.Dycore(g, z, gpu_params(op))
+    t = to_torch(st, cuda)
+    m0 = d.diagnostics(t)
+    masses = []
+    for n in range(100):
+        d.step(t)
+        if (n + 1) % 10 == 0:
+            masses.append(d.diagnostics(t))
+    d.close()
+    g.close()
+    drift = max(abs(m - m0) / m0 for m in masses)
+    assert drift <= 1e-13, drift
+    assert all(np.isfinite(to_numpy(t)[k]).all() for k in t)
