@@ -3,11 +3,19 @@
 whole-step parity with the oracle after 1 step (1e-12) and 10 steps (1e-9),
 and conservation of the total mass over 100 steps (|dM/M| <= 1e-13).
 
-The oracle's 10 steps take a few minutes on the host cores; they are run
-once per module."""
+Where a field's own conditioning is coarser than the gate, the gate is the
+probtest reading of Sec. 4.4 instead: five times the spread of the oracle
+itself when its input is changed at the level of FP64 rounding (two members,
+relative perturbations of 1e-16, oracle/probtest.py).  This matters for w
+after one step: 0.011 m/s at most, the residual of buoyancy and vertical
+pressure-gradient terms of about 20 m/s per substep, so a last-bit change of
+the input moves the oracle's own w by 5e-12 of its maximum.
+
+The oracle's 10 steps (and those of the two members) run once per module."""
 import numpy as np
 import pytest
 
+from oracle import probtest
 from parity import setup, gpu_params, to_torch, to_numpy, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -21,13 +29,19 @@ def oracle_run():
     states = [st]
     for _ in range(10):
         states.append(od.step(states[-1]))
-    return grid, z, op, od, states
+    spread = probtest.ensemble_spread(od, st, 1e-16, (1, 2), 10, control=states[1:])
+    return grid, z, op, od, states, spread
+
+
+def gate(base, spread, n):
+    """max(base, 5 x the rounding-level spread of the oracle) per field after step n."""
+    return {k: max(base, 5.0 * spread[k][n - 1]) for k in spread}
 
 
 @pytest.mark.parametrize("use_graph", [1, 0], ids=["graph", "direct"])
 def test_r2b4_l65_steps_match_the_oracle(built_lib, cuda, oracle_run, use_graph):
     import paper_2608_21150_gb300 as P
-    grid, z, op, od, states = oracle_run
+    grid, z, op, od, states, spread = oracle_run
     g = P.Grid(grid, radius=op.radius)
     d = P.Dycore(g, z, gpu_params(op, use_graph=use_graph))
     t = to_torch(states[0], cuda)
@@ -38,8 +52,11 @@ def test_r2b4_l65_steps_match_the_oracle(built_lib, cuda, oracle_run, use_graph)
             errs[n] = rel_err(to_numpy(t), states[n], od)
     d.close()
     g.close()
-    assert all(e < 1e-12 for e in errs[1].values()), errs[1]
-    assert all(e < 1e-9 for e in errs[10].values()), errs[10]
+    for n, base in ((1, 1e-12), (10, 1e-9)):
+        tol = gate(base, spread, n)
+        assert all(errs[n][k] < tol.get(k, base) for k in errs[n]), (n, errs[n], tol)
+    # the rounding-level spread relaxes the gate for w after one step only
+    assert all(spread[k][0] * 5.0 < 1e-12 for k in spread if k != "w")
     # the state has developed: the steps are not a trivial balance
     assert np.max(np.abs(states[10]["w"])) > 1e-3
 
