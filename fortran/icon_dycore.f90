@@ -40,7 +40,7 @@ module icon_dycore
   end type
 
   public :: icon_grid_create, icon_grid_destroy, icon_dycore_params_default, icon_dycore_create, &
-       icon_dycore_destroy, icon_dycore_step, icon_nh_solve, icon_nh_diff, icon_dycore_diagnostics, &
+       icon_dycore_create_terrain, icon_dycore_reference_columns, icon_dycore_destroy, icon_dycore_step, icon_nh_solve, icon_nh_diff, icon_dycore_diagnostics, &
        icon_state_from_blocked, icon_state_to_blocked, icon_dycore_step_blocked, icon_last_error_string, &
        icon_dycore_save, icon_dycore_load
 
@@ -65,6 +65,23 @@ module icon_dycore
       real(c_double), intent(in) :: z_ifc(*)
       type(icon_dycore_params_t), intent(in) :: params
       type(c_ptr), intent(out) :: dycore
+    end function
+    ! terrain-following heights per column: z_ifc(nlev+1, n_cells)
+    integer(c_int) function icon_dycore_create_terrain(grid, nlev, z_ifc, params, dycore) &
+        bind(c, name="icon_dycore_create_terrain")
+      import :: c_int, c_int32_t, c_double, c_ptr, icon_dycore_params_t
+      type(c_ptr), value :: grid
+      integer(c_int32_t), value :: nlev
+      real(c_double), intent(in) :: z_ifc(*)
+      type(icon_dycore_params_t), intent(in) :: params
+      type(c_ptr), intent(out) :: dycore
+    end function
+    ! reference theta_v and exner per column: (nlev, n_cells) each
+    integer(c_int) function icon_dycore_reference_columns(dycore, theta_ref, exner_ref) &
+        bind(c, name="icon_dycore_reference_columns")
+      import :: c_int, c_double, c_ptr
+      type(c_ptr), value :: dycore
+      real(c_double), intent(out) :: theta_ref(*), exner_ref(*)
     end function
     integer(c_int) function icon_dycore_destroy(dycore) bind(c, name="icon_dycore_destroy")
       import :: c_int, c_ptr

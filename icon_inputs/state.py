@@ -91,21 +91,29 @@ def jw_type_state(grid, z_ifc, seed=0, amp=1.0, constants=None, **jw):
     """Prognostic state dict (vn, w, rho, exner, theta_v), level-contiguous float64.
 
     Shapes: vn [ne, nlev], w [nc, nlev+1], rho/exner/theta_v [nc, nlev].
-    ``amp`` = 0 gives the unperturbed balanced jet.
+    ``amp`` = 0 gives the unperturbed balanced jet.  z_ifc is one column of
+    half-level heights [nlev+1], or one per cell [nc, nlev+1] (terrain): the
+    fields are then evaluated at each cell's full-level heights, and vn at the
+    mean of the two adjacent cells' heights.
     """
     c = dict(CONSTANTS if constants is None else constants)
     p = dict(JW_DEFAULTS)
     p.update(jw)
     z_ifc = np.asarray(z_ifc, dtype=np.float64)
-    z_mc = 0.5 * (z_ifc[:-1] + z_ifc[1:])
-    nlev = z_mc.size
+    if z_ifc.ndim == 1:
+        z_mc = 0.5 * (z_ifc[:-1] + z_ifc[1:])
+        zc = ze = z_mc[None, :]
+    else:
+        zc = 0.5 * (z_ifc[:, :-1] + z_ifc[:, 1:])
+        ze = 0.5 * (zc[grid.e2c[:, 0]] + zc[grid.e2c[:, 1]])
+    nlev = zc.shape[1]
     phi_c = _lat(grid.cell_xyz)[:, None]
-    pi_c, th_c, _ = _jw_fields(phi_c, z_mc[None, :], c, p["T0"], p["eps0"], p["z_jet"])
+    pi_c, th_c, _ = _jw_fields(phi_c, zc, c, p["T0"], p["eps0"], p["z_jet"])
     rho_c = c["p00"] * pi_c ** (c["cvd"] / c["rd"]) / (c["rd"] * th_c)
 
     xe = grid.edge_xyz
     phi_e = _lat(xe)[:, None]
-    _, _, u_e = _jw_fields(phi_e, z_mc[None, :], c, p["T0"], p["eps0"], p["z_jet"])
+    _, _, u_e = _jw_fields(phi_e, ze, c, p["T0"], p["eps0"], p["z_jet"])
     if amp != 0.0:
         xc = gaussian_perturbation_centre(seed)
         r = c["radius"] * np.arctan2(np.linalg.norm(np.cross(xe, xc), axis=1), xe @ xc)

@@ -152,6 +152,34 @@ void icon_dycore_params_default(icon_dycore_params_t* p);
  */
 int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
                        const icon_dycore_params_t* params, icon_dycore_t** out);
+/*
+ * Create a dycore over terrain: a terrain-following height coordinate with
+ * half-level heights per column (Sec. 4.1: ICON's dynamical core runs over
+ * real orography; Sec. 5: the global configurations include topography).
+ *   z_ifc [n_cells*(nlev+1)]: HOST pointer, level-contiguous like a w field,
+ *          z_ifc[c*(nlev+1) + k] the height of half level k of column c in m;
+ *          strictly decreasing in every column, the model top z_ifc[c*(nlev+1)]
+ *          the same in every column (a flat top); the ground
+ *          z_ifc[c*(nlev+1) + nlev] is the topography.
+ * Per column: the vertical metrics, the reference state (discretely balanced
+ * along the column) and the column solve's coefficients.  At edges: layer
+ * thicknesses and interpolation weights from the mean of the two cells'
+ * heights, and the slopes of the coordinate surfaces.  The step then uses the
+ * contravariant vertical velocity w - w_concorr (w_concorr the vertical
+ * velocity of a parcel following the coordinate surface) for vertical
+ * advection and in the implicit solve, which keeps w = w_concorr at the
+ * ground (kinematic condition); the horizontal pressure gradient is taken
+ * along the true horizontal; horizontal fluxes carry the edge layer
+ * thickness, so the total mass stays conserved.  Diffusion acts along the
+ * coordinate surfaces.  With equal columns the step equals that of
+ * icon_dycore_create on the same heights bit for bit.  exner_pr and the
+ * diagnostics use the per-column reference state (icon_dycore_reference_columns).
+ * Errors: as icon_dycore_create; ICON_ERR_ARG for heights that are not finite,
+ * not decreasing or without a common top.
+ */
+int icon_dycore_create_terrain(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
+                               const icon_dycore_params_t* params, icon_dycore_t** out);
+
 /* NULL-safe; frees library-owned memory only (Sec. 4.3: the state arrays
  * stay the caller's). */
 int icon_dycore_destroy(icon_dycore_t* dycore);
@@ -203,9 +231,15 @@ int icon_velocity_tendencies(icon_dycore_t* dycore, const double* vn, const doub
 
 /* The reference state the dycore derived (HOST outputs, [nlev] each):
  * theta_ref and exner_ref at full levels; exner_ref is in exact discrete
- * hydrostatic balance with theta_ref on this vertical grid. */
+ * hydrostatic balance with theta_ref on this vertical grid.  Over terrain the
+ * reference state differs by column: ICON_ERR_UNSUPPORTED (use
+ * icon_dycore_reference_columns). */
 int icon_dycore_reference_state(const icon_dycore_t* dycore, double* theta_ref,
                                 double* exner_ref);
+/* The reference state per column (HOST outputs [n_cells*nlev] each, level-
+ * contiguous): each column's own over terrain, the same profile in every
+ * column over flat ground. */
+int icon_dycore_reference_columns(const icon_dycore_t* dycore, double* theta_ref, double* exner_ref);
 
 /* Diagnostics of a DEVICE state (outside the step):
  *   ps   [n_cells] DEVICE or NULL: surface pressure, Pa (exner at the ground

@@ -6,7 +6,8 @@ smaller ndyn_substeps) two networks propose increments towards the plain step
 taken from the same input.  Definitions, in the order the step applies them:
 
 * column features of cell c, five blocks of nlev values (levels top first):
-  w at full levels (w_k + w_{k+1}) / 2, exner - exner_ref, theta_v - theta_ref,
+  w at full levels (w_k + w_{k+1}) / 2, exner - exner_ref, theta_v - theta_ref
+  (the reference state of the cell's own column over terrain),
   and the east and north components of the Perot cell velocity
   (1/A_c) sum_e s l_e vn_e (x_e - x_c) with east = unit(z x r_c), north = r_c x east;
 * edge features of edge e: the column features of e2c[e,0], then those of
@@ -45,8 +46,10 @@ def column_features(dycore, st):
     east, north = east_north(g.C)
     u = np.einsum("ckx,cx->ck", u3, east)
     v = np.einsum("ckx,cx->ck", u3, north)
-    return np.concatenate([0.5 * (w[:, :-1] + w[:, 1:]), st["exner"] - ex_ref[None, :],
-                           st["theta_v"] - th_ref[None, :], u, v], axis=1)
+    if ex_ref.ndim == 1:      # one profile for all columns (flat ground); per column over terrain
+        th_ref, ex_ref = th_ref[None, :], ex_ref[None, :]
+    return np.concatenate([0.5 * (w[:, :-1] + w[:, 1:]), st["exner"] - ex_ref,
+                           st["theta_v"] - th_ref, u, v], axis=1)
 
 
 def edge_features(dycore, st, col_x=None):

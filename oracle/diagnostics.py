@@ -3,12 +3,13 @@ surface pressure, 850 hPa temperature, total mass, area-weighted RMS.
 
 Readings:
 * ps: exner at the ground extrapolated hydrostatically from the lowest full
-  level with its theta_v, exner_sfc = exner + g z_mc / (cpd theta_v), and
+  level with its theta_v, exner_sfc = exner + g (z_mc - z_sfc) / (cpd theta_v),
+  z_sfc the ground height of the column (0 over flat ground), and
   ps = p00 exner_sfc^(cpd/rd);
 * T850: T = theta_v exner at full levels, p = p00 exner^(cpd/rd); linear
   interpolation in ln p between the two levels around 850 hPa (the lowest
   level's T when the whole column is above 850 hPa);
-* mass: sum over cells of A_c sum_k rho dz_k;
+* mass: sum over cells of A_c sum_k rho dz_k (each column's own dz over terrain);
 * RMS of a difference: sqrt(sum A_c d^2 / sum A_c).
 """
 import numpy as np
@@ -18,7 +19,8 @@ def surface_pressure(dycore, exner, theta_v):
     """Diagnostics outside the step; a reading, the paper defines none (its results, Sec. 5, are ICON
     runs)."""
     p, v = dycore.p, dycore.v
-    ex_sfc = exner[:, -1] + p.grav * v.z_mc[-1] / (p.cpd * theta_v[:, -1])
+    dz_low = v.z_mc[..., -1] - v.z_ifc[..., -1]     # lowest full level above the ground
+    ex_sfc = exner[:, -1] + p.grav * dz_low / (p.cpd * theta_v[:, -1])
     return p.p00 * ex_sfc ** (p.cpd / p.rd)
 
 
@@ -43,7 +45,8 @@ def temperature_850(dycore, exner, theta_v, p_target=85000.0):
 def total_mass(dycore, rho):
     """Diagnostics outside the step; a reading, the paper defines none (its results, Sec. 5, are ICON
     runs)."""
-    return float(np.sum(dycore.g.cell_area[:, None] * rho * dycore.v.dz[None, :]))
+    dz = dycore.v.dz
+    return float(np.sum(dycore.g.cell_area[:, None] * rho * (dz if dz.ndim == 2 else dz[None, :])))
 
 
 def area_rms(dycore, diff):

@@ -30,13 +30,15 @@ def differences(a, b, dycore):
     """Per-field relative max-norm difference of state a from the control b.
     Sec. 4.4: probtest-style ensemble verification, a reading."""
     th_ref, ex_ref = dycore.reference_state()
+    if ex_ref.ndim == 1:      # per column over terrain
+        th_ref, ex_ref = th_ref[None, :], ex_ref[None, :]
     out = {}
     for k in FIELDS:
         x, y = np.asarray(a[k]), np.asarray(b[k])
         if k == "exner":
-            x, y = x - ex_ref[None, :], y - ex_ref[None, :]
+            x, y = x - ex_ref, y - ex_ref
         if k == "theta_v":
-            x, y = x - th_ref[None, :], y - th_ref[None, :]
+            x, y = x - th_ref, y - th_ref
         scale = np.max(np.abs(y))
         out[k] = float(np.max(np.abs(x - y)) / scale) if scale > 0 else float(np.max(np.abs(x - y)))
     return out

@@ -75,12 +75,16 @@ _sig = {
     "icon_dycore_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _f64p,
                                           ctypes.POINTER(icon_dycore_params_t),
                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "icon_dycore_create_terrain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _f64p,
+                                                  ctypes.POINTER(icon_dycore_params_t),
+                                                  ctypes.POINTER(ctypes.c_void_p)]),
     "icon_dycore_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "icon_dycore_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t)]),
     "icon_nh_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t)]),
     "icon_nh_diff": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t)]),
     "icon_velocity_tendencies": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
     "icon_dycore_reference_state": (ctypes.c_int, [ctypes.c_void_p, _f64p, _f64p]),
+    "icon_dycore_reference_columns": (ctypes.c_int, [ctypes.c_void_p, _f64p, _f64p]),
     "icon_dycore_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
     "icon_dycore_launch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]),
     "icon_dycore_debug_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -324,10 +328,19 @@ class Dycore:
         if stream is not None:
             params.stream = stream
         z = np.ascontiguousarray(z_ifc, dtype=np.float64)
-        self.nlev = z.size - 1
         h = ctypes.c_void_p()
-        _check(icon_dycore_create(grid.handle, self.nlev, z.ctypes.data_as(_f64p), ctypes.byref(params),
-                                  ctypes.byref(h)))
+        # one column of heights: flat ground; [n_cells, nlev+1]: terrain-following
+        self.terrain = z.ndim == 2
+        if self.terrain:
+            if z.shape[0] != grid.n_cells:
+                raise ValueError("terrain heights must be [n_cells, nlev+1]")
+            self.nlev = z.shape[1] - 1
+            _check(icon_dycore_create_terrain(grid.handle, self.nlev, z.ctypes.data_as(_f64p), ctypes.byref(params),
+                                              ctypes.byref(h)))
+        else:
+            self.nlev = z.size - 1
+            _check(icon_dycore_create(grid.handle, self.nlev, z.ctypes.data_as(_f64p), ctypes.byref(params),
+                                      ctypes.byref(h)))
         self.handle = h
         self.grid = grid
         self.params = params
@@ -381,6 +394,13 @@ class Dycore:
         th = np.empty(self.nlev)
         ex = np.empty(self.nlev)
         _check(icon_dycore_reference_state(self.handle, th.ctypes.data_as(_f64p), ex.ctypes.data_as(_f64p)))
+        return th, ex
+
+    def reference_columns(self):
+        """Reference theta_v and exner per column, [n_cells, nlev] each."""
+        th = np.empty((self.grid.n_cells, self.nlev))
+        ex = np.empty((self.grid.n_cells, self.nlev))
+        _check(icon_dycore_reference_columns(self.handle, th.ctypes.data_as(_f64p), ex.ctypes.data_as(_f64p)))
         return th, ex
 
     def profile(self, st, nsteps):

@@ -229,6 +229,11 @@ static void free_graphs(icon_dycore* d) {
 namespace {
 
 void enqueue_op(icon_dycore* d, int op, const StateView& st, cudaStream_t s);
+// The common part of icon_dycore_create and icon_dycore_create_terrain:
+// z_ifc [nlev+1] the heights the per-level tables use (column 0's over
+// terrain), z_cols [nc*(nlev+1)] the per-column heights (NULL: flat ground).
+int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const double* z_cols,
+                  const icon_dycore_params_t* p, icon_dycore_t** out, const char* fn);
 
 // Autotuner: time every kernel of one step on a temporary uniform state with
 // each candidate launch shape (CUDA events around every launch) and keep the
@@ -241,6 +246,15 @@ bool grid_complete(const GridT<T>& g) {
   const void* p[] = {g.c2e, g.c2e2c, g.e2c, g.e2v, g.e2c2v, g.e2c2e, g.v2e, g.v2c, g.div_c, g.lap_c, g.e2c_w,
                      g.grad_c, g.k4w_c, g.inv_d, g.inv_l, g.f_e, g.vt_w, g.upw, g.nt, g.inv_dn, g.smag_a, g.k4_a,
                      g.fdiv_e, g.ddamp_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl};
+  for (const void* q : p)
+    if (!q) return false;
+  return true;
+}
+
+template <class T>
+bool terrain_complete(const TerrT<T>& t) {
+  const void* p[] = {t.wgt_e, t.inv_dz_e, t.ddxn_ifc, t.ddxt_ifc, t.ddxn_mc, t.inv_dzh_c, t.inv_dzm_c, t.fx_ratio,
+                     t.wcc0, t.wcc1};
   for (const void* q : p)
     if (!q) return false;
   return true;
@@ -295,7 +309,8 @@ int autotune(icon_dycore* d) {
       if (!stencils) continue;
       for (int k = 0; k < kNumStencils; ++k) {
         const std::string base = kStencilNames[k];
-        if (nm == base || nm == base + "_f32") t[k][ci] += ms;
+        if (nm == base || nm == base + "_f32" || nm == base + "_terrain" || nm == base + "_terrain_f32")
+          t[k][ci] += ms;
       }
     }
     return ICON_OK;
@@ -338,15 +353,43 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   for (int k = 0; k < nlev; ++k)
     if (!(z_ifc[k] > z_ifc[k + 1])) return fail(ICON_ERR_ARG, "icon_dycore_create: z_ifc must decrease");
   if (z_ifc[nlev] != 0.0) return fail(ICON_ERR_ARG, "icon_dycore_create: z_ifc[nlev] must be 0 (flat ground)");
+  return create_dycore(grid, nlev, z_ifc, nullptr, p, out, "icon_dycore_create");
+}
+
+int icon_dycore_create_terrain(const icon_grid_t* grid, int32_t nlev, const double* z_ifc,
+                               const icon_dycore_params_t* p, icon_dycore_t** out) {
+  if (!grid || !z_ifc || !p || !out) return fail(ICON_ERR_ARG, "icon_dycore_create_terrain: NULL argument");
+  *out = nullptr;
+  if (nlev < 2) return fail(ICON_ERR_ARG, "icon_dycore_create_terrain: nlev must be >= 2");
+  return create_dycore(grid, nlev, z_ifc, z_ifc, p, out, "icon_dycore_create_terrain");
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const double* z_cols,
+                  const icon_dycore_params_t* p, icon_dycore_t** out, const char* fn) {
+  const std::string fname = fn;
   if (!(p->dtime > 0.0) || p->ndyn_substeps < 1)
-    return fail(ICON_ERR_ARG, "icon_dycore_create: dtime must be > 0 and ndyn_substeps >= 1");
+    return fail(ICON_ERR_ARG, fname + ": dtime must be > 0 and ndyn_substeps >= 1");
   if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED)
-    return fail(ICON_ERR_ARG, "icon_dycore_create: precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
+    return fail(ICON_ERR_ARG, fname + ": precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
   if (p->column_chunk != 0 && p->column_chunk != 4 && p->column_chunk != 6 && p->column_chunk != 8)
-    return fail(ICON_ERR_ARG, "icon_dycore_create: column_chunk must be 0, 4, 6 or 8");
+    return fail(ICON_ERR_ARG, fname + ": column_chunk must be 0, 4, 6 or 8");
+  // terrain: every column validated and its metrics derived before any allocation
+  HostTerrain ht;
+  if (z_cols) {
+    Scalars s0{};
+    s0.dt_s = p->dtime / p->ndyn_substeps;
+    s0.beta = p->vwind_impl_wgt;
+    s0.rd_o_cvd = p->rd / (p->cpd - p->rd);
+    std::string err = build_terrain(grid->host, nlev, z_cols, *p, s0, &ht);
+    if (!err.empty()) return fail(ICON_ERR_ARG, fname + ": " + err);
+  }
 
   icon_dycore* d = new (std::nothrow) icon_dycore();
-  if (!d) return fail(ICON_ERR_ARG, "icon_dycore_create: out of host memory");
+  if (!d) return fail(ICON_ERR_ARG, fname + ": out of host memory");
   d->grid = grid;
   d->params = *p;
   d->nlev = nlev;
@@ -375,58 +418,20 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   s.cvd_o_rd = s.cvd / p->rd;
   s.hdiff_temp = p->hdiff_temp ? 1 : 0;
 
-  // vertical metrics and reference state (row A0)
+  // vertical metrics and reference state (row A0); over terrain those of
+  // column 0, which serve as the mixed mode's FP32 perturbation offsets
   d->z_ifc.assign(z_ifc, z_ifc + nlev + 1);
-  std::vector<double> z_mc(nlev), dz(nlev), inv_dz(nlev), inv_dzh(nlev + 1, 0.0), wgt(nlev + 1, 0.0);
-  std::vector<double> dref(nlev + 1, 0.0), ray(nlev + 1, 1.0);
-  for (int k = 0; k < nlev; ++k) {
-    z_mc[k] = 0.5 * (z_ifc[k] + z_ifc[k + 1]);
-    dz[k] = z_ifc[k] - z_ifc[k + 1];
-    inv_dz[k] = 1.0 / dz[k];
-  }
-  for (int k = 1; k < nlev; ++k) {
-    inv_dzh[k] = 1.0 / (z_mc[k - 1] - z_mc[k]);
-    wgt[k] = (z_ifc[k] - z_mc[k]) / (z_mc[k - 1] - z_mc[k]);
-  }
-  const double T0 = p->ref_T0, H = p->cpd * T0 / p->grav;
-  d->theta_ref.resize(nlev);
-  d->exner_ref.resize(nlev);
-  for (int k = 0; k < nlev; ++k) d->theta_ref[k] = T0 * std::exp(z_mc[k] / H);
-  d->exner_ref[nlev - 1] = std::exp(-z_mc[nlev - 1] / H);
-  for (int k = nlev - 1; k >= 1; --k) {
-    double th_ic = wgt[k] * d->theta_ref[k - 1] + (1.0 - wgt[k]) * d->theta_ref[k];
-    d->exner_ref[k - 1] = d->exner_ref[k] - p->grav * (z_mc[k - 1] - z_mc[k]) / (p->cpd * th_ic);
-  }
-  for (int k = 1; k < nlev; ++k) dref[k] = (d->exner_ref[k - 1] - d->exner_ref[k]) * inv_dzh[k];
-  if (p->rayleigh_coeff > 0.0) {
-    const double top = z_ifc[0], zd = p->damp_height;
-    for (int k = 0; k <= nlev; ++k)
-      if (z_ifc[k] > zd) {
-        double sn = std::sin(0.5 * M_PI * (z_ifc[k] - zd) / (top - zd));
-        ray[k] = 1.0 / (1.0 + s.dt_s * p->rayleigh_coeff * sn * sn);
-      }
-  }
-
-  // per-level coefficients of the column solve (layout documented in DevVert)
-  std::vector<double> colc(8 * (size_t)(nlev + 1), 0.0);
-  {
-    const double dts = s.dt_s, beta = s.beta;
-    for (int k = 0; k <= nlev; ++k) {
-      double* c = &colc[8 * (size_t)k];
-      if (k < nlev) {
-        c[0] = dts * s.rd_o_cvd / dz[k];
-        c[1] = dts * (1.0 - beta) / dz[k];
-        c[2] = dts * beta / dz[k];
-      }
-      if (k >= 1 && k < nlev) {
-        c[3] = dts * p->cpd * (1.0 - beta) * inv_dzh[k];
-        c[4] = dts * p->cpd * dref[k];
-        c[5] = dts * p->cpd * beta * inv_dzh[k];
-        c[6] = wgt[k];
-        c[7] = 1.0 - wgt[k];
-      }
-    }
-  }
+  ColumnMetrics cm0;
+  column_metrics(z_ifc, nlev, *p, s, &cm0);
+  std::vector<double>& dz = cm0.dz;
+  std::vector<double>& inv_dz = cm0.inv_dz;
+  std::vector<double>& inv_dzh = cm0.inv_dzh;
+  std::vector<double>& wgt = cm0.wgt;
+  std::vector<double>& dref = cm0.dref;
+  std::vector<double>& ray = cm0.ray;
+  std::vector<double>& colc = cm0.colc;
+  d->theta_ref = cm0.theta_ref;
+  d->exner_ref = cm0.exner_ref;
   // reference density: the offset of the FP32 rho perturbation (mixed mode)
   std::vector<double> rho_ref(nlev);
   for (int k = 0; k < nlev; ++k)
@@ -572,6 +577,42 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     m.w_p = A.alloc<float>(ch);
   }
 
+  // terrain: per-column reference state and column-solve table, and the
+  // stencils' per-point metrics in their compute type
+  if (z_cols) {
+    en.terrain = true;
+    v.exner_ref_c = A.upload(ht.exner_ref_c);
+    v.theta_ref_c = A.upload(ht.theta_ref_c);
+    v.dz_c = A.upload(ht.dz_c);
+    if (p->precision == ICON_PREC_MIXED) {
+      std::vector<float> pairs(2 * ht.colt.size());
+      for (size_t i = 0; i < ht.colt.size(); ++i) split_hl(ht.colt[i], &pairs[2 * i]);
+      v.colt = reinterpret_cast<const double*>(A.upload(pairs));
+    } else {
+      v.colt = A.upload(ht.colt);
+    }
+    auto build_terr = [&](auto& x, auto tag) {
+      using T = decltype(tag);
+      auto up = [&](const std::vector<double>& src) { return A.upload(std::vector<T>(src.begin(), src.end())); };
+      TerrT<T>& t = x.tr;
+      t.wgt_e = up(ht.wgt_e);
+      t.inv_dz_e = up(ht.inv_dz_e);
+      t.ddxn_ifc = up(ht.ddxn_ifc);
+      t.ddxt_ifc = up(ht.ddxt_ifc);
+      t.ddxn_mc = up(ht.ddxn_mc);
+      t.inv_dzh_c = up(ht.inv_dzh_c);
+      t.inv_dzm_c = up(ht.inv_dzm_c);
+      t.fx_ratio = up(ht.fx_ratio);
+      t.wcc0 = A.template alloc<T>(ch);
+      t.wcc1 = A.template alloc<T>(ch);
+    };
+    if (p->precision == ICON_PREC_FP64)
+      build_terr(en.c64, double{});
+    else
+      build_terr(en.c32, float{});
+    std::vector<double>().swap(ht.colt);  // the largest host copy, released early
+  }
+
   // FP64 work of the column solve and the predicted state
   DevWork& w = en.wk;
   w.div_m = A.alloc<double>(cf);
@@ -590,10 +631,11 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   }
   if (A.status == cudaSuccess) {
     cudaError_t e = init_column_kernels();
+    if (e == cudaSuccess && z_cols) e = init_column_terrain_kernels();
     if (e != cudaSuccess) A.status = e;
   }
   if (A.status != cudaSuccess) {
-    std::string m = std::string("icon_dycore_create: ") + cudaGetErrorString(A.status);
+    std::string m = fname + ": " + cudaGetErrorString(A.status);
     A.release();
     if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
     delete d;
@@ -604,13 +646,15 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
     const DevVert& vv = en.v;
     const bool vert_ok = vv.dz && vv.inv_dz && vv.inv_dzh && vv.wgt && vv.theta_ref && vv.exner_ref &&
                          vv.dexner_ref_ic && vv.ray_fac && vv.colc && vv.lev_hl && vv.lev64;
-    const bool ok = vert_ok && grid_complete(en.g64) && work_complete(en.wk) &&
+    const bool terr_ok = !z_cols || (vv.exner_ref_c && vv.theta_ref_c && vv.dz_c && vv.colt &&
+                                     (mixed ? terrain_complete(en.c32.tr) : terrain_complete(en.c64.tr)));
+    const bool ok = vert_ok && terr_ok && grid_complete(en.g64) && work_complete(en.wk) &&
                     (mixed ? grid_complete(en.c32.g) : grid_complete(en.c64.g));
     if (!ok) {
       A.release();
       cudaStreamDestroy(d->cap_stream);
       delete d;
-      return fail(ICON_ERR_CUDA, "icon_dycore_create: internal error: a coefficient or work array is missing");
+      return fail(ICON_ERR_CUDA, fname + ": internal error: a coefficient or work array is missing");
     }
   }
   for (int k = 0; k < kNumStencils; ++k) en.threads[k] = 256;
@@ -628,6 +672,10 @@ int icon_dycore_create(const icon_grid_t* grid, int32_t nlev, const double* z_if
   *out = d;
   return ICON_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int icon_dycore_destroy(icon_dycore_t* d) {
   if (!d) return ICON_OK;
@@ -1000,14 +1048,34 @@ int icon_velocity_tendencies(icon_dycore_t* d, const double* vn, const double* w
   if (!d || !vn || !w || !ddt_vn || !ddt_w) return fail(ICON_ERR_ARG, "icon_velocity_tendencies: NULL argument");
   if (d->en.precision != ICON_PREC_FP64)
     return fail(ICON_ERR_UNSUPPORTED, "icon_velocity_tendencies: stage output is provided in FP64 mode only");
-  launch_velocity_tendencies<double>(d->en.c64, vn, w, ddt_vn, ddt_w, nullptr, nullptr, d->stream, d->en.threads);
+  launch_velocity_tendencies<double>(d->en.c64, vn, w, ddt_vn, ddt_w, nullptr, nullptr, d->stream, d->en.threads,
+                                     d->en.terrain ? d->en.c64.tr.wcc0 : nullptr);
   CUDA_TRY(cudaGetLastError());
   if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
   return ICON_OK;
 }
 
+int icon_dycore_reference_columns(const icon_dycore_t* d, double* theta_ref, double* exner_ref) {
+  if (!d || !theta_ref || !exner_ref) return fail(ICON_ERR_ARG, "icon_dycore_reference_columns: NULL argument");
+  const size_t nc = d->grid->host.nc, nlev = d->nlev;
+  if (d->en.terrain) {
+    CUDA_TRY(cudaMemcpy(theta_ref, d->en.v.theta_ref_c, nc * nlev * sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(exner_ref, d->en.v.exner_ref_c, nc * nlev * sizeof(double), cudaMemcpyDeviceToHost));
+    return ICON_OK;
+  }
+  for (size_t c = 0; c < nc; ++c) {
+    std::memcpy(theta_ref + c * nlev, d->theta_ref.data(), nlev * sizeof(double));
+    std::memcpy(exner_ref + c * nlev, d->exner_ref.data(), nlev * sizeof(double));
+  }
+  return ICON_OK;
+}
+
 int icon_dycore_reference_state(const icon_dycore_t* d, double* theta_ref, double* exner_ref) {
   if (!d || !theta_ref || !exner_ref) return fail(ICON_ERR_ARG, "icon_dycore_reference_state: NULL argument");
+  if (d->en.terrain)
+    return fail(ICON_ERR_UNSUPPORTED,
+                "icon_dycore_reference_state: the reference state varies by column over terrain; use "
+                "icon_dycore_reference_columns");
   std::memcpy(theta_ref, d->theta_ref.data(), d->nlev * sizeof(double));
   std::memcpy(exner_ref, d->exner_ref.data(), d->nlev * sizeof(double));
   return ICON_OK;

@@ -65,6 +65,23 @@ struct VertT {
   const double* exner_ref;  // [nlev] (FP64 mode: exner perturbation)
 };
 
+// Terrain-following vertical coordinate (half-level heights per column): the
+// per-point metrics of the stencil kernels in the compute type T, all null
+// over flat ground.  Edge heights are the mean of the two cells'; slopes are
+// those of the coordinate surfaces.
+template <class T>
+struct TerrT {
+  const T* wgt_e;     // [ne*(nlev+1)] interpolation weight of level k-1 at edge half level k (0 at the ends)
+  const T* inv_dz_e;  // [ne*nlev] 1/(edge layer thickness)
+  const T* ddxn_ifc;  // [ne*(nlev+1)] normal slope of the half levels, (z_c1 - z_c0)/d_e
+  const T* ddxt_ifc;  // [ne*(nlev+1)] tangential slope of the half levels from the vertex heights
+  const T* ddxn_mc;   // [ne*nlev] normal slope of the full levels
+  const T* inv_dzh_c; // [nc*(nlev+1)] 1/(z_mc[k-1] - z_mc[k]) per cell (0 at the ends)
+  const T* inv_dzm_c; // [nc*nlev] 1/(z_mc[k-1] - z_mc[k+1]) per cell, one-sided at the top and the ground
+  const T* fx_ratio;  // [nc*3*nlev] dz_e / dz_c of the cell's three edges (horizontal flux thickness)
+  T *wcc0, *wcc1;     // work [nc*(nlev+1)]: contravariant correction of the predictor's and corrector's winds
+};
+
 // Scalars of the stencil kernels in the compute type T.
 template <class T>
 struct ScalT {
@@ -93,6 +110,16 @@ struct DevVert {
   const float* lev_hl;     // [(nlev+1)*32]
   // the same 16 quantities per level in FP64, lev64[16 k + j]
   const double* lev64;     // [(nlev+1)*16]
+  // terrain (null over flat ground): the reference state per column and the
+  // column solve's per-level quantities per column, slot-major and level-major
+  // colt[(j * (nlev+1) + k) * nc + c] (slots 0..11 as lev64; FP64 in FP64
+  // mode, double-word pairs in 8-byte slots in mixed mode).  The per-level
+  // tables above then hold column 0's values: the offsets of the mixed
+  // mode's FP32 perturbations (any horizontally uniform profile serves).
+  const double* exner_ref_c;  // [nc*nlev]
+  const double* theta_ref_c;  // [nc*nlev]
+  const double* dz_c;         // [nc*nlev]
+  const double* colt;         // [12*(nlev+1)*nc]
 };
 
 // double -> (hi, lo) FP32 pair with hi + lo = x to about 48 bits
@@ -200,6 +227,34 @@ struct HostGrid {
   std::vector<double> curl_v, c2v_w, uv_w, coriolis_z, edge_area, uv_c;
   double mean_area;
 };
+
+// Vertical metrics, reference state, Rayleigh factors and column-solve
+// coefficients of one column of half-level heights z[nlev+1] (top first).
+// One routine for the flat grid and every terrain column, so that equal
+// columns get bit-identical metrics.
+struct ColumnMetrics {
+  std::vector<double> z_mc, dz, inv_dz;      // [nlev]
+  std::vector<double> inv_dzh, wgt, dref;    // [nlev+1], 0 at the top and the ground
+  std::vector<double> theta_ref, exner_ref;  // [nlev]
+  std::vector<double> ray;                   // [nlev+1] (1 where Rayleigh damping is off)
+  std::vector<double> colc;                  // [(nlev+1)*8], layout of DevVert::colc
+};
+void column_metrics(const double* z, int nlev, const icon_dycore_params_t& p, const Scalars& s, ColumnMetrics* m);
+
+// Terrain metrics on the host (see TerrT and the terrain part of DevVert).
+struct HostTerrain {
+  std::vector<double> exner_ref_c, theta_ref_c, dz_c, inv_dzm_c;  // [nc*nlev]
+  std::vector<double> inv_dzh_c;                                  // [nc*(nlev+1)]
+  std::vector<double> fx_ratio;                                   // [nc*3*nlev]
+  std::vector<double> colt;                                       // [12*(nlev+1)*nc]
+  std::vector<double> wgt_e, ddxn_ifc, ddxt_ifc;                  // [ne*(nlev+1)]
+  std::vector<double> inv_dz_e, ddxn_mc;                          // [ne*nlev]
+};
+// Validates the per-column heights z_ifc[nc*(nlev+1)] (finite, strictly
+// decreasing in every column, one common model top) and derives the terrain
+// metrics; returns an error message or "".
+std::string build_terrain(const HostGrid& g, int nlev, const double* z_ifc, const icon_dycore_params_t& p,
+                          const Scalars& s, HostTerrain* t);
 
 // Records `msg` as the calling thread's last error and returns `code`.
 int report_error(int code, const std::string& msg);

@@ -62,6 +62,7 @@ struct Ctx {
   VertT<T> v;
   ScalT<T> s;
   WorkT<T> w;
+  TerrT<T> tr;   // terrain metrics (all null over flat ground)
 };
 
 // Device-side state of one dycore: FP64 factors and column-solve work, the
@@ -80,16 +81,19 @@ struct Engine {
   // stencil kernel (by kernel id) and the level-chunk depth of the column solve
   int threads[32] = {};
   int col_kc = 4;
+  bool terrain = false;  // per-column heights: the terrain forms of the kernels
 };
 
 // Rows A1-A4 on (vn, w) in compute type T: writes ddt_vn [ne*nlev] and ddt_w
 // [nc*(nlev+1)].  With divd2 != nullptr also the divergence-damping Laplacian
 // of divd (A8).
+// With terrain metrics in x.tr, the contravariant correction of vn goes to wcc
+// (cells, half levels) and the advection uses w - wcc.
 template <class T>
 void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
-                                T* divd2, cudaStream_t s, const int* threads = nullptr);
+                                T* divd2, cudaStream_t s, const int* threads = nullptr, T* wcc = nullptr);
 // Stencil kernel ids (index of Engine::threads) and their base names.
-constexpr int kNumStencils = 14;
+constexpr int kNumStencils = 15;
 extern const char* const kStencilNames[kNumStencils];
 // Fill n doubles with v (the autotuner's temporary state).
 void launch_fill(double* p, size_t n, double v, cudaStream_t s);
@@ -107,6 +111,11 @@ void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t 
 template <class T>
 void launch_column(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
                    cudaStream_t s);
+// The same over terrain: per-column metrics (en.v.colt) and the solve in
+// w - wcc, wcc the contravariant correction (cells, half levels, type T).
+template <class T>
+void launch_column_terrain(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
+                           const T* wcc, cudaStream_t s);
 // Diagnostics: per-cell ps and T850 (either may be null), per-block partial
 // column masses [diag_partials(nc)] and a non-finite flag (set to 1, never cleared).
 int diag_partials(int nc);
@@ -142,5 +151,6 @@ void launch_targets(const Engine& en, const StateView& reduced, const StateView&
 void launch_blocked(bool to_blocked, int n, int nlev_x, int nproma, const double* src, double* dst, cudaStream_t s);
 // One-time kernel attributes (dynamic shared memory above 48 KB).
 cudaError_t init_column_kernels();
+cudaError_t init_column_terrain_kernels();
 
 }  // namespace icon

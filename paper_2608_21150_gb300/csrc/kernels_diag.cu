@@ -14,7 +14,9 @@ namespace {
 
 constexpr int kDiagThreads = 256;
 
-__global__ void diag_columns(int nc, int nlev, const double* __restrict__ dz, const double* __restrict__ area,
+// dz_c: per-column layer thicknesses over terrain (NULL: the per-level dz)
+__global__ void diag_columns(int nc, int nlev, const double* __restrict__ dz, const double* __restrict__ dz_c,
+                             const double* __restrict__ area,
                              double grav, double cpd, double rd, double p00, const double* __restrict__ w,
                              const double* __restrict__ rho, const double* __restrict__ exner,
                              const double* __restrict__ theta, double* __restrict__ ps, double* __restrict__ t850,
@@ -27,16 +29,17 @@ __global__ void diag_columns(int nc, int nlev, const double* __restrict__ dz, co
     const double* th = theta + (size_t)c * nlev;
     const double* r = rho + (size_t)c * nlev;
     const double* wc = w + (size_t)c * (nlev + 1);
+    const double* dzk = dz_c ? dz_c + (size_t)c * nlev : dz;
     bool finite = true;
     for (int k = 0; k < nlev; ++k) {
       finite = finite && isfinite(ex[k]) && isfinite(th[k]) && isfinite(r[k]) && isfinite(wc[k]);
-      m += r[k] * dz[k];
+      m += r[k] * dzk[k];
     }
     finite = finite && isfinite(wc[nlev]);
     if (!finite) atomicOr(bad, 1);
     m *= area[c];
     const double kappa_inv = cpd / rd;
-    const double z_low = 0.5 * dz[nlev - 1];  // flat ground: lowest full level at dz/2
+    const double z_low = 0.5 * dzk[nlev - 1];  // the lowest full level, dz/2 above the ground
     const double ex_sfc = ex[nlev - 1] + grav * z_low / (cpd * th[nlev - 1]);
     if (ps) ps[c] = p00 * pow(ex_sfc, kappa_inv);
     if (t850) {
@@ -78,7 +81,7 @@ int diag_partials(int nc) { return (nc + kDiagThreads - 1) / kDiagThreads; }
 void launch_diagnostics(const Engine& en, const double* area, const StateView& st, double* ps, double* t850,
                         double* partial, int* bad, cudaStream_t s) {
   const int nc = en.g64.nc, nlev = en.v.nlev;
-  ICON_LAUNCH("diag_columns", (unsigned)diag_partials(nc), kDiagThreads, s, diag_columns, nc, nlev, en.v.dz, area,
+  ICON_LAUNCH("diag_columns", (unsigned)diag_partials(nc), kDiagThreads, s, diag_columns, nc, nlev, en.v.dz, en.v.dz_c, area,
               en.sc.grav, en.sc.cpd, en.sc.rd, en.sc.p00, st.w, st.rho, st.exner, st.theta_v, ps, t850, partial,
               bad);
   const size_t nvn = (size_t)en.g64.ne * nlev;

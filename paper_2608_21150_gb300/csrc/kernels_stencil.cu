@@ -124,6 +124,45 @@ __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
 }
 
 // -------------------------------------------------------------------------
+// A1-A2 over terrain: contravariant correction at cell half levels, the
+// vertical velocity of a parcel that follows the coordinate surface,
+//   wcc = sum_e q_e (vn_ie dz/dn + vt_ie dz/dt)
+// with vn, vt interpolated to the edge half levels by the edge weights (the
+// lowest full level's values at the ground; the slopes vanish at the flat
+// model top, where wcc = 0).
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void va_concorr(GridT<T> g, VertT<T> v, TerrT<T> tr, const T* __restrict__ vn, const T* __restrict__ vt,
+                           T* __restrict__ wcc) {
+  int c, k;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  if (!flat_index(g.nc, nlevp, c, k)) return;
+  T s = 0;
+  if (k > 0) {
+    const int* ce = g.c2e + 3 * (size_t)c;
+    const T* q = g.e2c_w + 3 * (size_t)c;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int e = ce[j];
+      const T* x = vn + (size_t)e * nlev;
+      const T* y = vt + (size_t)e * nlev;
+      const size_t ih = (size_t)e * nlevp + k;
+      T a, b;
+      if (k == nlev) {
+        a = x[nlev - 1];
+        b = y[nlev - 1];
+      } else {
+        const T wg = tr.wgt_e[ih];
+        a = x[k] + wg * (x[k - 1] - x[k]);
+        b = y[k] + wg * (y[k - 1] - y[k]);
+      }
+      s += q[j] * (a * tr.ddxn_ifc[ih] + b * tr.ddxt_ifc[ih]);
+    }
+  }
+  wcc[(size_t)c * nlevp + k] = s;
+}
+
+// -------------------------------------------------------------------------
 // A2: cells: K_c = sum q_e K_e  (and, in the corrector, the divergence-damping
 //     Laplacian dd2 = lapc(div vn*));  vertices: zeta = curl vn (full levels),
 //     w_v = sum r_c w_c (half levels).  One launch over nc*nlev + nv*(nlev+1).
@@ -179,10 +218,13 @@ __global__ void va_cell_vert(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
 //   ddt_vn = -(K_c1 - K_c0)/d + (zeta_e + f) vt - wbar (vn_ie_k - vn_ie_k+1)/dz
 //   gw_e   = vn_ie (w_c1 - w_c0)/d + vt_ie (w_vp - w_vm)/l
 // -------------------------------------------------------------------------
-template <class T>
+// Over terrain (kTerr): edge interpolation weights and layer thicknesses, and
+// the contravariant velocity w - wcc as the advecting vertical velocity.
+template <class T, bool kTerr = false>
 __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, const T* __restrict__ w,
                              const T* __restrict__ vt, const T* __restrict__ ekin_c, const T* __restrict__ zeta,
-                             const T* __restrict__ w_v, T* __restrict__ ddt_vn, T* __restrict__ gw_e) {
+                             const T* __restrict__ w_v, T* __restrict__ ddt_vn, T* __restrict__ gw_e, TerrT<T> tr,
+                             const T* __restrict__ wcc) {
   int e, k;
   const int nlev = v.nlev, nlevp = nlev + 1;
   if (!flat_index(g.ne, nlevp, e, k)) return;
@@ -191,27 +233,35 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
   const T inv_d = g.inv_d[e];
   const T* vne = vn + (size_t)e * nlev;
   const T* vte = vt + (size_t)e * nlev;
+  auto wg = [&](int kh) -> T { return kTerr ? tr.wgt_e[(size_t)e * nlevp + kh] : v.wgt[kh]; };
   // vn at half levels k and k+1 (top: vn_0, ground: vn_{nlev-1})
   // linear interpolation to half level kh written as x_kh + wgt (x_kh-1 - x_kh)
   auto vn_ie = [&](int kh) -> T {
     if (kh == 0) return vne[0];
     if (kh == nlev) return vne[nlev - 1];
-    return vne[kh] + v.wgt[kh] * (vne[kh - 1] - vne[kh]);
+    return vne[kh] + wg(kh) * (vne[kh - 1] - vne[kh]);
   };
   const T vnie_k = vn_ie(k);
   if (k < nlev) {
     const T vnie_k1 = vn_ie(k + 1);
     const T* w0 = w + (size_t)c0 * nlevp;
     const T* w1 = w + (size_t)c1 * nlevp;
-    const T wbar = T(0.25) * ((w0[k] + w0[k + 1]) + (w1[k] + w1[k + 1]));
+    T wbar;
+    if constexpr (kTerr) {
+      const T* q0 = wcc + (size_t)c0 * nlevp;
+      const T* q1 = wcc + (size_t)c1 * nlevp;
+      wbar = T(0.25) * (((w0[k] - q0[k]) + (w0[k + 1] - q0[k + 1])) + ((w1[k] - q1[k]) + (w1[k + 1] - q1[k + 1])));
+    } else {
+      wbar = T(0.25) * ((w0[k] + w0[k + 1]) + (w1[k] + w1[k + 1]));
+    }
     const T zeta_e = T(0.5) * (zeta[(size_t)vm * nlev + k] + zeta[(size_t)vp * nlev + k]);
     const T dkdn = (ekin_c[(size_t)c1 * nlev + k] - ekin_c[(size_t)c0 * nlev + k]) * inv_d;
-    const T dvdz = (vnie_k - vnie_k1) * v.inv_dz[k];
+    const T dvdz = (vnie_k - vnie_k1) * (kTerr ? tr.inv_dz_e[(size_t)e * nlev + k] : v.inv_dz[k]);
     ddt_vn[(size_t)e * nlev + k] = -dkdn + (zeta_e + g.f_e[e]) * vte[k] - wbar * dvdz;
   }
   T gw = 0;
   if (k > 0 && k < nlev) {
-    const T vtie = vte[k] + v.wgt[k] * (vte[k - 1] - vte[k]);
+    const T vtie = vte[k] + wg(k) * (vte[k - 1] - vte[k]);
     const T dwdn = (w[(size_t)c1 * nlevp + k] - w[(size_t)c0 * nlevp + k]) * inv_d;
     const T dwdt = (w_v[(size_t)vp * nlevp + k] - w_v[(size_t)vm * nlevp + k]) * g.inv_l[e];
     gw = vnie_k * dwdn + vtie * dwdt;
@@ -223,9 +273,10 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
 // A4: w advective tendency at interior half levels (0 at top and ground)
 //   ddt_w = -sum q_e gw_e - w (wf_{k-1} - wf_k)/dzh,  wf full-level averages
 // -------------------------------------------------------------------------
-template <class T>
+// Over terrain (kTerr): advected by w - wcc, per-cell half-level spacing.
+template <class T, bool kTerr = false>
 __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const T* __restrict__ gw_e,
-                          T* __restrict__ ddt_w) {
+                          T* __restrict__ ddt_w, TerrT<T> tr, const T* __restrict__ wcc) {
   const int nlev = v.nlev, nlevp = nlev + 1;
   if constexpr (kMixed<T>) {
     const int c = warp_point();
@@ -243,7 +294,12 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
         T h = q0 * g0[k];
         h += q1 * g1[k];
         h += q2 * g2[k];
-        r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+        if constexpr (kTerr) {
+          const size_t ih = (size_t)c * nlevp + k;
+          r = -h - (wc[k] - wcc[ih]) * (T(0.5) * (wc[k - 1] - wc[k + 1])) * tr.inv_dzh_c[ih];
+        } else {
+          r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+        }
       }
       ddt_w[(size_t)c * nlevp + k] = r;
     }
@@ -260,7 +316,12 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
     h += q[2] * gw_e[(size_t)ce[2] * nlevp + k];
     const T* wc = w + (size_t)c * nlevp;
     // the difference of the full-level means above and below, (w_k-1 - w_k+1) / 2
-    r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+    if constexpr (kTerr) {
+      const size_t ih = (size_t)c * nlevp + k;
+      r = -h - (wc[k] - wcc[ih]) * (T(0.5) * (wc[k - 1] - wc[k + 1])) * tr.inv_dzh_c[ih];
+    } else {
+      r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+    }
   }
   ddt_w[(size_t)c * nlevp + k] = r;
 }
@@ -270,10 +331,12 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
 // mixed mode: the reference is horizontally uniform) in each cell's local
 // frame: grad4 = (drho_x, drho_y, dth_x, dth_y) as 4 planes [4][nc*nlev].
 // -------------------------------------------------------------------------
-template <class T>
+// exner_ref_c: the per-column reference exner over terrain (kTerr).
+template <class T, bool kTerr = false>
 __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, const T* __restrict__ theta,
                              T* __restrict__ grad4, const double* __restrict__ exner,
-                             const double* __restrict__ exner_pr, double exfac, double* __restrict__ pex) {
+                             const double* __restrict__ exner_pr, double exfac, double* __restrict__ pex,
+                             const double* __restrict__ exner_ref_c) {
   int c, k;
   const int nlev = v.nlev;
   if (!flat_index(g.nc, nlev, c, k)) return;
@@ -281,14 +344,15 @@ __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, 
   const int* cc = g.c2e2c + 3 * (size_t)c;
   const T* G = g.grad_c + 6 * (size_t)c;
   const size_t i = (size_t)c * nlev + k;
+  const double ex_ref = kTerr ? exner_ref_c[i] : v.exner_ref[k];
   // extrapolated exner perturbation (1 + a) pr - a pr_old of this cell, for the
   // pressure gradient at its edges: FP64, or a double-word pair in mixed mode
   // (exner is near 1, the difference across an edge ~1e-5 of it)
   if constexpr (kMixed<T>) {
     const df a = to_df(1.0 + exfac), b = to_df(exfac);
-    reinterpret_cast<df*>(pex)[i] = a * (to_df(exner[i]) - to_df(v.exner_ref[k])) - b * to_df(exner_pr[i]);
+    reinterpret_cast<df*>(pex)[i] = a * (to_df(exner[i]) - to_df(ex_ref)) - b * to_df(exner_pr[i]);
   } else {
-    pex[i] = (1.0 + exfac) * (exner[i] - v.exner_ref[k]) - exfac * exner_pr[i];
+    pex[i] = (1.0 + exfac) * (exner[i] - ex_ref) - exfac * exner_pr[i];
   }
   const size_t i0 = (size_t)cc[0] * nlev + k, i1 = (size_t)cc[1] * nlev + k, i2 = (size_t)cc[2] * nlev + k;
   const T r = rho[i], t = theta[i];
@@ -309,13 +373,17 @@ __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, 
 // difference across the edge is taken in FP64 (double-word FP32 in mixed
 // mode): neighbouring perturbations agree to 4-5 digits, more than FP32 carries.
 // -------------------------------------------------------------------------
-template <class T>
+// Over terrain (kTerr) the pressure gradient is taken along the true
+// horizontal: the along-level difference minus the slope of the full level
+// times the edge mean of the two cells' vertical derivatives (centred, one-
+// sided at the top and the ground) of the extrapolated exner perturbation.
+template <class T, bool kTerr = false>
 __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ vn,
                              const T* __restrict__ vt, const T* __restrict__ ddt_vn, const T* __restrict__ rho,
                              const T* __restrict__ theta, const double* __restrict__ pex,
                              const double* __restrict__ inv_d64, const T* __restrict__ grad4, T* __restrict__ rho_e,
                              T* __restrict__ theta_e,
-                             T* __restrict__ hpg, T* __restrict__ vn_p) {
+                             T* __restrict__ hpg, T* __restrict__ vn_p, TerrT<T> tr) {
   int e, k;
   const int nlev = v.nlev;
   if (!flat_index(g.ne, nlev, e, k)) return;
@@ -339,11 +407,26 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
   const size_t i0 = (size_t)c0 * nlev + k, i1 = (size_t)c1 * nlev + k;
   T h;
+  const int km = k > 0 ? k - 1 : 0, kp = k + 1 < nlev ? k + 1 : nlev - 1;
   if constexpr (kMixed<T>) {
     const df* p = reinterpret_cast<const df*>(pex);
-    h = sc.cpd * te * (to_float(p[i1] - p[i0]) * g.inv_d[e]);
+    if constexpr (kTerr) {
+      const size_t b0 = (size_t)c0 * nlev, b1 = (size_t)c1 * nlev;
+      const T dz0 = to_float(p[b0 + km] - p[b0 + kp]) * tr.inv_dzm_c[i0];
+      const T dz1 = to_float(p[b1 + km] - p[b1 + kp]) * tr.inv_dzm_c[i1];
+      h = sc.cpd * te * (to_float(p[i1] - p[i0]) * g.inv_d[e] - tr.ddxn_mc[ie] * (T(0.5) * (dz0 + dz1)));
+    } else {
+      h = sc.cpd * te * (to_float(p[i1] - p[i0]) * g.inv_d[e]);
+    }
   } else {
-    h = sc.cpd * te * (T)((pex[i1] - pex[i0]) * inv_d64[e]);
+    if constexpr (kTerr) {
+      const size_t b0 = (size_t)c0 * nlev, b1 = (size_t)c1 * nlev;
+      const double dz0 = (pex[b0 + km] - pex[b0 + kp]) * tr.inv_dzm_c[i0];
+      const double dz1 = (pex[b1 + km] - pex[b1 + kp]) * tr.inv_dzm_c[i1];
+      h = sc.cpd * te * (T)((pex[i1] - pex[i0]) * inv_d64[e] - tr.ddxn_mc[ie] * (0.5 * (dz0 + dz1)));
+    } else {
+      h = sc.cpd * te * (T)((pex[i1] - pex[i0]) * inv_d64[e]);
+    }
   }
   rho_e[ie] = re;
   theta_e[ie] = te;
@@ -400,9 +483,10 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
 // The predictor launch also updates the exner extrapolation history,
 // exner_pr = exner - exner_ref (sn_edge_pred, its last reader, has completed).
 // -------------------------------------------------------------------------
-template <class T>
+template <class T, bool kTerr = false>
 __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ divd,
-                            const double* __restrict__ exner, double* __restrict__ exner_pr) {
+                            const double* __restrict__ exner, double* __restrict__ exner_pr,
+                            const double* __restrict__ exner_ref_c) {
   const int nlev = v.nlev;
   if constexpr (kMixed<T>) {
     const int c = warp_point();
@@ -416,7 +500,7 @@ __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
     for (int k = lane_id(); k < nlev; k += 32) {
       const size_t i = (size_t)c * nlev + k;
       divd[i] = dv0 * x0[k] + dv1 * x1[k] + dv2 * x2[k];
-      if (exner_pr) exner_pr[i] = exner[i] - v.exner_ref[k];
+      if (exner_pr) exner_pr[i] = exner[i] - (kTerr ? exner_ref_c[i] : v.exner_ref[k]);
     }
     return;
   }
@@ -427,7 +511,7 @@ __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
   const size_t i = (size_t)c * nlev + k;
   divd[i] = dv[0] * vn[(size_t)ce[0] * nlev + k] + dv[1] * vn[(size_t)ce[1] * nlev + k] +
             dv[2] * vn[(size_t)ce[2] * nlev + k];
-  if (exner_pr) exner_pr[i] = exner[i] - v.exner_ref[k];
+  if (exner_pr) exner_pr[i] = exner[i] - (kTerr ? exner_ref_c[i] : v.exner_ref[k]);
 }
 
 // -------------------------------------------------------------------------
@@ -437,11 +521,14 @@ __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
 //   vf_e = vn_e + divflux (D_c1 - D_c0)/d_e,  F_e = rho_e vf_e,
 //   div_m = sum s l F / A,  div_t = sum s l F theta_e / A
 // -------------------------------------------------------------------------
-template <class T>
+// Over terrain (kTerr) each flux carries its edge layer thickness over the
+// cell's, fx_ratio = dz_e / dz_c: div_m = (1/dz_c) sum s l F dz_e / A.
+template <class T, bool kTerr = false>
 __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ vn,
                                 const T* __restrict__ divd, const T* __restrict__ rho_e,
                                 const T* __restrict__ theta_e, const double* __restrict__ div_c64,
-                                double* __restrict__ div_m, double* __restrict__ div_t) {
+                                double* __restrict__ div_m, double* __restrict__ div_t,
+                                const T* __restrict__ fx_ratio) {
   const int nlev = v.nlev;
   if constexpr (kMixed<T>) {
     // FP32 fluxes, sums in double-word FP32: FP64-grade accumulation (mass
@@ -469,7 +556,8 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
       for (int j = 0; j < 3; ++j) {
         const size_t ie = be[j] + k;
         const T vf = vn[ie] + fd[j] * (divd[bd1[j] + k] - divd[bd0[j] + k]);
-        const T f = rho_e[ie] * vf;
+        T f = rho_e[ie] * vf;
+        if constexpr (kTerr) f = f * fx_ratio[((size_t)c * 3 + j) * nlev + k];
         const T ft = f * theta_e[ie];
         const df w = dv[j];
         dm = dm + w * f;
@@ -491,7 +579,8 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
       const size_t ie = (size_t)e * nlev + k;
       const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
       const T vf = vn[ie] + g.fdiv_e[e] * (divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k]);
-      const T f = rho_e[ie] * vf;
+      T f = rho_e[ie] * vf;
+      if constexpr (kTerr) f = f * fx_ratio[((size_t)c * 3 + j) * nlev + k];
       const T ft = f * theta_e[ie];
       dm += dv[j] * (double)f;
       dt += dv[j] * (double)ft;
@@ -709,31 +798,49 @@ __global__ void diff_cell_update(GridT<T> g, VertT<T> v, ScalT<T> sc, const doub
 // -------------------------------------------------------------------------
 template <class T>
 void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
-                                T* divd2, cudaStream_t s, const int* threads) {
+                                T* divd2, cudaStream_t s, const int* threads, T* wcc) {
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
+  const TerrT<T>& tr = x.tr;
   const int nlev = v.nlev, nlevp = nlev + 1;
+  const bool terr = tr.wgt_e != nullptr && wcc != nullptr;
   ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_by_point<T>(g.ne, nlev, TH(0)), TH(0), s,
               va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e);
+  if (terr)
+    ICON_LAUNCH(kname<T>("va_concorr", "va_concorr_f32"), blocks_for((long long)g.nc * nlevp, TH(14)), TH(14), s,
+                va_concorr<T>, g, v, tr, vn, wk.vt, wcc);
   const long long n2 = (long long)g.nc * nlev + (long long)g.nv * nlevp;
   ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, TH(1)), TH(1), s, va_cell_vert<T>, g,
               v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v);
-  ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, TH(2)), TH(2),
-              s, va_edge_tend<T>, g, v, vn, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e);
-  ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_by_point<T>(g.nc, nlevp, TH(3)), TH(3), s,
-              va_cell_w<T>, g, v, w, wk.gw_e, ddt_w);
+  if (terr) {
+    ICON_LAUNCH(kname<T>("va_edge_tend_terrain", "va_edge_tend_terrain_f32"),
+                blocks_for((long long)g.ne * nlevp, TH(2)), TH(2), s, (va_edge_tend<T, true>), g, v, vn, w, wk.vt,
+                wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr, wcc);
+    ICON_LAUNCH(kname<T>("va_cell_w_terrain", "va_cell_w_terrain_f32"), blocks_by_point<T>(g.nc, nlevp, TH(3)),
+                TH(3), s, (va_cell_w<T, true>), g, v, w, wk.gw_e, ddt_w, tr, wcc);
+  } else {
+    ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, TH(2)), TH(2),
+                s, (va_edge_tend<T, false>), g, v, vn, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr,
+                wcc);
+    ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_by_point<T>(g.nc, nlevp, TH(3)), TH(3), s,
+                (va_cell_w<T, false>), g, v, w, wk.gw_e, ddt_w, tr, wcc);
+  }
 }
 
-template <class T>
-void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
+// Rows A5-A9 of one substep; kTerr: the terrain forms, with the contravariant
+// corrections of the predictor's and the corrector's winds in x.tr.wcc0/wcc1.
+template <class T, bool kTerr>
+void substep_impl(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
   const int* threads = en.threads;
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
+  const TerrT<T>& tr = x.tr;
   const Mirrors& m = en.m;
   const int nlev = v.nlev;
   const long long nce = (long long)g.nc * nlev, nee = (long long)g.ne * nlev;
+  const double* ex_ref_c = en.v.exner_ref_c;
   // stencil views of the state: the FP64 state itself, or the FP32 mirrors
   const T *s_vn, *s_w, *s_rho, *s_th, *s_wp;
   if constexpr (kMixed<T>) {
@@ -741,27 +848,51 @@ void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cuda
   } else {
     s_vn = st.vn, s_w = st.w, s_rho = st.rho, s_th = st.theta_v, s_wp = en.wk.w_p;
   }
+  const char* nm_grad = kTerr ? kname<T>("sn_cell_grad_terrain", "sn_cell_grad_terrain_f32")
+                              : kname<T>("sn_cell_grad", "sn_cell_grad_f32");
+  const char* nm_pred = kTerr ? kname<T>("sn_edge_pred_terrain", "sn_edge_pred_terrain_f32")
+                              : kname<T>("sn_edge_pred", "sn_edge_pred_f32");
+  const char* nm_div = kTerr ? kname<T>("sn_cell_div_terrain", "sn_cell_div_terrain_f32")
+                             : kname<T>("sn_cell_div", "sn_cell_div_f32");
+  const char* nm_flx = kTerr ? kname<T>("sn_cell_fluxdiv_terrain", "sn_cell_fluxdiv_terrain_f32")
+                             : kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32");
   // ---------------- predictor ----------------
-  launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s, threads);
-  ICON_LAUNCH(kname<T>("sn_cell_grad", "sn_cell_grad_f32"), blocks_for(nce, TH(4)), TH(4), s, sn_cell_grad<T>, g, v, s_rho, s_th,
-              wk.grad4, st.exner, st.exner_pr, en.sc.exfac, en.wk.pex);
-  ICON_LAUNCH(kname<T>("sn_edge_pred", "sn_edge_pred_f32"), blocks_for(nee, TH(5)), TH(5), s, sn_edge_pred<T>, g, v, x.s, s_vn, wk.vt,
-              wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p);
-  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, sn_cell_div<T>, g, v, wk.vn_p, wk.divd,
-              st.exner, st.exner_pr);
-  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
-              wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
-  launch_column<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, s);
+  launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s, threads,
+                                kTerr ? tr.wcc0 : nullptr);
+  ICON_LAUNCH(nm_grad, blocks_for(nce, TH(4)), TH(4), s, (sn_cell_grad<T, kTerr>), g, v, s_rho, s_th, wk.grad4,
+              st.exner, st.exner_pr, en.sc.exfac, en.wk.pex, ex_ref_c);
+  ICON_LAUNCH(nm_pred, blocks_for(nee, TH(5)), TH(5), s, (sn_edge_pred<T, kTerr>), g, v, x.s, s_vn, wk.vt,
+              wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p, tr);
+  ICON_LAUNCH(nm_div, blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, wk.vn_p,
+              wk.divd, st.exner, st.exner_pr, ex_ref_c);
+  ICON_LAUNCH(nm_flx, blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, (sn_cell_fluxdiv<T, kTerr>), g, v, x.s,
+              wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t, tr.fx_ratio);
+  if constexpr (kTerr)
+    launch_column_terrain<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, tr.wcc0, s);
+  else
+    launch_column<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, s);
   // ---------------- corrector ----------------
-  launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s, threads);
-  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_by_point<T>(g.ne, nlev, TH(8)), TH(8), s, sn_edge_corr<T>, g, v, x.s, st.vn,
-              wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn);
+  launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s, threads,
+                                kTerr ? tr.wcc1 : nullptr);
+  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_by_point<T>(g.ne, nlev, TH(8)), TH(8), s,
+              sn_edge_corr<T>, g, v, x.s, st.vn, wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn);
   const T* vn_new = kMixed<T> ? (const T*)m.vn : (const T*)st.vn;
-  ICON_LAUNCH(kname<T>("sn_cell_div", "sn_cell_div_f32"), blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, sn_cell_div<T>, g, v, vn_new, wk.divd,
-              nullptr, nullptr);
-  ICON_LAUNCH(kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32"), blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, sn_cell_fluxdiv<T>, g, v, x.s,
-              vn_new, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t);
-  launch_column<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, s);
+  ICON_LAUNCH(nm_div, blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, vn_new,
+              wk.divd, nullptr, nullptr, ex_ref_c);
+  ICON_LAUNCH(nm_flx, blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, (sn_cell_fluxdiv<T, kTerr>), g, v, x.s,
+              vn_new, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t, tr.fx_ratio);
+  if constexpr (kTerr)
+    launch_column_terrain<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, tr.wcc1, s);
+  else
+    launch_column<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, s);
+}
+
+template <class T>
+void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
+  if (en.terrain)
+    substep_impl<T, true>(en, x, st, s);
+  else
+    substep_impl<T, false>(en, x, st, s);
 }
 
 template <class T>
@@ -807,7 +938,7 @@ void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
 const char* const kStencilNames[kNumStencils] = {
     "va_edge_pre", "va_cell_vert", "va_edge_tend", "va_cell_w", "sn_cell_grad", "sn_edge_pred", "sn_cell_div",
     "sn_cell_fluxdiv", "sn_edge_corr", "diff_div_curl_uv", "diff_edge_smag", "diff_second", "diff_edge_update",
-    "diff_cell_update"};
+    "diff_cell_update", "va_concorr"};
 
 void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t s) {
   const int nlev = en.v.nlev;
@@ -817,7 +948,7 @@ void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t 
 }
 
 template void launch_velocity_tendencies<double>(const Ctx<double>&, const double*, const double*, double*, double*,
-                                                 const double*, double*, cudaStream_t, const int*);
+                                                 const double*, double*, cudaStream_t, const int*, double*);
 template void launch_substep<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
 template void launch_substep<float>(const Engine&, const Ctx<float>&, const StateView&, cudaStream_t);
 template void launch_diffusion<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);

@@ -36,11 +36,13 @@ __device__ __forceinline__ __nv_bfloat16 feature_out<__nv_bfloat16>(float f, con
 
 // Column features, one thread per (cell, level): raw FP32 rows [nc][5 nlev]
 // into raw (if given), and rows [nc][ldx] of type O into x (normalised with
-// mean/istd when given; O = BF16 requires them).
+// mean/istd when given; O = BF16 requires them).  The reference profiles are
+// per level ([nlev], ref_stride 0) or, over terrain, per column ([nc*nlev],
+// ref_stride nlev).
 template <class O>
 __global__ void col_features(int nc, int nlev, const int* __restrict__ c2e, const float* __restrict__ uv_c,
                              const double* __restrict__ exner_ref, const double* __restrict__ theta_ref,
-                             StateView st, float* __restrict__ raw, O* __restrict__ x, int ldx,
+                             int ref_stride, StateView st, float* __restrict__ raw, O* __restrict__ x, int ldx,
                              const float* __restrict__ mean, const float* __restrict__ istd) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)nc * nlev) return;
@@ -50,8 +52,9 @@ __global__ void col_features(int nc, int nlev, const int* __restrict__ c2e, cons
   const double* wc = st.w + (size_t)c * (nlev + 1);
   float f[5];
   f[0] = 0.5f * (f32(wc[k]) + f32(wc[k + 1]));
-  f[1] = f32(st.exner[ic] - exner_ref[k]);
-  f[2] = f32(st.theta_v[ic] - theta_ref[k]);
+  const size_t ir = (size_t)c * ref_stride + k;
+  f[1] = f32(st.exner[ic] - exner_ref[ir]);
+  f[2] = f32(st.theta_v[ic] - theta_ref[ir]);
   const int* ce = c2e + 3 * (size_t)c;
   const float* w = uv_c + 6 * (size_t)c;
   float u = 0.f, v = 0.f;
@@ -229,15 +232,19 @@ inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 void launch_col_features(const Engine& en, const StateView& st, float* raw, float* x, int ldx, const float* mean,
                          const float* istd, cudaStream_t s) {
   const int nc = en.g64.nc, nlev = en.v.nlev;
+  const bool tr = en.terrain;
   ICON_LAUNCH("lc_col_features", cdiv((size_t)nc * nlev, kT), kT, s, col_features<float>, nc, nlev, en.g64.c2e,
-              en.g64.uv_c, en.v.exner_ref, en.v.theta_ref, st, raw, x, ldx, mean, istd);
+              en.g64.uv_c, tr ? en.v.exner_ref_c : en.v.exner_ref, tr ? en.v.theta_ref_c : en.v.theta_ref,
+              tr ? nlev : 0, st, raw, x, ldx, mean, istd);
 }
 
 void launch_col_inputs(const Engine& en, const StateView& st, float* raw, __nv_bfloat16* x, int ldx,
                        const float* mean, const float* istd, cudaStream_t s) {
   const int nc = en.g64.nc, nlev = en.v.nlev;
+  const bool tr = en.terrain;
   ICON_LAUNCH("lc_col_inputs", cdiv((size_t)nc * nlev, kT), kT, s, col_features<__nv_bfloat16>, nc, nlev,
-              en.g64.c2e, en.g64.uv_c, en.v.exner_ref, en.v.theta_ref, st, raw, x, ldx, mean, istd);
+              en.g64.c2e, en.g64.uv_c, tr ? en.v.exner_ref_c : en.v.exner_ref, tr ? en.v.theta_ref_c : en.v.theta_ref,
+              tr ? nlev : 0, st, raw, x, ldx, mean, istd);
 }
 
 void launch_edge_features(const Engine& en, const float* colx, const double* vn, float* x, int ldx,

@@ -42,12 +42,14 @@ def rel_err(gpu, ref, od):
     oracle's reference profiles; exner_pr as is."""
     out = {}
     th_ref, ex_ref = od.reference_state()
+    if ex_ref.ndim == 1:      # per column over terrain
+        th_ref, ex_ref = th_ref[None, :], ex_ref[None, :]
     for k in ref:
         a, b = np.asarray(gpu[k]), np.asarray(ref[k])
         if k == "exner":
-            a, b = a - ex_ref[None, :], b - ex_ref[None, :]
+            a, b = a - ex_ref, b - ex_ref
         if k == "theta_v":
-            a, b = a - th_ref[None, :], b - th_ref[None, :]
+            a, b = a - th_ref, b - th_ref
         scale = np.max(np.abs(b))
         out[k] = float(np.max(np.abs(a - b)) / scale) if scale > 0 else float(np.max(np.abs(a - b)))
     return out

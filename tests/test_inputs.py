@@ -113,3 +113,21 @@ def test_perturbation_is_an_eastward_bump_of_the_given_amplitude():
     assert near.any() and np.all(du[near] > 1.9) and np.all(du[near] <= 2.0 + 1e-12)
     far = r > 0.5
     assert np.max(np.abs(dvn[far])) < 1e-6
+
+
+def test_jw_state_over_terrain_is_evaluated_at_each_columns_heights():
+    """Over per-column heights the balanced jet of a cell is the one-column
+    state at that cell's own heights; vn uses the mean of the adjacent cells'."""
+    from icon_inputs import mountain_height, terrain_following_z
+    grid, z = make_grid(2), make_vct(12)
+    zz = terrain_following_z(z, mountain_height(grid.cell_xyz))
+    st = jw_type_state(grid, zz, seed=3)
+    c = int(np.argmax(zz[:, -1]))
+    assert zz[c, -1] > 1000.0
+    one = jw_type_state(grid, zz[c], seed=3)
+    for k in ("rho", "exner", "theta_v"):
+        assert np.array_equal(st[k][c], one[k][c])
+    flat = jw_type_state(grid, z, seed=3)
+    far = int(np.argmin(zz[:, -1]))
+    assert zz[far, -1] < 1e-6 * 2000.0 or np.allclose(st["exner"][far], flat["exner"][far], rtol=1e-6)
+    assert not np.allclose(st["exner"][c], flat["exner"][c], rtol=1e-3)

@@ -202,3 +202,33 @@ def test_pressure_gradient_error_over_the_mountain_converges_at_second_order():
         along = np.max(np.abs(p.cpd * th_e * t.grad_n(pr)))
     assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
     assert errs[2] < 0.02 * along
+
+
+def test_diagnostics_use_each_columns_ground(mountain3):
+    """Surface pressure over the mountain: the resting reference atmosphere
+    extrapolated from its lowest level to its own ground matches the
+    continuous reference p00 exp(-z_sfc/H)^(cpd/rd) to the discretisation
+    error (1e-4); the mass diagnostic sums each column's own layers."""
+    from oracle import diagnostics
+    grid, z, t = mountain3
+    st = _resting(t)
+    p = t.p
+    ps = diagnostics.surface_pressure(t, st["exner"], st["theta_v"])
+    z_sfc = t.v.z_ifc[:, -1]
+    assert z_sfc.max() > 1500.0
+    H = p.cpd * p.ref_T0 / p.grav
+    exact = p.p00 * np.exp(-z_sfc / H) ** (p.cpd / p.rd)
+    assert np.max(np.abs(ps / exact - 1.0)) < 1e-4
+    assert diagnostics.total_mass(t, st["rho"]) == t.total_mass(st["rho"])
+
+
+def test_corrector_features_use_each_columns_reference(mountain3):
+    """The corrector's exner and theta_v features are deviations from the
+    cell's own reference column: zero for the resting reference atmosphere."""
+    from oracle import corrector
+    grid, z, t = mountain3
+    st = _resting(t)
+    x = corrector.column_features(t, st)
+    nlev = st["exner"].shape[1]
+    assert x.shape == (grid.n_cells, 5 * nlev)
+    assert np.all(x[:, nlev:3 * nlev] == 0.0)
