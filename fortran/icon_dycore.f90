@@ -13,7 +13,7 @@ module icon_dycore
 
   integer(c_int), parameter, public :: ICON_OK = 0, ICON_ERR_ARG = -1, ICON_ERR_CUDA = -2, &
        ICON_ERR_GRID = -3, ICON_ERR_NUMERIC = -4, ICON_ERR_UNSUPPORTED = -5
-  integer(c_int32_t), parameter, public :: ICON_PREC_FP64 = 0, ICON_PREC_MIXED = 1
+  integer(c_int32_t), parameter, public :: ICON_PREC_FP64 = 0, ICON_PREC_MIXED = 1, ICON_PREC_MIXED_F64COL = 2
 
   type, bind(c), public :: icon_grid_desc_t
     integer(c_int32_t) :: n_cells, n_edges, n_verts, index_base

@@ -51,6 +51,7 @@ extern "C" {
 
 #define ICON_PREC_FP64 0           /* every stencil and update in FP64 */
 #define ICON_PREC_MIXED 1          /* FP32 stencils, double-word FP32 column solve, FP64 state updates */
+#define ICON_PREC_MIXED_F64COL 2   /* FP32 stencils, FP64 column solve, FP64 state updates */
 
 typedef struct icon_grid icon_grid_t;      /* opaque */
 typedef struct icon_dycore icon_dycore_t;  /* opaque */
@@ -122,7 +123,7 @@ typedef struct icon_dycore_params {
   /* reference state theta_ref(z) = ref_T0 exp(z/H), H = cpd ref_T0 / grav */
   double ref_T0;
   /* execution */
-  int32_t precision;       /* ICON_PREC_FP64 or ICON_PREC_MIXED */
+  int32_t precision;       /* ICON_PREC_FP64, ICON_PREC_MIXED or ICON_PREC_MIXED_F64COL */
   int32_t use_graph;       /* logical: replay a captured CUDA graph per step */
   int32_t autotune;        /* logical: pick per-kernel launch shapes at create time */
   int32_t synchronous;     /* logical: return only after the GPU work ended */

@@ -34,6 +34,7 @@ ICON_ERR_NUMERIC = -4
 ICON_ERR_UNSUPPORTED = -5
 ICON_PREC_FP64 = 0
 ICON_PREC_MIXED = 1
+ICON_PREC_MIXED_F64COL = 2
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)

@@ -373,8 +373,8 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
   const std::string fname = fn;
   if (!(p->dtime > 0.0) || p->ndyn_substeps < 1)
     return fail(ICON_ERR_ARG, fname + ": dtime must be > 0 and ndyn_substeps >= 1");
-  if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED)
-    return fail(ICON_ERR_ARG, fname + ": precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
+  if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED && p->precision != ICON_PREC_MIXED_F64COL)
+    return fail(ICON_ERR_ARG, fname + ": precision must be ICON_PREC_FP64, ICON_PREC_MIXED or ICON_PREC_MIXED_F64COL");
   if (p->column_chunk != 0 && p->column_chunk != 4 && p->column_chunk != 6 && p->column_chunk != 8)
     return fail(ICON_ERR_ARG, fname + ": column_chunk must be 0, 4, 6 or 8");
   // terrain: every column validated and its metrics derived before any allocation
@@ -584,7 +584,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     v.exner_ref_c = A.upload(ht.exner_ref_c);
     v.theta_ref_c = A.upload(ht.theta_ref_c);
     v.dz_c = A.upload(ht.dz_c);
-    if (p->precision == ICON_PREC_MIXED) {
+    if (p->precision == ICON_PREC_MIXED) {  // the double-word solve reads pairs
       std::vector<float> pairs(2 * ht.colt.size());
       for (size_t i = 0; i < ht.colt.size(); ++i) split_hl(ht.colt[i], &pairs[2 * i]);
       v.colt = reinterpret_cast<const double*>(A.upload(pairs));
@@ -642,7 +642,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     return fail(ICON_ERR_CUDA, m);
   }
   {
-    const bool mixed = p->precision == ICON_PREC_MIXED;
+    const bool mixed = is_mixed(p->precision);
     const DevVert& vv = en.v;
     const bool vert_ok = vv.dz && vv.inv_dz && vv.inv_dzh && vv.wgt && vv.theta_ref && vv.exner_ref &&
                          vv.dexner_ref_ic && vv.ray_fac && vv.colc && vv.lev_hl && vv.lev64;
@@ -736,7 +736,7 @@ enum class Op { kStep, kSubstep, kDiffusion };
 void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
   if (op == Op::kStep || op == Op::kSubstep) {
     int n = op == Op::kStep ? d->params.ndyn_substeps : 1;
-    const bool mixed = d->en.precision == ICON_PREC_MIXED;
+    const bool mixed = is_mixed(d->en.precision);
     if (mixed) launch_refresh_mirrors(d->en, st, s);
     for (int i = 0; i < n; ++i) {
       if (mixed)
@@ -746,7 +746,7 @@ void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
     }
   }
   if (op == Op::kStep || op == Op::kDiffusion) {
-    if (d->en.precision == ICON_PREC_MIXED) {
+    if (is_mixed(d->en.precision)) {
       if (op == Op::kDiffusion) launch_refresh_mirrors(d->en, st, s);
       launch_diffusion<float>(d->en, d->en.c32, st, s);
     } else {
@@ -1126,7 +1126,7 @@ int icon_dycore_debug_field(icon_dycore_t* d, const char* name, void* dst, int64
   if (!d || !name || !dst) return fail(ICON_ERR_ARG, "icon_dycore_debug_field: NULL argument");
   const HostGrid& h = d->grid->host;
   const size_t nlev = d->nlev, ef = h.ne * nlev, cf = h.nc * nlev, ch = h.nc * (nlev + 1);
-  const bool mixed = d->en.precision == ICON_PREC_MIXED;
+  const bool mixed = is_mixed(d->en.precision);
   const size_t es = mixed ? sizeof(float) : sizeof(double);
   const void* src = nullptr;
   size_t n = 0;

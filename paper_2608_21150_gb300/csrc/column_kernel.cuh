@@ -317,6 +317,20 @@ __device__ __forceinline__ R levc(const DevVert& v, const double* Ls, int k, int
   }
 }
 
+// FP32 mirror value of a solve result: the double-word pair's leading sum,
+// or the FP64 value narrowed without the FP64 pipe
+__device__ __forceinline__ float mirror_f32(dws x) { return to_float(x); }
+__device__ __forceinline__ float mirror_f32(double x) { return to_float(to_df(x)); }
+
+// x - q for the terrain's contravariant correction q (type T): x itself where
+// q is exactly zero, so that the double-word pairs the FP64 inputs are split
+// into (a truncated leading word) are not renormalised over flat ground and
+// equal columns step like the flat dycore bit for bit.
+template <class R, class T>
+__device__ __forceinline__ R minus_corr(R x, T q) {
+  return q == T(0) ? x : x - Ar<R>::in(q);
+}
+
 // A value the mixed-precision step (T = float) keeps as a double-word pair in
 // an 8-byte slot -- the flux divergences and the predictor's rho and theta_v
 // -- read as the pair; otherwise an FP64 value, converted.
@@ -324,6 +338,23 @@ template <class T, class R>
 __device__ __forceinline__ R stored_in(const double* p) {
   if constexpr (std::is_same<T, float>::value && !std::is_same<R, double>::value) {
     return *reinterpret_cast<const R*>(p);
+  } else {
+    return Ar<R>::in(*p);
+  }
+}
+
+// A horizontal flux divergence: the mixed-precision stencils (T = float)
+// store it as a double-word pair in its 8-byte slot whatever the solve's
+// arithmetic R (read as the pair, or widened to FP64 exactly); else FP64.
+template <class T, class R>
+__device__ __forceinline__ R stored_div(const double* p) {
+  if constexpr (std::is_same<T, float>::value) {
+    const df x = *reinterpret_cast<const df*>(p);
+    if constexpr (std::is_same<R, double>::value) {
+      return f2d_exact(x.hi) + f2d_exact(x.lo);
+    } else {
+      return to_dws(x);
+    }
   } else {
     return Ar<R>::in(*p);
   }
@@ -362,6 +393,8 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
   constexpr bool kDW = !std::is_same<R, double>::value;
   // the mixed step's engine path (FP32 stencil inputs, double-word solve)
   constexpr bool kPairs = std::is_same<T, float>::value && kDW;
+  // FP32 stencils read FP32 mirrors of the solve's outputs (either arithmetic)
+  constexpr bool kMirror = std::is_same<T, float>::value;
   constexpr int kTile = tile_doubles<KC>();
   constexpr int kBackIn = KC * kCW;
   constexpr int kOut = KC * kLD;
@@ -390,9 +423,9 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
   T* T_wc = T_dw0 + (kCT ? 2 : 1) * kTile;  // terrain: contravariant correction
   // the per-level table is staged per chunk, except in the FP64 form of the
   // allocation-free entry, which has no FP64 copy of the table
-  // (over terrain only the double-word form reads it: the FP32 mirrors'
-  // offsets; every physical quantity is the column's own)
-  constexpr bool kStage = kTerr ? kDW : (kDW || !kOwnZb);
+  // (over terrain only for the FP32 mirrors' offsets of the mixed modes;
+  // every physical quantity is the column's own)
+  constexpr bool kStage = kTerr ? (kDW || kMirror) : (kDW || !kOwnZb);
   double* L_s = sm + lev_offset_bytes<T, KC, kCT, kTerr>() / 8;
   const double* lev_src = kDW ? reinterpret_cast<const double*>(v.lev_hl) : v.lev64;
 
@@ -456,7 +489,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
         ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * stored_in<T, R>(T_tp + o)) : th_c;
         tpa_c = ta_c - levc<R, LTH, kStage, kTerr>(v, L_s, 0, k0, c, nc);
         wk_c = A::in(T_w[o]);
-        const R wf = kTerr ? wk_c - A::in(T_wc[o]) : wk_c;
+        const R wf = kTerr ? minus_corr(wk_c, T_wc[o]) : wk_c;
         fr_c = ric_k * wf;
         fg_c = rt_k * wf;
         al_c = beta * rt_k;
@@ -488,10 +521,10 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       }
       const R wk = wk_c, wk1 = A::in(T_w[o + kLD]);
       const R rt_k1 = ric_k1 * tic_k1;
-      const R wf1 = kTerr ? wk1 - A::in(T_wc[o + kLD]) : wk1;
+      const R wf1 = kTerr ? minus_corr(wk1, T_wc[o + kLD]) : wk1;
       const R fr_k1 = ric_k1 * wf1, fg_k1 = rt_k1 * wf1;
-      const R rstar = rho_n - dt * stored_in<T, R>(T_dm + o) - levc<R, CR, kStage, kTerr>(v, L_s, k, k0, c, nc) * (fr_c - fr_k1);
-      const R pstar = pr_k - zb * (levc<R, LDZ, kStage, kTerr>(v, L_s, k, k0, c, nc) * stored_in<T, R>(T_dt + o) + ombeta * (fg_c - fg_k1));
+      const R rstar = rho_n - dt * stored_div<T, R>(T_dm + o) - levc<R, CR, kStage, kTerr>(v, L_s, k, k0, c, nc) * (fr_c - fr_k1);
+      const R pstar = pr_k - zb * (levc<R, LDZ, kStage, kTerr>(v, L_s, k, k0, c, nc) * stored_div<T, R>(T_dt + o) + ombeta * (fg_c - fg_k1));
       const R al_k = al_c, al_k1 = beta * rt_k1;
       put(rs_s + ik, rstar);
       put(ps_s + ik, pstar);
@@ -509,7 +542,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
         const R am = -(gam * zb_km1 * al_km1);
         const R bm = add_pos(one, gam * al_k * add_pos(zb_km1, zb));
         const R cm = -(gam * zb * al_k1);
-        const R rm = (kTerr ? wstar - A::in(T_wc[o]) : wstar) - gam * (ps_km1 - pstar);
+        const R rm = (kTerr ? minus_corr(wstar, T_wc[o]) : wstar) - gam * (ps_km1 - pstar);
         R cpk, rpk;
         if (k == 1) {
           const R inv = A::inv(bm);
@@ -598,7 +631,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
         const R prnew = get<R>(B_ps + b) - zb * (fa - fa_k1);
         const R thnew = levc<R, CZB, kStage, kTerr>(v, L_s, k, k0, c, nc) * (get<R>(B_eb + b) + cvd_o_rd * prnew) * A::inv(zb * rnew);
         const int o = kk * kLD + t;
-        const R wt = kTerr ? wd + A::in(W_c[o]) : wd;  // w = w_con + wcc
+        const R wt = kTerr ? minus_corr(wd, -W_c[o]) : wd;  // w = w_con + wcc
         if (a.w_o) O_w[o] = A::out(wt);
         if (kPairs && !corrector) {
           // the mixed predictor's rho and theta_v stay double-word pairs (read by the corrector)
@@ -609,13 +642,13 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
           O_th[o] = A::out(thnew);
         }
         if (a.exner_o) O_pi[o] = A::out(levc<R, LEX, kStage, kTerr>(v, L_s, k, k0, c, nc) + prnew);
-        if constexpr (kDW) {
-          // FP32 mirrors straight from the double-word values, into this
+        if constexpr (kMirror) {
+          // FP32 mirrors straight from the solve's values, into this
           // thread's consumed scratch slots: (w, rho - rho_ref) and theta_v - theta_ref
           float* m0 = reinterpret_cast<float*>(B_cp + b);
-          m0[0] = to_float(wt);
-          m0[1] = to_float(rnew - levs<R, LRHO, kStage>(v, L_s, k, k0));
-          reinterpret_cast<float*>(B_rp + b)[0] = to_float(thnew - levs<R, LTH, kStage>(v, L_s, k, k0));
+          m0[0] = mirror_f32(wt);
+          m0[1] = mirror_f32(rnew - levs<R, LRHO, kStage>(v, L_s, k, k0));
+          reinterpret_cast<float*>(B_rp + b)[0] = mirror_f32(thnew - levs<R, LTH, kStage>(v, L_s, k, k0));
         }
         w_und_k1 = w_und;
         fr_k1 = fr;
@@ -627,7 +660,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
     store_tile<KC>(O_rho, a.rho_o, nlev, c0, nc, k0, nk);
     if (a.exner_o) store_tile<KC>(O_pi, a.exner_o, nlev, c0, nc, k0, nk);
     store_tile<KC>(O_th, a.theta_o, nlev, c0, nc, k0, nk);
-    if constexpr (kDW) {
+    if constexpr (kMirror) {
       if (a.m_w) mirror_chunk<KC>(B_cp, B_rp, a.m_w, a.m_rho, a.m_th, nlev, c0, nc, k0, nk);
     }
   }
@@ -682,6 +715,72 @@ ColArgs<T> col_args(const Engine& en, int corrector, const StateView& st, const 
     if (mixed) a.m_w = en.m.w_p;
   }
   return a;
+}
+
+
+// Launch of one column-solve form: chunk depth en.col_kc (4, 6 or 8),
+// predictor or corrector, compute type T of the stencil inputs, arithmetic RA,
+// flat ground or terrain.
+template <class T, class RA, bool kTerr>
+void launch_col_form(const Engine& en, int corrector, const ColArgs<T>& a, const char* name, cudaStream_t s) {
+  const int nc = en.g64.nc;
+  const unsigned blocks = (unsigned)((nc + kCW - 1) / kCW);
+  switch (en.col_kc * 2 + (corrector ? 1 : 0)) {
+    case 6 * 2 + 1:
+      ICON_LAUNCH_SMEM(name, blocks, kCW, (smem_bytes<T, 6, true, kTerr>()), s,
+                       (sn_column_tiled<T, false, 6, RA, 1, kTerr>), nc, en.v, en.sc, 1, a);
+      break;
+    case 6 * 2:
+      ICON_LAUNCH_SMEM(name, blocks, kCW, (smem_bytes<T, 6, false, kTerr>()), s,
+                       (sn_column_tiled<T, false, 6, RA, 0, kTerr>), nc, en.v, en.sc, 0, a);
+      break;
+    case 4 * 2 + 1:
+      ICON_LAUNCH_SMEM(name, blocks, kCW, (smem_bytes<T, 4, true, kTerr>()), s,
+                       (sn_column_tiled<T, false, 4, RA, 1, kTerr>), nc, en.v, en.sc, 1, a);
+      break;
+    case 4 * 2:
+      ICON_LAUNCH_SMEM(name, blocks, kCW, (smem_bytes<T, 4, false, kTerr>()), s,
+                       (sn_column_tiled<T, false, 4, RA, 0, kTerr>), nc, en.v, en.sc, 0, a);
+      break;
+    case 8 * 2 + 1:
+      ICON_LAUNCH_SMEM(name, blocks, kCW, (smem_bytes<T, 8, true, kTerr>()), s,
+                       (sn_column_tiled<T, false, 8, RA, 1, kTerr>), nc, en.v, en.sc, 1, a);
+      break;
+    default:
+      ICON_LAUNCH_SMEM(name, blocks, kCW, (smem_bytes<T, 8, false, kTerr>()), s,
+                       (sn_column_tiled<T, false, 8, RA, 0, kTerr>), nc, en.v, en.sc, 0, a);
+      break;
+  }
+}
+
+// The dynamic shared-memory limit of the six forms of one (T, RA, kTerr).
+template <class T, class RA, bool kTerr>
+cudaError_t init_col_forms() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto kernel, size_t bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  set(sn_column_tiled<T, false, 8, RA, 0, kTerr>, smem_bytes<T, 8, false, kTerr>());
+  set(sn_column_tiled<T, false, 8, RA, 1, kTerr>, smem_bytes<T, 8, true, kTerr>());
+  set(sn_column_tiled<T, false, 6, RA, 0, kTerr>, smem_bytes<T, 6, false, kTerr>());
+  set(sn_column_tiled<T, false, 6, RA, 1, kTerr>, smem_bytes<T, 6, true, kTerr>());
+  set(sn_column_tiled<T, false, 4, RA, 0, kTerr>, smem_bytes<T, 4, false, kTerr>());
+  set(sn_column_tiled<T, false, 4, RA, 1, kTerr>, smem_bytes<T, 4, true, kTerr>());
+  return e;
+}
+
+// Kernel name of a launch (the profile tables and the autotuner key on it).
+inline const char* column_name(bool mixed, bool f64col, bool terrain, int corrector) {
+  if (!mixed) {
+    if (terrain) return corrector ? "sn_column_corr_terrain" : "sn_column_pred_terrain";
+    return corrector ? "sn_column_corr" : "sn_column_pred";
+  }
+  if (f64col) {
+    if (terrain) return corrector ? "sn_column_corr_terrain_mx64" : "sn_column_pred_terrain_mx64";
+    return corrector ? "sn_column_corr_mx64" : "sn_column_pred_mx64";
+  }
+  if (terrain) return corrector ? "sn_column_corr_terrain_mx" : "sn_column_pred_terrain_mx";
+  return corrector ? "sn_column_corr_mx" : "sn_column_pred_mx";
 }
 
 }  // namespace

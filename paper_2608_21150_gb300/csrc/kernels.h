@@ -67,6 +67,9 @@ struct Ctx {
 
 // Device-side state of one dycore: FP64 factors and column-solve work, the
 // FP32 mirrors (mixed mode) and the stencil context of the active mode.
+// The mixed modes (FP32 stencils) differ only in the column solve's arithmetic.
+inline bool is_mixed(int precision) { return precision != ICON_PREC_FP64; }
+
 struct Engine {
   int precision = ICON_PREC_FP64;
   DevGrid g64{};

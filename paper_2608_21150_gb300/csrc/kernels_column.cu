@@ -12,22 +12,9 @@
 namespace icon {
 
 cudaError_t init_column_kernels() {
-  cudaError_t e = cudaSuccess;
-  auto set = [&](auto kernel, size_t bytes) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  };
-  set(sn_column_tiled<double, false, 8, double, 0>, smem_bytes<double, 8, false>());
-  set(sn_column_tiled<double, false, 8, double, 1>, smem_bytes<double, 8, true>());
-  set(sn_column_tiled<float, false, 8, dws, 0>, smem_bytes<float, 8, false>());
-  set(sn_column_tiled<float, false, 8, dws, 1>, smem_bytes<float, 8, true>());
-  set(sn_column_tiled<double, false, 6, double, 0>, smem_bytes<double, 6, false>());
-  set(sn_column_tiled<double, false, 6, double, 1>, smem_bytes<double, 6, true>());
-  set(sn_column_tiled<float, false, 6, dws, 0>, smem_bytes<float, 6, false>());
-  set(sn_column_tiled<float, false, 6, dws, 1>, smem_bytes<float, 6, true>());
-  set(sn_column_tiled<double, false, 4, double, 0>, smem_bytes<double, 4, false>());
-  set(sn_column_tiled<double, false, 4, double, 1>, smem_bytes<double, 4, true>());
-  set(sn_column_tiled<float, false, 4, dws, 0>, smem_bytes<float, 4, false>());
-  set(sn_column_tiled<float, false, 4, dws, 1>, smem_bytes<float, 4, true>());
+  cudaError_t e = init_col_forms<double, double, false>();
+  if (e == cudaSuccess) e = init_col_forms<float, dws, false>();
+  if (e == cudaSuccess) e = init_col_forms<float, double, false>();
   return e;
 }
 
@@ -35,30 +22,14 @@ template <class T>
 void launch_column(const Engine& en, int corrector, const StateView& st, const T* ddt_w0, const T* ddt_w1,
                    cudaStream_t s) {
   const ColArgs<T> a = col_args<T>(en, corrector, st, ddt_w0, ddt_w1);
-  const bool mixed = std::is_same<T, float>::value;
-  const unsigned blocks = (unsigned)((en.g64.nc + kCW - 1) / kCW);
-  const char* name = mixed ? (corrector ? "sn_column_corr_mx" : "sn_column_pred_mx")
-                           : (corrector ? "sn_column_corr" : "sn_column_pred");
-  using RA = ColArith<T>;
-  const size_t sm4c = smem_bytes<T, 4, true>(), sm4p = smem_bytes<T, 4, false>();
-  const size_t sm8c = smem_bytes<T, 8, true>(), sm8p = smem_bytes<T, 8, false>();
-  const size_t sm6c = smem_bytes<T, 6, true>(), sm6p = smem_bytes<T, 6, false>();
-  if (en.col_kc == 6 && corrector)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, sm6c, s, (sn_column_tiled<T, false, 6, RA, 1>), en.g64.nc, en.v, en.sc, 1, a);
-  else if (en.col_kc == 6)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, sm6p, s, (sn_column_tiled<T, false, 6, RA, 0>), en.g64.nc, en.v, en.sc, 0, a);
-  else if (en.col_kc == 4 && corrector)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, sm4c, s, (sn_column_tiled<T, false, 4, RA, 1>), en.g64.nc, en.v,
-                     en.sc, 1, a);
-  else if (en.col_kc == 4)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, sm4p, s, (sn_column_tiled<T, false, 4, RA, 0>), en.g64.nc, en.v,
-                     en.sc, 0, a);
-  else if (corrector)
-    ICON_LAUNCH_SMEM(name, blocks, kCW, sm8c, s, (sn_column_tiled<T, false, 8, RA, 1>), en.g64.nc, en.v,
-                     en.sc, 1, a);
+  constexpr bool mixed = std::is_same<T, float>::value;
+  // the mixed step's solve: double-word FP32, or FP64 (ICON_PREC_MIXED_F64COL)
+  const bool f64col = mixed && en.precision == ICON_PREC_MIXED_F64COL;
+  const char* name = column_name(mixed, f64col, false, corrector);
+  if (f64col)
+    launch_col_form<T, double, false>(en, corrector, a, name, s);
   else
-    ICON_LAUNCH_SMEM(name, blocks, kCW, sm8p, s, (sn_column_tiled<T, false, 8, RA, 0>), en.g64.nc, en.v,
-                     en.sc, 0, a);
+    launch_col_form<T, ColArith<T>, false>(en, corrector, a, name, s);
 }
 
 template void launch_column<double>(const Engine&, int, const StateView&, const double*, const double*, cudaStream_t);

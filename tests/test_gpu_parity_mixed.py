@@ -1,4 +1,5 @@
-"""Mixed precision (FP32 stencils, FP64 column solve and prognostic updates)
+"""Mixed precision (FP32 stencils, FP64 prognostic updates; the column solve
+in double-word FP32, ICON_PREC_MIXED, or in FP64, ICON_PREC_MIXED_F64COL)
 against the FP64 oracle.  Tolerances come from FP32 rounding (6e-8)
 amplified by the cancellation of reference and perturbation parts in the
 stencils."""
@@ -16,14 +17,19 @@ def lib(built_lib, cuda):
     return P
 
 
-def make(P, grid, z, op, **over):
+MODES = ["dw", "f64col"]
+
+
+def make(P, grid, z, op, mode="dw", **over):
     g = P.Grid(grid, radius=op.radius)
-    return g, P.Dycore(g, z, gpu_params(op, precision=P.ICON_PREC_MIXED, **over))
+    prec = P.ICON_PREC_MIXED_F64COL if mode == "f64col" else P.ICON_PREC_MIXED
+    return g, P.Dycore(g, z, gpu_params(op, precision=prec, **over))
 
 
-def test_mixed_step_close_to_fp64_oracle(lib, cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_step_close_to_fp64_oracle(lib, cuda, mode):
     grid, z, op, od, st = setup(2, 30, 1800.0, rayleigh=0.05)
-    g, d = make(lib, grid, z, op, rayleigh_coeff=0.05)
+    g, d = make(lib, grid, z, op, mode, rayleigh_coeff=0.05)
     t = to_torch(st, cuda)
     ref = dict(st)
     errs = []
@@ -37,9 +43,10 @@ def test_mixed_step_close_to_fp64_oracle(lib, cuda):
     assert max(errs[-1].values()) < 1e-3, errs[-1]
 
 
-def test_mixed_conserves_mass_to_fp64_rounding(lib, cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_conserves_mass_to_fp64_rounding(lib, cuda, mode):
     grid, z, op, od, st = setup(2, 30, 1800.0)
-    g, d = make(lib, grid, z, op)
+    g, d = make(lib, grid, z, op, mode)
     t = to_torch(st, cuda)
     area = od.g.cell_area[:, None]
 
@@ -52,10 +59,11 @@ def test_mixed_conserves_mass_to_fp64_rounding(lib, cuda):
     assert abs(mass(to_numpy(t)) / m0 - 1) < 1e-13
 
 
-def test_mixed_resting_atmosphere_stays_at_rest(lib, cuda):
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_resting_atmosphere_stays_at_rest(lib, cuda, mode):
     import torch
     grid, z, op, od, st = setup(2, 30, 1800.0)
-    g, d = make(lib, grid, z, op)
+    g, d = make(lib, grid, z, op, mode)
     th, ex = d.reference_state()
     nc, ne, nlev = grid.n_cells, grid.n_edges, z.size - 1
     rest = dict(vn=np.zeros((ne, nlev)), w=np.zeros((nc, nlev + 1)), theta_v=np.tile(th, (nc, 1)),
@@ -77,3 +85,19 @@ def test_mixed_stage_entry_is_fp64_only(lib, cuda):
     with pytest.raises(lib.IconError) as e:
         d.velocity_tendencies(t["vn"], t["w"], torch.empty_like(t["vn"]), torch.empty_like(t["w"]))
     assert e.value.code == lib.ICON_ERR_UNSUPPORTED
+
+
+def test_fp64_column_of_the_mixed_step_is_closer_to_fp64_than_the_double_word_one(lib, cuda):
+    """The two mixed modes share every FP32 stencil; only the column solve's
+    arithmetic differs, and its FP64 form follows the FP64 oracle at least as
+    closely in w (the field the solve decides) after one step."""
+    grid, z, op, od, st = setup(2, 30, 1800.0, rayleigh=0.05)
+    ref = od.step(st)
+    errs = {}
+    for mode in MODES:
+        g, d = make(lib, grid, z, op, mode, rayleigh_coeff=0.05)
+        t = to_torch(st, cuda)
+        d.step(t)
+        errs[mode] = rel_err(to_numpy(t), ref, od)
+    assert errs["f64col"]["w"] <= errs["dw"]["w"] * 1.5, errs
+    assert all(e < 2e-5 for e in errs["f64col"].values()), errs

@@ -69,14 +69,15 @@ def test_terrain_steps_match_the_oracle(built_lib, cuda, mountain, use_graph):
     assert np.max(np.abs(states[10]["w"][:, -1])) > 1e-4
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "f64col"])
 def test_equal_columns_step_like_the_flat_dycore_bitwise(built_lib, cuda, prec):
     import paper_2608_21150_gb300 as P
     grid, z = make_grid(BIS), make_vct(NLEV)
     st = jw_type_state(grid, z, seed=SEED)
     op = DycoreParams(dtime=DT, ndyn_substeps=5, rayleigh_coeff=0.05)
     g = P.Grid(grid, radius=op.radius)
-    params = gpu_params(op, precision=P.ICON_PREC_MIXED if prec == "mixed" else P.ICON_PREC_FP64)
+    prec_id = {"fp64": P.ICON_PREC_FP64, "mixed": P.ICON_PREC_MIXED, "f64col": P.ICON_PREC_MIXED_F64COL}[prec]
+    params = gpu_params(op, precision=prec_id)
     flat = P.Dycore(g, z, params)
     terr = P.Dycore(g, np.tile(z, (grid.n_cells, 1)), params)
     st["exner_pr"] = st["exner"] - flat.reference_state()[1][None, :]
@@ -137,11 +138,13 @@ def test_mass_and_diagnostics_over_the_mountain(built_lib, cuda, mountain):
     assert np.max(np.abs(t850.cpu().numpy() - ref_t) / ref_t) < 1e-12
 
 
-def test_mixed_over_terrain_close_to_the_fp64_oracle(built_lib, cuda, mountain):
+@pytest.mark.parametrize("prec", ["mixed", "f64col"])
+def test_mixed_over_terrain_close_to_the_fp64_oracle(built_lib, cuda, mountain, prec):
     import paper_2608_21150_gb300 as P
     grid, z, zz, op, od, states, spread = mountain
     g = P.Grid(grid, radius=op.radius)
-    d = P.Dycore(g, zz, gpu_params(op, precision=P.ICON_PREC_MIXED))
+    prec_id = P.ICON_PREC_MIXED if prec == "mixed" else P.ICON_PREC_MIXED_F64COL
+    d = P.Dycore(g, zz, gpu_params(op, precision=prec_id))
     t = to_torch(states[0], cuda)
     errs = {}
     for n in range(1, 11):
