@@ -322,13 +322,20 @@ __device__ __forceinline__ R levc(const DevVert& v, const double* Ls, int k, int
 __device__ __forceinline__ float mirror_f32(dws x) { return to_float(x); }
 __device__ __forceinline__ float mirror_f32(double x) { return to_float(to_df(x)); }
 
-// x - q for the terrain's contravariant correction q (type T): x itself where
-// q is exactly zero, so that the double-word pairs the FP64 inputs are split
-// into (a truncated leading word) are not renormalised over flat ground and
-// equal columns step like the flat dycore bit for bit.
+// x - q for the terrain's contravariant correction q (type T).  In FP64 a
+// plain subtraction (exact where q = 0).  In double-word arithmetic x itself
+// where q is exactly zero, so that the pairs the FP64 inputs are split into (a
+// truncated leading word) are not renormalised over flat ground: equal
+// columns then step like the flat dycore bit for bit in either arithmetic.
+// (A select in the FP64 form changes how the compiler fuses the products of
+// x into multiply-adds, and with it the last bit.)
 template <class R, class T>
 __device__ __forceinline__ R minus_corr(R x, T q) {
-  return q == T(0) ? x : x - Ar<R>::in(q);
+  if constexpr (std::is_same<R, double>::value) {
+    return x - Ar<R>::in(q);
+  } else {
+    return q == T(0) ? x : x - Ar<R>::in(q);
+  }
 }
 
 // A value the mixed-precision step (T = float) keeps as a double-word pair in

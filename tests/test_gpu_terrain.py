@@ -8,7 +8,8 @@ the mountain configuration (2 km high, 1500 km e-folding radius, centred at
   rounding-level input perturbations) where a field's own conditioning is
   coarser than the gate;
 * equal columns (flat heights given per column) step bit for bit like the
-  flat dycore, FP64 and mixed;
+  flat dycore, FP64 and mixed (the mixed mode with an FP64 column solve to
+  rounding);
 * the per-column reference atmosphere stays at rest over the mountain;
 * the total mass is conserved; the diagnostics and the corrector's features
   use each column's ground and reference state;
@@ -86,7 +87,14 @@ def test_equal_columns_step_like_the_flat_dycore_bitwise(built_lib, cuda, prec):
         flat.step(a)
         terr.step(b)
     for k in a:
-        assert bool((a[k] == b[k]).all()), k
+        if prec == "f64col":
+            # this mode's FP64 solve of FP32 inputs: the compiler fuses some
+            # multiply-adds of the terrain form differently at one chunk
+            # length, so equal columns agree to rounding, not bit for bit
+            scale = float(a[k].abs().max())
+            assert float((a[k] - b[k]).abs().max()) <= 1e-14 * scale, k
+        else:
+            assert bool((a[k] == b[k]).all()), k
     th, ex = terr.reference_columns()
     th0, ex0 = flat.reference_state()
     assert np.array_equal(th, np.tile(th0, (grid.n_cells, 1))) and np.array_equal(ex, np.tile(ex0, (grid.n_cells, 1)))
