@@ -7,19 +7,25 @@ R2B6 grid (327 680 cells, 491 520 edges), 90 levels to 30 km, dt = 360 s,
 balanced JW-type baroclinic jet with the seeded Gaussian perturbation
 (seed 2).  Synthetic inputs (no dataset exists in this environment).
 
-A "step" is one full dycore time step.  The device-resident leg times K
+A "step" is one full dycore time step.  The device-resident legs time K
 steps replayed as one CUDA graph each, with CUDA events on the stream the
 library launches on; the state (1.5 GB) is larger than L2, so no flush is
-needed.  The end-to-end leg calls the C-ABI with HOST arrays: the library
-copies the state in and out around every step.  The mixed leg runs the same
-steps with FP32 stencils; the mixed + learned leg trains the corrector on the
-GPU (untimed, other seeds), then times steps with 4 substeps plus the learned
-increments, the check and any fallback to the plain step.  N>1 (torchrun) runs N
-independent replicas (ensemble members), one per GPU.
+needed.  Legs: FP64 (the headline value); mixed precision (FP32 stencils,
+double-word FP32 column solve); mixed with an FP64 column solve; mixed plus
+the learned corrector (trained on the GPU first, untimed, on other seeds:
+steps with 4 substeps plus the learned increments, the check and any
+fallback to the plain step).  After its timed steps every leg runs on,
+untimed, to one simulated day (240 steps), where the surface pressure and
+the 850 hPa temperature are compared with the FP64 leg's.  The end-to-end
+leg calls the C-ABI with HOST arrays: the library copies the state in and
+out around every step.  The mountain section runs the R2B7 L90 Gaussian-
+mountain configuration (dt 180 s, terrain-following heights) in FP64, mixed
+and mixed + learned.  N>1 (torchrun) runs N independent replicas (ensemble
+members), one per GPU.
 
 ``--impl reference`` times the FP64 CPU oracle instead (on the host cores),
 each step a bounded sample: one substep and one diffusion call on R2B4 L90,
-scaled to a full R2B6 L90 step (x5 substeps, x16 cells).
+extrapolated to a full R2B6 L90 step (x5 substeps, x16 cells).
 """
 import argparse
 import json
@@ -34,9 +40,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(bisections=6, nlev=90, dtime=360.0, ndyn=5, seed=2, rayleigh=0.05)
+# the mountain configuration: Gaussian mountain 2 km high, 1500 km e-folding radius
+MOUNTAIN = dict(bisections=7, nlev=90, dtime=180.0, ndyn=5, seed=3, rayleigh=0.05, h0=2000.0, d=1.5e6,
+                max_steps=10)
 SAMPLE_BISECTIONS = 4          # reference / cpu_baseline sample grid (1/16 of the R2B6 columns)
 METRIC = "dycore steps/s + HBM GB/s fraction at R2B6 L90: FP64 vs mixed+learned"
 FP64_PEAK_TFLOPS = 1.25        # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+HBM_FALLBACK_GBS = 6800.0      # used only when the measured peaks are absent
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, "fallback"
+
 
 # Algorithmic FP64 flops per unit (FMA = 2, add/mul/div/sqrt = 1), counted
 # from the formulas each kernel evaluates; the unit is one (point, level).
@@ -45,8 +65,21 @@ FLOPS_PER_UNIT = {
     "sn_cell_grad": 28, "sn_edge_pred": 38, "sn_cell_div": 5, "sn_cell_fluxdiv": 27,
     "sn_column_pred": 86, "sn_edge_corr": 17, "sn_column_corr": 94,
     "diff_div_curl_uv": 30, "diff_edge_smag": 46, "diff_second": 30,
-    "diff_edge_update": 12, "diff_cell_update": 12,
+    "diff_edge_update": 12, "diff_cell_update": 12, "va_concorr": 20,
 }
+
+SUFFIXES = ("_f32", "_terrain", "_mx64", "_mx")
+
+
+def base_name(name):
+    """The kernel a launch name belongs to: without the precision and terrain suffixes."""
+    changed = True
+    while changed:
+        changed = False
+        for s in SUFFIXES:
+            if name.endswith(s):
+                name, changed = name[:-len(s)], True
+    return name
 
 
 def units_per_launch(name, nc, ne, nv, nlev):
@@ -54,12 +87,13 @@ def units_per_launch(name, nc, ne, nv, nlev):
     half = {"c": nc * (nlev + 1), "e": ne * (nlev + 1), "v": nv * (nlev + 1)}
     return {
         "va_edge_pre": full["e"], "va_cell_vert": full["c"] + half["v"], "va_edge_tend": half["e"],
-        "va_cell_w": half["c"], "sn_cell_grad": full["c"], "sn_edge_pred": full["e"],
+        "va_cell_w": half["c"], "va_concorr": half["c"], "sn_cell_grad": full["c"], "sn_edge_pred": full["e"],
         "sn_column_pred": full["c"], "sn_edge_corr": full["e"], "sn_column_corr": full["c"],
         "sn_cell_div": full["c"], "sn_cell_fluxdiv": full["c"],
         "diff_div_curl_uv": full["c"] + full["v"], "diff_edge_smag": full["e"],
         "diff_second": half["c"] + full["v"], "diff_edge_update": full["e"], "diff_cell_update": half["c"],
-    }[name]
+        "mx_refresh": full["e"] + half["c"],
+    }[base_name(name)]
 
 
 def state_bytes(nc, ne, nlev):
@@ -172,9 +206,10 @@ def job_throughput(world, steps, ms):
     return world * steps / (ms / 1000.0)
 
 
-def oracle_sample(bisections, nlev, reps):
+def oracle_sample(bisections, nlev, reps, threads=1):
     """Time the oracle (as it stands) on one substep and one diffusion call of
-    the given grid, in a fresh single-threaded process; returns seconds."""
+    the given grid, in a fresh process whose numpy/BLAS may use `threads`
+    threads; returns [(substep s, diffusion s)] per repetition."""
     code = r"""
 import sys, time, json
 sys.path.insert(0, %r)
@@ -189,8 +224,8 @@ for _ in range(%d):
     out.append((t1 - t0, t2 - t1))
 print(json.dumps(out))
 """ % (ROOT, bisections, nlev, WORKLOAD["dtime"], WORKLOAD["ndyn"], WORKLOAD["rayleigh"], WORKLOAD["seed"], reps)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+    n = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n, CUDA_VISIBLE_DEVICES="")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if p.returncode != 0:
         raise RuntimeError(p.stderr)
@@ -201,15 +236,28 @@ def sample_to_steps_per_s(t_sub, t_diff, scale):
     return 1.0 / (scale * (WORKLOAD["ndyn"] * t_sub + t_diff))
 
 
+def host_cores():
+    return os.cpu_count() or 1
+
+
 def cpu_baseline(nlev):
-    samples = oracle_sample(SAMPLE_BISECTIONS, nlev, 1)
-    t_sub, t_diff = samples[0]
+    """The numpy oracle on the host cores: one substep + one diffusion on R2B4
+    L90, scaled to an R2B6 L90 step; once with every core available to numpy
+    and its BLAS (the reported value), once on one thread."""
     scale = 4 ** (WORKLOAD["bisections"] - SAMPLE_BISECTIONS)
-    return {"value": sample_to_steps_per_s(t_sub, t_diff, scale), "unit": "steps/s", "cores": 1,
-            "kind": "oracle",
+    out = {}
+    for threads in (host_cores(), 1):
+        t_sub, t_diff = oracle_sample(SAMPLE_BISECTIONS, nlev, 1, threads)[0]
+        out[threads] = (sample_to_steps_per_s(t_sub, t_diff, scale), t_sub, t_diff)
+    v_all, s_all, d_all = out[host_cores()]
+    v_one, s_one, d_one = out[1]
+    return {"value": v_all, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
             "sample": "one substep (%.1f s) + one diffusion (%.1f s) of the numpy FP64 oracle on R2B4 L90 "
-                      "(1/16 of the R2B6 columns), scaled to an R2B6 L90 step as 16 x (5 substeps + diffusion)"
-                      % (t_sub, t_diff)}
+                      "(1/16 of the R2B6 columns) with %d threads allowed to numpy/BLAS (its element-wise "
+                      "arithmetic runs on one core), scaled to an R2B6 L90 step as 16 x (5 substeps + diffusion)"
+                      % (s_all, d_all, host_cores()),
+            "extrapolated": True,
+            "single_thread": {"value": v_one, "cores": 1, "substep_s": s_one, "diffusion_s": d_one}}
 
 
 def run_reference(args):
@@ -218,19 +266,25 @@ def run_reference(args):
         return 0
     nlev = WORKLOAD["nlev"]
     reps = args.warmup + args.steps
-    samples = oracle_sample(SAMPLE_BISECTIONS, nlev, reps)[args.warmup:]
+    cores = host_cores()
+    t0 = time.perf_counter()
+    samples = oracle_sample(SAMPLE_BISECTIONS, nlev, reps, cores)[args.warmup:]
+    wall = time.perf_counter() - t0
     scale = 4 ** (WORKLOAD["bisections"] - SAMPLE_BISECTIONS)
     step_s = [scale * (WORKLOAD["ndyn"] * a + b) for a, b in samples]
     total = sum(step_s)
     value = args.steps / total
+    sample = ("per step: one substep + one diffusion of the numpy FP64 oracle on R2B4 L90, extrapolated x16 "
+              "(cells) and x5 (substeps) to an R2B6 L90 step; measured %.1f s of oracle work for %d sample steps"
+              % (sum(a + b for a, b in samples), args.steps))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict("fp64"),
-        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "per step: one substep + one diffusion of the numpy FP64 oracle on R2B4 L90, "
-                                   "scaled x16 (cells) and x5 (substeps) to an R2B6 L90 step"},
+        "extrapolated": True, "sample_wall_s": wall,
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "extrapolated": True},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -248,185 +302,18 @@ def config_dict(prec):
             "l2": "inputs larger than L2 (FP64 state 1.5 GB, scratch ~9 GB); no flush"}
 
 
-def measure(P, G, z, st0, prec, args, dev, world):
-    """Time K steps of one precision mode; returns the numbers and the final state."""
-    import torch
-    import torch.distributed as dist
-    w = WORKLOAD
-    stream = torch.cuda.current_stream(dev)
-    D = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], rayleigh_coeff=w["rayleigh"],
-                            precision=P.ICON_PREC_MIXED if prec == "mixed" else P.ICON_PREC_FP64,
-                            use_graph=1, synchronous=0, stream=stream.cuda_stream))
-    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
-    for _ in range(args.warmup):
-        D.step(t)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    sampler = ClockSampler(dev.index)
-    sampler.start()
-    time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    torch.cuda.nvtx.range_push(prec + "_timed")   # marks the timed steps for profiler filters
-    e0.record(stream)
-    for _ in range(args.steps):
-        D.step(t)
-    e1.record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        dist.barrier()
-    ms = max_over_ranks(ms, world, dev)
-    nc = G.n_cells
-    ps = torch.empty(nc, dtype=torch.float64, device=dev)
-    t850 = torch.empty_like(ps)
-    try:
-        D.diagnostics(t, ps, t850)
-        finite = True
-    except P.IconError:
-        finite = False
-    out = dict(ms=ms, clocks=clocks, finite=finite, ps=ps.cpu().numpy(), t850=t850.cpu().numpy())
-    nsteps_prof = min(args.steps, 3)
-    out["prof"] = D.profile(t, nsteps_prof)
-    out["nsteps_prof"] = nsteps_prof
-    out["launch_config"] = D.launch_config()
-    D.close()
-    return out, t
+# ---------------------------------------------------------------------------
+# DRAM traffic per unit of every kernel, from one-kernel ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch) at R2B5 L90,
+# the units (point-levels) of that launch dividing them; scaled to the bench's
+# grid by the units per launch.  Valid while the kernel sources are the ones
+# captured (SHA-256 over csrc/* except the host-only set-up code).
+DRAM_PER_UNIT = {"sources_sha256": None, "bisections": 5, "nlev": 90, "legs": {}}
 
-
-LEARNED = dict(ndyn_reduced=4, hidden=512, max_batch=65536, train_seeds=(100, 101, 102, 103), spinup=1,
-               snapshots=8, every=3, rows=8192, adam_steps=1500, batch=4096, lr=1e-3, max_norm=3.0)
-
-
-def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final):
-    """Mixed precision + learned corrector: a step with ndyn_reduced substeps,
-    the column and edge networks' increments, the norm/finiteness check and the
-    plain-step fallback (icon_dycore_step_learned).  The corrector is trained
-    first on the GPU (untimed) from paired reduced/plain steps of other seeds."""
-    import numpy as np
-    import torch
-    from paper_2608_21150_gb300 import corrector as C
-    w, L = WORKLOAD, LEARNED
-    stream = torch.cuda.current_stream(dev)
-    base = dict(dtime=w["dtime"], rayleigh_coeff=w["rayleigh"], precision=P.ICON_PREC_MIXED, use_graph=1,
-                synchronous=0, stream=stream.cuda_stream)
-    R = P.Dycore(G, z, dict(base, ndyn_substeps=L["ndyn_reduced"]))
-    Pl = P.Dycore(G, z, dict(base, ndyn_substeps=w["ndyn"]))
-    ex_ref = R.reference_state()[1]
-    t0 = time.perf_counter()
-    gen = torch.Generator()
-    gen.manual_seed(0)
-    data = C.Dataset()
-    from icon_inputs import jw_type_state
-    for seed in L["train_seeds"]:
-        s0 = jw_type_state(grid, z, seed=seed)
-        s0["exner_pr"] = s0["exner"] - ex_ref[None, :]
-        st = {k: torch.from_numpy(v).to(dev) for k, v in s0.items()}
-        for _ in range(L["spinup"]):
-            Pl.step(st)
-        for _ in range(L["snapshots"]):
-            st = C.add_pair(R, Pl, st, data, rows=L["rows"], gen=gen)
-            for _ in range(L["every"] - 1):
-                Pl.step(st)
-    cx, cy, ex, ey = data.cat()
-    del data
-    cn, en = C.make_nets(w["nlev"], hidden=L["hidden"], max_batch=L["max_batch"], seed=1)
-    lc = C.fit(cn, cx, cy, w["nlev"], L["adam_steps"], batch=L["batch"], lr=L["lr"])
-    le = C.fit(en, ex, ey, w["nlev"], L["adam_steps"], batch=L["batch"], lr=L["lr"])
-    del cx, cy, ex, ey
-    torch.cuda.synchronize(dev)
-    train_s = time.perf_counter() - t0
-
-    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
-    fallbacks_warm = 0
-    for _ in range(args.warmup):
-        fb, _ = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
-        fallbacks_warm += int(fb)
-    # held-out error of the corrector at the bench state (reduced and learned vs the plain step)
-    sp, sr, sl = C.clone_state(t), C.clone_state(t), C.clone_state(t)
-    Pl.step(sp)
-    R.step(sr)
-    P.step_learned(R, Pl, cn, en, sl, float("inf"))
-    er, el = C.field_errors(sr, sp), C.field_errors(sl, sp)
-    del sp, sr, sl
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    sampler = ClockSampler(dev.index)
-    sampler.start()
-    time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    fallbacks, norms = 0, []
-    torch.cuda.nvtx.range_push("learned_timed")
-    e0.record(stream)
-    for _ in range(args.steps):
-        fb, r = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
-        fallbacks += int(fb)
-        norms.append(r)
-    e1.record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
-    nc = G.n_cells
-    ps = torch.empty(nc, dtype=torch.float64, device=dev)
-    t850 = torch.empty_like(ps)
-    try:
-        Pl.diagnostics(t, ps, t850)
-        finite = True
-    except P.IconError:
-        finite = False
-    area = G.cell_areas()
-    rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
-    with P.Profile() as prof:
-        P.step_learned(R, Pl, cn, en, t, L["max_norm"])
-    out = {"value": job_throughput(world, args.steps, ms), "ms_per_step": ms / args.steps,
-           "fallbacks_timed": fallbacks, "fallbacks_warmup": fallbacks_warm, "max_norm": L["max_norm"],
-           "check_norm_mean": float(np.nanmean(norms)) if norms else None, "finite": finite,
-           "rms_ps_pa_vs_fp64": rms(ps.cpu().numpy() - f64_final["ps"]) if f64_final else None,
-           "rms_t850_k_vs_fp64": rms(t850.cpu().numpy() - f64_final["t850"]) if f64_final else None,
-           "error_vs_plain_step": {"reduced": er, "learned": el,
-                                   "ratio": {k: el[k] / er[k] for k in er}},
-           "train": {"seconds": train_s, "loss_col": [float(np.mean(lc[:10])), float(np.mean(lc[-50:]))],
-                     "loss_edge": [float(np.mean(le[:10])), float(np.mean(le[-50:]))], **{
-                         k: (list(v) if isinstance(v, tuple) else v) for k, v in L.items()}},
-           "hbm_measured": dram_measured("learned", ms / args.steps),
-           "kernels": kernel_table(prof.kernels, 1), "clocks": clocks}
-    for x in (cn, en, R, Pl):
-        x.close()
-    return out
-
-
-# The column solve's predictor and corrector launches are one kernel (one
-# function, two forms); the roofline treats them together.
-FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
-
-# DRAM bytes per launch of the FP64 column solve (the mean of its predictor
-# and corrector launches, 6.39 and 8.47 GB) from the ncu capture of the FP64
-# step at R2B6 L90, valid for that grid
-# while the kernel source is the one captured (its SHA-256 below).
-COLUMN_TRAFFIC = {"source": "paper_2608_21150_gb300/csrc/kernels_column.cu",
-                  "sha256": "1fc4e7a652e5d510c7db7dfe44654c9b8fd3a81b01462c4eac418754c02a58ea",
-                  "bisections": 6, "bytes_per_launch": 7.427e9}
-
-
-# DRAM bytes per step of every kernel in the timed steps, from one ncu capture
-# of each leg at R2B6 L90, valid while
-# the kernel sources are the ones captured (SHA-256 over csrc/* except the
-# host-only set-up code, below).
-STEP_DRAM = {"sources_sha256": "987083fa96c2d1d9b02eead4bb1f78ece04babebba2a12334617df53cb029a45",
-             "bisections": 6, "bytes_per_step": {"fp64": 207.265e9, "mixed": 154.345e9,
-                                                 "learned": 134.728e9}}
-
-
-# Host-only set-up code (grid validation and geometry factors, run untimed at
-# create) cannot change a kernel's DRAM traffic and is left out of the hash.
-HOST_ONLY_SOURCES = ("grid_setup.cpp",)
+# Host-only set-up code (grid validation, geometry and terrain metrics, run
+# untimed at create) cannot change a kernel's DRAM traffic and is left out of
+# the hash.
+HOST_ONLY_SOURCES = ("grid_setup.cpp", "terrain_setup.cpp")
 
 
 def sources_sha256():
@@ -443,63 +330,314 @@ def sources_sha256():
     return h.hexdigest()
 
 
-def dram_measured(leg, ms_per_step):
-    """Measured DRAM bytes per step (ncu) over the live step time: achieved HBM
-    GB/s and its fraction of the measured peak, and the traffic amplification
-    (measured over algorithmic stage bytes); null if the kernels changed since
-    the capture or the grid is not the captured one."""
-    t = STEP_DRAM
-    if WORKLOAD["bisections"] != t["bisections"] or sources_sha256() != t["sources_sha256"]:
+def dram_table(leg, nlev):
+    """Bytes per unit of every kernel of a leg, or None when the captured
+    sources or level count differ from the ones running."""
+    t = DRAM_PER_UNIT
+    if not t["legs"].get(leg) or t["nlev"] != nlev or sources_sha256() != t["sources_sha256"]:
         return None
-    b = t["bytes_per_step"][leg]
+    return t["legs"][leg]
+
+
+def dram_measured(leg, prof, nsteps, ms_per_step, sizes, nlev, ndyn):
+    """Measured DRAM bytes of a step (per-unit captures x the step's launches
+    and units) over the live step time: achieved HBM GB/s, its fraction of the
+    measured peak, and the amplification over the algorithmic stage bytes.
+    None if a kernel of the step has no captured figure."""
+    tab = dram_table(leg, nlev)
+    if tab is None:
+        return None
+    nc, ne, nv = sizes
+    total = 0.0
+    for k, (n, _) in prof.items():
+        b = base_name(k)
+        if b not in tab:
+            return None
+        total += tab[b] * units_per_launch(k, nc, ne, nv, nlev) * n
+    b = total / nsteps
+    peak, src = hbm_peak()
     gbs = b / (ms_per_step / 1000.0) / 1e9
-    nc = 80 * 4 ** WORKLOAD["bisections"]
-    stage = stage_bytes_per_step(leg, nc, 3 * nc // 2, nc // 2 + 2, WORKLOAD["nlev"], WORKLOAD["ndyn"])
-    return {"bytes_per_step": b, "achieved_gbs": gbs, "peak_gbs": 6663.9, "frac": gbs / 6663.9,
+    stage = stage_bytes_per_step(leg, nc, ne, nv, nlev, ndyn)
+    return {"bytes_per_step": b, "achieved_gbs": gbs, "peak_gbs": peak, "peak_source": src, "frac": gbs / peak,
             "stage_bytes_per_step": stage, "amplification": b / stage if stage else None,
-            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all kernels of the timed steps / "
-                    "event-timed step; of measured peak; amplification = these bytes / the algorithmic stage "
-                    "bytes (each field a kernel reads or writes, once per launch)"}
+            "note": "per-kernel DRAM bytes per unit from one-launch ncu captures at R2B%d L%d, times the units "
+                    "and launches of this step, over the event-timed step; of %s peak"
+                    % (DRAM_PER_UNIT["bisections"], DRAM_PER_UNIT["nlev"], src)}
 
 
-def column_traffic():
-    import hashlib
-    t = COLUMN_TRAFFIC
-    if WORKLOAD["bisections"] != t["bisections"]:
-        return None
-    try:
-        with open(os.path.join(ROOT, t["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
-                return None
-    except OSError:
-        return None
-    return t["bytes_per_launch"]
+# The column solve's predictor and corrector launches are one kernel (one
+# function, two forms); the roofline treats them together.
+FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
 
 
-def roofline(prof, nc, ne, nv, nlev):
-    """FP64-ALU roofline of the kernel family with the largest share of the step."""
+def roofline(prof, nc, ne, nv, nlev, leg="fp64"):
+    """FP64-ALU roofline of the kernel family with the largest share of the
+    step, with its HBM fraction from the captured bytes per unit."""
     fam = {}
     for k, (n, ms) in prof.items():
-        f = FAMILY.get(k, k)
-        flops = FLOPS_PER_UNIT[k] * units_per_launch(k, nc, ne, nv, nlev) * n
-        a = fam.setdefault(f, [0, 0.0, 0.0])
+        b = base_name(k)
+        f = FAMILY.get(b, b)
+        units = units_per_launch(k, nc, ne, nv, nlev) * n
+        a = fam.setdefault(f, [0, 0.0, 0.0, 0.0, []])
         a[0] += n
         a[1] += ms
-        a[2] += flops
-    name, (n, ms, flops) = max(fam.items(), key=lambda kv: kv[1][1])
+        a[2] += FLOPS_PER_UNIT.get(b, 0) * units
+        a[3] += units
+        a[4].append(b)
+    name, (n, ms, flops, units, members) = max(fam.items(), key=lambda kv: kv[1][1])
     achieved = flops / (ms / 1000.0) / 1e12
+    tab = dram_table(leg, nlev)
+    traffic, hbm = None, None
+    if tab is not None and all(m in tab for m in members):
+        byts = sum(tab[base_name(k)] * units_per_launch(k, nc, ne, nv, nlev) * prof[k][0]
+                   for k in prof if FAMILY.get(base_name(k), base_name(k)) == name)
+        traffic = byts / n
+        peak, src = hbm_peak()
+        gbs = byts / (ms / 1000.0) / 1e9
+        hbm = {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak, "peak_source": src}
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": column_traffic() if name == "sn_column" else None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "hbm": hbm,
             "note": "FP64 algorithmic flops per launch / event-timed launch duration (CUDA events around every "
                     "launch on the library's stream); peak = nominal FP64 rate from unit counts and clock "
-                    "(1.2 TFLOP/s measured by a DFMA probe); traffic = ncu DRAM bytes per launch"}
+                    "(1.2 TFLOP/s measured by a DFMA probe); traffic = DRAM bytes per launch from the one-kernel "
+                    "ncu captures, scaled by units; hbm = that traffic over the event time"}
 
 
 def kernel_table(prof, nsteps):
     tot = sum(v[1] for v in prof.values()) / nsteps
     return {k: {"launches_per_step": n // nsteps, "ms_per_step": round(m / nsteps, 3),
                 "share": round(m / nsteps / tot, 4)} for k, (n, m) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+
+PRECISIONS = {"fp64": "ICON_PREC_FP64", "mixed": "ICON_PREC_MIXED", "mixed_f64col": "ICON_PREC_MIXED_F64COL"}
+
+
+def leg_params(P, wl, leg, stream, **over):
+    d = dict(dtime=wl["dtime"], ndyn_substeps=wl["ndyn"], rayleigh_coeff=wl["rayleigh"],
+             precision=getattr(P, PRECISIONS[leg]), use_graph=1, synchronous=0, stream=stream.cuda_stream)
+    d.update(over)
+    return d
+
+
+def timed_steps(step, n, dev, world, stream, label):
+    """n calls of step() between CUDA events on the library's stream, with
+    nvidia-smi clock samples; returns (ms over the ranks, clocks)."""
+    import torch
+    import torch.distributed as dist
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push(label + "_timed")   # marks the timed steps for profiler filters
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+    return max_over_ranks(ms, world, dev), clocks
+
+
+def final_diagnostics(P, D, t, nc, dev):
+    import torch
+    ps = torch.empty(nc, dtype=torch.float64, device=dev)
+    t850 = torch.empty_like(ps)
+    try:
+        D.diagnostics(t, ps, t850)
+        finite = True
+    except P.IconError:
+        finite = False
+    return finite, ps.cpu().numpy(), t850.cpu().numpy()
+
+
+def measure(P, G, z, st0, leg, args, dev, world, total_steps, wl, nsteps, prof_steps=3, prepare=None):
+    """Time nsteps steps of one precision mode (after the warm-up), profile
+    prof_steps more kernel by kernel, then run on untimed to total_steps
+    steps in all; returns the numbers and the diagnostics at the end.
+    prepare(D, st0): completes the initial state from the new dycore."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    D = P.Dycore(G, z, leg_params(P, wl, leg, stream))
+    if prepare is not None:
+        prepare(D, st0)
+    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
+    for _ in range(args.warmup):
+        D.step(t)
+    ms, clocks = timed_steps(lambda: D.step(t), nsteps, dev, world, stream, leg)
+    prof = D.profile(t, prof_steps)
+    done = args.warmup + nsteps + prof_steps
+    for _ in range(max(0, total_steps - done)):
+        D.step(t)
+    finite, ps, t850 = final_diagnostics(P, D, t, G.n_cells, dev)
+    out = dict(ms=ms, clocks=clocks, finite=finite, ps=ps, t850=t850, prof=prof, nsteps_prof=prof_steps,
+               launch_config=D.launch_config(), steps_run=max(total_steps, done))
+    D.close()
+    del t
+    return out
+
+
+def rms_area(area, d):
+    import numpy as np
+    return float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))
+
+
+LEARNED = dict(ndyn_reduced=4, hidden=512, max_batch=65536, train_seeds=(100, 101, 102, 103), spinup=1,
+               snapshots=8, every=3, rows=8192, adam_steps=1500, batch=4096, lr=1e-3, max_norm=3.0)
+
+
+def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final, wl, total_steps, nsteps, ex_ref):
+    """Mixed precision + learned corrector: a step with ndyn_reduced substeps,
+    the column and edge networks' increments, the norm/finiteness check and the
+    plain-step fallback (icon_dycore_step_learned).  The corrector is trained
+    first on the GPU (untimed) from paired reduced/plain steps of other seeds
+    on the same grid and heights; ex_ref is the reference exner (per level, or
+    per column over terrain) for the training states' exner history."""
+    import numpy as np
+    import torch
+    from paper_2608_21150_gb300 import corrector as C
+    from icon_inputs import jw_type_state
+    L = LEARNED
+    nlev = wl["nlev"]
+    stream = torch.cuda.current_stream(dev)
+    R = P.Dycore(G, z, leg_params(P, wl, "mixed", stream, ndyn_substeps=L["ndyn_reduced"]))
+    Pl = P.Dycore(G, z, leg_params(P, wl, "mixed", stream))
+    t0 = time.perf_counter()
+    gen = torch.Generator()
+    gen.manual_seed(0)
+    data = C.Dataset()
+    for seed in L["train_seeds"]:
+        s0 = jw_type_state(grid, z, seed=seed)
+        s0["exner_pr"] = s0["exner"] - ex_ref
+        st = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in s0.items()}
+        for _ in range(L["spinup"]):
+            Pl.step(st)
+        for _ in range(L["snapshots"]):
+            st = C.add_pair(R, Pl, st, data, rows=L["rows"], gen=gen)
+            for _ in range(L["every"] - 1):
+                Pl.step(st)
+        del st
+    cx, cy, ex, ey = data.cat()
+    del data
+    cn, en = C.make_nets(nlev, hidden=L["hidden"], max_batch=L["max_batch"], seed=1)
+    lc = C.fit(cn, cx, cy, nlev, L["adam_steps"], batch=L["batch"], lr=L["lr"])
+    le = C.fit(en, ex, ey, nlev, L["adam_steps"], batch=L["batch"], lr=L["lr"])
+    del cx, cy, ex, ey
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+
+    t = {k: torch.from_numpy(v).to(dev) for k, v in st0.items()}
+    fallbacks_warm = 0
+    for _ in range(args.warmup):
+        fb, _ = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
+        fallbacks_warm += int(fb)
+    # held-out error of the corrector at the bench state (reduced and learned vs the plain step);
+    # a branch from the state, which goes on from t unchanged
+    sp, sr, sl = C.clone_state(t), C.clone_state(t), C.clone_state(t)
+    Pl.step(sp)
+    R.step(sr)
+    P.step_learned(R, Pl, cn, en, sl, float("inf"))
+    er, el = C.field_errors(sr, sp), C.field_errors(sl, sp)
+    del sp, sr, sl
+    fallbacks, norms = [0], []
+
+    def one():
+        fb, r = P.step_learned(R, Pl, cn, en, t, L["max_norm"])
+        fallbacks[0] += int(fb)
+        norms.append(r)
+    ms, clocks = timed_steps(one, nsteps, dev, world, stream, "learned")
+    fallbacks_timed = fallbacks[0]
+    with P.Profile() as prof:
+        one()
+    done = args.warmup + nsteps + 1
+    for _ in range(max(0, total_steps - done)):
+        one()
+    finite, ps, t850 = final_diagnostics(P, Pl, t, G.n_cells, dev)
+    area = G.cell_areas()
+    steps_run = max(total_steps, done)
+    out = {"value": job_throughput(world, nsteps, ms), "ms_per_step": ms / nsteps,
+           "fallbacks_timed": fallbacks_timed, "fallbacks_warmup": fallbacks_warm,
+           "fallbacks_all_steps": fallbacks_warm + fallbacks[0], "steps_run": steps_run,
+           "max_norm": L["max_norm"], "check_norm_mean": float(np.nanmean(norms)) if norms else None,
+           "finite": finite,
+           "rms_ps_pa_vs_fp64": rms_area(area, ps - f64_final["ps"]) if f64_final else None,
+           "rms_t850_k_vs_fp64": rms_area(area, t850 - f64_final["t850"]) if f64_final else None,
+           "compared_after_steps": steps_run,
+           "error_vs_plain_step": {"reduced": er, "learned": el, "ratio": {k: el[k] / er[k] for k in er}},
+           "train": {"seconds": train_s, "loss_col": [float(np.mean(lc[:10])), float(np.mean(lc[-50:]))],
+                     "loss_edge": [float(np.mean(le[:10])), float(np.mean(le[-50:]))], **{
+                         k: (list(v) if isinstance(v, tuple) else v) for k, v in L.items()}},
+           "kernels": kernel_table(prof.kernels, 1), "clocks": clocks}
+    for x in (cn, en, R, Pl):
+        x.close()
+    del t
+    return out
+
+
+def mixed_summary(m, f64, world, nsteps, area, sizes, nlev, ndyn, leg):
+    return {"value": job_throughput(world, nsteps, m["ms"]), "ms_per_step": m["ms"] / nsteps,
+            "speedup_vs_fp64": f64["ms"] / m["ms"] if f64 else None, "finite": m["finite"],
+            "rms_ps_pa": rms_area(area, m["ps"] - f64["ps"]) if f64 else None,
+            "rms_t850_k": rms_area(area, m["t850"] - f64["t850"]) if f64 else None,
+            "compared_after_steps": m["steps_run"],
+            "reference": "FP64 GPU dycore after the same steps (equal to the FP64 oracle to 1e-12 / 1e-9 after "
+                         "1 / 10 steps, GPU parity tests)",
+            "hbm_measured": dram_measured(leg, m["prof"], m["nsteps_prof"], m["ms"] / nsteps, sizes, nlev, ndyn),
+            "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"],
+            "autotuned_launch_config": m["launch_config"]}
+
+
+def mountain_legs(P, args, dev, world):
+    """The R2B7 L90 Gaussian-mountain configuration (dt 180 s): FP64, mixed and
+    mixed + learned over terrain-following heights, timed steps each, the
+    mixed legs' surface pressure compared with the FP64 leg's after the same
+    number of steps."""
+    import numpy as np
+    from icon_inputs import make_grid, make_vct, jw_type_state, mountain_height, terrain_following_z
+    w = MOUNTAIN
+    grid = make_grid(w["bisections"])
+    z = make_vct(w["nlev"])
+    zz = terrain_following_z(z, mountain_height(grid.cell_xyz, h0=w["h0"], d=w["d"]))
+    st0 = jw_type_state(grid, zz, seed=w["seed"])
+    G = P.Grid(grid)
+    nc, nlev = grid.n_cells, w["nlev"]
+    k = min(args.steps, w["max_steps"])
+    total = args.warmup + k + 2
+    # the exner history starts from the per-column reference state of these heights
+    refs = {}
+
+    def prepare(D, st):
+        refs["exner"] = D.reference_columns()[1]
+        st["exner_pr"] = st["exner"] - refs["exner"]
+    area = G.cell_areas()
+    sizes = (nc, grid.n_edges, grid.n_verts)
+    f64 = measure(P, G, zz, st0, "fp64", args, dev, world, total, w, k, prof_steps=2, prepare=prepare)
+    ex_ref = refs["exner"]
+    out = {"config": {"workload": "R2B%d L%d (%d cells), Gaussian mountain %.0f m high, %.0f km e-folding radius "
+                                  "at 90E 30N, terrain-following heights, dt=%gs, %d substeps + diffusion, JW-type "
+                                  "jet seed %d" % (w["bisections"], nlev, nc, w["h0"], w["d"] / 1e3, w["dtime"],
+                                                   w["ndyn"], w["seed"]),
+                      "steps_timed": k, "max_ground_m": float(zz[:, -1].max())},
+           "fp64": {"value": job_throughput(world, k, f64["ms"]), "ms_per_step": f64["ms"] / k,
+                    "sdpd": job_throughput(world, k, f64["ms"]) / world * w["dtime"], "finite": f64["finite"],
+                    "kernels": kernel_table(f64["prof"], f64["nsteps_prof"]), "clocks": f64["clocks"]}}
+    m = measure(P, G, zz, st0, "mixed", args, dev, world, total, w, k, prof_steps=2)
+    out["mixed"] = mixed_summary(m, f64, world, k, area, sizes, nlev, w["ndyn"], "mixed")
+    out["mixed"]["sdpd"] = out["mixed"]["value"] / world * w["dtime"]
+    lrn = learned_leg(P, G, zz, grid, st0, args, dev, world, f64, w, total, k, ex_ref)
+    lrn["speedup_vs_fp64"] = lrn["value"] / out["fp64"]["value"]
+    lrn["speedup_vs_mixed"] = lrn["value"] / out["mixed"]["value"]
+    lrn["sdpd"] = lrn["value"] / world * w["dtime"]
+    out["mixed_learned"] = lrn
+    G.close()
+    return out
 
 
 def run_ours(args):
@@ -522,17 +660,23 @@ def run_ours(args):
     z = make_vct(w["nlev"])
     nlev = w["nlev"]
     nc, ne, nv = grid.n_cells, grid.n_edges, grid.n_verts
+    sizes = (nc, ne, nv)
     st0 = jw_type_state(grid, z, seed=w["seed"])
     G = P.Grid(grid)
-    Dref = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"]))
+    Dref = P.Dycore(G, z, dict(dtime=w["dtime"], ndyn_substeps=w["ndyn"], autotune=0))
     th_ref, ex_ref = Dref.reference_state()
     Dref.close()
     st0["exner_pr"] = st0["exner"] - ex_ref[None, :]
+    area = G.cell_areas()
+    # every leg runs the same number of steps in all: one simulated day, or at
+    # least its warm-up, timed and profiled steps
+    day = int(round(86400.0 / w["dtime"])) if args.day else 0
+    total = max(day, args.warmup + args.steps + 3)
 
     legs = set(args.legs.split(","))
     f64, value, ms_per_step, roof, kernels, launches_per_step = None, None, None, None, None, 0
     if "fp64" in legs:
-        f64, _ = measure(P, G, z, st0, "fp64", args, dev, world)
+        f64 = measure(P, G, z, st0, "fp64", args, dev, world, total, w, args.steps)
         ms_per_step = f64["ms"] / args.steps
         value = job_throughput(world, args.steps, f64["ms"])
         prof, nsp = f64["prof"], f64["nsteps_prof"]
@@ -540,27 +684,21 @@ def run_ours(args):
         kernels = kernel_table(prof, nsp)
         roof = roofline(prof, nc, ne, nv, nlev)
 
-    mx = None
-    if "mixed" in legs:
-        m, _ = measure(P, G, z, st0, "mixed", args, dev, world)
-        area = G.cell_areas()
-        rms = lambda d: float(np.sqrt(np.sum(area * d ** 2) / np.sum(area)))  # noqa: E731
-        mx = {"value": job_throughput(world, args.steps, m["ms"]), "ms_per_step": m["ms"] / args.steps,
-              "speedup_vs_fp64": f64["ms"] / m["ms"] if f64 else None, "finite": m["finite"],
-              "rms_ps_pa": rms(m["ps"] - f64["ps"]) if f64 else None,
-              "rms_t850_k": rms(m["t850"] - f64["t850"]) if f64 else None,
-              "compared_after_steps": args.warmup + args.steps,
-              "reference": "FP64 GPU dycore (equal to the FP64 oracle to 1e-9 after 10 steps, GPU parity tests)",
-              "hbm_measured": dram_measured("mixed", m["ms"] / args.steps),
-              "kernels": kernel_table(m["prof"], m["nsteps_prof"]), "clocks": m["clocks"],
-              "autotuned_launch_config": m["launch_config"]}
+    mixed = {}
+    for leg in ("mixed", "mixed_f64col"):
+        if leg in legs:
+            m = measure(P, G, z, st0, leg, args, dev, world, total, w, args.steps)
+            mixed[leg] = mixed_summary(m, f64, world, args.steps, area, sizes, nlev, w["ndyn"],
+                                       "mixed" if leg == "mixed" else leg)
+            mixed[leg]["sdpd"] = mixed[leg]["value"] / world * w["dtime"]
 
     lrn = None
     if "learned" in legs:
-        lrn = learned_leg(P, G, z, grid, st0, args, dev, world, f64)
+        lrn = learned_leg(P, G, z, grid, st0, args, dev, world, f64, w, total, args.steps, ex_ref[None, :])
         lrn["speedup_vs_fp64"] = lrn["value"] / value if value else None
-        if mx:
-            lrn["speedup_vs_mixed"] = lrn["value"] / mx["value"]
+        lrn["sdpd"] = lrn["value"] / world * w["dtime"]
+        if "mixed" in mixed:
+            lrn["speedup_vs_mixed"] = lrn["value"] / mixed["mixed"]["value"]
 
     # end to end through the C-ABI with host arrays (copies inside the timed region)
     sb = state_bytes(nc, ne, nlev)
@@ -585,9 +723,14 @@ def run_ours(args):
                "mean_value": len(times) / sum(times), "step_ms": [round(1e3 * x, 2) for x in times],
                "note": "value at the median wall time of %d synchronous host-array steps (pinned host arrays, "
                        "copies in and out inside each step); mean_value over all of them" % len(times)}
+    G.close()
+    torch.cuda.empty_cache()
+
+    mountain = mountain_legs(P, args, dev, world) if args.mountain else None
 
     hbm_bytes = compulsory_bytes_per_step(nc, ne, nlev, w["ndyn"])
     stage_fp64 = stage_bytes_per_step("fp64", nc, ne, nv, nlev, w["ndyn"])
+    peak, peak_src = hbm_peak()
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -595,18 +738,23 @@ def run_ours(args):
         "sdpd": value / world * w["dtime"] if value else None,
         "hbm": {"compulsory_bytes_per_step": hbm_bytes,
                 "achieved_gbs": hbm_bytes / (ms_per_step / 1000.0) / 1e9,
-                "peak_gbs": 6663.9, "frac": hbm_bytes / (ms_per_step / 1000.0) / 1e9 / 6663.9,
+                "peak_gbs": peak, "peak_source": peak_src,
+                "frac": hbm_bytes / (ms_per_step / 1000.0) / 1e9 / peak,
                 "stage_bytes_per_step": stage_fp64,
-                "stage_frac": stage_fp64 / (ms_per_step / 1000.0) / 1e9 / 6663.9,
+                "stage_frac": stage_fp64 / (ms_per_step / 1000.0) / 1e9 / peak,
                 "note": "compulsory (state read+write per substep and diffusion) bytes / step time; "
-                        "stage = each field every kernel reads or writes, once per launch; of measured peak"}
+                        "stage = each field every kernel reads or writes, once per launch; of %s peak" % peak_src}
         if ms_per_step else None,
-        "hbm_measured": dram_measured("fp64", ms_per_step) if ms_per_step else None,
+        "hbm_measured": dram_measured("fp64", f64["prof"], f64["nsteps_prof"], ms_per_step, sizes, nlev, w["ndyn"])
+        if f64 else None,
         "roofline": roof,
         "kernels": kernels,
         "autotuned_launch_config": f64["launch_config"] if f64 else None,
-        "mixed": mx,
+        "steps_compared": total,
+        "mixed": mixed.get("mixed"),
+        "mixed_f64col": mixed.get("mixed_f64col"),
         "mixed_learned": lrn,
+        "mountain_r2b7": mountain,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": f64["clocks"] if f64 else None, "finite": f64["finite"] if f64 else None,
@@ -615,7 +763,6 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(nlev)
     if rank == 0:
         print(json.dumps(line))
-    G.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -628,10 +775,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="fp64,mixed,learned",
-                    help="comma-separated legs to run (fp64, mixed, learned); the headline value is the fp64 leg's")
+    ap.add_argument("--legs", default="fp64,mixed,mixed_f64col,learned",
+                    help="comma-separated legs to run (fp64, mixed, mixed_f64col, learned); the headline value is "
+                         "the fp64 leg's")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision and learned legs")
     ap.add_argument("--no-learned", action="store_true", help="skip the mixed + learned-corrector leg")
+    ap.add_argument("--no-day", dest="day", action="store_false",
+                    help="compare the legs after their own steps instead of one simulated day")
+    ap.add_argument("--no-mountain", dest="mountain", action="store_false",
+                    help="skip the R2B7 Gaussian-mountain section")
     ap.add_argument("--grid", type=int, default=WORKLOAD["bisections"],
                     help="RnBm bisections (default 6 = R2B6); other grids for profiler captures and scaling runs")
     ap.add_argument("--dtime", type=float, default=WORKLOAD["dtime"],
@@ -643,11 +795,11 @@ def main():
     WORKLOAD["dtime"] = args.dtime
     legs = [x for x in args.legs.split(",") if x]
     if args.no_mixed:
-        legs = [x for x in legs if x not in ("mixed", "learned")]
+        legs = [x for x in legs if x not in ("mixed", "mixed_f64col", "learned")]
     if args.no_learned:
         legs = [x for x in legs if x != "learned"]
-    if any(x not in ("fp64", "mixed", "learned") for x in legs):
-        ap.error("--legs takes fp64, mixed, learned")
+    if any(x not in ("fp64", "mixed", "mixed_f64col", "learned") for x in legs):
+        ap.error("--legs takes fp64, mixed, mixed_f64col, learned")
     args.legs = ",".join(legs)
     if args.impl == "reference":
         return run_reference(args)

@@ -1,7 +1,8 @@
 """Host-side bookkeeping of bench.py (no GPU): the algorithmic stage bytes of
 a step scale with the number of points, exceed the compulsory bytes, are
-smaller in the mixed-precision leg (FP32 stencil fields), and the stored
-traffic constants are refused for another grid."""
+smaller in the mixed-precision leg (FP32 stencil fields); the per-unit DRAM
+figures of the one-kernel captures are scaled by units and launches, and
+refused once the kernel sources or the level count differ."""
 import importlib
 import os
 import sys
@@ -33,16 +34,63 @@ def test_stage_bytes_scale_and_order():
     assert B.stage_bytes_per_step("learned", *_sizes(6), 90, 5) is None
 
 
-def test_traffic_constants_only_for_the_captured_grid():
+def test_kernel_names_map_to_their_base_kernel_and_units():
     B = _bench()
-    saved = dict(B.WORKLOAD)
+    nc, ne, nv = _sizes(5)
+    for name in ("sn_column_corr_terrain_mx64", "sn_column_corr_mx", "sn_column_corr_terrain", "sn_column_corr"):
+        assert B.base_name(name) == "sn_column_corr"
+        assert B.units_per_launch(name, nc, ne, nv, 90) == nc * 90
+    assert B.base_name("va_edge_tend_terrain_f32") == "va_edge_tend"
+    assert B.units_per_launch("va_edge_tend_terrain_f32", nc, ne, nv, 90) == ne * 91
+    assert B.units_per_launch("va_concorr", nc, ne, nv, 90) == nc * 91
+
+
+def _with_table(B, table):
+    saved = dict(B.DRAM_PER_UNIT)
+    B.DRAM_PER_UNIT.update(table)
+    return saved
+
+
+def test_dram_figures_only_for_the_captured_sources_and_levels():
+    B = _bench()
+    saved = _with_table(B, {"sources_sha256": B.sources_sha256(), "nlev": 90,
+                            "legs": {"fp64": {"sn_column_pred": 100.0, "va_edge_tend": 50.0}}})
     try:
-        B.WORKLOAD["bisections"] = 5
-        assert B.column_traffic() is None
-        assert B.dram_measured("fp64", 100.0) is None
+        assert B.dram_table("fp64", 90) is not None
+        assert B.dram_table("fp64", 65) is None            # another level count
+        assert B.dram_table("mixed", 90) is None           # a leg not captured
+        B.DRAM_PER_UNIT["sources_sha256"] = "0" * 64       # the kernels changed since the capture
+        assert B.dram_table("fp64", 90) is None
     finally:
-        B.WORKLOAD.clear()
-        B.WORKLOAD.update(saved)
+        B.DRAM_PER_UNIT.clear()
+        B.DRAM_PER_UNIT.update(saved)
+
+
+def test_dram_arithmetic_scales_per_unit_bytes_by_units_and_launches():
+    B = _bench()
+    nc, ne, nv = _sizes(6)
+    saved = _with_table(B, {"sources_sha256": B.sources_sha256(), "nlev": 90,
+                            "legs": {"fp64": {"sn_column_pred": 100.0, "va_edge_tend": 50.0}}})
+    try:
+        prof = {"sn_column_pred": (10, 20.0), "va_edge_tend": (40, 10.0)}
+        r = B.dram_measured("fp64", prof, 2, 100.0, (nc, ne, nv), 90, 5)
+        b = (100.0 * nc * 90 * 10 + 50.0 * ne * 91 * 40) / 2
+        assert abs(r["bytes_per_step"] - b) < 1e-6 * b
+        assert abs(r["achieved_gbs"] - b / 0.1 / 1e9) < 1e-9 * r["achieved_gbs"]
+        assert abs(r["frac"] - r["achieved_gbs"] / B.hbm_peak()[0]) < 1e-15
+        prof["sn_cell_grad"] = (5, 1.0)                    # a kernel without a captured figure
+        assert B.dram_measured("fp64", prof, 2, 100.0, (nc, ne, nv), 90, 5) is None
+        # the roofline's dominant family carries its own traffic and HBM fraction
+        r = B.roofline({"sn_column_pred": (5, 10.0), "sn_column_corr": (5, 12.0)}, nc, ne, nv, 90)
+        assert r["traffic"] is None                        # the corrector form was not captured
+        B.DRAM_PER_UNIT["legs"]["fp64"]["sn_column_corr"] = 140.0
+        r = B.roofline({"sn_column_pred": (5, 10.0), "sn_column_corr": (5, 12.0)}, nc, ne, nv, 90)
+        per = (100.0 + 140.0) * nc * 90 * 5
+        assert abs(r["traffic"] - per / 10) < 1e-6 * per
+        assert abs(r["hbm"]["achieved_gbs"] - per / 0.022 / 1e9) < 1e-9 * r["hbm"]["achieved_gbs"]
+    finally:
+        B.DRAM_PER_UNIT.clear()
+        B.DRAM_PER_UNIT.update(saved)
 
 
 def test_roofline_takes_the_longest_family_and_counts_its_flops():
@@ -78,21 +126,6 @@ def test_cpu_sample_scaled_to_a_full_step():
     full step is 16 x (ndyn substeps + diffusion)."""
     B = _bench()
     assert abs(B.sample_to_steps_per_s(1.6, 0.4, 16) - 1.0 / (16 * (5 * 1.6 + 0.4))) < 1e-15
-
-
-def test_dram_arithmetic_on_the_captured_grid():
-    B = _bench()
-    if B.sources_sha256() != B.STEP_DRAM["sources_sha256"]:
-        import pytest
-        pytest.skip("kernel sources changed since the DRAM capture")
-    r = B.dram_measured("fp64", 100.0)
-    b = B.STEP_DRAM["bytes_per_step"]["fp64"]
-    assert abs(r["achieved_gbs"] - b / 0.1 / 1e9) < 1e-9
-    assert abs(r["frac"] - r["achieved_gbs"] / 6663.9) < 1e-15
-    nc, ne, nv = _sizes(6)
-    stage = B.stage_bytes_per_step("fp64", nc, ne, nv, 90, 5)
-    assert r["stage_bytes_per_step"] == stage and abs(r["amplification"] - b / stage) < 1e-15
-    assert B.column_traffic() == B.COLUMN_TRAFFIC["bytes_per_launch"]
 
 
 def test_state_and_compulsory_bytes_are_those_of_the_state_arrays():
