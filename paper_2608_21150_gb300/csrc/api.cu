@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -245,7 +246,8 @@ template <class T>
 bool grid_complete(const GridT<T>& g) {
   const void* p[] = {g.c2e, g.c2e2c, g.e2c, g.e2v, g.e2c2v, g.e2c2e, g.v2e, g.v2c, g.div_c, g.lap_c, g.e2c_w,
                      g.grad_c, g.k4w_c, g.inv_d, g.inv_l, g.f_e, g.vt_w, g.upw, g.nt, g.inv_dn, g.smag_a, g.k4_a,
-                     g.fdiv_e, g.ddamp_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl};
+                     g.fdiv_e, g.ddamp_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl,
+                     g.upw_s, g.cpd_inv_d};
   for (const void* q : p)
     if (!q) return false;
   return true;
@@ -253,7 +255,7 @@ bool grid_complete(const GridT<T>& g) {
 
 template <class T>
 bool terrain_complete(const TerrT<T>& t) {
-  const void* p[] = {t.wgt_e, t.inv_dz_e, t.ddxn_ifc, t.ddxt_ifc, t.ddxn_mc, t.inv_dzh_c, t.inv_dzm_c, t.fx_ratio,
+  const void* p[] = {t.wgt_e, t.qdz_e, t.ddxn_ifc, t.ddxt_ifc, t.ddxn_mc, t.qdzh_c, t.inv_dzm_c, t.fx_ratio,
                      t.wcc0, t.wcc1};
   for (const void* q : p)
     if (!q) return false;
@@ -284,12 +286,24 @@ int autotune(icon_dycore* d) {
       launch_fill(*fields[i], sizes[i], values[i], d->stream);
     }
   }
+  // Candidates: threads per CTA (128, 256, 512) x tile shape (one thread per
+  // (point, level), or one warp per point with its lanes over the levels) for
+  // the stencil kernels; levels per shared-memory chunk (8, 6, 4) for the
+  // column solve.  Each candidate runs kReps steps; a kernel's time is the
+  // smallest of its per-step sums, so a single noisy sample cannot decide.
+  constexpr int kReps = 3;
   const int cand[3] = {128, 256, 512};
-  std::vector<std::vector<double>> t(kNumStencils, std::vector<double>(3, 0.0));
-  const int col_cand[3] = {8, 6, 4};   // levels per chunk of the column solve
-  double col_t[3] = {0.0, 0.0, 0.0};
-  auto run = [&](int ci, int kc, bool stencils) -> int {
-    for (int k = 0; k < kNumStencils; ++k) d->en.threads[k] = cand[ci];
+  constexpr double kInf = 1e300;
+  // t[k][shape][ci]: best per-step time of stencil kernel k
+  std::vector<double> t(kNumStencils * 2 * 3, kInf);
+  auto tk = [&](int k, int sh, int ci) -> double& { return t[((size_t)k * 2 + sh) * 3 + ci]; };
+  const int col_cand[3] = {8, 6, 4};
+  double col_t[3] = {kInf, kInf, kInf};
+  auto run = [&](int ci, int shape, int kc, bool stencils) -> int {
+    for (int k = 0; k < kNumStencils; ++k) {
+      d->en.threads[k] = cand[ci];
+      d->en.shape[k] = shape;
+    }
     d->en.col_kc = kc;
     Prof prof;
     g_prof = &prof;
@@ -297,40 +311,51 @@ int autotune(icon_dycore* d) {
     g_prof = nullptr;
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(d->stream));
+    std::vector<double> sum(kNumStencils, 0.0);
+    double col = 0.0;
     for (const auto& r : prof.recs) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, r.e0, r.e1));
-      const std::string nm = r.name;
+      std::string nm = r.name;
       if (nm.compare(0, 9, "sn_column") == 0) {
-        for (int j = 0; j < 3; ++j)
-          if (col_cand[j] == kc) col_t[j] += ms;
+        col += ms;
         continue;
       }
-      if (!stencils) continue;
+      if (nm.compare(0, 15, "sn_cell_fluxsum") == 0) nm = "sn_cell_fluxdiv" + nm.substr(15);  // same id
       for (int k = 0; k < kNumStencils; ++k) {
         const std::string base = kStencilNames[k];
         if (nm == base || nm == base + "_f32" || nm == base + "_terrain" || nm == base + "_terrain_f32")
-          t[k][ci] += ms;
+          sum[k] += ms;
       }
     }
+    if (stencils)
+      for (int k = 0; k < kNumStencils; ++k)
+        if (sum[k] > 0.0) tk(k, shape, ci) = std::min(tk(k, shape, ci), sum[k]);
+    for (int j = 0; j < 3; ++j)
+      if (col_cand[j] == kc) col_t[j] = std::min(col_t[j], col);
     return ICON_OK;
   };
-  if (rc == ICON_OK) rc = run(1, 8, false);  // warm-up (module load, first-touch)
-  if (rc == ICON_OK) col_t[0] = 0.0;
-  for (int ci = 0; ci < 3 && rc == ICON_OK; ++ci) rc = run(ci, 8, true);
-  if (rc == ICON_OK) {
-    col_t[0] /= 3.0;
-    rc = run(1, 6, false);
-  }
-  if (rc == ICON_OK) rc = run(1, 4, false);
+  if (rc == ICON_OK) rc = run(1, 0, 8, false);  // warm-up (module load, first-touch)
+  if (rc == ICON_OK) col_t[0] = kInf;
+  for (int shape = 0; shape < 2; ++shape)
+    for (int ci = 0; ci < 3; ++ci)
+      for (int r = 0; r < kReps && rc == ICON_OK; ++r) rc = run(ci, shape, 8, true);
+  for (int j = 1; j < 3; ++j)
+    for (int r = 0; r < kReps && rc == ICON_OK; ++r) rc = run(1, 0, col_cand[j], false);
   for (double* p : {st.vn, st.w, st.rho, st.exner, st.theta_v, st.exner_pr})
     if (p) cudaFree(p);
   if (rc != ICON_OK) return rc;
   for (int k = 0; k < kNumStencils; ++k) {
-    int best = 1;
-    for (int ci = 0; ci < 3; ++ci)
-      if (t[k][ci] > 0.0 && t[k][ci] < t[k][best]) best = ci;
-    d->en.threads[k] = cand[best];
+    int best_sh = 0, best_ci = 1;
+    for (int sh = 0; sh < 2; ++sh)
+      for (int ci = 0; ci < 3; ++ci)
+        if (tk(k, sh, ci) < tk(k, best_sh, best_ci)) {
+          best_sh = sh;
+          best_ci = ci;
+        }
+    d->en.threads[k] = cand[best_ci];
+    // only va_edge_pre, va_cell_w, sn_cell_div and sn_edge_corr have both shapes
+    d->en.shape[k] = (k == 0 || k == 3 || k == 6 || k == 8) ? best_sh : -1;
   }
   int best_kc = 0;
   for (int j = 1; j < 3; ++j)
@@ -468,7 +493,17 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     ddamp[e] = s.divdamp * h.mean_area * h.mean_area * h.inv_d[e];
   }
   for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
+  // dycore-level factors of the predictor's edge kernel: upwind offsets with
+  // the half-substep scaling folded in, and cpd / d_e
+  std::vector<double> upw_s(h.upw), cid(ne);
+  for (int e = 0; e < ne; ++e) {
+    for (int side = 0; side < 2; ++side)
+      for (int j = 2; j < 6; ++j) upw_s[12 * (size_t)e + 6 * side + j] *= 0.5 * s.dt_s;
+    cid[e] = p->cpd * h.inv_d[e];
+  }
   en.g64 = grid->dev;
+  en.g64.upw_s = A.upload(upw_s);
+  en.g64.cpd_inv_d = A.upload(cid);
   en.g64.f_e = A.upload(fe);
   en.g64.smag_a = A.upload(smag);
   en.g64.k4_a = A.upload(k4);
@@ -505,6 +540,8 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     g.f_e = up(fe);
     g.vt_w = up(h.vt_w);
     g.upw = up(h.upw);
+    g.upw_s = up(upw_s);
+    g.cpd_inv_d = up(cid);
     g.nt = up(h.nt);
     g.inv_dn = up(h.inv_dn);
     g.smag_a = up(smag);
@@ -522,6 +559,13 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     vt.nlev = nlev;
     vt.inv_dz = up(inv_dz);
     vt.inv_dzh = up(inv_dzh);
+    {
+      std::vector<double> q(inv_dz), qh(inv_dzh);
+      for (double& x : q) x *= 0.25;
+      for (double& x : qh) x *= 0.5;
+      vt.qdz = up(q);
+      vt.qdzh = up(qh);
+    }
     vt.wgt = up(wgt);
     vt.theta_ref = up(d->theta_ref);
     vt.rho_ref = up(rho_ref);
@@ -548,6 +592,11 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     w.lap_vn = A.template alloc<T>(ef);
     w.nu = A.template alloc<T>(ef);
     w.gw_e = A.template alloc<T>(eh);
+    w.vn_ie = A.template alloc<T>(eh);
+    if constexpr (std::is_same<T, double>::value) {
+      w.flx_m = A.template alloc<T>(ef);
+      w.flx_t = A.template alloc<T>(ef);
+    }
     w.ekin_c = A.template alloc<T>(cf);
     w.grad4 = A.template alloc<T>(4 * cf);
     w.divd = A.template alloc<T>(cf);
@@ -596,11 +645,17 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
       auto up = [&](const std::vector<double>& src) { return A.upload(std::vector<T>(src.begin(), src.end())); };
       TerrT<T>& t = x.tr;
       t.wgt_e = up(ht.wgt_e);
-      t.inv_dz_e = up(ht.inv_dz_e);
+      std::vector<double> q(ht.inv_dz_e);
+      for (double& x : q) x *= 0.25;
+      t.qdz_e = up(q);
       t.ddxn_ifc = up(ht.ddxn_ifc);
       t.ddxt_ifc = up(ht.ddxt_ifc);
-      t.ddxn_mc = up(ht.ddxn_mc);
-      t.inv_dzh_c = up(ht.inv_dzh_c);
+      std::vector<double> cpd_ddxn(ht.ddxn_mc);
+      for (double& x : cpd_ddxn) x *= p->cpd;
+      t.ddxn_mc = up(cpd_ddxn);
+      std::vector<double> qh(ht.inv_dzh_c);
+      for (double& x : qh) x *= 0.5;
+      t.qdzh_c = up(qh);
       t.inv_dzm_c = up(ht.inv_dzm_c);
       t.fx_ratio = up(ht.fx_ratio);
       t.wcc0 = A.template alloc<T>(ch);
@@ -1049,7 +1104,7 @@ int icon_velocity_tendencies(icon_dycore_t* d, const double* vn, const double* w
   if (d->en.precision != ICON_PREC_FP64)
     return fail(ICON_ERR_UNSUPPORTED, "icon_velocity_tendencies: stage output is provided in FP64 mode only");
   launch_velocity_tendencies<double>(d->en.c64, vn, w, ddt_vn, ddt_w, nullptr, nullptr, d->stream, d->en.threads,
-                                     d->en.terrain ? d->en.c64.tr.wcc0 : nullptr);
+                                     d->en.terrain ? d->en.c64.tr.wcc0 : nullptr, d->en.shape);
   CUDA_TRY(cudaGetLastError());
   if (d->params.synchronous) CUDA_TRY(cudaStreamSynchronize(d->stream));
   return ICON_OK;
@@ -1205,7 +1260,9 @@ int icon_dycore_launch_config(const icon_dycore_t* d, char* buf, int32_t len) {
   std::string s;
   for (int k = 0; k < kNumStencils; ++k) {
     s += kStencilNames[k];
-    s += "=" + std::to_string(d->en.threads[k]) + ",";
+    s += "=" + std::to_string(d->en.threads[k]);
+    if (d->en.shape[k] >= 0) s += d->en.shape[k] ? "w" : "t";
+    s += ",";
   }
   s += "column_threads=64;column_chunk=" + std::to_string(d->en.col_kc);
   std::snprintf(buf, (size_t)len, "%s", s.c_str());

@@ -36,6 +36,8 @@ struct GridT {
   const T* f_e;     // [ne] Coriolis parameter
   const T* vt_w;    // [ne*5] tangential-wind weights: self, e2c2e[0..3]
   const T* upw;     // [ne*12] per upwind side s: (dx, dy, nx, ny, tx, ty) in that cell's frame
+  const T* upw_s;   // [ne*12] the same with n and t scaled by dt_s/2 (the back trajectory's half substep)
+  const T* cpd_inv_d;  // [ne] cpd / d_e (the horizontal pressure gradient's factor)
   const T* nt;      // [ne*6] normal xyz, tangent xyz
   const T* inv_dn;  // [ne] 1/(arc between the two opposite diamond vertices)
   const T* smag_a;  // [ne] hdiff_smag_fac * A_e
@@ -59,6 +61,8 @@ struct VertT {
   int nlev;
   const T* inv_dz;     // [nlev]
   const T* inv_dzh;    // [nlev+1]
+  const T* qdz;        // [nlev] inv_dz / 4 (the vertical advection of vn: a mean of four w values)
+  const T* qdzh;       // [nlev+1] inv_dzh / 2 (the vertical advection of w: a centred difference)
   const T* wgt;        // [nlev+1]
   const T* theta_ref;  // [nlev]
   const T* rho_ref;    // [nlev] (mixed mode: offset of the rho perturbation)
@@ -72,11 +76,11 @@ struct VertT {
 template <class T>
 struct TerrT {
   const T* wgt_e;     // [ne*(nlev+1)] interpolation weight of level k-1 at edge half level k (0 at the ends)
-  const T* inv_dz_e;  // [ne*nlev] 1/(edge layer thickness)
+  const T* qdz_e;     // [ne*nlev] 1/(4 edge layer thickness): the vertical advection's factor
   const T* ddxn_ifc;  // [ne*(nlev+1)] normal slope of the half levels, (z_c1 - z_c0)/d_e
   const T* ddxt_ifc;  // [ne*(nlev+1)] tangential slope of the half levels from the vertex heights
-  const T* ddxn_mc;   // [ne*nlev] normal slope of the full levels
-  const T* inv_dzh_c; // [nc*(nlev+1)] 1/(z_mc[k-1] - z_mc[k]) per cell (0 at the ends)
+  const T* ddxn_mc;   // [ne*nlev] cpd times the normal slope of the full levels
+  const T* qdzh_c;    // [nc*(nlev+1)] 1/(2 (z_mc[k-1] - z_mc[k])) per cell (0 at the ends)
   const T* inv_dzm_c; // [nc*nlev] 1/(z_mc[k-1] - z_mc[k+1]) per cell, one-sided at the top and the ground
   const T* fx_ratio;  // [nc*3*nlev] dz_e / dz_c of the cell's three edges (horizontal flux thickness)
   T *wcc0, *wcc1;     // work [nc*(nlev+1)]: contravariant correction of the predictor's and corrector's winds
@@ -178,6 +182,9 @@ struct WorkT {
   T *vt, *ekin_e, *ddt_vn0, *ddt_vn1, *rho_e, *theta_e, *hpg, *vn_p, *lap_vn, *nu;
   // edges, half levels
   T* gw_e;
+  T* vn_ie;  // vn interpolated to the half levels (top: level 0, ground: level nlev-1)
+  // edges, full levels (FP64 mode): the horizontal mass and theta fluxes, one value per edge
+  T *flx_m, *flx_t;
   // cells, full levels
   T *ekin_c, *grad4, *divd, *divd2, *dtheta, *div_l, *div_vn;
   // cells, half levels

@@ -83,6 +83,11 @@ struct Engine {
   // launch configuration picked by the autotuner: threads per CTA of each
   // stencil kernel (by kernel id) and the level-chunk depth of the column solve
   int threads[32] = {};
+  // tile shape of the two-shape kernels (va_edge_pre, va_cell_w, sn_cell_div,
+  // sn_edge_corr): 1 one warp per point (lanes over its levels), 0 one thread
+  // per (point, level); -1 the compute type's default
+  int shape[32] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+                   -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
   int col_kc = 4;
   bool terrain = false;  // per-column heights: the terrain forms of the kernels
 };
@@ -94,9 +99,10 @@ struct Engine {
 // (cells, half levels) and the advection uses w - wcc.
 template <class T>
 void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
-                                T* divd2, cudaStream_t s, const int* threads = nullptr, T* wcc = nullptr);
+                                T* divd2, cudaStream_t s, const int* threads = nullptr, T* wcc = nullptr,
+                                const int* shapes = nullptr);
 // Stencil kernel ids (index of Engine::threads) and their base names.
-constexpr int kNumStencils = 15;
+constexpr int kNumStencils = 16;
 extern const char* const kStencilNames[kNumStencils];
 // Fill n doubles with v (the autotuner's temporary state).
 void launch_fill(double* p, size_t n, double v, cudaStream_t s);

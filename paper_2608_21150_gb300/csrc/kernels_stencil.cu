@@ -48,6 +48,10 @@ __device__ __forceinline__ bool flat_index(int n_h, int nk, int& h, int& k) {
 
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// a * b + c with one rounding, in the compute type
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Second launch shape, used by the FP32 forms of the kernels whose per-point
 // gathers dominate (va_edge_pre, va_cell_w, sn_cell_div, sn_cell_fluxdiv,
 // sn_edge_corr): one warp per horizontal point, its lanes striding over the
@@ -65,12 +69,24 @@ template <class T>
 unsigned blocks_by_point(long long n_h, int nk, int threads) {
   return kMixed<T> ? blocks_for_points(n_h, threads) : blocks_for(n_h * nk, threads);
 }
+// CTAs of a two-shape kernel: shape 1 one warp per point, 0 one thread per (point, level)
+inline unsigned blocks_by_shape(int shape, long long n_h, int nk, int threads) {
+  return shape ? blocks_for_points(n_h, threads) : blocks_for(n_h * nk, threads);
+}
 
 constexpr int kThreads = 256;
 
 // threads per CTA of stencil kernel `id` from the autotuner's table (0: default)
 inline int tuned(const int* threads, int id) { return threads && threads[id] > 0 ? threads[id] : kThreads; }
 #define TH(id) tuned(threads, id)
+// tile shape of a two-shape kernel from the autotuner's table (-1: the
+// compute type's default, one warp per point in FP32, one thread per
+// (point, level) in FP64)
+template <class T>
+inline int shaped(const int* shapes, int id) {
+  return shapes && shapes[id] >= 0 ? shapes[id] : (kMixed<T> ? 1 : 0);
+}
+#define SH(id) shaped<T>(shapes, id)
 
 template <class T>
 const char* kname(const char* f64, const char* f32) {
@@ -82,11 +98,14 @@ const char* kname(const char* f64, const char* f32) {
 //   vt = sum_j vt_w[j] vn[e_j] (Perot reconstruction averaged over the two
 //   cells, projected on t_e), K_e = (vn^2 + vt^2)/2
 // -------------------------------------------------------------------------
+// Also vn at the half levels, vn_ie (interpolated inside with the level
+// weights -- the edge weights wgt_e over terrain -- the top level's value at the
+// top and the lowest level's at the ground), for the edge tendency kernel.
 template <class T>
 __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ vt,
-                            T* __restrict__ ekin) {
-  const int nlev = v.nlev;
-  if constexpr (kMixed<T>) {
+                            T* __restrict__ ekin, T* __restrict__ vn_ie, const T* __restrict__ wgt_e, int shape) {
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  if (shape) {
     const int e = warp_point();
     if (e >= g.ne) return;
     const T* w = g.vt_w + 5 * (size_t)e;
@@ -106,6 +125,9 @@ __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
       t += w4 * x4[k];
       vt[(size_t)e * nlev + k] = t;
       ekin[(size_t)e * nlev + k] = T(0.5) * (vne * vne + t * t);
+      const T wg = wgt_e ? wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
+      vn_ie[(size_t)e * nlevp + k] = k == 0 ? vne : vne + wg * (x0[k - 1] - vne);
+      if (k == nlev - 1) vn_ie[(size_t)e * nlevp + nlev] = vne;
     }
     return;
   }
@@ -121,6 +143,9 @@ __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
   t += w[4] * vn[(size_t)q[3] * nlev + k];
   vt[(size_t)e * nlev + k] = t;
   ekin[(size_t)e * nlev + k] = T(0.5) * (vne * vne + t * t);
+  const T wg = wgt_e ? wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
+  vn_ie[(size_t)e * nlevp + k] = k == 0 ? vne : vne + wg * (vn[(size_t)e * nlev + k - 1] - vne);
+  if (k == nlev - 1) vn_ie[(size_t)e * nlevp + nlev] = vne;
 }
 
 // -------------------------------------------------------------------------
@@ -128,12 +153,12 @@ __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
 // vertical velocity of a parcel that follows the coordinate surface,
 //   wcc = sum_e q_e (vn_ie dz/dn + vt_ie dz/dt)
 // with vn, vt interpolated to the edge half levels by the edge weights (the
-// lowest full level's values at the ground; the slopes vanish at the flat
-// model top, where wcc = 0).
+// lowest full level's values at the ground; vn_ie from va_edge_pre; the
+// slopes vanish at the flat model top, where wcc = 0).
 // -------------------------------------------------------------------------
 template <class T>
-__global__ void va_concorr(GridT<T> g, VertT<T> v, TerrT<T> tr, const T* __restrict__ vn, const T* __restrict__ vt,
-                           T* __restrict__ wcc) {
+__global__ void va_concorr(GridT<T> g, VertT<T> v, TerrT<T> tr, const T* __restrict__ vn_ie,
+                           const T* __restrict__ vt, T* __restrict__ wcc) {
   int c, k;
   const int nlev = v.nlev, nlevp = nlev + 1;
   if (!flat_index(g.nc, nlevp, c, k)) return;
@@ -144,18 +169,10 @@ __global__ void va_concorr(GridT<T> g, VertT<T> v, TerrT<T> tr, const T* __restr
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int e = ce[j];
-      const T* x = vn + (size_t)e * nlev;
       const T* y = vt + (size_t)e * nlev;
       const size_t ih = (size_t)e * nlevp + k;
-      T a, b;
-      if (k == nlev) {
-        a = x[nlev - 1];
-        b = y[nlev - 1];
-      } else {
-        const T wg = tr.wgt_e[ih];
-        a = x[k] + wg * (x[k - 1] - x[k]);
-        b = y[k] + wg * (y[k - 1] - y[k]);
-      }
+      const T a = vn_ie[ih];
+      const T b = k == nlev ? y[nlev - 1] : y[k] + tr.wgt_e[ih] * (y[k - 1] - y[k]);
       s += q[j] * (a * tr.ddxn_ifc[ih] + b * tr.ddxt_ifc[ih]);
     }
   }
@@ -220,8 +237,12 @@ __global__ void va_cell_vert(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
 // -------------------------------------------------------------------------
 // Over terrain (kTerr): edge interpolation weights and layer thicknesses, and
 // the contravariant velocity w - wcc as the advecting vertical velocity.
+// Arithmetic arranged for few FP64 instructions (the FP64 mode is bound by
+// GB300's FP64 issue rate): wbar dvn/dz = (sum of the four w) (vn_ie_k -
+// vn_ie_k+1) dz^-1/4 with dz^-1/4 stored, the Coriolis term's 1/2 folded into a
+// multiply-add, the gradient of K into the final multiply-add.
 template <class T, bool kTerr = false>
-__global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, const T* __restrict__ w,
+__global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn_ie, const T* __restrict__ w,
                              const T* __restrict__ vt, const T* __restrict__ ekin_c, const T* __restrict__ zeta,
                              const T* __restrict__ w_v, T* __restrict__ ddt_vn, T* __restrict__ gw_e, TerrT<T> tr,
                              const T* __restrict__ wcc) {
@@ -229,39 +250,33 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
   const int nlev = v.nlev, nlevp = nlev + 1;
   if (!flat_index(g.ne, nlevp, e, k)) return;
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-  const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
   const T inv_d = g.inv_d[e];
-  const T* vne = vn + (size_t)e * nlev;
   const T* vte = vt + (size_t)e * nlev;
-  auto wg = [&](int kh) -> T { return kTerr ? tr.wgt_e[(size_t)e * nlevp + kh] : v.wgt[kh]; };
-  // vn at half levels k and k+1 (top: vn_0, ground: vn_{nlev-1})
-  // linear interpolation to half level kh written as x_kh + wgt (x_kh-1 - x_kh)
-  auto vn_ie = [&](int kh) -> T {
-    if (kh == 0) return vne[0];
-    if (kh == nlev) return vne[nlev - 1];
-    return vne[kh] + wg(kh) * (vne[kh - 1] - vne[kh]);
-  };
-  const T vnie_k = vn_ie(k);
+  const T vnie_k = vn_ie[(size_t)e * nlevp + k];
   if (k < nlev) {
-    const T vnie_k1 = vn_ie(k + 1);
+    const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
+    const T vnie_k1 = vn_ie[(size_t)e * nlevp + k + 1];
     const T* w0 = w + (size_t)c0 * nlevp;
     const T* w1 = w + (size_t)c1 * nlevp;
-    T wbar;
+    T ws;
     if constexpr (kTerr) {
       const T* q0 = wcc + (size_t)c0 * nlevp;
       const T* q1 = wcc + (size_t)c1 * nlevp;
-      wbar = T(0.25) * (((w0[k] - q0[k]) + (w0[k + 1] - q0[k + 1])) + ((w1[k] - q1[k]) + (w1[k + 1] - q1[k + 1])));
+      ws = ((w0[k] - q0[k]) + (w0[k + 1] - q0[k + 1])) + ((w1[k] - q1[k]) + (w1[k + 1] - q1[k + 1]));
     } else {
-      wbar = T(0.25) * ((w0[k] + w0[k + 1]) + (w1[k] + w1[k + 1]));
+      ws = (w0[k] + w0[k + 1]) + (w1[k] + w1[k + 1]);
     }
-    const T zeta_e = T(0.5) * (zeta[(size_t)vm * nlev + k] + zeta[(size_t)vp * nlev + k]);
-    const T dkdn = (ekin_c[(size_t)c1 * nlev + k] - ekin_c[(size_t)c0 * nlev + k]) * inv_d;
-    const T dvdz = (vnie_k - vnie_k1) * (kTerr ? tr.inv_dz_e[(size_t)e * nlev + k] : v.inv_dz[k]);
-    ddt_vn[(size_t)e * nlev + k] = -dkdn + (zeta_e + g.f_e[e]) * vte[k] - wbar * dvdz;
+    const T qdz = kTerr ? tr.qdz_e[(size_t)e * nlev + k] : v.qdz[k];
+    const T adv = (ws * (vnie_k - vnie_k1)) * qdz;
+    const T zf = fmat(T(0.5), zeta[(size_t)vm * nlev + k] + zeta[(size_t)vp * nlev + k], g.f_e[e]);
+    const T dk = ekin_c[(size_t)c0 * nlev + k] - ekin_c[(size_t)c1 * nlev + k];
+    ddt_vn[(size_t)e * nlev + k] = fmat(dk, inv_d, fmat(zf, vte[k], -adv));
   }
   T gw = 0;
   if (k > 0 && k < nlev) {
-    const T vtie = vte[k] + wg(k) * (vte[k - 1] - vte[k]);
+    const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
+    const T wg = kTerr ? tr.wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
+    const T vtie = vte[k] + wg * (vte[k - 1] - vte[k]);
     const T dwdn = (w[(size_t)c1 * nlevp + k] - w[(size_t)c0 * nlevp + k]) * inv_d;
     const T dwdt = (w_v[(size_t)vp * nlevp + k] - w_v[(size_t)vm * nlevp + k]) * g.inv_l[e];
     gw = vnie_k * dwdn + vtie * dwdt;
@@ -276,9 +291,9 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
 // Over terrain (kTerr): advected by w - wcc, per-cell half-level spacing.
 template <class T, bool kTerr = false>
 __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const T* __restrict__ gw_e,
-                          T* __restrict__ ddt_w, TerrT<T> tr, const T* __restrict__ wcc) {
+                          T* __restrict__ ddt_w, TerrT<T> tr, const T* __restrict__ wcc, int shape) {
   const int nlev = v.nlev, nlevp = nlev + 1;
-  if constexpr (kMixed<T>) {
+  if (shape) {
     const int c = warp_point();
     if (c >= g.nc) return;
     const int* ce = g.c2e + 3 * (size_t)c;
@@ -296,9 +311,9 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
         h += q2 * g2[k];
         if constexpr (kTerr) {
           const size_t ih = (size_t)c * nlevp + k;
-          r = -h - (wc[k] - wcc[ih]) * (T(0.5) * (wc[k - 1] - wc[k + 1])) * tr.inv_dzh_c[ih];
+          r = -h - (wc[k] - wcc[ih]) * (wc[k - 1] - wc[k + 1]) * tr.qdzh_c[ih];
         } else {
-          r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+          r = -h - wc[k] * (wc[k - 1] - wc[k + 1]) * v.qdzh[k];
         }
       }
       ddt_w[(size_t)c * nlevp + k] = r;
@@ -315,12 +330,13 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
     h += q[1] * gw_e[(size_t)ce[1] * nlevp + k];
     h += q[2] * gw_e[(size_t)ce[2] * nlevp + k];
     const T* wc = w + (size_t)c * nlevp;
-    // the difference of the full-level means above and below, (w_k-1 - w_k+1) / 2
+    // the difference of the full-level means above and below, (w_k-1 - w_k+1) / 2,
+    // with the 1/2 folded into the stored 1/(2 dzh)
     if constexpr (kTerr) {
       const size_t ih = (size_t)c * nlevp + k;
-      r = -h - (wc[k] - wcc[ih]) * (T(0.5) * (wc[k - 1] - wc[k + 1])) * tr.inv_dzh_c[ih];
+      r = -h - (wc[k] - wcc[ih]) * (wc[k - 1] - wc[k + 1]) * tr.qdzh_c[ih];
     } else {
-      r = -h - wc[k] * (T(0.5) * (wc[k - 1] - wc[k + 1])) * v.inv_dzh[k];
+      r = -h - wc[k] * (wc[k - 1] - wc[k + 1]) * v.qdzh[k];
     }
   }
   ddt_w[(size_t)c * nlevp + k] = r;
@@ -381,7 +397,7 @@ template <class T, bool kTerr = false>
 __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ vn,
                              const T* __restrict__ vt, const T* __restrict__ ddt_vn, const T* __restrict__ rho,
                              const T* __restrict__ theta, const double* __restrict__ pex,
-                             const double* __restrict__ inv_d64, const T* __restrict__ grad4, T* __restrict__ rho_e,
+                             const double* __restrict__ cid64, const T* __restrict__ grad4, T* __restrict__ rho_e,
                              T* __restrict__ theta_e,
                              T* __restrict__ hpg, T* __restrict__ vn_p, TerrT<T> tr) {
   int e, k;
@@ -392,20 +408,23 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
   const T vne = vn[ie], vte = vt[ie];
   const int side = vne >= T(0) ? 0 : 1;
   const int cu = g.e2c[2 * e + side];
-  const T* u = g.upw + 12 * (size_t)e + 6 * side;
-  const T hdt = T(0.5) * sc.dt_s;
-  const T dx = u[0] - hdt * (vne * u[2] + vte * u[4]);
-  const T dy = u[1] - hdt * (vne * u[3] + vte * u[5]);
+  // offset of the back-trajectory point from the upwind cell's centre, with
+  // the half substep folded into the stored normal and tangent: two FMAs each
+  const T* u = g.upw_s + 12 * (size_t)e + 6 * side;
+  const T dx = fmat(-vne, u[2], fmat(-vte, u[4], u[0]));
+  const T dy = fmat(-vne, u[3], fmat(-vte, u[5], u[1]));
   const size_t iu = (size_t)cu * nlev + k;
   T ru = rho[iu], tu = theta[iu];
   if constexpr (kMixed<T>) {
     ru += v.rho_ref[k];
     tu += v.theta_ref[k];
   }
-  const T re = ru + (grad4[iu] * dx + grad4[n + iu] * dy);
-  const T te = tu + (grad4[2 * n + iu] * dx + grad4[3 * n + iu] * dy);
+  const T re = fmat(grad4[iu], dx, fmat(grad4[n + iu], dy, ru));
+  const T te = fmat(grad4[2 * n + iu], dx, fmat(grad4[3 * n + iu], dy, tu));
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
   const size_t i0 = (size_t)c0 * nlev + k, i1 = (size_t)c1 * nlev + k;
+  // cpd theta_e d(pr)/dn with cpd folded into the edge factor cpd / d_e (and,
+  // over terrain, into the stored slope)
   T h;
   const int km = k > 0 ? k - 1 : 0, kp = k + 1 < nlev ? k + 1 : nlev - 1;
   if constexpr (kMixed<T>) {
@@ -414,18 +433,18 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
       const size_t b0 = (size_t)c0 * nlev, b1 = (size_t)c1 * nlev;
       const T dz0 = to_float(p[b0 + km] - p[b0 + kp]) * tr.inv_dzm_c[i0];
       const T dz1 = to_float(p[b1 + km] - p[b1 + kp]) * tr.inv_dzm_c[i1];
-      h = sc.cpd * te * (to_float(p[i1] - p[i0]) * g.inv_d[e] - tr.ddxn_mc[ie] * (T(0.5) * (dz0 + dz1)));
+      h = te * (to_float(p[i1] - p[i0]) * g.cpd_inv_d[e] - tr.ddxn_mc[ie] * (T(0.5) * (dz0 + dz1)));
     } else {
-      h = sc.cpd * te * (to_float(p[i1] - p[i0]) * g.inv_d[e]);
+      h = te * (to_float(p[i1] - p[i0]) * g.cpd_inv_d[e]);
     }
   } else {
     if constexpr (kTerr) {
       const size_t b0 = (size_t)c0 * nlev, b1 = (size_t)c1 * nlev;
       const double dz0 = (pex[b0 + km] - pex[b0 + kp]) * tr.inv_dzm_c[i0];
       const double dz1 = (pex[b1 + km] - pex[b1 + kp]) * tr.inv_dzm_c[i1];
-      h = sc.cpd * te * (T)((pex[i1] - pex[i0]) * inv_d64[e] - tr.ddxn_mc[ie] * (0.5 * (dz0 + dz1)));
+      h = te * (T)((pex[i1] - pex[i0]) * cid64[e] - tr.ddxn_mc[ie] * (0.5 * (dz0 + dz1)));
     } else {
-      h = sc.cpd * te * (T)((pex[i1] - pex[i0]) * inv_d64[e]);
+      h = te * (T)((pex[i1] - pex[i0]) * cid64[e]);
     }
   }
   rho_e[ie] = re;
@@ -442,9 +461,10 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
 template <class T>
 __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __restrict__ vn,
                              const T* __restrict__ ddt_vn0, const T* __restrict__ ddt_vn1,
-                             const T* __restrict__ hpg, const T* __restrict__ divd2, float* __restrict__ m_vn) {
+                             const T* __restrict__ hpg, const T* __restrict__ divd2, float* __restrict__ m_vn,
+                             int shape) {
   const int nlev = v.nlev;
-  if constexpr (kMixed<T>) {
+  if (shape) {
     const int e = warp_point();
     if (e >= g.ne) return;
     const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
@@ -455,9 +475,13 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
       const size_t ie = (size_t)e * nlev + k;
       const T damp = ddamp * (d1[k] - d0[k]);
       const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - damp;
-      const double vnn = vn[ie] + f2d(inc);
-      vn[ie] = vnn;
-      m_vn[ie] = d2f(vnn);
+      if constexpr (kMixed<T>) {
+        const double vnn = vn[ie] + f2d(inc);
+        vn[ie] = vnn;
+        m_vn[ie] = d2f(vnn);
+      } else {
+        vn[ie] = vn[ie] + (double)inc;
+      }
     }
     return;
   }
@@ -486,9 +510,9 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
 template <class T, bool kTerr = false>
 __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ divd,
                             const double* __restrict__ exner, double* __restrict__ exner_pr,
-                            const double* __restrict__ exner_ref_c) {
+                            const double* __restrict__ exner_ref_c, int shape) {
   const int nlev = v.nlev;
-  if constexpr (kMixed<T>) {
+  if (shape) {
     const int c = warp_point();
     if (c >= g.nc) return;
     const int* ce = g.c2e + 3 * (size_t)c;
@@ -588,6 +612,55 @@ __global__ void sn_cell_fluxdiv(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __
     div_m[(size_t)c * nlev + k] = dm;
     div_t[(size_t)c * nlev + k] = dt;
   }
+}
+
+// -------------------------------------------------------------------------
+// FP64 mode: the same divergences from fluxes computed once per edge (the
+// cell form above computes each edge's flux once for each of its two cells,
+// and the FP64 mode is bound by the FP64 issue rate):
+//   sn_edge_flux:    F_e = rho_e vf_e, Ft_e = F_e theta_e (edges, full levels)
+//   sn_cell_fluxsum: div_m = sum s l F / A, div_t = sum s l Ft / A, over
+//                    terrain with each flux times dz_e / dz_c
+// -------------------------------------------------------------------------
+__global__ void sn_edge_flux(GridT<double> g, VertT<double> v, const double* __restrict__ vn,
+                             const double* __restrict__ divd, const double* __restrict__ rho_e,
+                             const double* __restrict__ theta_e, double* __restrict__ flx_m,
+                             double* __restrict__ flx_t) {
+  int e, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const size_t ie = (size_t)e * nlev + k;
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  const double vf = fma(g.fdiv_e[e], divd[(size_t)c1 * nlev + k] - divd[(size_t)c0 * nlev + k], vn[ie]);
+  const double f = rho_e[ie] * vf;
+  flx_m[ie] = f;
+  flx_t[ie] = f * theta_e[ie];
+}
+
+template <bool kTerr>
+__global__ void sn_cell_fluxsum(GridT<double> g, VertT<double> v, const double* __restrict__ flx_m,
+                                const double* __restrict__ flx_t, double* __restrict__ div_m,
+                                double* __restrict__ div_t, const double* __restrict__ fx_ratio) {
+  int c, k;
+  const int nlev = v.nlev;
+  if (!flat_index(g.nc, nlev, c, k)) return;
+  const int* ce = g.c2e + 3 * (size_t)c;
+  const double* dv = g.div_c + 3 * (size_t)c;
+  double dm = 0.0, dt = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const size_t ie = (size_t)ce[j] * nlev + k;
+    double fm = flx_m[ie], ft = flx_t[ie];
+    if constexpr (kTerr) {
+      const double r = fx_ratio[((size_t)c * 3 + j) * nlev + k];
+      fm = fm * r;
+      ft = ft * r;
+    }
+    dm = fma(dv[j], fm, dm);
+    dt = fma(dv[j], ft, dt);
+  }
+  div_m[(size_t)c * nlev + k] = dm;
+  div_t[(size_t)c * nlev + k] = dt;
 }
 
 // -------------------------------------------------------------------------
@@ -798,33 +871,55 @@ __global__ void diff_cell_update(GridT<T> g, VertT<T> v, ScalT<T> sc, const doub
 // -------------------------------------------------------------------------
 template <class T>
 void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt_vn, T* ddt_w, const T* divd,
-                                T* divd2, cudaStream_t s, const int* threads, T* wcc) {
+                                T* divd2, cudaStream_t s, const int* threads, T* wcc, const int* shapes) {
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
   const TerrT<T>& tr = x.tr;
   const int nlev = v.nlev, nlevp = nlev + 1;
   const bool terr = tr.wgt_e != nullptr && wcc != nullptr;
-  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_by_point<T>(g.ne, nlev, TH(0)), TH(0), s,
-              va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e);
+  ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_by_shape(SH(0), g.ne, nlev, TH(0)), TH(0), s,
+              va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e, wk.vn_ie, terr ? tr.wgt_e : nullptr, SH(0));
   if (terr)
     ICON_LAUNCH(kname<T>("va_concorr", "va_concorr_f32"), blocks_for((long long)g.nc * nlevp, TH(14)), TH(14), s,
-                va_concorr<T>, g, v, tr, vn, wk.vt, wcc);
+                va_concorr<T>, g, v, tr, wk.vn_ie, wk.vt, wcc);
   const long long n2 = (long long)g.nc * nlev + (long long)g.nv * nlevp;
   ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, TH(1)), TH(1), s, va_cell_vert<T>, g,
               v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v);
   if (terr) {
     ICON_LAUNCH(kname<T>("va_edge_tend_terrain", "va_edge_tend_terrain_f32"),
-                blocks_for((long long)g.ne * nlevp, TH(2)), TH(2), s, (va_edge_tend<T, true>), g, v, vn, w, wk.vt,
+                blocks_for((long long)g.ne * nlevp, TH(2)), TH(2), s, (va_edge_tend<T, true>), g, v, wk.vn_ie, w, wk.vt,
                 wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr, wcc);
-    ICON_LAUNCH(kname<T>("va_cell_w_terrain", "va_cell_w_terrain_f32"), blocks_by_point<T>(g.nc, nlevp, TH(3)),
-                TH(3), s, (va_cell_w<T, true>), g, v, w, wk.gw_e, ddt_w, tr, wcc);
+    ICON_LAUNCH(kname<T>("va_cell_w_terrain", "va_cell_w_terrain_f32"), blocks_by_shape(SH(3), g.nc, nlevp, TH(3)),
+                TH(3), s, (va_cell_w<T, true>), g, v, w, wk.gw_e, ddt_w, tr, wcc, SH(3));
   } else {
     ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, TH(2)), TH(2),
-                s, (va_edge_tend<T, false>), g, v, vn, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr,
+                s, (va_edge_tend<T, false>), g, v, wk.vn_ie, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr,
                 wcc);
-    ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_by_point<T>(g.nc, nlevp, TH(3)), TH(3), s,
-                (va_cell_w<T, false>), g, v, w, wk.gw_e, ddt_w, tr, wcc);
+    ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_by_shape(SH(3), g.nc, nlevp, TH(3)), TH(3), s,
+                (va_cell_w<T, false>), g, v, w, wk.gw_e, ddt_w, tr, wcc, SH(3));
+  }
+}
+
+// Flux divergences of the mass and theta fluxes of the velocity vn (with the
+// flux filter): the mixed mode sums FP32 fluxes per cell in double-word
+// arithmetic; the FP64 mode computes each edge's fluxes once, then sums them.
+template <class T, bool kTerr>
+void launch_fluxdiv(const Engine& en, const Ctx<T>& x, const T* vn, const char* name, cudaStream_t s) {
+  const int* threads = en.threads;
+  const GridT<T>& g = x.g;
+  const VertT<T>& v = x.v;
+  const WorkT<T>& wk = x.w;
+  const int nlev = v.nlev;
+  if constexpr (kMixed<T>) {
+    ICON_LAUNCH(name, blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, (sn_cell_fluxdiv<T, kTerr>), g, v, x.s, vn,
+                wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t, x.tr.fx_ratio);
+  } else {
+    ICON_LAUNCH("sn_edge_flux", blocks_for((long long)g.ne * nlev, TH(15)), TH(15), s, sn_edge_flux, g, v, vn,
+                wk.divd, wk.rho_e, wk.theta_e, wk.flx_m, wk.flx_t);
+    ICON_LAUNCH(kTerr ? "sn_cell_fluxsum_terrain" : "sn_cell_fluxsum", blocks_for((long long)g.nc * nlev, TH(7)),
+                TH(7), s, (sn_cell_fluxsum<kTerr>), g, v, wk.flx_m, wk.flx_t, en.wk.div_m, en.wk.div_t,
+                x.tr.fx_ratio);
   }
 }
 
@@ -833,6 +928,7 @@ void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt
 template <class T, bool kTerr>
 void substep_impl(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
   const int* threads = en.threads;
+  const int* shapes = en.shape;
   const GridT<T>& g = x.g;
   const VertT<T>& v = x.v;
   const WorkT<T>& wk = x.w;
@@ -858,29 +954,27 @@ void substep_impl(const Engine& en, const Ctx<T>& x, const StateView& st, cudaSt
                              : kname<T>("sn_cell_fluxdiv", "sn_cell_fluxdiv_f32");
   // ---------------- predictor ----------------
   launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s, threads,
-                                kTerr ? tr.wcc0 : nullptr);
+                                kTerr ? tr.wcc0 : nullptr, shapes);
   ICON_LAUNCH(nm_grad, blocks_for(nce, TH(4)), TH(4), s, (sn_cell_grad<T, kTerr>), g, v, s_rho, s_th, wk.grad4,
               st.exner, st.exner_pr, en.sc.exfac, en.wk.pex, ex_ref_c);
   ICON_LAUNCH(nm_pred, blocks_for(nee, TH(5)), TH(5), s, (sn_edge_pred<T, kTerr>), g, v, x.s, s_vn, wk.vt,
-              wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p, tr);
-  ICON_LAUNCH(nm_div, blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, wk.vn_p,
-              wk.divd, st.exner, st.exner_pr, ex_ref_c);
-  ICON_LAUNCH(nm_flx, blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, (sn_cell_fluxdiv<T, kTerr>), g, v, x.s,
-              wk.vn_p, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t, tr.fx_ratio);
+              wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.cpd_inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p, tr);
+  ICON_LAUNCH(nm_div, blocks_by_shape(SH(6), g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, wk.vn_p,
+              wk.divd, st.exner, st.exner_pr, ex_ref_c, SH(6));
+  launch_fluxdiv<T, kTerr>(en, x, wk.vn_p, nm_flx, s);
   if constexpr (kTerr)
     launch_column_terrain<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, tr.wcc0, s);
   else
     launch_column<T>(en, 0, st, wk.ddt_w0, wk.ddt_w1, s);
   // ---------------- corrector ----------------
   launch_velocity_tendencies<T>(x, wk.vn_p, s_wp, wk.ddt_vn1, wk.ddt_w1, wk.divd, wk.divd2, s, threads,
-                                kTerr ? tr.wcc1 : nullptr);
-  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_by_point<T>(g.ne, nlev, TH(8)), TH(8), s,
-              sn_edge_corr<T>, g, v, x.s, st.vn, wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn);
+                                kTerr ? tr.wcc1 : nullptr, shapes);
+  ICON_LAUNCH(kname<T>("sn_edge_corr", "sn_edge_corr_f32"), blocks_by_shape(SH(8), g.ne, nlev, TH(8)), TH(8), s,
+              sn_edge_corr<T>, g, v, x.s, st.vn, wk.ddt_vn0, wk.ddt_vn1, wk.hpg, wk.divd2, m.vn, SH(8));
   const T* vn_new = kMixed<T> ? (const T*)m.vn : (const T*)st.vn;
-  ICON_LAUNCH(nm_div, blocks_by_point<T>(g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, vn_new,
-              wk.divd, nullptr, nullptr, ex_ref_c);
-  ICON_LAUNCH(nm_flx, blocks_by_point<T>(g.nc, nlev, TH(7)), TH(7), s, (sn_cell_fluxdiv<T, kTerr>), g, v, x.s,
-              vn_new, wk.divd, wk.rho_e, wk.theta_e, en.g64.div_c, en.wk.div_m, en.wk.div_t, tr.fx_ratio);
+  ICON_LAUNCH(nm_div, blocks_by_shape(SH(6), g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, vn_new,
+              wk.divd, nullptr, nullptr, ex_ref_c, SH(6));
+  launch_fluxdiv<T, kTerr>(en, x, vn_new, nm_flx, s);
   if constexpr (kTerr)
     launch_column_terrain<T>(en, 1, st, wk.ddt_w0, wk.ddt_w1, tr.wcc1, s);
   else
@@ -938,7 +1032,7 @@ void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
 const char* const kStencilNames[kNumStencils] = {
     "va_edge_pre", "va_cell_vert", "va_edge_tend", "va_cell_w", "sn_cell_grad", "sn_edge_pred", "sn_cell_div",
     "sn_cell_fluxdiv", "sn_edge_corr", "diff_div_curl_uv", "diff_edge_smag", "diff_second", "diff_edge_update",
-    "diff_cell_update", "va_concorr"};
+    "diff_cell_update", "va_concorr", "sn_edge_flux"};
 
 void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t s) {
   const int nlev = en.v.nlev;
@@ -948,7 +1042,8 @@ void launch_refresh_mirrors(const Engine& en, const StateView& st, cudaStream_t 
 }
 
 template void launch_velocity_tendencies<double>(const Ctx<double>&, const double*, const double*, double*, double*,
-                                                 const double*, double*, cudaStream_t, const int*, double*);
+                                                 const double*, double*, cudaStream_t, const int*, double*,
+                                                 const int*);
 template void launch_substep<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
 template void launch_substep<float>(const Engine&, const Ctx<float>&, const StateView&, cudaStream_t);
 template void launch_diffusion<double>(const Engine&, const Ctx<double>&, const StateView&, cudaStream_t);
