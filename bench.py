@@ -61,9 +61,10 @@ def hbm_peak():
 # Algorithmic FP64 flops per unit (FMA = 2, add/mul/div/sqrt = 1), counted
 # from the formulas each kernel evaluates; the unit is one (point, level).
 FLOPS_PER_UNIT = {
-    "va_edge_pre": 13, "va_cell_vert": 17, "va_edge_tend": 38, "va_cell_w": 13,
-    "sn_cell_grad": 28, "sn_edge_pred": 38, "sn_cell_div": 5, "sn_cell_fluxdiv": 27,
-    "sn_column_pred": 86, "sn_edge_corr": 17, "sn_column_corr": 94,
+    "va_edge_pre": 16, "va_cell_vert": 17, "va_edge_tend": 30, "va_cell_w": 11,
+    "sn_cell_grad": 28, "sn_edge_pred": 24, "sn_cell_div": 5, "sn_cell_fluxdiv": 27,
+    "sn_edge_flux": 6, "sn_cell_fluxsum": 12,
+    "sn_column_pred": 86, "sn_edge_corr": 11, "sn_column_corr": 94,
     "diff_div_curl_uv": 30, "diff_edge_smag": 46, "diff_second": 30,
     "diff_edge_update": 12, "diff_cell_update": 12, "va_concorr": 20,
 }
@@ -89,7 +90,8 @@ def units_per_launch(name, nc, ne, nv, nlev):
         "va_edge_pre": full["e"], "va_cell_vert": full["c"] + half["v"], "va_edge_tend": half["e"],
         "va_cell_w": half["c"], "va_concorr": half["c"], "sn_cell_grad": full["c"], "sn_edge_pred": full["e"],
         "sn_column_pred": full["c"], "sn_edge_corr": full["e"], "sn_column_corr": full["c"],
-        "sn_cell_div": full["c"], "sn_cell_fluxdiv": full["c"],
+        "sn_cell_div": full["c"], "sn_cell_fluxdiv": full["c"], "sn_edge_flux": full["e"],
+        "sn_cell_fluxsum": full["c"],
         "diff_div_curl_uv": full["c"] + full["v"], "diff_edge_smag": full["e"],
         "diff_second": half["c"] + full["v"], "diff_edge_update": full["e"], "diff_cell_update": half["c"],
         "mx_refresh": full["e"] + half["c"],

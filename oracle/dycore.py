@@ -397,6 +397,8 @@ class Dycore:
           w  <- w - k4w A_c^2 lapc(lapc(w))          (interior half levels)
           theta <- theta + dt (1/A_c) sum_e l_e nu_e (theta_nbr - theta_c)/d_e
           exner <- exner (1 + (R_d/c_vd)(theta_new - theta)/theta)
+        with, for theta only and when hdiff_tenh_fac > 0, nu_e raised by
+        hdiff_tenh_fac A_e / dt max(e_c0, e_c1) (enhanced_edge_factor).
         Row A10, Sec. 4.1 (nh_diffusion), a reading."""
         p, g, v = self.p, self.g, self.v
         dt = p.dtime
@@ -413,6 +415,8 @@ class Dycore:
         out = dict(st)
         out["vn"], out["w"] = vn_new, w_new
         if p.hdiff_temp:
+            if p.hdiff_tenh_fac > 0.0:   # enhanced near-surface temperature diffusion
+                nu = nu + p.hdiff_tenh_fac * g.edge_area[:, None] / dt * self.enhanced_edge_factor(theta)
             flux = np.zeros_like(theta)
             for j in range(3):
                 e = g.c2e[:, j]
@@ -422,6 +426,18 @@ class Dycore:
             out["theta_v"] = th_new
             out["exner"] = exner * (1.0 + (p.rd / p.cvd) * (th_new - theta) / theta)
         return out
+
+    def enhanced_edge_factor(self, theta):
+        """max(e_c0, e_c1) per edge and level: e_c = min(1, (|theta_c - mean of
+        its three neighbours| - thresh) / thresh) in the lowest
+        hdiff_tenh_levels levels where above the threshold, else 0.
+        Row A10, the diffusion's increased coefficients for strong near-surface
+        temperature gradients (Sec. 4.1), a reading."""
+        p, g = self.p, self.g
+        nbr = (theta[g.c2e2c[:, 0]] + theta[g.c2e2c[:, 1]] + theta[g.c2e2c[:, 2]]) / 3.0
+        ex = np.clip((np.abs(theta - nbr) - p.hdiff_tenh_thresh) / p.hdiff_tenh_thresh, 0.0, 1.0)
+        ex[:, :theta.shape[1] - p.hdiff_tenh_levels] = 0.0
+        return np.maximum(ex[g.e2c[:, 0]], ex[g.e2c[:, 1]])
 
     # ------------------------------------------------------------------
     def step(self, st):

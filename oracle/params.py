@@ -42,6 +42,15 @@ class DycoreParams:
     hdiff_temp: bool = True
     # reference state theta_ref(z) = T0 * exp(z / H), H = cpd * T0 / grav
     ref_T0: float = 250.0
+    # steep terrain (terrain-following heights only): the horizontal pressure
+    # gradient at constant height where the levels of the two cells of an edge
+    # are offset by more than half a layer (steep_hpg), and enhanced
+    # temperature diffusion where the lowest levels hold strong horizontal
+    # temperature differences (factor 0 switches it off)
+    steep_hpg: bool = False
+    hdiff_tenh_fac: float = 0.0
+    hdiff_tenh_thresh: float = 5.0
+    hdiff_tenh_levels: int = 5
 
     @property
     def cvd(self):

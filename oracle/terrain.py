@@ -40,6 +40,21 @@ Readings:
 * Diffusion along model levels as in the flat oracle (the truly horizontal
   diffusion of steep terrain is not part of this reading); it leaves the ground
   value of w unchanged.
+
+Steep terrain (the paper's diffusion raises its coefficients for strong
+near-surface temperature gradients, Sec. 4.1; its dycore runs over real,
+steep orography), two options of DycoreParams:
+
+* steep_hpg: at an edge full level whose two cells' levels are offset by more
+  than half a layer -- the level of a neighbour column nearest to the edge's
+  height z_e (the mean of the two cells' full-level heights) is not the same
+  level -- the pressure gradient is taken at constant height: each cell's
+  extrapolated exner perturbation is interpolated to z_e by the quadratic
+  through the three consecutive levels of that column nearest to z_e
+  (Lagrange weights), and hpg = cpd theta_e (pi_c1(z_e) - pi_c0(z_e)) / d_e.
+  Elsewhere the chain-rule form above.
+* hdiff_tenh_fac > 0: the enhanced near-surface temperature diffusion of the
+  flat oracle's diffusion (dycore.py), here along the terrain-following levels.
 """
 import numpy as np
 
@@ -88,6 +103,34 @@ class TerrainColumns:
         # normal slopes on half and full levels
         self.ddxn_ifc = (z[c1] - z[c0]) / g.dual_length[:, None]
         self.ddxn_mc = (self.z_mc[c1] - self.z_mc[c0]) / g.dual_length[:, None]
+        self.steep = self.constant_height_stencil(g)
+
+    def constant_height_stencil(self, g):
+        """For every edge full level: the steep flag and, per adjacent cell s,
+        the first of the three consecutive levels nearest to the edge height
+        z_e and the Lagrange weights of z_e on them (steep_hpg option).
+        Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
+        nlev = self.nlev
+        c0, c1 = g.e2c[:, 0], g.e2c[:, 1]
+        z_e = 0.5 * (self.z_mc[c0] + self.z_mc[c1])
+        out = {"flag": np.zeros(z_e.shape, dtype=bool)}
+        levels = np.arange(nlev)[None, :]
+        for s, c in enumerate((c0, c1)):
+            zc = self.z_mc[c]
+            nearest = np.empty(z_e.shape, dtype=np.int64)
+            for k in range(nlev):
+                nearest[:, k] = np.argmin(np.abs(zc - z_e[:, k:k + 1]), axis=1)
+            k0 = np.clip(nearest - 1, 0, nlev - 3)
+            zz = [np.take_along_axis(zc, k0 + j, axis=1) for j in range(3)]
+            L = []
+            for j in range(3):
+                a, b = [zz[i] for i in range(3) if i != j]
+                L.append((z_e - a) * (z_e - b) / ((zz[j] - a) * (zz[j] - b)))
+            out["k0_%d" % s] = k0
+            out["w_%d" % s] = np.stack(L, axis=-1)
+            out["flag"] |= nearest != levels
+        out["z_e"] = z_e
+        return out
 
     def interp_ic(self, x):
         """Interior half-level values [nc, nlev+1] of a cell field; ends NaN.
@@ -205,7 +248,18 @@ class TerrainDycore(Dycore):
         dpdz[:, 0] = (pr_ex[:, 0] - pr_ex[:, 1]) / (zm[:, 0] - zm[:, 1])
         dpdz[:, -1] = (pr_ex[:, -2] - pr_ex[:, -1]) / (zm[:, -2] - zm[:, -1])
         dpdz_e = 0.5 * (dpdz[g.e2c[:, 0]] + dpdz[g.e2c[:, 1]])
-        return self.p.cpd * theta_e * (self.grad_n(pr_ex) - v.ddxn_mc * dpdz_e)
+        hpg = self.p.cpd * theta_e * (self.grad_n(pr_ex) - v.ddxn_mc * dpdz_e)
+        if self.p.steep_hpg:
+            st = v.steep
+            at_z = []
+            tot = pr_ex + v.exner_ref          # the total exner is smooth in height
+            for s in (0, 1):
+                col = tot[g.e2c[:, s]]
+                k0, w = st["k0_%d" % s], st["w_%d" % s]
+                at_z.append(sum(w[..., j] * np.take_along_axis(col, k0 + j, axis=1) for j in range(3)))
+            flat_z = self.p.cpd * theta_e * (at_z[1] - at_z[0]) / g.dual_length[:, None]
+            hpg = np.where(st["flag"], flat_z, hpg)
+        return hpg
 
     def layer_div(self, F):
         """Flux divergence per unit volume of a layer: (1/dz_c) div(F dz_e).
@@ -310,8 +364,9 @@ class TerrainDycore(Dycore):
 
     # ---------------------------------------------------------------- A10
     def diffusion(self, st):
-        """The flat diffusion along model levels; the ground value of w (the
-        kinematic condition) is left as it is.
+        """The flat diffusion along model levels (with the enhanced near-surface
+        temperature diffusion when hdiff_tenh_fac > 0); the ground value of w
+        (the kinematic condition) is left as it is.
         Terrain reading of rows A0-A7 (Sec. 4.1), stated in the module docstring."""
         out = super().diffusion(st)
         out["w"][:, self.v.nlev] = st["w"][:, self.v.nlev]

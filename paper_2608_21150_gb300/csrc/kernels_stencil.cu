@@ -101,51 +101,49 @@ const char* kname(const char* f64, const char* f32) {
 // Also vn at the half levels, vn_ie (interpolated inside with the level
 // weights -- the edge weights wgt_e over terrain -- the top level's value at the
 // top and the lowest level's at the ground), for the edge tendency kernel.
+// Both tile shapes evaluate every (edge, level) with the same explicit FMAs
+// (va_edge_pre_at), so the autotuner's choice of shape does not change a bit.
+template <class T>
+__device__ __forceinline__ void va_edge_pre_at(const VertT<T>& v, int e, int k, int nlev, const T* x0, const T* x1,
+                                               const T* x2, const T* x3, const T* x4, const T* w, T* vt, T* ekin,
+                                               T* vn_ie, const T* wgt_e) {
+  const int nlevp = nlev + 1;
+  const T vne = x0[k];
+  T t = w[0] * vne;
+  t = fmat(w[1], x1[k], t);
+  t = fmat(w[2], x2[k], t);
+  t = fmat(w[3], x3[k], t);
+  t = fmat(w[4], x4[k], t);
+  vt[(size_t)e * nlev + k] = t;
+  ekin[(size_t)e * nlev + k] = T(0.5) * fmat(vne, vne, t * t);
+  const T wg = wgt_e ? wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
+  vn_ie[(size_t)e * nlevp + k] = k == 0 ? vne : fmat(wg, x0[k - 1] - vne, vne);
+  if (k == nlev - 1) vn_ie[(size_t)e * nlevp + nlev] = vne;
+}
+
 template <class T>
 __global__ void va_edge_pre(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ vt,
                             T* __restrict__ ekin, T* __restrict__ vn_ie, const T* __restrict__ wgt_e, int shape) {
-  const int nlev = v.nlev, nlevp = nlev + 1;
-  if (shape) {
+  const int nlev = v.nlev;
+  if (shape) {  // one warp per edge, its lanes over the levels
     const int e = warp_point();
     if (e >= g.ne) return;
     const T* w = g.vt_w + 5 * (size_t)e;
+    const T wl[5] = {w[0], w[1], w[2], w[3], w[4]};
     const int* q = g.e2c2e + 4 * (size_t)e;
-    const T w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
     const T* x0 = vn + (size_t)e * nlev;
     const T* x1 = vn + (size_t)q[0] * nlev;
     const T* x2 = vn + (size_t)q[1] * nlev;
     const T* x3 = vn + (size_t)q[2] * nlev;
     const T* x4 = vn + (size_t)q[3] * nlev;
-    for (int k = lane_id(); k < nlev; k += 32) {
-      const T vne = x0[k];
-      T t = w0 * vne;
-      t += w1 * x1[k];
-      t += w2 * x2[k];
-      t += w3 * x3[k];
-      t += w4 * x4[k];
-      vt[(size_t)e * nlev + k] = t;
-      ekin[(size_t)e * nlev + k] = T(0.5) * (vne * vne + t * t);
-      const T wg = wgt_e ? wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
-      vn_ie[(size_t)e * nlevp + k] = k == 0 ? vne : vne + wg * (x0[k - 1] - vne);
-      if (k == nlev - 1) vn_ie[(size_t)e * nlevp + nlev] = vne;
-    }
+    for (int k = lane_id(); k < nlev; k += 32) va_edge_pre_at(v, e, k, nlev, x0, x1, x2, x3, x4, wl, vt, ekin, vn_ie, wgt_e);
     return;
   }
   int e, k;
   if (!flat_index(g.ne, nlev, e, k)) return;
-  const T* w = g.vt_w + 5 * (size_t)e;
   const int* q = g.e2c2e + 4 * (size_t)e;
-  const T vne = vn[(size_t)e * nlev + k];
-  T t = w[0] * vne;
-  t += w[1] * vn[(size_t)q[0] * nlev + k];
-  t += w[2] * vn[(size_t)q[1] * nlev + k];
-  t += w[3] * vn[(size_t)q[2] * nlev + k];
-  t += w[4] * vn[(size_t)q[3] * nlev + k];
-  vt[(size_t)e * nlev + k] = t;
-  ekin[(size_t)e * nlev + k] = T(0.5) * (vne * vne + t * t);
-  const T wg = wgt_e ? wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
-  vn_ie[(size_t)e * nlevp + k] = k == 0 ? vne : vne + wg * (vn[(size_t)e * nlev + k - 1] - vne);
-  if (k == nlev - 1) vn_ie[(size_t)e * nlevp + nlev] = vne;
+  va_edge_pre_at(v, e, k, nlev, vn + (size_t)e * nlev, vn + (size_t)q[0] * nlev, vn + (size_t)q[1] * nlev,
+                 vn + (size_t)q[2] * nlev, vn + (size_t)q[3] * nlev, g.vt_w + 5 * (size_t)e, vt, ekin, vn_ie, wgt_e);
 }
 
 // -------------------------------------------------------------------------
@@ -289,57 +287,51 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn_ie
 //   ddt_w = -sum q_e gw_e - w (wf_{k-1} - wf_k)/dzh,  wf full-level averages
 // -------------------------------------------------------------------------
 // Over terrain (kTerr): advected by w - wcc, per-cell half-level spacing.
+// Both tile shapes evaluate every (cell, half level) with va_cell_w_at.
+template <class T, bool kTerr>
+__device__ __forceinline__ T va_cell_w_at(const VertT<T>& v, const TerrT<T>& tr, int c, int k, int nlev,
+                                          const T* g0, const T* g1, const T* g2, const T* q, const T* wc,
+                                          const T* wcc) {
+  if (k == 0 || k >= nlev) return T(0);
+  const T h = fmat(q[2], g2[k], fmat(q[1], g1[k], q[0] * g0[k]));
+  // the difference of the full-level means above and below, (w_k-1 - w_k+1) / 2,
+  // with the 1/2 folded into the stored 1/(2 dzh)
+  T wa, qd;
+  if constexpr (kTerr) {
+    const size_t ih = (size_t)c * (nlev + 1) + k;
+    wa = wc[k] - wcc[ih];
+    qd = tr.qdzh_c[ih];
+  } else {
+    wa = wc[k];
+    qd = v.qdzh[k];
+  }
+  return fmat(-(wa * (wc[k - 1] - wc[k + 1])), qd, -h);
+}
+
 template <class T, bool kTerr = false>
 __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const T* __restrict__ gw_e,
                           T* __restrict__ ddt_w, TerrT<T> tr, const T* __restrict__ wcc, int shape) {
   const int nlev = v.nlev, nlevp = nlev + 1;
-  if (shape) {
+  if (shape) {  // one warp per cell, its lanes over the half levels
     const int c = warp_point();
     if (c >= g.nc) return;
     const int* ce = g.c2e + 3 * (size_t)c;
-    const T* q = g.e2c_w + 3 * (size_t)c;
-    const T q0 = q[0], q1 = q[1], q2 = q[2];
+    const T* qp = g.e2c_w + 3 * (size_t)c;
+    const T q[3] = {qp[0], qp[1], qp[2]};
     const T* g0 = gw_e + (size_t)ce[0] * nlevp;
     const T* g1 = gw_e + (size_t)ce[1] * nlevp;
     const T* g2 = gw_e + (size_t)ce[2] * nlevp;
     const T* wc = w + (size_t)c * nlevp;
-    for (int k = lane_id(); k < nlevp; k += 32) {
-      T r = 0;
-      if (k > 0 && k < nlev) {
-        T h = q0 * g0[k];
-        h += q1 * g1[k];
-        h += q2 * g2[k];
-        if constexpr (kTerr) {
-          const size_t ih = (size_t)c * nlevp + k;
-          r = -h - (wc[k] - wcc[ih]) * (wc[k - 1] - wc[k + 1]) * tr.qdzh_c[ih];
-        } else {
-          r = -h - wc[k] * (wc[k - 1] - wc[k + 1]) * v.qdzh[k];
-        }
-      }
-      ddt_w[(size_t)c * nlevp + k] = r;
-    }
+    for (int k = lane_id(); k < nlevp; k += 32)
+      ddt_w[(size_t)c * nlevp + k] = va_cell_w_at<T, kTerr>(v, tr, c, k, nlev, g0, g1, g2, q, wc, wcc);
     return;
   }
   int c, k;
   if (!flat_index(g.nc, nlevp, c, k)) return;
-  T r = 0;
-  if (k > 0 && k < nlev) {
-    const int* ce = g.c2e + 3 * (size_t)c;
-    const T* q = g.e2c_w + 3 * (size_t)c;
-    T h = q[0] * gw_e[(size_t)ce[0] * nlevp + k];
-    h += q[1] * gw_e[(size_t)ce[1] * nlevp + k];
-    h += q[2] * gw_e[(size_t)ce[2] * nlevp + k];
-    const T* wc = w + (size_t)c * nlevp;
-    // the difference of the full-level means above and below, (w_k-1 - w_k+1) / 2,
-    // with the 1/2 folded into the stored 1/(2 dzh)
-    if constexpr (kTerr) {
-      const size_t ih = (size_t)c * nlevp + k;
-      r = -h - (wc[k] - wcc[ih]) * (wc[k - 1] - wc[k + 1]) * tr.qdzh_c[ih];
-    } else {
-      r = -h - wc[k] * (wc[k - 1] - wc[k + 1]) * v.qdzh[k];
-    }
-  }
-  ddt_w[(size_t)c * nlevp + k] = r;
+  const int* ce = g.c2e + 3 * (size_t)c;
+  ddt_w[(size_t)c * nlevp + k] =
+      va_cell_w_at<T, kTerr>(v, tr, c, k, nlev, gw_e + (size_t)ce[0] * nlevp, gw_e + (size_t)ce[1] * nlevp,
+                             gw_e + (size_t)ce[2] * nlevp, g.e2c_w + 3 * (size_t)c, w + (size_t)c * nlevp, wcc);
 }
 
 // -------------------------------------------------------------------------
@@ -458,40 +450,15 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
 // tendencies, the predictor's pressure gradient and fourth-order divergence
 // damping; the increment is formed in T, the update in FP64 (in place).
 // -------------------------------------------------------------------------
+// Both tile shapes update every (edge, level) with sn_edge_corr_at.
 template <class T>
-__global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __restrict__ vn,
-                             const T* __restrict__ ddt_vn0, const T* __restrict__ ddt_vn1,
-                             const T* __restrict__ hpg, const T* __restrict__ divd2, float* __restrict__ m_vn,
-                             int shape) {
-  const int nlev = v.nlev;
-  if (shape) {
-    const int e = warp_point();
-    if (e >= g.ne) return;
-    const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-    const T ddamp = g.ddamp_e[e];
-    const T* d0 = divd2 + (size_t)c0 * nlev;
-    const T* d1 = divd2 + (size_t)c1 * nlev;
-    for (int k = lane_id(); k < nlev; k += 32) {
-      const size_t ie = (size_t)e * nlev + k;
-      const T damp = ddamp * (d1[k] - d0[k]);
-      const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - damp;
-      if constexpr (kMixed<T>) {
-        const double vnn = vn[ie] + f2d(inc);
-        vn[ie] = vnn;
-        m_vn[ie] = d2f(vnn);
-      } else {
-        vn[ie] = vn[ie] + (double)inc;
-      }
-    }
-    return;
-  }
-  int e, k;
-  if (!flat_index(g.ne, nlev, e, k)) return;
-  const size_t ie = (size_t)e * nlev + k;
-  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+__device__ __forceinline__ void sn_edge_corr_at(const ScalT<T>& sc, size_t ie, T ddamp, T d0k, T d1k,
+                                                double* vn, const T* ddt_vn0, const T* ddt_vn1, const T* hpg,
+                                                float* m_vn) {
   // fourth-order divergence damping: divdamp_fac Abar^2 grad_n(dd2), coefficient per edge
-  const T damp = g.ddamp_e[e] * (divd2[(size_t)c1 * nlev + k] - divd2[(size_t)c0 * nlev + k]);
-  const T inc = sc.dt_s * (sc.wnow_vel * ddt_vn0[ie] + sc.wnew_vel * ddt_vn1[ie] - hpg[ie]) - damp;
+  const T damp = ddamp * (d1k - d0k);
+  const T tend = fmat(sc.wnow_vel, ddt_vn0[ie], fmat(sc.wnew_vel, ddt_vn1[ie], -hpg[ie]));
+  const T inc = fmat(sc.dt_s, tend, -damp);
   if constexpr (kMixed<T>) {
     const double vnn = vn[ie] + f2d(inc);
     vn[ie] = vnn;
@@ -501,18 +468,43 @@ __global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __rest
   }
 }
 
+template <class T>
+__global__ void sn_edge_corr(GridT<T> g, VertT<T> v, ScalT<T> sc, double* __restrict__ vn,
+                             const T* __restrict__ ddt_vn0, const T* __restrict__ ddt_vn1,
+                             const T* __restrict__ hpg, const T* __restrict__ divd2, float* __restrict__ m_vn,
+                             int shape) {
+  const int nlev = v.nlev;
+  if (shape) {  // one warp per edge, its lanes over the levels
+    const int e = warp_point();
+    if (e >= g.ne) return;
+    const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+    const T ddamp = g.ddamp_e[e];
+    const T* d0 = divd2 + (size_t)c0 * nlev;
+    const T* d1 = divd2 + (size_t)c1 * nlev;
+    for (int k = lane_id(); k < nlev; k += 32)
+      sn_edge_corr_at(sc, (size_t)e * nlev + k, ddamp, d0[k], d1[k], vn, ddt_vn0, ddt_vn1, hpg, m_vn);
+    return;
+  }
+  int e, k;
+  if (!flat_index(g.ne, nlev, e, k)) return;
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  sn_edge_corr_at(sc, (size_t)e * nlev + k, g.ddamp_e[e], divd2[(size_t)c0 * nlev + k],
+                  divd2[(size_t)c1 * nlev + k], vn, ddt_vn0, ddt_vn1, hpg, m_vn);
+}
+
 // -------------------------------------------------------------------------
 // Cell divergence D = (1/A_c) sum_e s l_e vn_e of vn* (fourth-order damping and
 // flux filter of the predictor) or vn^{n+1} (flux filter of the corrector).
 // The predictor launch also updates the exner extrapolation history,
 // exner_pr = exner - exner_ref (sn_edge_pred, its last reader, has completed).
+// Both tile shapes evaluate every (cell, level) with the same FMAs.
 // -------------------------------------------------------------------------
 template <class T, bool kTerr = false>
 __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T* __restrict__ divd,
                             const double* __restrict__ exner, double* __restrict__ exner_pr,
                             const double* __restrict__ exner_ref_c, int shape) {
   const int nlev = v.nlev;
-  if (shape) {
+  if (shape) {  // one warp per cell, its lanes over the levels
     const int c = warp_point();
     if (c >= g.nc) return;
     const int* ce = g.c2e + 3 * (size_t)c;
@@ -523,7 +515,7 @@ __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
     const T* x2 = vn + (size_t)ce[2] * nlev;
     for (int k = lane_id(); k < nlev; k += 32) {
       const size_t i = (size_t)c * nlev + k;
-      divd[i] = dv0 * x0[k] + dv1 * x1[k] + dv2 * x2[k];
+      divd[i] = fmat(dv2, x2[k], fmat(dv1, x1[k], dv0 * x0[k]));
       if (exner_pr) exner_pr[i] = exner[i] - (kTerr ? exner_ref_c[i] : v.exner_ref[k]);
     }
     return;
@@ -533,8 +525,8 @@ __global__ void sn_cell_div(GridT<T> g, VertT<T> v, const T* __restrict__ vn, T*
   const int* ce = g.c2e + 3 * (size_t)c;
   const T* dv = g.div_c + 3 * (size_t)c;
   const size_t i = (size_t)c * nlev + k;
-  divd[i] = dv[0] * vn[(size_t)ce[0] * nlev + k] + dv[1] * vn[(size_t)ce[1] * nlev + k] +
-            dv[2] * vn[(size_t)ce[2] * nlev + k];
+  divd[i] = fmat(dv[2], vn[(size_t)ce[2] * nlev + k], fmat(dv[1], vn[(size_t)ce[1] * nlev + k],
+                                                           dv[0] * vn[(size_t)ce[0] * nlev + k]));
   if (exner_pr) exner_pr[i] = exner[i] - (kTerr ? exner_ref_c[i] : v.exner_ref[k]);
 }
 
