@@ -33,6 +33,9 @@ module icon_dycore
     integer(c_int32_t) :: precision, use_graph, autotune, synchronous
     type(c_ptr) :: stream
     integer(c_int32_t) :: column_chunk
+    integer(c_int32_t) :: steep_hpg
+    real(c_double) :: hdiff_tenh_fac, hdiff_tenh_thresh
+    integer(c_int32_t) :: hdiff_tenh_levels
   end type
 
   type, bind(c), public :: icon_state_t

@@ -130,6 +130,16 @@ typedef struct icon_dycore_params {
   void* stream;            /* cudaStream_t to enqueue on; NULL = default stream */
   int32_t column_chunk;    /* levels per shared-memory chunk of the column solve: 4, 6 or 8;
                               0 = 4, or the autotuner's choice when autotune is set */
+  /* steep terrain (Sec. 4.1: the dycore runs over real orography; its diffusion
+   * raises the coefficients for strong near-surface temperature gradients) */
+  int32_t steep_hpg;       /* logical, terrain only: the horizontal pressure gradient at
+                              constant height (quadratic interpolation of the total exner
+                              of each cell to the edge's height) at edge levels where the
+                              two cells' levels are offset by more than half a layer */
+  double hdiff_tenh_fac;   /* enhanced temperature diffusion: edge coefficient
+                              fac A_e / dtime max(e_c0, e_c1); 0 = off */
+  double hdiff_tenh_thresh;  /* K: e_c = min(1, (|theta_c - mean of its 3 neighbours| - thresh)/thresh) */
+  int32_t hdiff_tenh_levels; /* the lowest levels where e_c may be nonzero */
 } icon_dycore_params_t;
 
 /* Writes the defaults (Sec. 4.1 names the scheme's parts, not its values;
@@ -137,7 +147,9 @@ typedef struct icon_dycore_params {
  * weights 0.25/0.75, rho/theta weights 0.6/0.4, exner_exfac 1/3,
  * divdamp_fac 0.0025, divflux_fac 0.07, Rayleigh off (coeff 0, height 20 km), Smagorinsky
  * 0.015, k4 = k4w = 1/288, hdiff_temp 1, ref_T0 250, FP64, graph on,
- * autotune on, synchronous, default stream.  NULL-safe (does nothing). */
+ * autotune on, synchronous, default stream, steep_hpg off, enhanced
+ * temperature diffusion off (factor 0, threshold 5 K, lowest 5 levels).
+ * NULL-safe (does nothing). */
 void icon_dycore_params_default(icon_dycore_params_t* p);
 
 /*

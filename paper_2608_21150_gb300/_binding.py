@@ -60,7 +60,9 @@ class icon_dycore_params_t(ctypes.Structure):
                 ("hdiff_k4", ctypes.c_double), ("hdiff_w_k4", ctypes.c_double),
                 ("hdiff_temp", ctypes.c_int32), ("ref_T0", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("synchronous", ctypes.c_int32), ("stream", ctypes.c_void_p), ("column_chunk", ctypes.c_int32)]
+                ("synchronous", ctypes.c_int32), ("stream", ctypes.c_void_p), ("column_chunk", ctypes.c_int32),
+                ("steep_hpg", ctypes.c_int32), ("hdiff_tenh_fac", ctypes.c_double),
+                ("hdiff_tenh_thresh", ctypes.c_double), ("hdiff_tenh_levels", ctypes.c_int32)]
 
 
 class icon_state_t(ctypes.Structure):

@@ -147,6 +147,10 @@ void icon_dycore_params_default(icon_dycore_params_t* p) {
   p->synchronous = 1;
   p->stream = nullptr;
   p->column_chunk = 0;
+  p->steep_hpg = 0;
+  p->hdiff_tenh_fac = 0.0;
+  p->hdiff_tenh_thresh = 5.0;
+  p->hdiff_tenh_levels = 5;
 }
 
 int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
@@ -402,6 +406,10 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     return fail(ICON_ERR_ARG, fname + ": precision must be ICON_PREC_FP64, ICON_PREC_MIXED or ICON_PREC_MIXED_F64COL");
   if (p->column_chunk != 0 && p->column_chunk != 4 && p->column_chunk != 6 && p->column_chunk != 8)
     return fail(ICON_ERR_ARG, fname + ": column_chunk must be 0, 4, 6 or 8");
+  if (!(p->hdiff_tenh_fac >= 0.0) || (p->hdiff_tenh_fac > 0.0 && !(p->hdiff_tenh_thresh > 0.0)) ||
+      p->hdiff_tenh_levels < 0 || p->hdiff_tenh_levels > nlev)
+    return fail(ICON_ERR_ARG, fname + ": enhanced temperature diffusion needs fac >= 0, thresh > 0, 0 <= levels <= nlev");
+  if (p->steep_hpg && nlev < 3) return fail(ICON_ERR_ARG, fname + ": steep_hpg needs nlev >= 3");
   // terrain: every column validated and its metrics derived before any allocation
   HostTerrain ht;
   if (z_cols) {
@@ -495,7 +503,9 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
   for (int c = 0; c < nc; ++c) k4w[c] = p->hdiff_w_k4 * h.cell_area[c] * h.cell_area[c];
   // dycore-level factors of the predictor's edge kernel: upwind offsets with
   // the half-substep scaling folded in, and cpd / d_e
-  std::vector<double> upw_s(h.upw), cid(ne);
+  std::vector<double> upw_s(h.upw), cid(ne), tenh(ne);
+  for (int e = 0; e < ne; ++e) tenh[e] = p->hdiff_tenh_fac * h.edge_area[e] / p->dtime;
+  const bool tenh_on = p->hdiff_temp && p->hdiff_tenh_fac > 0.0 && p->hdiff_tenh_levels > 0;
   for (int e = 0; e < ne; ++e) {
     for (int side = 0; side < 2; ++side)
       for (int j = 2; j < 6; ++j) upw_s[12 * (size_t)e + 6 * side + j] *= 0.5 * s.dt_s;
@@ -504,6 +514,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
   en.g64 = grid->dev;
   en.g64.upw_s = A.upload(upw_s);
   en.g64.cpd_inv_d = A.upload(cid);
+  en.g64.tenh_a = tenh_on ? A.upload(tenh) : nullptr;
   en.g64.f_e = A.upload(fe);
   en.g64.smag_a = A.upload(smag);
   en.g64.k4_a = A.upload(k4);
@@ -542,6 +553,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     g.upw = up(h.upw);
     g.upw_s = up(upw_s);
     g.cpd_inv_d = up(cid);
+    g.tenh_a = tenh_on ? up(tenh) : nullptr;
     g.nt = up(h.nt);
     g.inv_dn = up(h.inv_dn);
     g.smag_a = up(smag);
@@ -580,6 +592,8 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     st.wnow_vel = (T)s.wnow_vel;
     st.wnew_vel = (T)s.wnew_vel;
     st.hdiff_temp = s.hdiff_temp;
+    st.tenh_levels = tenh_on ? p->hdiff_tenh_levels : 0;
+    st.tenh_thresh = (T)p->hdiff_tenh_thresh;
     WorkT<T>& w = x.w;
     w.vt = A.template alloc<T>(ef);
     w.ekin_e = A.template alloc<T>(ef);
@@ -604,6 +618,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     w.dtheta = A.template alloc<T>(cf);
     w.div_l = A.template alloc<T>(cf);
     w.div_vn = A.template alloc<T>(cf);
+    w.tenh_ex = tenh_on ? A.template alloc<T>(cf) : nullptr;
     w.ddt_w0 = A.template alloc<T>(ch);
     w.ddt_w1 = A.template alloc<T>(ch);
     w.lap_w = A.template alloc<T>(ch);
@@ -666,6 +681,11 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     else
       build_terr(en.c32, float{});
     std::vector<double>().swap(ht.colt);  // the largest host copy, released early
+    v.n_steep = (int)(ht.steep_w.size() / 6);
+    if (v.n_steep > 0) {
+      v.steep_idx = A.upload(ht.steep_idx);
+      v.steep_w = A.upload(ht.steep_w);
+    }
   }
 
   // FP64 work of the column solve and the predicted state

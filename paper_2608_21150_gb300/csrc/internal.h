@@ -38,6 +38,7 @@ struct GridT {
   const T* upw;     // [ne*12] per upwind side s: (dx, dy, nx, ny, tx, ty) in that cell's frame
   const T* upw_s;   // [ne*12] the same with n and t scaled by dt_s/2 (the back trajectory's half substep)
   const T* cpd_inv_d;  // [ne] cpd / d_e (the horizontal pressure gradient's factor)
+  const T* tenh_a;  // [ne] hdiff_tenh_fac A_e / dtime (enhanced temperature diffusion; null when off)
   const T* nt;      // [ne*6] normal xyz, tangent xyz
   const T* inv_dn;  // [ne] 1/(arc between the two opposite diamond vertices)
   const T* smag_a;  // [ne] hdiff_smag_fac * A_e
@@ -91,6 +92,8 @@ template <class T>
 struct ScalT {
   T dt_s, dtime, cpd, exfac, divdamp, divflux, wnow_vel, wnew_vel;
   int hdiff_temp;
+  int tenh_levels;  // enhanced temperature diffusion: the lowest levels it may act on (0: off)
+  T tenh_thresh;    // its theta_v threshold, K
 };
 
 // Vertical metrics and reference state in device memory.
@@ -124,6 +127,12 @@ struct DevVert {
   const double* theta_ref_c;  // [nc*nlev]
   const double* dz_c;         // [nc*nlev]
   const double* colt;         // [12*(nlev+1)*nc]
+  // steep terrain: the edge levels where the pressure gradient is taken at
+  // constant height, steep_idx[4 i] = (edge, level, first level of the
+  // quadratic in e2c[0], in e2c[1]), steep_w[6 i] = its Lagrange weights
+  int n_steep;
+  const int* steep_idx;
+  const double* steep_w;
 };
 
 // double -> (hi, lo) FP32 pair with hi + lo = x to about 48 bits
@@ -189,6 +198,7 @@ struct WorkT {
   T *ekin_c, *grad4, *divd, *divd2, *dtheta, *div_l, *div_vn;
   // cells, half levels
   T *ddt_w0, *ddt_w1, *lap_w;
+  T* tenh_ex;  // cells, full levels: the enhanced temperature diffusion's excess factor
   // vertices
   T *zeta, *uv3, *curl_l;  // full levels (uv3: 3 fields)
   T* w_v;                  // half levels
@@ -256,6 +266,8 @@ struct HostTerrain {
   std::vector<double> colt;                                       // [12*(nlev+1)*nc]
   std::vector<double> wgt_e, ddxn_ifc, ddxt_ifc;                  // [ne*(nlev+1)]
   std::vector<double> inv_dz_e, ddxn_mc;                          // [ne*nlev]
+  std::vector<int> steep_idx;                                     // [4 n_steep] (steep_hpg)
+  std::vector<double> steep_w;                                    // [6 n_steep]
 };
 // Validates the per-column heights z_ifc[nc*(nlev+1)] (finite, strictly
 // decreasing in every column, one common model top) and derives the terrain

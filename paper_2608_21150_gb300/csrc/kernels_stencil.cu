@@ -446,6 +446,50 @@ __global__ void sn_edge_pred(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __res
 }
 
 // -------------------------------------------------------------------------
+// A6 over steep terrain: at the listed edge levels the pressure gradient is
+// taken at the edge's height, each cell's total exner (extrapolated
+// perturbation plus the column's reference) interpolated there by the
+// quadratic through three of its levels; the predictor's vn at those points
+// follows.  Runs after sn_edge_pred, over the listed points only.
+// -------------------------------------------------------------------------
+template <class T>
+__global__ void sn_edge_hpg_steep(GridT<T> g, VertT<T> v, ScalT<T> sc, int n, const int* __restrict__ idx,
+                                  const double* __restrict__ wts, const double* __restrict__ pex,
+                                  const double* __restrict__ exref_c, const double* __restrict__ cid64,
+                                  const T* __restrict__ theta_e, const T* __restrict__ vn,
+                                  const T* __restrict__ ddt_vn, T* __restrict__ hpg, T* __restrict__ vn_p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nlev = v.nlev;
+  const int e = idx[4 * i], k = idx[4 * i + 1];
+  const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
+  const size_t b0 = (size_t)c0 * nlev + idx[4 * i + 2], b1 = (size_t)c1 * nlev + idx[4 * i + 3];
+  const double* w = wts + 6 * (size_t)i;
+  const size_t ie = (size_t)e * nlev + k;
+  T h;
+  if constexpr (kMixed<T>) {
+    const df* p = reinterpret_cast<const df*>(pex);
+    df s0{0.f, 0.f}, s1{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      s0 = s0 + to_df(w[j]) * (p[b0 + j] + to_df(exref_c[b0 + j]));
+      s1 = s1 + to_df(w[3 + j]) * (p[b1 + j] + to_df(exref_c[b1 + j]));
+    }
+    h = theta_e[ie] * (to_float(s1 - s0) * g.cpd_inv_d[e]);
+  } else {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      s0 = fma(w[j], pex[b0 + j] + exref_c[b0 + j], s0);
+      s1 = fma(w[3 + j], pex[b1 + j] + exref_c[b1 + j], s1);
+    }
+    h = theta_e[ie] * (T)((s1 - s0) * cid64[e]);
+  }
+  hpg[ie] = h;
+  vn_p[ie] = vn[ie] + sc.dt_s * (ddt_vn[ie] - h);
+}
+
+// -------------------------------------------------------------------------
 // A8 + A9 (corrector edges): vn corrector with time-weighted advective
 // tendencies, the predictor's pressure gradient and fourth-order divergence
 // damping; the increment is formed in T, the update in FP64 (in place).
@@ -750,7 +794,8 @@ __global__ void diff_edge_smag(GridT<T> g, VertT<T> v, const T* __restrict__ div
 template <class T>
 __global__ void diff_second(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ lap, const T* __restrict__ nu,
                             const T* __restrict__ w, const T* __restrict__ theta, T* __restrict__ div_l,
-                            T* __restrict__ lap_w, T* __restrict__ dtheta, T* __restrict__ curl_l) {
+                            T* __restrict__ lap_w, T* __restrict__ dtheta, T* __restrict__ curl_l,
+                            const T* __restrict__ tenh_ex) {
   const int nlev = v.nlev, nlevp = nlev + 1;
   unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned ncell = (unsigned)g.nc * nlevp;
@@ -771,9 +816,18 @@ __global__ void diff_second(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __rest
                   dv[2] * lap[(size_t)ce[2] * nlev + k];
       if (sc.hdiff_temp) {
         const T tc = theta[ic];
-        T f = L[0] * nu[(size_t)ce[0] * nlev + k] * (theta[(size_t)cc[0] * nlev + k] - tc);
-        f += L[1] * nu[(size_t)ce[1] * nlev + k] * (theta[(size_t)cc[1] * nlev + k] - tc);
-        f += L[2] * nu[(size_t)ce[2] * nlev + k] * (theta[(size_t)cc[2] * nlev + k] - tc);
+        T n0 = nu[(size_t)ce[0] * nlev + k], n1 = nu[(size_t)ce[1] * nlev + k], n2 = nu[(size_t)ce[2] * nlev + k];
+        if (k >= nlev - sc.tenh_levels) {
+          // enhanced near-surface temperature diffusion: the edge coefficient
+          // raised by fac A_e / dtime max(e_c, e_nbr)
+          const T ex = tenh_ex[ic];
+          n0 += g.tenh_a[ce[0]] * max(ex, tenh_ex[(size_t)cc[0] * nlev + k]);
+          n1 += g.tenh_a[ce[1]] * max(ex, tenh_ex[(size_t)cc[1] * nlev + k]);
+          n2 += g.tenh_a[ce[2]] * max(ex, tenh_ex[(size_t)cc[2] * nlev + k]);
+        }
+        T f = L[0] * n0 * (theta[(size_t)cc[0] * nlev + k] - tc);
+        f += L[1] * n1 * (theta[(size_t)cc[1] * nlev + k] - tc);
+        f += L[2] * n2 * (theta[(size_t)cc[2] * nlev + k] - tc);
         dtheta[ic] = sc.dtime * f;
       }
     }
@@ -788,6 +842,26 @@ __global__ void diff_second(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __rest
 #pragma unroll
   for (int j = 0; j < 6; ++j) z += cw[j] * lap[(size_t)ve[j] * nlev + k];
   curl_l[i] = z;
+}
+
+// cells, the lowest tenh_levels levels: the excess factor of the enhanced
+// temperature diffusion, e_c = min(1, (|theta_c - mean of the three neighbours|
+// - thresh) / thresh) where above the threshold, else 0 (theta as the stencil
+// views it: the FP64 state, or the mixed mode's perturbation from a per-level
+// offset, which the difference does not see)
+template <class T>
+__global__ void diff_tenh_excess(GridT<T> g, VertT<T> v, ScalT<T> sc, const T* __restrict__ theta,
+                                 T* __restrict__ ex) {
+  const int nlev = v.nlev, nl = sc.tenh_levels;
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)g.nc * (unsigned)nl) return;
+  const int c = (int)(i / (unsigned)nl), k = nlev - nl + (int)(i - (unsigned)c * (unsigned)nl);
+  const int* cc = g.c2e2c + 3 * (size_t)c;
+  const size_t ic = (size_t)c * nlev + k;
+  const T nbr = (theta[(size_t)cc[0] * nlev + k] + theta[(size_t)cc[1] * nlev + k] + theta[(size_t)cc[2] * nlev + k]) /
+                T(3);
+  const T x = (abs(theta[ic] - nbr) - sc.tenh_thresh) / sc.tenh_thresh;
+  ex[ic] = x < T(0) ? T(0) : (x > T(1) ? T(1) : x);
 }
 
 // edges: vn update (FP64, in place)
@@ -951,6 +1025,10 @@ void substep_impl(const Engine& en, const Ctx<T>& x, const StateView& st, cudaSt
               st.exner, st.exner_pr, en.sc.exfac, en.wk.pex, ex_ref_c);
   ICON_LAUNCH(nm_pred, blocks_for(nee, TH(5)), TH(5), s, (sn_edge_pred<T, kTerr>), g, v, x.s, s_vn, wk.vt,
               wk.ddt_vn0, s_rho, s_th, en.wk.pex, en.g64.cpd_inv_d, wk.grad4, wk.rho_e, wk.theta_e, wk.hpg, wk.vn_p, tr);
+  if (kTerr && en.v.n_steep > 0)
+    ICON_LAUNCH(kname<T>("sn_edge_hpg_steep", "sn_edge_hpg_steep_f32"), blocks_for(en.v.n_steep, 128), 128, s,
+                sn_edge_hpg_steep<T>, g, v, x.s, en.v.n_steep, en.v.steep_idx, en.v.steep_w, en.wk.pex,
+                en.v.exner_ref_c, en.g64.cpd_inv_d, wk.theta_e, s_vn, wk.ddt_vn0, wk.hpg, wk.vn_p);
   ICON_LAUNCH(nm_div, blocks_by_shape(SH(6), g.nc, nlev, TH(6)), TH(6), s, (sn_cell_div<T, kTerr>), g, v, wk.vn_p,
               wk.divd, st.exner, st.exner_pr, ex_ref_c, SH(6));
   launch_fluxdiv<T, kTerr>(en, x, wk.vn_p, nm_flx, s);
@@ -1000,9 +1078,13 @@ void launch_diffusion(const Engine& en, const Ctx<T>& x, const StateView& st, cu
               diff_div_curl_uv<T>, g, v, s_vn, wk.div_vn, wk.zeta, wk.uv3);
   ICON_LAUNCH(kname<T>("diff_edge_smag", "diff_edge_smag_f32"), blocks_for((long long)g.ne * nlev, TH(10)),
               TH(10), s, diff_edge_smag<T>, g, v, wk.div_vn, wk.zeta, wk.uv3, wk.nu, wk.lap_vn);
+  if (x.s.tenh_levels > 0 && x.s.hdiff_temp)
+    ICON_LAUNCH(kname<T>("diff_tenh_excess", "diff_tenh_excess_f32"),
+                blocks_for((long long)g.nc * x.s.tenh_levels, kThreads), kThreads, s, diff_tenh_excess<T>, g, v, x.s,
+                s_th, wk.tenh_ex);
   const long long n3 = (long long)g.nc * nlevp + (long long)g.nv * nlev;
   ICON_LAUNCH(kname<T>("diff_second", "diff_second_f32"), blocks_for(n3, TH(11)), TH(11), s, diff_second<T>, g, v,
-              x.s, wk.lap_vn, wk.nu, s_w, s_th, wk.div_l, wk.lap_w, wk.dtheta, wk.curl_l);
+              x.s, wk.lap_vn, wk.nu, s_w, s_th, wk.div_l, wk.lap_w, wk.dtheta, wk.curl_l, wk.tenh_ex);
   ICON_LAUNCH(kname<T>("diff_edge_update", "diff_edge_update_f32"), blocks_for((long long)g.ne * nlev, TH(12)),
               TH(12), s, diff_edge_update<T>, g, v, x.s, st.vn, wk.nu, wk.lap_vn, wk.div_l, wk.curl_l, m.vn);
   ICON_LAUNCH(kname<T>("diff_cell_update", "diff_cell_update_f32"), blocks_for((long long)g.nc * nlevp, TH(13)),

@@ -165,6 +165,48 @@ std::string build_terrain(const HostGrid& g, int nlev, const double* z_ifc, cons
     for (int k = 0; k <= nlev; ++k)
       t->ddxt_ifc[(size_t)e * nlevp + k] = (zv[(size_t)vp * nlevp + k] - zv[(size_t)vm * nlevp + k]) / l;
   }
+  // steep terrain: edge levels whose two cells' levels are offset by more than
+  // half a layer (the level of a neighbour column nearest to the edge height
+  // z_e, the mean of the two cells' full-level heights, is not the same level);
+  // there the pressure gradient is taken at z_e, each cell's total exner
+  // interpolated by the quadratic through its three consecutive levels
+  // nearest to z_e (Lagrange weights).  Heights decrease with the level, so
+  // the nearest level is found by a walk that never goes back.
+  // steep_idx: (edge, level, first level in e2c[0], first level in e2c[1]);
+  // steep_w: the three weights in e2c[0], then the three in e2c[1]
+  if (p.steep_hpg) {
+    std::vector<double> ze(nlev);
+    for (int e = 0; e < ne; ++e) {
+      const int cs[2] = {g.e2c[2 * e], g.e2c[2 * e + 1]};
+      for (int k = 0; k < nlev; ++k)
+        ze[k] = 0.5 * (z_mc[(size_t)cs[0] * nlev + k] + z_mc[(size_t)cs[1] * nlev + k]);
+      std::vector<int> nearest[2] = {std::vector<int>(nlev), std::vector<int>(nlev)};
+      for (int sd = 0; sd < 2; ++sd) {
+        const double* zc = &z_mc[(size_t)cs[sd] * nlev];
+        int j = 0;
+        for (int k = 0; k < nlev; ++k) {
+          while (j + 1 < nlev && std::fabs(zc[j + 1] - ze[k]) < std::fabs(zc[j] - ze[k])) ++j;
+          nearest[sd][k] = j;
+        }
+      }
+      for (int k = 0; k < nlev; ++k) {
+        if (nearest[0][k] == k && nearest[1][k] == k) continue;
+        t->steep_idx.push_back(e);
+        t->steep_idx.push_back(k);
+        for (int sd = 0; sd < 2; ++sd) {
+          const double* zc = &z_mc[(size_t)cs[sd] * nlev];
+          int k0 = nearest[sd][k] - 1;
+          k0 = k0 < 0 ? 0 : (k0 > nlev - 3 ? nlev - 3 : k0);
+          t->steep_idx.push_back(k0);
+          const double z[3] = {zc[k0], zc[k0 + 1], zc[k0 + 2]};
+          for (int jj = 0; jj < 3; ++jj) {
+            const double a = z[jj == 0 ? 1 : 0], b = z[jj == 2 ? 1 : 2];
+            t->steep_w.push_back((ze[k] - a) * (ze[k] - b) / ((z[jj] - a) * (z[jj] - b)));
+          }
+        }
+      }
+    }
+  }
   // flux thickness ratio of each cell's three edges
   t->fx_ratio.assign((size_t)nc * 3 * nlev, 0.0);
   for (int c = 0; c < nc; ++c)
