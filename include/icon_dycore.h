@@ -414,6 +414,30 @@ int icon_mlp_train_step(icon_mlp_t* mlp, const float* x, const float* target, in
  * output y stands for the physical increment y y_std + y_mean. */
 int icon_mlp_set_normalization(icon_mlp_t* mlp, const float* x_mean, const float* x_std, const float* y_mean,
                                const float* y_std);
+/* The statistics in use (HOST outputs [n_in], [n_in], [n_out], [n_out]);
+ * ICON_ERR_ARG when the network has none. */
+int icon_mlp_get_normalization(const icon_mlp_t* mlp, float* x_mean, float* x_std, float* y_mean, float* y_std);
+/* Training statistics on the GPU: the mean and the sample standard deviation
+ * (divisor rows - 1, FP64 accumulation in a fixed order) of every feature of
+ * the training rows x [rows][n_in] and targets y [rows][n_out] (DEVICE, FP32),
+ * a standard deviation below rel_floor times the largest of its group raised
+ * to that floor (groups: HOST int32 arrays of the groups' first features,
+ * ascending from 0; a group runs to the next one's start, the last to the
+ * end), set as the network's normalisation, and the normalised rows written
+ * to xn [rows][n_in] and yn [rows][n_out] (DEVICE).  Allocates and frees its
+ * own scratch; synchronises the stream before returning.
+ * Errors: ICON_ERR_ARG (NULL, rows < 2, bad groups), ICON_ERR_CUDA. */
+int icon_mlp_fit_normalization(icon_mlp_t* mlp, const float* x, const float* y, int64_t rows, const int32_t* x_groups,
+                               int32_t n_x_groups, const int32_t* y_groups, int32_t n_y_groups, float rel_floor,
+                               float* xn, float* yn, void* stream);
+/* One training step (as icon_mlp_train_step) on a random batch of `batch`
+ * rows of the normalised training set xn [rows][n_in], yn [rows][n_out]
+ * (DEVICE): batch row i is training row splitmix64(seed + 2^32 step + i) mod
+ * rows (SplitMix64: a counter-based generator, so the batches need no host
+ * work and step s draws the same rows whatever ran before).  batch a multiple
+ * of 64 up to max_batch. */
+int icon_mlp_train_step_sampled(icon_mlp_t* mlp, const float* xn, const float* yn, int64_t rows, int32_t batch,
+                                uint64_t seed, int64_t step, float lr, double* loss, void* stream);
 
 /*
  * Learned corrector on the state after a step with fewer acoustic substeps

@@ -113,6 +113,13 @@ _sig = {
     "icon_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "icon_mlp_set_normalization": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_float)] * 4),
+    "icon_mlp_get_normalization": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_float)] * 4),
+    "icon_mlp_fit_normalization": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                  _i32p, ctypes.c_int32, _i32p, ctypes.c_int32, ctypes.c_float,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "icon_mlp_train_step_sampled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                   ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_float,
+                                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "icon_corrector_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t), ctypes.c_void_p,
                                                ctypes.c_void_p]),
     "icon_corrector_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(icon_state_t),
@@ -232,6 +239,29 @@ class MLP:
     def train_step(self, x, target, lr, stream=None):
         loss = ctypes.c_double()
         _check(icon_mlp_train_step(self.handle, _ptr(x), _ptr(target), x.shape[0], lr, ctypes.byref(loss), stream))
+        return loss.value
+
+    def get_normalization(self):
+        """The statistics in use (host float32 arrays x_mean, x_std, y_mean, y_std)."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        arrs = [np.empty(n, dtype=np.float32) for n in (self.n_in, self.n_in, self.n_out, self.n_out)]
+        _check(icon_mlp_get_normalization(self.handle, *[a.ctypes.data_as(fp) for a in arrs]))
+        return tuple(arrs)
+
+    def fit_normalization(self, x, y, x_groups, y_groups, rel_floor, xn, yn, stream=None):
+        """icon_mlp_fit_normalization on device tensors x, y (and outputs xn, yn)."""
+        xg = np.ascontiguousarray(x_groups, dtype=np.int32)
+        yg = np.ascontiguousarray(y_groups, dtype=np.int32)
+        _check(icon_mlp_fit_normalization(self.handle, _ptr(x), _ptr(y), x.shape[0], xg.ctypes.data_as(_i32p),
+                                          xg.size, yg.ctypes.data_as(_i32p), yg.size, rel_floor, _ptr(xn), _ptr(yn),
+                                          stream))
+        self.normalization = self.get_normalization()
+
+    def train_step_sampled(self, xn, yn, batch, seed, step, lr, stream=None):
+        """icon_mlp_train_step_sampled: one step on a random batch of the normalised rows."""
+        loss = ctypes.c_double()
+        _check(icon_mlp_train_step_sampled(self.handle, _ptr(xn), _ptr(yn), xn.shape[0], batch, seed, step, lr,
+                                           ctypes.byref(loss), stream))
         return loss.value
 
     def close(self):

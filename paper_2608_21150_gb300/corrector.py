@@ -5,10 +5,11 @@ The corrector maps the state after a step with fewer acoustic substeps (the
 the same input (interior w, exner and theta_v per cell column; vn per edge
 column); rho is never corrected.  Everything numerical runs in the library:
 features and targets (``Dycore.corrector_features/corrector_targets``), the
-networks' forward/backward/Adam (``MLP.train_step``) and the corrected step
-itself (``step_learned``).  This module only drives them: it keeps the
-training rows in device tensors, draws batches, and computes the per-feature
-normalisation statistics that the networks are given.
+networks' forward/backward/Adam (``MLP.train_step``), the per-feature
+normalisation statistics and the random training batches
+(``MLP.fit_normalization``, ``MLP.train_step_sampled``) and the corrected
+step itself (``step_learned``).  This module only drives them: it keeps the
+training rows in device tensors and computes each step's learning rate.
 """
 import numpy as np
 
@@ -88,49 +89,31 @@ def add_pair(reduced, plain, st, data, rows=None, gen=None):
 
 
 def feature_groups(n, nlev):
-    """Index groups of features (or outputs) that share a physical field: runs of
-    nlev (the column's w interior outputs: nlev - 1)."""
-    groups, start = [], 0
+    """First feature of every group of features (or outputs) that share a
+    physical field: runs of nlev (the column's w interior outputs: nlev - 1)."""
+    starts, start = [], 0
     while start < n:
-        size = nlev - 1 if (n == 3 * nlev - 1 and start == 0) else nlev
-        groups.append((start, start + size))
-        start += size
-    return groups
+        starts.append(start)
+        start += nlev - 1 if (n == 3 * nlev - 1 and start == 0) else nlev
+    return starts
 
 
-def statistics(x, nlev, rel_floor=1e-3):
-    """Per-feature mean and standard deviation (float64 accumulation); a standard
-    deviation below rel_floor times its field's largest is raised to that floor,
-    so near-constant features (e.g. w at the lowest level) are not amplified."""
-    xd = x.double()
-    mean = xd.mean(0)
-    std = xd.std(0)
-    for a, b in feature_groups(x.shape[1], nlev):
-        top = float(std[a:b].max())
-        std[a:b] = std[a:b].clamp(min=max(top * rel_floor, 1e-30))
-    return mean.float().cpu().numpy(), std.float().cpu().numpy()
-
-
-def fit(net, x, y, nlev, steps, batch=4096, lr=1e-3, lr_final=1e-5, seed=0, log_every=0):
-    """Set the network's normalisation from (x, y) and train it on the normalised
-    rows for `steps` Adam steps of `batch` random rows (cosine learning-rate
-    decay from lr to lr_final).  Returns the loss history."""
+def fit(net, x, y, nlev, steps, batch=4096, lr=1e-3, lr_final=1e-5, seed=0, rel_floor=1e-3, log_every=0):
+    """Set the network's normalisation from the training rows (x, y) and train it
+    for `steps` Adam steps on random batches of `batch` normalised rows, with a
+    cosine learning-rate decay from lr to lr_final.  The statistics, the
+    normalisation, the batches and the steps run in the library
+    (icon_mlp_fit_normalization, icon_mlp_train_step_sampled); only the
+    learning rate of each step is computed here.  Returns the loss history."""
     import torch
-    xm, xs = statistics(x, nlev)
-    ym, ys = statistics(y, nlev)
-    net.set_normalization(xm, xs, ym, ys)
-    dev = x.device
-    xn = ((x - torch.from_numpy(xm).to(dev)) / torch.from_numpy(xs).to(dev)).contiguous()
-    yn = ((y - torch.from_numpy(ym).to(dev)) / torch.from_numpy(ys).to(dev)).contiguous()
+    xn, yn = torch.empty_like(x), torch.empty_like(y)
+    net.fit_normalization(x, y, feature_groups(x.shape[1], nlev), feature_groups(y.shape[1], nlev), rel_floor,
+                          xn, yn)
     batch = min(batch, net.max_batch, (x.shape[0] // 64) * 64)
-    gen = torch.Generator(device="cpu")
-    gen.manual_seed(seed)
     losses = []
     for t in range(steps):
-        idx = torch.randint(0, x.shape[0], (batch,), generator=gen).to(dev)
-        xb, yb = xn.index_select(0, idx), yn.index_select(0, idx)
         a = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * t / max(steps - 1, 1)))
-        losses.append(net.train_step(xb, yb, float(a)))
+        losses.append(net.train_step_sampled(xn, yn, batch, seed, t, float(a)))
         if log_every and t % log_every == 0:
             print("step %5d loss %.4e" % (t, losses[-1]), flush=True)
     return losses

@@ -1,5 +1,6 @@
 // MLP building blocks of the learned corrector (internal).
 #pragma once
+#include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -45,5 +46,15 @@ int mlp_dims(const icon_mlp_t* m, int* n_in, int* n_out, int* max_batch);
 // normalisation statistics (DEVICE, FP32): x_mean and 1/x_std [n_in], y_mean and
 // y_std [n_out]; null if unset
 void mlp_norm(const icon_mlp_t* m, const float** xm, const float** xis, const float** ym, const float** ys);
+// Training data (mlp_data.cu): FP64 column statistics of [rows][n] with the
+// group floor (scratch of mlp_stats_scratch_doubles doubles), normalised rows,
+// and the random batch of a training step.
+size_t mlp_stats_scratch_doubles(int64_t rows, int n);
+void mlp_column_stats(const float* x, int64_t rows, int n, const int* groups_dev, int n_groups, double rel_floor,
+                      double* scratch, float* mean32, float* sd32, cudaStream_t s);
+void mlp_normalise_rows(const float* x, int64_t rows, int n, const float* mean, const float* sd, float* xn,
+                        cudaStream_t s);
+void mlp_gather_batch(const float* x, int nx, const float* y, int ny, int64_t rows, int batch, uint64_t seed,
+                      int64_t step, float* bx, float* by, cudaStream_t s);
 
 }  // namespace icon

@@ -29,6 +29,8 @@ struct icon_mlp {
   __nv_bfloat16 *dz16, *dzT, *hT;
   double* rowloss;
   float *x_mean = nullptr, *x_istd = nullptr, *y_mean = nullptr, *y_std = nullptr;  // normalisation
+  float *x_std = nullptr;                 // the input standard deviations themselves (icon_mlp_get_normalization)
+  float *bx = nullptr, *by = nullptr;     // a sampled training batch [max_batch][n_in], [max_batch][n_out]
 };
 
 namespace {
@@ -51,6 +53,24 @@ T* alloc(icon_mlp* m, size_t n, cudaError_t& st) {
 
 int layer_in(const icon_mlp* m, int l) { return m->dims[l]; }
 int layer_out(const icon_mlp* m, int l) { return m->dims[l + 1]; }
+
+// device buffers of the normalisation statistics (allocated on first use)
+cudaError_t ensure_norm(icon_mlp* m) {
+  cudaError_t st = cudaSuccess;
+  if (!m->x_mean) {
+    m->x_mean = alloc<float>(m, m->dims[0], st);
+    m->x_istd = alloc<float>(m, m->dims[0], st);
+    m->x_std = alloc<float>(m, m->dims[0], st);
+    m->y_mean = alloc<float>(m, m->dims[3], st);
+    m->y_std = alloc<float>(m, m->dims[3], st);
+  }
+  return st;
+}
+
+__global__ void reciprocal_kernel(const float* __restrict__ x, float* __restrict__ y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = 1.0f / x[i];
+}
 
 int64_t param_count(const icon_mlp* m) {
   int64_t n = 0;
@@ -184,18 +204,87 @@ int icon_mlp_set_normalization(icon_mlp_t* m, const float* x_mean, const float* 
     istd[j] = 1.0f / x_std[j];
   }
   cudaError_t st = cudaSuccess;
-  if (!m->x_mean) {
-    m->x_mean = alloc<float>(m, m->dims[0], st);
-    m->x_istd = alloc<float>(m, m->dims[0], st);
-    m->y_mean = alloc<float>(m, m->dims[3], st);
-    m->y_std = alloc<float>(m, m->dims[3], st);
-  }
+  st = ensure_norm(m);
+  if (st == cudaSuccess) st = cudaMemcpy(m->x_std, x_std, m->dims[0] * 4, cudaMemcpyHostToDevice);
   if (st == cudaSuccess) st = cudaMemcpy(m->x_mean, x_mean, m->dims[0] * 4, cudaMemcpyHostToDevice);
   if (st == cudaSuccess) st = cudaMemcpy(m->x_istd, istd.data(), m->dims[0] * 4, cudaMemcpyHostToDevice);
   if (st == cudaSuccess) st = cudaMemcpy(m->y_mean, y_mean, m->dims[3] * 4, cudaMemcpyHostToDevice);
   if (st == cudaSuccess) st = cudaMemcpy(m->y_std, y_std, m->dims[3] * 4, cudaMemcpyHostToDevice);
   if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_set_normalization: ") + cudaGetErrorString(st));
   return ICON_OK;
+}
+
+int icon_mlp_get_normalization(const icon_mlp_t* m, float* x_mean, float* x_std, float* y_mean, float* y_std) {
+  if (!m || !x_mean || !x_std || !y_mean || !y_std) return fail_m(ICON_ERR_ARG, "icon_mlp_get_normalization: NULL");
+  if (!m->x_mean) return fail_m(ICON_ERR_ARG, "icon_mlp_get_normalization: the network has no statistics");
+  cudaError_t st = cudaMemcpy(x_mean, m->x_mean, m->dims[0] * 4, cudaMemcpyDeviceToHost);
+  if (st == cudaSuccess) st = cudaMemcpy(x_std, m->x_std, m->dims[0] * 4, cudaMemcpyDeviceToHost);
+  if (st == cudaSuccess) st = cudaMemcpy(y_mean, m->y_mean, m->dims[3] * 4, cudaMemcpyDeviceToHost);
+  if (st == cudaSuccess) st = cudaMemcpy(y_std, m->y_std, m->dims[3] * 4, cudaMemcpyDeviceToHost);
+  if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string("icon_mlp_get_normalization: ") + cudaGetErrorString(st));
+  return ICON_OK;
+}
+
+int icon_mlp_fit_normalization(icon_mlp_t* m, const float* x, const float* y, int64_t rows, const int32_t* x_groups,
+                               int32_t n_x_groups, const int32_t* y_groups, int32_t n_y_groups, float rel_floor,
+                               float* xn, float* yn, void* stream) {
+  const char* fn = "icon_mlp_fit_normalization: ";
+  if (!m || !x || !y || !xn || !yn || !x_groups || !y_groups) return fail_m(ICON_ERR_ARG, std::string(fn) + "NULL");
+  if (rows < 2 || n_x_groups < 1 || n_y_groups < 1 || !(rel_floor >= 0.0f))
+    return fail_m(ICON_ERR_ARG, std::string(fn) + "need rows >= 2, groups and rel_floor >= 0");
+  const int nx = m->dims[0], ny = m->dims[3];
+  for (int k = 0; k < 2; ++k) {
+    const int32_t* gr = k ? y_groups : x_groups;
+    const int ng = k ? n_y_groups : n_x_groups, n = k ? ny : nx;
+    for (int g = 0; g < ng; ++g)
+      if (gr[g] < 0 || gr[g] >= n || (g > 0 && gr[g] <= gr[g - 1]) || (g == 0 && gr[0] != 0))
+        return fail_m(ICON_ERR_ARG, std::string(fn) + "groups must start at 0 and increase within the features");
+  }
+  cudaError_t st = ensure_norm(m);
+  if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(st));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // scratch of this call only (the training set is sized by the caller)
+  const size_t nd = mlp_stats_scratch_doubles(rows, nx > ny ? nx : ny);
+  double* scratch = nullptr;
+  int* groups = nullptr;
+  st = cudaMalloc(&scratch, nd * sizeof(double));
+  if (st == cudaSuccess) st = cudaMalloc(&groups, (n_x_groups + n_y_groups) * sizeof(int));
+  if (st == cudaSuccess)
+    st = cudaMemcpyAsync(groups, x_groups, n_x_groups * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (st == cudaSuccess)
+    st = cudaMemcpyAsync(groups + n_x_groups, y_groups, n_y_groups * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (st == cudaSuccess) {
+    mlp_column_stats(x, rows, nx, groups, n_x_groups, rel_floor, scratch, m->x_mean, m->x_std, s);
+    mlp_column_stats(y, rows, ny, groups + n_x_groups, n_y_groups, rel_floor, scratch, m->y_mean, m->y_std, s);
+    reciprocal_kernel<<<(nx + 127) / 128, 128, 0, s>>>(m->x_std, m->x_istd, nx);
+    mlp_normalise_rows(x, rows, nx, m->x_mean, m->x_std, xn, s);
+    mlp_normalise_rows(y, rows, ny, m->y_mean, m->y_std, yn, s);
+    st = cudaGetLastError();
+  }
+  // the host arrays and the scratch are released only after the GPU used them
+  const cudaError_t sy = cudaStreamSynchronize(s);
+  if (st == cudaSuccess) st = sy;
+  cudaFree(scratch);
+  cudaFree(groups);
+  if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(st));
+  return ICON_OK;
+}
+
+int icon_mlp_train_step_sampled(icon_mlp_t* m, const float* xn, const float* yn, int64_t rows, int32_t batch,
+                                uint64_t seed, int64_t step, float lr, double* loss, void* stream) {
+  const char* fn = "icon_mlp_train_step_sampled: ";
+  if (!m || !xn || !yn) return fail_m(ICON_ERR_ARG, std::string(fn) + "NULL argument");
+  if (rows < 1 || batch < 64 || batch % 64 || batch > m->max_batch)
+    return fail_m(ICON_ERR_ARG, std::string(fn) + "need rows >= 1 and batch a multiple of 64 up to max_batch");
+  cudaError_t st = cudaSuccess;
+  if (!m->bx) {
+    m->bx = alloc<float>(m, (size_t)m->max_batch * m->dims[0], st);
+    m->by = alloc<float>(m, (size_t)m->max_batch * m->dims[3], st);
+  }
+  if (st != cudaSuccess) return fail_m(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(st));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mlp_gather_batch(xn, m->dims[0], yn, m->dims[3], rows, batch, seed, step, m->bx, m->by, s);
+  return icon_mlp_train_step(m, m->bx, m->by, batch, lr, loss, stream);
 }
 
 int icon_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, icon_mlp_t** out) {

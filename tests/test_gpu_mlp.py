@@ -83,3 +83,57 @@ def test_mlp_training_reduces_the_loss(built_lib, cuda):
         s = (it % 4) * B
         losses.append(net.train_step(xd[s:s + B], td[s:s + B], 3e-3))
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def _splitmix64(z):
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) on Python integers."""
+    m = (1 << 64) - 1
+    z = (z + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def test_training_statistics_and_batches_on_the_gpu(built_lib, cuda):
+    """icon_mlp_fit_normalization: per-feature mean and sample standard
+    deviation (numpy, FP64) with the group floor, set as the network's
+    statistics and applied to the rows; icon_mlp_train_step_sampled trains on
+    the rows SplitMix64 picks (a step on exactly those rows, given explicitly,
+    gives the same loss and parameters)."""
+    import torch
+    import paper_2608_21150_gb300 as P
+    I, H, O, rows = 40, 64, 9, 5000
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal((rows, I)) * np.linspace(0.5, 4.0, I) + np.linspace(-3, 3, I)).astype(np.float32)
+    x[:, 7] = 2.0 + 1e-9 * rng.standard_normal(rows)         # near-constant feature: floored
+    y = (rng.standard_normal((rows, O)) * 3.0 + 1.0).astype(np.float32)
+    xg, yg = [0, 10, 20, 30], [0, 4]
+    net = P.MLP(I, H, O, max_batch=256)
+    net.set_params(init_params(rng, I, H, O))
+    xd, yd = torch.from_numpy(x).to(cuda), torch.from_numpy(y).to(cuda)
+    xn, yn = torch.empty_like(xd), torch.empty_like(yd)
+    net.fit_normalization(xd, yd, xg, yg, 1e-3, xn, yn)
+    xm, xs, ym, ys = net.normalization
+
+    def ref_stats(a, groups):
+        mean, sd = a.astype(np.float64).mean(0), a.astype(np.float64).std(0, ddof=1)
+        bounds = list(groups) + [a.shape[1]]
+        for g0, g1 in zip(bounds[:-1], bounds[1:]):
+            sd[g0:g1] = np.maximum(sd[g0:g1], max(sd[g0:g1].max() * 1e-3, 1e-30))
+        return mean, sd
+    rm, rs = ref_stats(x, xg)
+    assert np.allclose(xm, rm, rtol=1e-6, atol=1e-6) and np.allclose(xs, rs, rtol=1e-6)
+    assert np.isclose(xs[7], rs[7], rtol=1e-6) and rs[7] > 1e-3     # the floor: a thousandth of the group largest
+    rm, rs = ref_stats(y, yg)
+    assert np.allclose(ym, rm, rtol=1e-6, atol=1e-6) and np.allclose(ys, rs, rtol=1e-6)
+    assert np.allclose(xn.cpu().numpy(), (x - xm) / xs, rtol=1e-6, atol=1e-6)
+    # a sampled step is the explicit step on the rows SplitMix64 picks
+    seed, step, batch = 12345, 7, 128
+    idx = np.array([_splitmix64(seed + (step << 32) + i) % rows for i in range(batch)])
+    twin = P.MLP(I, H, O, max_batch=256)
+    twin.set_params(net.params())
+    la = net.train_step_sampled(xn, yn, batch, seed, step, 1e-3)
+    lb = twin.train_step(xn[torch.from_numpy(idx).to(cuda)].contiguous(), yn[torch.from_numpy(idx).to(cuda)].contiguous(),
+                         1e-3)
+    assert la == lb
+    assert np.array_equal(net.params(), twin.params())
