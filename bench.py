@@ -13,7 +13,7 @@ library launches on; the state (1.5 GB) is larger than L2, so no flush is
 needed.  Legs: FP64 (the headline value); mixed precision (FP32 stencils,
 double-word FP32 column solve); mixed with an FP64 column solve; mixed plus
 the learned corrector (trained on the GPU first, untimed, on other seeds:
-steps with 4 substeps plus the learned increments, the check and any
+steps with 3 substeps plus the learned increments, the check and any
 fallback to the plain step).  After its timed steps every leg runs on,
 untimed, to one simulated day (240 steps), where the surface pressure and
 the 850 hPa temperature are compared with the FP64 leg's.  The end-to-end
