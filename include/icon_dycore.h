@@ -107,7 +107,7 @@ typedef struct icon_dycore_params {
   /* physical constants */
   double grav, rd, cpd, p00, omega;
   /* solve_nonhydro */
-  double vwind_impl_wgt;   /* implicit weight beta of the vertical solve */
+  double vwind_impl_wgt;   /* implicit weight beta of the vertical solve, in (0, 1] */
   double wgt_nnow_vel, wgt_nnew_vel;  /* corrector weights of the advective tendencies */
   double wgt_nnow_rth, wgt_nnew_rth;  /* corrector weights of rho, theta_v */
   double exner_exfac;      /* exner-perturbation time extrapolation factor */
@@ -139,7 +139,8 @@ typedef struct icon_dycore_params {
   double hdiff_tenh_fac;   /* enhanced temperature diffusion: edge coefficient
                               fac A_e / dtime max(e_c0, e_c1); 0 = off */
   double hdiff_tenh_thresh;  /* K: e_c = min(1, (|theta_c - mean of its 3 neighbours| - thresh)/thresh) */
-  int32_t hdiff_tenh_levels; /* the lowest levels where e_c may be nonzero */
+  int32_t hdiff_tenh_levels; /* the lowest levels where e_c may be nonzero
+                                (>= 0; more than nlev means every level) */
 } icon_dycore_params_t;
 
 /* Writes the defaults (Sec. 4.1 names the scheme's parts, not its values;

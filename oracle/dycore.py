@@ -436,7 +436,7 @@ class Dycore:
         p, g = self.p, self.g
         nbr = (theta[g.c2e2c[:, 0]] + theta[g.c2e2c[:, 1]] + theta[g.c2e2c[:, 2]]) / 3.0
         ex = np.clip((np.abs(theta - nbr) - p.hdiff_tenh_thresh) / p.hdiff_tenh_thresh, 0.0, 1.0)
-        ex[:, :theta.shape[1] - p.hdiff_tenh_levels] = 0.0
+        ex[:, :max(0, theta.shape[1] - p.hdiff_tenh_levels)] = 0.0
         return np.maximum(ex[g.e2c[:, 0]], ex[g.e2c[:, 1]])
 
     # ------------------------------------------------------------------

@@ -404,11 +404,13 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     return fail(ICON_ERR_ARG, fname + ": dtime must be > 0 and ndyn_substeps >= 1");
   if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED && p->precision != ICON_PREC_MIXED_F64COL)
     return fail(ICON_ERR_ARG, fname + ": precision must be ICON_PREC_FP64, ICON_PREC_MIXED or ICON_PREC_MIXED_F64COL");
+  if (!(p->vwind_impl_wgt > 0.0 && p->vwind_impl_wgt <= 1.0))
+    return fail(ICON_ERR_ARG, fname + ": vwind_impl_wgt must be in (0, 1]");
   if (p->column_chunk != 0 && p->column_chunk != 4 && p->column_chunk != 6 && p->column_chunk != 8)
     return fail(ICON_ERR_ARG, fname + ": column_chunk must be 0, 4, 6 or 8");
   if (!(p->hdiff_tenh_fac >= 0.0) || (p->hdiff_tenh_fac > 0.0 && !(p->hdiff_tenh_thresh > 0.0)) ||
-      p->hdiff_tenh_levels < 0 || p->hdiff_tenh_levels > nlev)
-    return fail(ICON_ERR_ARG, fname + ": enhanced temperature diffusion needs fac >= 0, thresh > 0, 0 <= levels <= nlev");
+      p->hdiff_tenh_levels < 0)
+    return fail(ICON_ERR_ARG, fname + ": enhanced temperature diffusion needs fac >= 0, thresh > 0, levels >= 0");
   if (p->steep_hpg && nlev < 3) return fail(ICON_ERR_ARG, fname + ": steep_hpg needs nlev >= 3");
   // terrain: every column validated and its metrics derived before any allocation
   HostTerrain ht;
@@ -483,6 +485,9 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
   v.exner_ref = A.upload(d->exner_ref);
   v.dexner_ref_ic = A.upload(dref);
   v.ray_fac = A.upload(ray);
+  v.n_ray = 0;
+  for (int k = 0; k <= nlev; ++k)
+    if (ray[k] != 1.0) v.n_ray = k + 1;
   v.colc = A.upload(colc);
   v.lev_hl = A.upload(level_pairs(nlev, colc.data(), d->exner_ref.data(), d->theta_ref.data(), dz.data(), ray.data(),
                                   rho_ref.data()));
@@ -592,7 +597,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     st.wnow_vel = (T)s.wnow_vel;
     st.wnew_vel = (T)s.wnew_vel;
     st.hdiff_temp = s.hdiff_temp;
-    st.tenh_levels = tenh_on ? p->hdiff_tenh_levels : 0;
+    st.tenh_levels = tenh_on ? std::min(p->hdiff_tenh_levels, nlev) : 0;  // more levels than the column: all
     st.tenh_thresh = (T)p->hdiff_tenh_thresh;
     WorkT<T>& w = x.w;
     w.vt = A.template alloc<T>(ef);
@@ -681,6 +686,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     else
       build_terr(en.c32, float{});
     std::vector<double>().swap(ht.colt);  // the largest host copy, released early
+    v.n_ray = std::max(v.n_ray, ht.n_ray);
     v.n_steep = (int)(ht.steep_w.size() / 6);
     if (v.n_steep > 0) {
       v.steep_idx = A.upload(ht.steep_idx);

@@ -11,7 +11,14 @@
 // with Fw = rho_ic w, Gw = rho_ic theta_ic w, zb = dt (rd/cvd) exner/(rho theta dz)
 // and w = 0 at the top and the ground.  Eliminating pr' gives a tridiagonal
 // system in w'; Thomas elimination top-down, Rayleigh damping, then
-// back-substitution; theta'_v from the linearised equation of state
+// back-substitution.  Arranged for few FP64 operations (the FP64 pipe bounds
+// this kernel): with gam_k = dt cpd beta theta_ic/dzh_k, the explicit pressure
+// term is gam_k ((1-beta)/beta)(pr_k-1 - pr_k), carried in
+// S_k = pr*_k + ((1-beta)/beta) pr_k together with the implicit one; the
+// matrix entries use p_k = zb_k A_k and q_k = zb_k A_k+1 (A = beta (rho
+// theta)_ic at the half levels); theta_ic is the reference theta at the half
+// level plus the interpolated perturbation.  theta'_v from the linearised
+// equation of state
 //   theta' = theta (rho/rho')(1 + (cvd/rd)(pr' - pr)/exner)
 //          = (dt rd/(cvd dz)) (exner - (cvd/rd) pr + (cvd/rd) pr') / (zb rho').
 //
@@ -78,7 +85,10 @@ constexpr size_t smem_bytes() {
 }
 constexpr size_t kSmem = smem_bytes<double, kKC, true>();
 
-enum { CZB = 0, CR = 1, CRN = 2, CWX = 3, CB = 4, CGAM = 5, WG = 6, WG2 = 7 };
+// column coefficients: CTHI the reference theta_v at the half level (theta_ic
+// is it plus the interpolated perturbation); the explicit part
+// of the vertical pressure-gradient term is CGAM (1 - beta)/beta.
+enum { CZB = 0, CR = 1, CRN = 2, CTHI = 3, CB = 4, CGAM = 5, WG = 6, WG2 = 7 };
 
 // Reciprocal of a positive FP64 value far from the subnormal range (the
 // pivots and the equation-of-state denominator): a double-word FP32 seed
@@ -448,14 +458,17 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
   const R zero = A::in(0.0), one = A::in(1.0);
   const R dt = A::in(sc.dt_s), beta = A::in(sc.beta), ombeta = A::in(1.0 - sc.beta);
   const R wn_r = A::in(sc.wnow_rth), wnew_r = A::in(sc.wnew_rth);
-  const R wn_v = A::in(sc.wnow_vel), wnew_v = A::in(sc.wnew_vel), cvd_o_rd = A::in(sc.cvd_o_rd);
+  const R dt_wn_v = A::in(sc.dt_s * sc.wnow_vel), dt_wnew_v = A::in(sc.dt_s * sc.wnew_vel);
+  const R cvd_o_rd = A::in(sc.cvd_o_rd), ex_o_im = A::in((1.0 - sc.beta) / sc.beta);
   const float wn_vf = to_float(to_df(sc.wnow_vel)), wnew_vf = to_float(to_df(sc.wnew_vel));
+  // levels k < n_ray may be Rayleigh-damped (the factor is 1 below)
+  const int n_ray = v.n_ray;
 
   // carried values: half level k (interface above full level k), full level k-1,
   // and full level k itself (converted and time-averaged when it was level k+1)
   R ric_k = zero, tic_k = zero, tpic_k = zero, rt_k = zero;
-  R zb_km1 = zero, al_km1 = zero, ps_km1 = zero, pr_km1 = zero, cp_km1 = zero, rp_km1 = zero;
-  R rho_c = zero, th_c = zero, ra_c = zero, ta_c = zero, tpa_c = zero, wk_c = zero;
+  R p_km1 = zero, q_km1 = zero, s_km1 = zero, cp_km1 = zero, rp_km1 = zero;
+  R rho_c = zero, th_c = zero, ra_c = zero, tpa_c = zero, wk_c = zero;
   // products of half level k carried from level k-1: rho_ic w, (rho theta)_ic w, beta (rho theta)_ic
   R fr_c = zero, fg_c = zero, al_c = zero;
 
@@ -493,7 +506,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
         rho_c = A::in(T_rho[o]);
         th_c = A::in(T_th[o]);
         ra_c = corrector ? add_pos(wn_r * rho_c, wnew_r * stored_in<T, R>(T_rp + o)) : rho_c;
-        ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * stored_in<T, R>(T_tp + o)) : th_c;
+        const R ta_c = corrector ? add_pos(wn_r * th_c, wnew_r * stored_in<T, R>(T_tp + o)) : th_c;
         tpa_c = ta_c - levc<R, LTH, kStage, kTerr>(v, L_s, 0, k0, c, nc);
         wk_c = A::in(T_w[o]);
         const R wf = kTerr ? minus_corr(wk_c, T_wc[o]) : wk_c;
@@ -505,17 +518,19 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       const R pr_k = pi_n - levc<R, LEX, kStage, kTerr>(v, L_s, k, k0, c, nc);
       // interface k+1 from full levels k and k+1 (time-averaged in the corrector)
       R ric_k1 = zero, tic_k1 = zero, tpic_k1 = zero;
-      R rho_x = zero, th_x = zero, ra_x = zero, ta_x = zero, tpa_x = zero;
+      R rho_x = zero, th_x = zero, ra_x = zero, tpa_x = zero;
       if (k + 1 < nlev) {
         rho_x = A::in(T_rho[o + kLD]);
         th_x = A::in(T_th[o + kLD]);
         ra_x = corrector ? add_pos(wn_r * rho_x, wnew_r * stored_in<T, R>(T_rp + o + kLD)) : rho_x;
-        ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * stored_in<T, R>(T_tp + o + kLD)) : th_x;
+        const R ta_x = corrector ? add_pos(wn_r * th_x, wnew_r * stored_in<T, R>(T_tp + o + kLD)) : th_x;
         tpa_x = ta_x - levc<R, LTH, kStage, kTerr>(v, L_s, k + 1, k0, c, nc);
         const R g1 = levc<R, WG, kStage, kTerr>(v, L_s, k + 1, k0, c, nc), g2 = levc<R, WG2, kStage, kTerr>(v, L_s, k + 1, k0, c, nc);
         ric_k1 = add_pos(g1 * ra_c, g2 * ra_x);
-        tic_k1 = add_pos(g1 * ta_c, g2 * ta_x);
+        // the perturbation interpolated from the levels' perturbations (no
+        // cancellation against the reference), the total from it
         tpic_k1 = g1 * tpa_c + g2 * tpa_x;
+        tic_k1 = levc<R, CTHI, kStage, kTerr>(v, L_s, k + 1, k0, c, nc) + tpic_k1;
       }
       const size_t ik = (size_t)k * nc + c;
       R zb;
@@ -533,42 +548,36 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       const R rstar = rho_n - dt * stored_div<T, R>(T_dm + o) - levc<R, CR, kStage, kTerr>(v, L_s, k, k0, c, nc) * (fr_c - fr_k1);
       const R pstar = pr_k - zb * (levc<R, LDZ, kStage, kTerr>(v, L_s, k, k0, c, nc) * stored_div<T, R>(T_dt + o) + ombeta * (fg_c - fg_k1));
       const R al_k = al_c, al_k1 = beta * rt_k1;
+      const R p_k = zb * al_k, q_k = zb * al_k1;
+      const R s_k = pstar + ex_o_im * pr_k;
       put(rs_s + ik, rstar);
       put(ps_s + ik, pstar);
       put(ri_s + ik, ric_k);
       put(al_s + ik, al_k);
       if (k >= 1) {
-        R ddtw;
+        // w + dt (time-averaged tendency)
+        R w0;
         if constexpr (std::is_same<T, float>::value) {  // FP32 tendencies: their time average in FP32
-          ddtw = A::in(corrector ? fmaf(wn_vf, T_dw0[o], wnew_vf * T_dw1[o]) : T_dw0[o]);
+          w0 = wk + dt * A::in(corrector ? fmaf(wn_vf, T_dw0[o], wnew_vf * T_dw1[o]) : T_dw0[o]);
         } else {
-          ddtw = corrector ? wn_v * A::in(T_dw0[o]) + wnew_v * A::in(T_dw1[o]) : A::in(T_dw0[o]);
+          w0 = corrector ? (wk + dt_wn_v * A::in(T_dw0[o])) + dt_wnew_v * A::in(T_dw1[o]) : wk + dt * A::in(T_dw0[o]);
         }
-        const R wstar = wk + dt * ddtw - (levc<R, CWX, kStage, kTerr>(v, L_s, k, k0, c, nc) * tic_k * (pr_km1 - pr_k) + levc<R, CB, kStage, kTerr>(v, L_s, k, k0, c, nc) * tpic_k);
         const R gam = levc<R, CGAM, kStage, kTerr>(v, L_s, k, k0, c, nc) * tic_k;
-        const R am = -(gam * zb_km1 * al_km1);
-        const R bm = add_pos(one, gam * al_k * add_pos(zb_km1, zb));
-        const R cm = -(gam * zb * al_k1);
-        const R rm = (kTerr ? minus_corr(wstar, T_wc[o]) : wstar) - gam * (ps_km1 - pstar);
-        R cpk, rpk;
-        if (k == 1) {
-          const R inv = A::inv(bm);
-          cpk = cm * inv;
-          rpk = rm * inv;
-        } else {
-          const R inv = A::inv(bm - am * cp_km1);
-          cpk = cm * inv;
-          rpk = (rm - am * rp_km1) * inv;
-        }
+        const R rhs = (kTerr ? minus_corr(w0, T_wc[o]) : w0) - levc<R, CB, kStage, kTerr>(v, L_s, k, k0, c, nc) * tpic_k;
+        const R rm = rhs - gam * (s_km1 - s_k);
+        // row k: -gam p_k-1 w'_k-1 + (1 + gam (q_k-1 + p_k)) w'_k - gam q_k w'_k+1 = rm
+        const R gp = gam * p_km1;
+        const R inv = A::inv(add_pos(one, gam * add_pos(q_km1, p_k)) + gp * cp_km1);
+        const R cpk = -(gam * q_k) * inv;
+        const R rpk = (rm + gp * rp_km1) * inv;
         put(cp_s + ik, cpk);
         put(rp_s + ik, rpk);
         cp_km1 = cpk;
         rp_km1 = rpk;
       }
-      zb_km1 = zb;
-      al_km1 = al_k;
-      ps_km1 = pstar;
-      pr_km1 = pr_k;
+      p_km1 = p_k;
+      q_km1 = q_k;
+      s_km1 = s_k;
       ric_k = ric_k1;
       tic_k = tic_k1;
       tpic_k = tpic_k1;
@@ -580,7 +589,6 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
       th_c = th_x;
       wk_c = wk1;
       ra_c = ra_x;
-      ta_c = ta_x;
       tpa_c = tpa_x;
     }
   }
@@ -630,7 +638,7 @@ __global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Sca
         R w_und = zero, wd = zero;
         if (k >= 1) {
           w_und = get<R>(B_rp + b) - get<R>(B_cp + b) * w_und_k1;
-          wd = w_und * levc<R, LRAY, kStage, kTerr>(v, L_s, k, k0, c, nc);
+          wd = k < n_ray ? w_und * levc<R, LRAY, kStage, kTerr>(v, L_s, k, k0, c, nc) : w_und;
         }
         const R ric = get<R>(B_ri + b), al = get<R>(B_al + b), zb = get<R>(B_zb + b);
         const R fr = ric * wd, fa = al * wd;

@@ -99,6 +99,7 @@ struct ScalT {
 // Vertical metrics and reference state in device memory.
 struct DevVert {
   int nlev;
+  int n_ray;               // levels 0..n_ray-1 may be Rayleigh-damped (ray_fac 1 below, every column)
   const double* dz;        // [nlev]
   const double* inv_dz;    // [nlev]
   const double* inv_dzh;   // [nlev+1] (0 at top and ground)
@@ -108,8 +109,10 @@ struct DevVert {
   const double* dexner_ref_ic;  // [nlev+1]
   const double* ray_fac;   // [nlev+1] 1/(1 + dt_s tau^-1 sin^2(..)) (1 where off)
   // per-level coefficients of the column solve, colc[k*8 + j]:
-  // 0 dt rd/(cvd dz_k), 1 dt (1-beta)/dz_k, 2 dt beta/dz_k, 3 dt cpd (1-beta)/dzh_k,
+  // 0 dt rd/(cvd dz_k), 1 dt (1-beta)/dz_k, 2 dt beta/dz_k,
+  // 3 theta_ref at half level k (wgt_k theta_ref_k-1 + (1 - wgt_k) theta_ref_k),
   // 4 dt cpd dexner_ref_ic_k, 5 dt cpd beta/dzh_k, 6 wgt_k, 7 1 - wgt_k
+  // (3 to 7 at the interior half levels 1..nlev-1 only)
   const double* colc;      // [(nlev+1)*8]
   // the same per level as double-word FP32 pairs (hi, lo), 16 pairs per level
   // k = 0..nlev: colc 0..7, then exner_ref, theta_ref, dz, ray_fac, rho_ref
@@ -268,6 +271,7 @@ struct HostTerrain {
   std::vector<double> inv_dz_e, ddxn_mc;                          // [ne*nlev]
   std::vector<int> steep_idx;                                     // [4 n_steep] (steep_hpg)
   std::vector<double> steep_w;                                    // [6 n_steep]
+  int n_ray = 0;  // the largest count of Rayleigh-damped top levels of a column
 };
 // Validates the per-column heights z_ifc[nc*(nlev+1)] (finite, strictly
 // decreasing in every column, one common model top) and derives the terrain

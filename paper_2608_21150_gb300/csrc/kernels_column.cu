@@ -141,11 +141,11 @@ __global__ void noalloc_metrics(NoallocSetup q, double* base) {
       cf[2] = q.dt_s * q.beta / dz[k];
     }
     if (k >= 1 && k < nlev) {
-      cf[3] = q.dt_s * q.cpd * (1.0 - q.beta) * inv_dzh[k];
       cf[4] = q.dt_s * q.cpd * dref[k];
       cf[5] = q.dt_s * q.cpd * q.beta * inv_dzh[k];
       cf[6] = wgt[k];
       cf[7] = 1.0 - wgt[k];
+      cf[3] = cf[6] * th_ref[k - 1] + cf[7] * th_ref[k];
     }
     // the double-word table: colc, then exner_ref, theta_ref, dz, ray_fac
     // (no rho offset: this entry point's inputs are FP64)
@@ -225,6 +225,8 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
     return report_error(ICON_ERR_ARG, std::string(fn) + "dtime must be > 0 and ndyn_substeps >= 1");
   if (p->precision != ICON_PREC_FP64 && p->precision != ICON_PREC_MIXED)
     return report_error(ICON_ERR_ARG, std::string(fn) + "precision must be ICON_PREC_FP64 or ICON_PREC_MIXED");
+  if (!(p->vwind_impl_wgt > 0.0 && p->vwind_impl_wgt <= 1.0))
+    return report_error(ICON_ERR_ARG, std::string(fn) + "vwind_impl_wgt must be in (0, 1]");
 
   // scalars with the same definitions as icon_dycore_create
   Scalars s{};
@@ -267,6 +269,11 @@ extern "C" int icon_column_solve_noalloc(int32_t n_cols, int32_t nlev, const dou
   if (e != cudaSuccess) return report_error(ICON_ERR_CUDA, std::string(fn) + cudaGetErrorString(e));
   DevVert v{};
   v.nlev = nlev;
+  // the levels noalloc_metrics may damp (an upper bound: ray_fac is 1 below)
+  v.n_ray = 0;
+  if (p->rayleigh_coeff > 0.0)
+    for (int k = 0; k <= nlev; ++k)
+      if (z_ifc[k] > p->damp_height) v.n_ray = k + 1;
   v.dz = base;
   v.inv_dz = base + kNoallocStride;
   v.inv_dzh = base + 2 * kNoallocStride;

@@ -17,6 +17,7 @@
 //     horizontal fluxes.
 #include <cmath>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -69,11 +70,11 @@ void column_metrics(const double* z, int nlev, const icon_dycore_params_t& p, co
       c[2] = dts * beta / m->dz[k];
     }
     if (k >= 1 && k < nlev) {
-      c[3] = dts * p.cpd * (1.0 - beta) * m->inv_dzh[k];
       c[4] = dts * p.cpd * m->dref[k];
       c[5] = dts * p.cpd * beta * m->inv_dzh[k];
       c[6] = m->wgt[k];
       c[7] = 1.0 - m->wgt[k];
+      c[3] = c[6] * m->theta_ref[k - 1] + c[7] * m->theta_ref[k];
     }
   }
 }
@@ -119,6 +120,7 @@ std::string build_terrain(const HostGrid& g, int nlev, const double* z_ifc, cons
         slot(10) = m.dz[k];
       }
       slot(11) = m.ray[k];
+      if (m.ray[k] != 1.0) t->n_ray = std::max(t->n_ray, k + 1);
     }
   }
   // edges: heights the mean of the two cells'
