@@ -58,13 +58,15 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-# Algorithmic FP64 flops per unit (FMA = 2, add/mul/div/sqrt = 1), counted
-# from the formulas each kernel evaluates; the unit is one (point, level).
+# FP64 flops per unit (FMA = 2, add/mul = 1, a reciprocal = its FP64 add and
+# two FMAs), counted from the arithmetic each kernel evaluates; the unit is
+# one (point, level).  va_cell_vert: the mean of its predictor and corrector
+# forms per unit of its combined cell and vertex launch.
 FLOPS_PER_UNIT = {
-    "va_edge_pre": 16, "va_cell_vert": 17, "va_edge_tend": 30, "va_cell_w": 11,
-    "sn_cell_grad": 28, "sn_edge_pred": 24, "sn_cell_div": 5, "sn_cell_fluxdiv": 27,
+    "va_edge_pre": 15, "va_cell_vert": 14, "va_edge_tend": 21, "va_cell_w": 11,
+    "sn_cell_grad": 32, "sn_edge_pred": 24, "sn_cell_div": 5, "sn_cell_fluxdiv": 27,
     "sn_edge_flux": 6, "sn_cell_fluxsum": 12,
-    "sn_column_pred": 86, "sn_edge_corr": 11, "sn_column_corr": 94,
+    "sn_column_pred": 84, "sn_edge_corr": 11, "sn_column_corr": 82,
     "diff_div_curl_uv": 30, "diff_edge_smag": 46, "diff_second": 30,
     "diff_edge_update": 12, "diff_cell_update": 12, "va_concorr": 20,
 }

@@ -288,7 +288,7 @@ int icon_dycore_profile(icon_dycore_t* dycore, const icon_state_t* state, int32_
  * layout as the state, element type double in FP64 mode and float for the
  * stencil fields and the predicted w in mixed mode, where div_m, div_t, rho_p
  * and theta_p hold double-word pairs (float hi, float lo; value hi + lo) in
- * 8-byte slots).  Names: vt, ekin_e, ddt_vn0, ddt_vn1,
+ * 8-byte slots).  Names: vt, ekin_e (twice the kinetic energy, vn^2 + vt^2), ddt_vn0, ddt_vn1,
  * rho_e, theta_e, hpg, vn_p, divd, divd2, ddt_w0, ddt_w1, grad4, div_m,
  * div_t, w_p, rho_p, theta_p.  Errors: ICON_ERR_ARG (unknown name, bytes too
  * small), ICON_ERR_CUDA. */

@@ -234,6 +234,13 @@ static void free_graphs(icon_dycore* d) {
 namespace {
 
 void enqueue_op(icon_dycore* d, int op, const StateView& st, cudaStream_t s);
+
+// The dycore's own stream for graph capture.
+void release_streams(icon_dycore* d) {
+  if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+  d->cap_stream = nullptr;
+}
+
 // The common part of icon_dycore_create and icon_dycore_create_terrain:
 // z_ifc [nlev+1] the heights the per-level tables use (column 0's over
 // terrain), z_cols [nc*(nlev+1)] the per-column heights (NULL: flat ground).
@@ -251,7 +258,7 @@ bool grid_complete(const GridT<T>& g) {
   const void* p[] = {g.c2e, g.c2e2c, g.e2c, g.e2v, g.e2c2v, g.e2c2e, g.v2e, g.v2c, g.div_c, g.lap_c, g.e2c_w,
                      g.grad_c, g.k4w_c, g.inv_d, g.inv_l, g.f_e, g.vt_w, g.upw, g.nt, g.inv_dn, g.smag_a, g.k4_a,
                      g.fdiv_e, g.ddamp_e, g.curl_v, g.c2v_w, g.uv_w, g.cell_area, g.uv_c, g.div_c_hl,
-                     g.upw_s, g.cpd_inv_d};
+                     g.upw_s, g.cpd_inv_d, g.hinv_d, g.d_o_l, g.grad_s, g.lap_s, g.e2c_wd};
   for (const void* q : p)
     if (!q) return false;
   return true;
@@ -516,7 +523,27 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
       for (int j = 2; j < 6; ++j) upw_s[12 * (size_t)e + 6 * side + j] *= 0.5 * s.dt_s;
     cid[e] = p->cpd * h.inv_d[e];
   }
+  // factors that fold constants of the stencils into stored products (fewer
+  // FP64 operations per point-level)
+  std::vector<double> hinv_d(ne), d_o_l(ne), grad_s(2 * (size_t)nc, 0.0), lap_s(nc, 0.0), e2c_wd(3 * (size_t)nc);
+  for (int e = 0; e < ne; ++e) {
+    hinv_d[e] = 0.5 * h.inv_d[e];
+    d_o_l[e] = h.inv_l[e] / h.inv_d[e];
+  }
+  for (int c = 0; c < nc; ++c)
+    for (int j = 0; j < 3; ++j) {
+      const size_t cj = 3 * (size_t)c + j;
+      grad_s[2 * (size_t)c] += h.grad_c[2 * cj];
+      grad_s[2 * (size_t)c + 1] += h.grad_c[2 * cj + 1];
+      lap_s[c] += h.lap_c[cj];
+      e2c_wd[cj] = h.e2c_w[cj] * h.inv_d[h.c2e[cj]];
+    }
   en.g64 = grid->dev;
+  en.g64.hinv_d = A.upload(hinv_d);
+  en.g64.d_o_l = A.upload(d_o_l);
+  en.g64.grad_s = A.upload(grad_s);
+  en.g64.lap_s = A.upload(lap_s);
+  en.g64.e2c_wd = A.upload(e2c_wd);
   en.g64.upw_s = A.upload(upw_s);
   en.g64.cpd_inv_d = A.upload(cid);
   en.g64.tenh_a = tenh_on ? A.upload(tenh) : nullptr;
@@ -553,6 +580,11 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     g.k4w_c = up(k4w);
     g.inv_d = up(h.inv_d);
     g.inv_l = up(h.inv_l);
+    g.hinv_d = up(hinv_d);
+    g.d_o_l = up(d_o_l);
+    g.grad_s = up(grad_s);
+    g.lap_s = up(lap_s);
+    g.e2c_wd = up(e2c_wd);
     g.f_e = up(fe);
     g.vt_w = up(h.vt_w);
     g.upw = up(h.upw);
@@ -623,6 +655,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     w.dtheta = A.template alloc<T>(cf);
     w.div_l = A.template alloc<T>(cf);
     w.div_vn = A.template alloc<T>(cf);
+    w.wq = A.template alloc<T>(cf);
     w.tenh_ex = tenh_on ? A.template alloc<T>(cf) : nullptr;
     w.ddt_w0 = A.template alloc<T>(ch);
     w.ddt_w1 = A.template alloc<T>(ch);
@@ -718,7 +751,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
   if (A.status != cudaSuccess) {
     std::string m = fname + ": " + cudaGetErrorString(A.status);
     A.release();
-    if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+    release_streams(d);
     delete d;
     return fail(ICON_ERR_CUDA, m);
   }
@@ -733,7 +766,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
                     (mixed ? grid_complete(en.c32.g) : grid_complete(en.c64.g));
     if (!ok) {
       A.release();
-      cudaStreamDestroy(d->cap_stream);
+      release_streams(d);
       delete d;
       return fail(ICON_ERR_CUDA, fname + ": internal error: a coefficient or work array is missing");
     }
@@ -744,7 +777,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     int rc = autotune(d);
     if (rc != ICON_OK) {
       A.release();
-      cudaStreamDestroy(d->cap_stream);
+      release_streams(d);
       delete d;
       return rc;
     }
@@ -784,7 +817,7 @@ int icon_dycore_destroy(icon_dycore_t* d) {
   if (d->edge16) cudaFree(d->edge16);
   if (d->partial) cudaFree(d->partial);
   d->arena.release();
-  if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+  release_streams(d);
   delete d;
   return ICON_OK;
 }

@@ -29,10 +29,15 @@ struct GridT {
   const T* lap_c;   // [nc*3] l_e / (d_e A_c)
   const T* e2c_w;   // [nc*3] edge->cell interpolation weights
   const T* grad_c;  // [nc*6] Green-Gauss gradient in the cell frame, (x,y) per nbr: sum G_j (psi_j - psi_c)
+  const T* grad_s;  // [nc*2] sum_j G_j (x, y): the FP64 gradient as sum G_j psi_j - (sum G_j) psi_c
+  const T* lap_s;   // [nc]   sum_j lap_c_j (the FP64 divergence Laplacian in the same form)
+  const T* e2c_wd;  // [nc*3] e2c_w times 1/d of that edge (the sum of the edges' w advection)
   const T* k4w_c;   // [nc]   hdiff_w_k4 * A_c^2
   // edge coefficients
   const T* inv_d;   // [ne] 1/d_e
   const T* inv_l;   // [ne] 1/l_e
+  const T* hinv_d;  // [ne] 1/(2 d_e) (the gradient of 2K)
+  const T* d_o_l;   // [ne] d_e / l_e
   const T* f_e;     // [ne] Coriolis parameter
   const T* vt_w;    // [ne*5] tangential-wind weights: self, e2c2e[0..3]
   const T* upw;     // [ne*12] per upwind side s: (dx, dy, nx, ny, tx, ty) in that cell's frame
@@ -191,14 +196,16 @@ inline std::vector<float> level_pairs(int nlev, const double* colc, const double
 template <class T>
 struct WorkT {
   // edges, full levels
+  // (ekin_e: twice the kinetic energy, vn^2 + vt^2)
   T *vt, *ekin_e, *ddt_vn0, *ddt_vn1, *rho_e, *theta_e, *hpg, *vn_p, *lap_vn, *nu;
-  // edges, half levels
+  // edges, half levels (gw_e: the horizontal advection of w times d_e)
   T* gw_e;
   T* vn_ie;  // vn interpolated to the half levels (top: level 0, ground: level nlev-1)
   // edges, full levels (FP64 mode): the horizontal mass and theta fluxes, one value per edge
   T *flx_m, *flx_t;
-  // cells, full levels
-  T *ekin_c, *grad4, *divd, *divd2, *dtheta, *div_l, *div_vn;
+  // cells, full levels (ekin_c: 2K at the cell; wq: the sum of the two w, or
+  // w - w_concorr, at the level's half levels)
+  T *ekin_c, *grad4, *divd, *divd2, *dtheta, *div_l, *div_vn, *wq;
   // cells, half levels
   T *ddt_w0, *ddt_w1, *lap_w;
   T* tenh_ex;  // cells, full levels: the enhanced temperature diffusion's excess factor

@@ -96,7 +96,8 @@ const char* kname(const char* f64, const char* f32) {
 // -------------------------------------------------------------------------
 // A1: tangential wind and edge kinetic energy
 //   vt = sum_j vt_w[j] vn[e_j] (Perot reconstruction averaged over the two
-//   cells, projected on t_e), K_e = (vn^2 + vt^2)/2
+//   cells, projected on t_e), K_e = (vn^2 + vt^2)/2, stored as 2 K_e (the
+//   1/2 is folded into the gradient's stored factor 1/(2 d_e))
 // -------------------------------------------------------------------------
 // Also vn at the half levels, vn_ie (interpolated inside with the level
 // weights -- the edge weights wgt_e over terrain -- the top level's value at the
@@ -115,7 +116,7 @@ __device__ __forceinline__ void va_edge_pre_at(const VertT<T>& v, int e, int k, 
   t = fmat(w[3], x3[k], t);
   t = fmat(w[4], x4[k], t);
   vt[(size_t)e * nlev + k] = t;
-  ekin[(size_t)e * nlev + k] = T(0.5) * fmat(vne, vne, t * t);
+  ekin[(size_t)e * nlev + k] = fmat(vne, vne, t * t);
   const T wg = wgt_e ? wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
   vn_ie[(size_t)e * nlevp + k] = k == 0 ? vne : fmat(wg, x0[k - 1] - vne, vne);
   if (k == nlev - 1) vn_ie[(size_t)e * nlevp + nlev] = vne;
@@ -182,10 +183,18 @@ __global__ void va_concorr(GridT<T> g, VertT<T> v, TerrT<T> tr, const T* __restr
 //     Laplacian dd2 = lapc(div vn*));  vertices: zeta = curl vn (full levels),
 //     w_v = sum r_c w_c (half levels).  One launch over nc*nlev + nv*(nlev+1).
 // -------------------------------------------------------------------------
+// Also, per cell and full level, wq = w_k + w_k+1 (over terrain the
+// contravariant w - wcc): the edge tendency's mean of four w is then the
+// sum of its two cells' wq, computed once per cell instead of once per edge.
+// In FP64 the Laplacian is sum L_j dd_j - (sum L_j) dd_c: fewer FP64
+// operations (the damping increment is a small part of vn, so the
+// cancellation in the sum costs nothing measurable); FP32 keeps the
+// differences.
 template <class T>
 __global__ void va_cell_vert(GridT<T> g, VertT<T> v, const T* __restrict__ vn, const T* __restrict__ w,
                              const T* __restrict__ ekin_e, T* __restrict__ ekin_c, const T* __restrict__ divd,
-                             T* __restrict__ divd2, T* __restrict__ zeta, T* __restrict__ w_v) {
+                             T* __restrict__ divd2, T* __restrict__ zeta, T* __restrict__ w_v, T* __restrict__ wq,
+                             const T* __restrict__ wcc) {
   const int nlev = v.nlev, nlevp = nlev + 1;
   unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned ncell = (unsigned)g.nc * nlev;
@@ -197,14 +206,27 @@ __global__ void va_cell_vert(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
     s += q[1] * ekin_e[(size_t)ce[1] * nlev + k];
     s += q[2] * ekin_e[(size_t)ce[2] * nlev + k];
     ekin_c[i] = s;
+    const T* wc = w + (size_t)c * nlevp;
+    if (wcc) {
+      const T* qc = wcc + (size_t)c * nlevp;
+      wq[i] = (wc[k] - qc[k]) + (wc[k + 1] - qc[k + 1]);
+    } else {
+      wq[i] = wc[k] + wc[k + 1];
+    }
     if (divd2) {
       const int* cc = g.c2e2c + 3 * (size_t)c;
       const T* L = g.lap_c + 3 * (size_t)c;
       const T dc = divd[i];
-      T r = L[0] * (divd[(size_t)cc[0] * nlev + k] - dc);
-      r += L[1] * (divd[(size_t)cc[1] * nlev + k] - dc);
-      r += L[2] * (divd[(size_t)cc[2] * nlev + k] - dc);
-      divd2[i] = r;
+      const T d0 = divd[(size_t)cc[0] * nlev + k], d1 = divd[(size_t)cc[1] * nlev + k],
+              d2 = divd[(size_t)cc[2] * nlev + k];
+      if constexpr (kMixed<T>) {
+        T r = L[0] * (d0 - dc);
+        r += L[1] * (d1 - dc);
+        r += L[2] * (d2 - dc);
+        divd2[i] = r;
+      } else {
+        divd2[i] = fmat(L[2], d2, fmat(L[1], d1, fmat(L[0], d0, -(g.lap_s[c] * dc))));
+      }
     }
     return;
   }
@@ -236,48 +258,40 @@ __global__ void va_cell_vert(GridT<T> g, VertT<T> v, const T* __restrict__ vn, c
 // Over terrain (kTerr): edge interpolation weights and layer thicknesses, and
 // the contravariant velocity w - wcc as the advecting vertical velocity.
 // Arithmetic arranged for few FP64 instructions (the FP64 mode is bound by
-// GB300's FP64 issue rate): wbar dvn/dz = (sum of the four w) (vn_ie_k -
-// vn_ie_k+1) dz^-1/4 with dz^-1/4 stored, the Coriolis term's 1/2 folded into a
-// multiply-add, the gradient of K into the final multiply-add.
+// GB300's FP64 issue rate): wbar dvn/dz = (wq_c0 + wq_c1) (vn_ie_k -
+// vn_ie_k+1) dz^-1/4 with the cells' sums of two w from va_cell_vert and
+// dz^-1/4 stored, the Coriolis term's 1/2 folded into a multiply-add, the
+// gradient of 2K times 1/(2 d) into the final multiply-add.  gw_e is stored
+// times d_e (its 1/d_e is folded into va_cell_w's weights).
 template <class T, bool kTerr = false>
 __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn_ie, const T* __restrict__ w,
                              const T* __restrict__ vt, const T* __restrict__ ekin_c, const T* __restrict__ zeta,
                              const T* __restrict__ w_v, T* __restrict__ ddt_vn, T* __restrict__ gw_e, TerrT<T> tr,
-                             const T* __restrict__ wcc) {
+                             const T* __restrict__ wq) {
   int e, k;
   const int nlev = v.nlev, nlevp = nlev + 1;
   if (!flat_index(g.ne, nlevp, e, k)) return;
   const int c0 = g.e2c[2 * e], c1 = g.e2c[2 * e + 1];
-  const T inv_d = g.inv_d[e];
   const T* vte = vt + (size_t)e * nlev;
   const T vnie_k = vn_ie[(size_t)e * nlevp + k];
   if (k < nlev) {
     const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
     const T vnie_k1 = vn_ie[(size_t)e * nlevp + k + 1];
-    const T* w0 = w + (size_t)c0 * nlevp;
-    const T* w1 = w + (size_t)c1 * nlevp;
-    T ws;
-    if constexpr (kTerr) {
-      const T* q0 = wcc + (size_t)c0 * nlevp;
-      const T* q1 = wcc + (size_t)c1 * nlevp;
-      ws = ((w0[k] - q0[k]) + (w0[k + 1] - q0[k + 1])) + ((w1[k] - q1[k]) + (w1[k + 1] - q1[k + 1]));
-    } else {
-      ws = (w0[k] + w0[k + 1]) + (w1[k] + w1[k + 1]);
-    }
+    const T ws = wq[(size_t)c0 * nlev + k] + wq[(size_t)c1 * nlev + k];
     const T qdz = kTerr ? tr.qdz_e[(size_t)e * nlev + k] : v.qdz[k];
     const T adv = (ws * (vnie_k - vnie_k1)) * qdz;
     const T zf = fmat(T(0.5), zeta[(size_t)vm * nlev + k] + zeta[(size_t)vp * nlev + k], g.f_e[e]);
     const T dk = ekin_c[(size_t)c0 * nlev + k] - ekin_c[(size_t)c1 * nlev + k];
-    ddt_vn[(size_t)e * nlev + k] = fmat(dk, inv_d, fmat(zf, vte[k], -adv));
+    ddt_vn[(size_t)e * nlev + k] = fmat(dk, g.hinv_d[e], fmat(zf, vte[k], -adv));
   }
   T gw = 0;
   if (k > 0 && k < nlev) {
     const int vm = g.e2v[2 * e], vp = g.e2v[2 * e + 1];
     const T wg = kTerr ? tr.wgt_e[(size_t)e * nlevp + k] : v.wgt[k];
     const T vtie = vte[k] + wg * (vte[k - 1] - vte[k]);
-    const T dwdn = (w[(size_t)c1 * nlevp + k] - w[(size_t)c0 * nlevp + k]) * inv_d;
-    const T dwdt = (w_v[(size_t)vp * nlevp + k] - w_v[(size_t)vm * nlevp + k]) * g.inv_l[e];
-    gw = vnie_k * dwdn + vtie * dwdt;
+    const T dwn = w[(size_t)c1 * nlevp + k] - w[(size_t)c0 * nlevp + k];
+    const T dwt = (w_v[(size_t)vp * nlevp + k] - w_v[(size_t)vm * nlevp + k]) * g.d_o_l[e];
+    gw = fmat(vnie_k, dwn, vtie * dwt);
   }
   gw_e[(size_t)e * nlevp + k] = gw;
 }
@@ -285,6 +299,7 @@ __global__ void va_edge_tend(GridT<T> g, VertT<T> v, const T* __restrict__ vn_ie
 // -------------------------------------------------------------------------
 // A4: w advective tendency at interior half levels (0 at top and ground)
 //   ddt_w = -sum q_e gw_e - w (wf_{k-1} - wf_k)/dzh,  wf full-level averages
+//   (q_e/d_e stored: gw_e holds the advection times d_e)
 // -------------------------------------------------------------------------
 // Over terrain (kTerr): advected by w - wcc, per-cell half-level spacing.
 // Both tile shapes evaluate every (cell, half level) with va_cell_w_at.
@@ -316,7 +331,7 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
     const int c = warp_point();
     if (c >= g.nc) return;
     const int* ce = g.c2e + 3 * (size_t)c;
-    const T* qp = g.e2c_w + 3 * (size_t)c;
+    const T* qp = g.e2c_wd + 3 * (size_t)c;
     const T q[3] = {qp[0], qp[1], qp[2]};
     const T* g0 = gw_e + (size_t)ce[0] * nlevp;
     const T* g1 = gw_e + (size_t)ce[1] * nlevp;
@@ -331,7 +346,7 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
   const int* ce = g.c2e + 3 * (size_t)c;
   ddt_w[(size_t)c * nlevp + k] =
       va_cell_w_at<T, kTerr>(v, tr, c, k, nlev, gw_e + (size_t)ce[0] * nlevp, gw_e + (size_t)ce[1] * nlevp,
-                             gw_e + (size_t)ce[2] * nlevp, g.e2c_w + 3 * (size_t)c, w + (size_t)c * nlevp, wcc);
+                             gw_e + (size_t)ce[2] * nlevp, g.e2c_wd + 3 * (size_t)c, w + (size_t)c * nlevp, wcc);
 }
 
 // -------------------------------------------------------------------------
@@ -364,12 +379,26 @@ __global__ void sn_cell_grad(GridT<T> g, VertT<T> v, const T* __restrict__ rho, 
   }
   const size_t i0 = (size_t)cc[0] * nlev + k, i1 = (size_t)cc[1] * nlev + k, i2 = (size_t)cc[2] * nlev + k;
   const T r = rho[i], t = theta[i];
-  const T r0 = rho[i0] - r, r1 = rho[i1] - r, r2 = rho[i2] - r;
-  const T t0 = theta[i0] - t, t1 = theta[i1] - t, t2 = theta[i2] - t;
-  grad4[i] = G[0] * r0 + G[2] * r1 + G[4] * r2;
-  grad4[n + i] = G[1] * r0 + G[3] * r1 + G[5] * r2;
-  grad4[2 * n + i] = G[0] * t0 + G[2] * t1 + G[4] * t2;
-  grad4[3 * n + i] = G[1] * t0 + G[3] * t1 + G[5] * t2;
+  if constexpr (kMixed<T>) {
+    const T r0 = rho[i0] - r, r1 = rho[i1] - r, r2 = rho[i2] - r;
+    const T t0 = theta[i0] - t, t1 = theta[i1] - t, t2 = theta[i2] - t;
+    grad4[i] = G[0] * r0 + G[2] * r1 + G[4] * r2;
+    grad4[n + i] = G[1] * r0 + G[3] * r1 + G[5] * r2;
+    grad4[2 * n + i] = G[0] * t0 + G[2] * t1 + G[4] * t2;
+    grad4[3 * n + i] = G[1] * t0 + G[3] * t1 + G[5] * t2;
+  } else {
+    // sum G_j psi_j - (sum G_j) psi_c: four FP64 operations per component
+    // instead of the differences' shared three plus three (the gradient only
+    // moves the upwind value by a small fraction of it, so the cancellation
+    // is harmless)
+    const T* S = g.grad_s + 2 * (size_t)c;
+    const T r0 = rho[i0], r1 = rho[i1], r2 = rho[i2];
+    const T t0 = theta[i0], t1 = theta[i1], t2 = theta[i2];
+    grad4[i] = fmat(G[4], r2, fmat(G[2], r1, fmat(G[0], r0, -(S[0] * r))));
+    grad4[n + i] = fmat(G[5], r2, fmat(G[3], r1, fmat(G[1], r0, -(S[1] * r))));
+    grad4[2 * n + i] = fmat(G[4], t2, fmat(G[2], t1, fmat(G[0], t0, -(S[0] * t))));
+    grad4[3 * n + i] = fmat(G[5], t2, fmat(G[3], t1, fmat(G[1], t0, -(S[1] * t))));
+  }
 }
 
 // -------------------------------------------------------------------------
@@ -951,17 +980,17 @@ void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt
                 va_concorr<T>, g, v, tr, wk.vn_ie, wk.vt, wcc);
   const long long n2 = (long long)g.nc * nlev + (long long)g.nv * nlevp;
   ICON_LAUNCH(kname<T>("va_cell_vert", "va_cell_vert_f32"), blocks_for(n2, TH(1)), TH(1), s, va_cell_vert<T>, g,
-              v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v);
+              v, vn, w, wk.ekin_e, wk.ekin_c, divd, divd2, wk.zeta, wk.w_v, wk.wq, terr ? (const T*)wcc : nullptr);
   if (terr) {
     ICON_LAUNCH(kname<T>("va_edge_tend_terrain", "va_edge_tend_terrain_f32"),
                 blocks_for((long long)g.ne * nlevp, TH(2)), TH(2), s, (va_edge_tend<T, true>), g, v, wk.vn_ie, w, wk.vt,
-                wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr, wcc);
+                wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr, (const T*)wk.wq);
     ICON_LAUNCH(kname<T>("va_cell_w_terrain", "va_cell_w_terrain_f32"), blocks_by_shape(SH(3), g.nc, nlevp, TH(3)),
                 TH(3), s, (va_cell_w<T, true>), g, v, w, wk.gw_e, ddt_w, tr, wcc, SH(3));
   } else {
     ICON_LAUNCH(kname<T>("va_edge_tend", "va_edge_tend_f32"), blocks_for((long long)g.ne * nlevp, TH(2)), TH(2),
                 s, (va_edge_tend<T, false>), g, v, wk.vn_ie, w, wk.vt, wk.ekin_c, wk.zeta, wk.w_v, ddt_vn, wk.gw_e, tr,
-                wcc);
+                (const T*)wk.wq);
     ICON_LAUNCH(kname<T>("va_cell_w", "va_cell_w_f32"), blocks_by_shape(SH(3), g.nc, nlevp, TH(3)), TH(3), s,
                 (va_cell_w<T, false>), g, v, w, wk.gw_e, ddt_w, tr, wcc, SH(3));
   }

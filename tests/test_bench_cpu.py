@@ -95,14 +95,14 @@ def test_dram_arithmetic_scales_per_unit_bytes_by_units_and_launches():
 
 def test_roofline_takes_the_longest_family_and_counts_its_flops():
     """The column solve's predictor and corrector form one family; with the
-    longest summed time it is the one reported, at (86 + 94 flops per
+    longest summed time it is the one reported, at (the two forms' flops per
     column-level) x columns x levels x launches over its summed time."""
     B = _bench()
     nc, ne, nv = _sizes(6)
     nlev = 90
     prof = {"sn_column_pred": (5, 10.0), "sn_column_corr": (5, 12.0), "va_edge_tend": (10, 15.0)}
     r = B.roofline(prof, nc, ne, nv, nlev)
-    flops = (86 + 94) * nc * nlev * 5
+    flops = (B.FLOPS_PER_UNIT["sn_column_pred"] + B.FLOPS_PER_UNIT["sn_column_corr"]) * nc * nlev * 5
     assert r["kernel"] == "sn_column" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - flops / 0.022 / 1e12) < 1e-12 * r["achieved"]
     assert abs(r["frac"] - r["achieved"] / B.FP64_PEAK_TFLOPS) < 1e-15
