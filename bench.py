@@ -500,7 +500,7 @@ def rms_area(area, d):
 # substeps blow up within 8 steps and 2 within 5; with the extrapolation off
 # 3 substeps run clean, 2 still blow up at every damping tried).
 LEARNED = dict(ndyn_reduced=3, reduced_scheme=dict(exner_exfac=0.0, divdamp_fac=0.004), hidden=512,
-               max_batch=65536, train_seeds=(100, 101, 102, 103), spinup=1, snapshots=8, every=3, rows=8192,
+               max_batch=262144, train_seeds=(100, 101, 102, 103), spinup=1, snapshots=8, every=3, rows=8192,
                adam_steps=1500, batch=4096, lr=1e-3, max_norm=3.0)
 
 

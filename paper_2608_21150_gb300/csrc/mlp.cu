@@ -61,7 +61,10 @@ constexpr int TBM = 128, TBN = 128, TBK = 64, kStages = 5;
 constexpr int kEpiWarps = 8;
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileBytesA = TBM * TBK * 2, kTileBytesB = TBN * TBK * 2;
-constexpr int kTcSmem = kStages * (kTileBytesA + kTileBytesB) + 1024 /* alignment slack */ + 256 /* barriers */;
+// per epilogue warp, a staging block of its 32 rows x 64 columns of BF16 output
+constexpr int kStageBytes = 32 * 64 * 2;
+constexpr int kTcSmem = kStages * (kTileBytesA + kTileBytesB) + kEpiWarps * kStageBytes +
+                        1024 /* alignment slack */ + 256 /* barriers */;
 constexpr uint32_t kTmemCols = 2 * TBN;
 // every wait gives up after this long (ns) and flags an error instead of hanging
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
@@ -240,7 +243,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc(const __grid_constant__
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + kStages * kTileBytesA;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kTileBytesB);
+  uint8_t* sOut = sB + kStages * kTileBytesB;  // the epilogue warps' staging blocks
+  uint64_t* full = reinterpret_cast<uint64_t*>(sOut + kEpiWarps * kStageBytes);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;   // [2] MMA -> epilogue
   uint64_t* acc_empty = acc_full + 2;     // [2] epilogue -> MMA
@@ -335,11 +339,93 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc(const __grid_constant__
       const int m0 = (tile / tiles_n) * TBM, n0 = (tile % tiles_n) * TBN;
       const int row = m0 + 32 * quarter + lane;
       const uint32_t trow = tmem + (uint32_t)(b * TBN) + ((uint32_t)(32 * quarter) << 16);
+      const int cw = n0 + half * (TBN / 2);  // first column of this warp's half
+      if (ep.mode == 1 && !ep.zpre && cw + TBN / 2 <= N && (ep.ldc & 1) == 0 &&
+          (reinterpret_cast<uintptr_t>(ep.out_bf16) & 3) == 0) {
+        // GELU to BF16 staged in this warp's block (row = lane, 16-byte chunks
+        // XOR-swizzled by the row so that 8 lanes writing one chunk hit all
+        // banks), then stored row by row as 128-byte runs
+        uint8_t* st = sOut + (warp - 2) * kStageBytes;
 #pragma unroll 1
-      for (int c = half * (TBN / 2); c < (half + 1) * (TBN / 2); c += 16) {
-        float v[16];
-        tmem_ld16(trow + (uint32_t)c, v);
-        epilogue16(v, row, n0 + c, M, N, ep);
+        for (int c = 0; c < TBN / 2; c += 16) {
+          float v[16];
+          tmem_ld16(trow + (uint32_t)(half * (TBN / 2) + c), v);
+          if (ep.bias) {
+            const float4* b4 = reinterpret_cast<const float4*>(ep.bias + cw + c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 bq = __ldg(b4 + q);
+              v[4 * q] += bq.x;
+              v[4 * q + 1] += bq.y;
+              v[4 * q + 2] += bq.z;
+              v[4 * q + 3] += bq.w;
+            }
+          }
+          uint32_t h[8];  // BF16 pairs, the lower column in the low half
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(gelu_fwd(v[2 * j]), gelu_fwd(v[2 * j + 1]));
+            h[j] = *reinterpret_cast<const uint32_t*>(&p2);
+          }
+          const int ch = c / 8;  // logical 16-byte chunk of the row
+          *reinterpret_cast<uint4*>(st + lane * 128 + ((ch ^ (lane & 7)) * 16)) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(st + lane * 128 + (((ch + 1) ^ (lane & 7)) * 16)) =
+              make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int grow = m0 + 32 * quarter + r;
+          const uint32_t val =
+              *reinterpret_cast<const uint32_t*>(st + r * 128 + (((lane >> 2) ^ (r & 7)) * 16) + (lane & 3) * 4);
+          if (grow < M) *reinterpret_cast<uint32_t*>(ep.out_bf16 + (size_t)grow * ep.ldc + cw + 2 * lane) = val;
+        }
+        __syncwarp();
+      } else if (ep.mode == 0 && cw + TBN / 2 <= N) {
+        // FP32 (+ bias) staged the same way, 32 columns (128 bytes a row) at a time
+        uint8_t* st = sOut + (warp - 2) * kStageBytes;
+#pragma unroll 1
+        for (int c2 = 0; c2 < TBN / 2; c2 += 32) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int c = c2 + 16 * hh;
+            float v[16];
+            tmem_ld16(trow + (uint32_t)(half * (TBN / 2) + c), v);
+            if (ep.bias) {
+              const float4* b4 = reinterpret_cast<const float4*>(ep.bias + cw + c);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 bq = __ldg(b4 + q);
+                v[4 * q] += bq.x;
+                v[4 * q + 1] += bq.y;
+                v[4 * q + 2] += bq.z;
+                v[4 * q + 3] += bq.w;
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int ch = 4 * hh + q;  // logical 16-byte chunk of the 128-byte row
+              *reinterpret_cast<float4*>(st + lane * 128 + ((ch ^ (lane & 7)) * 16)) =
+                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+          }
+          __syncwarp();
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const int grow = m0 + 32 * quarter + r;
+            const float val =
+                *reinterpret_cast<const float*>(st + r * 128 + (((lane >> 2) ^ (r & 7)) * 16) + (lane & 3) * 4);
+            if (grow < M) ep.out_f32[(size_t)grow * ep.ldc + cw + c2 + lane] = val;
+          }
+          __syncwarp();
+        }
+      } else {
+#pragma unroll 1
+        for (int c = half * (TBN / 2); c < (half + 1) * (TBN / 2); c += 16) {
+          float v[16];
+          tmem_ld16(trow + (uint32_t)c, v);
+          epilogue16(v, row, n0 + c, M, N, ep);
+        }
       }
       tc_fence_before();
       __syncwarp();
