@@ -96,7 +96,7 @@ def units_per_launch(name, nc, ne, nv, nlev):
         "sn_cell_fluxsum": full["c"],
         "diff_div_curl_uv": full["c"] + full["v"], "diff_edge_smag": full["e"],
         "diff_second": half["c"] + full["v"], "diff_edge_update": full["e"], "diff_cell_update": half["c"],
-        "mx_refresh": full["e"] + half["c"],
+        "mx_refresh": full["e"] + half["c"], "lc_col_inputs": full["c"], "lc_edge_inputs": full["e"],
     }[base_name(name)]
 
 
@@ -308,28 +308,35 @@ def config_dict(prec):
 
 # ---------------------------------------------------------------------------
 # DRAM traffic per unit of every kernel, from one-kernel ncu captures
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch) at R2B5 L90,
-# the units (point-levels) of that launch dividing them; scaled to the bench's
-# grid by the units per launch.  Valid while the kernel sources are the ones
-# captured (SHA-256 over csrc/* except the host-only set-up code).
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch, -c 1; the
+# column solve's predictor and corrector -c 2) at R2B5 L90 inside the leg's
+# timed steps, divided by the units (point-levels) of that launch; scaled to
+# the bench's grid by the units per launch.  Kernels that run in row chunks
+# (the learned step's networks and increments) carry bytes per unit of a
+# whole step instead (PER_STEP_UNITS).  Valid while the sources that define
+# the timed kernels are the ones captured (SHA-256 over KERNEL_SOURCES).
 DRAM_PER_UNIT = {"sources_sha256": None, "bisections": 5, "nlev": 90, "legs": {}}
 
-# Host-only set-up code (grid validation, geometry and terrain metrics, run
-# untimed at create) cannot change a kernel's DRAM traffic and is left out of
-# the hash.
-HOST_ONLY_SOURCES = ("grid_setup.cpp", "terrain_setup.cpp")
+# The files whose code runs on the device in the timed steps.
+KERNEL_SOURCES = ("kernels_stencil.cu", "kernels_column.cu", "column_kernel.cuh", "kernels_column_terrain.cu",
+                  "kernels_diag.cu", "mlp.cu", "learned.cu", "dfloat.cuh", "kernels.h", "internal.h")
+
+
+def per_step_units(name, nc, ne, nlev):
+    """Units of a whole step of the kernels that run in row chunks, or None:
+    the networks' GEMMs (both networks' rows scale with the cells), the
+    increments of the column and edge networks, the check's reductions."""
+    return {"mlp_gemm_tc": nc, "lc_apply_col": nc * (3 * nlev - 1), "lc_apply_edge": ne * nlev,
+            "lc_reduce_status": 1, "lc_reduce_status2": 1}.get(name)
 
 
 def sources_sha256():
-    """sha256 over the library sources that shape the timed kernels' traffic."""
-    import glob
+    """sha256 over the library sources that define the timed kernels."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2608_21150_gb300", "csrc", "*"))):
-        if os.path.basename(f) in HOST_ONLY_SOURCES:
-            continue
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2608_21150_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
@@ -357,7 +364,8 @@ def dram_measured(leg, prof, nsteps, ms_per_step, sizes, nlev, ndyn):
         b = base_name(k)
         if b not in tab:
             return None
-        total += tab[b] * units_per_launch(k, nc, ne, nv, nlev) * n
+        u = per_step_units(b, nc, ne, nlev)
+        total += tab[b] * (u * nsteps if u is not None else units_per_launch(k, nc, ne, nv, nlev) * n)
     b = total / nsteps
     peak, src = hbm_peak()
     gbs = b / (ms_per_step / 1000.0) / 1e9
@@ -585,7 +593,9 @@ def learned_leg(P, G, z, grid, st0, args, dev, world, f64_final, wl, total_steps
            "train": {"seconds": train_s, "loss_col": [float(np.mean(lc[:10])), float(np.mean(lc[-50:]))],
                      "loss_edge": [float(np.mean(le[:10])), float(np.mean(le[-50:]))], **{
                          k: (list(v) if isinstance(v, tuple) else v) for k, v in L.items()}},
-           "kernels": kernel_table(prof.kernels, 1), "clocks": clocks}
+           "kernels": kernel_table(prof.kernels, 1), "clocks": clocks,
+           "hbm_measured": dram_measured("learned", prof.kernels, 1, ms / nsteps,
+                                         (G.n_cells, G.n_edges, G.n_verts), nlev, L["ndyn_reduced"])}
     for x in (cn, en, R, Pl):
         x.close()
     del t

@@ -143,3 +143,23 @@ def test_state_and_compulsory_bytes_are_those_of_the_state_arrays():
                 for k in ("vn", "w", "rho", "exner", "theta_v", "exner_pr"))
     assert B.state_bytes(grid.n_cells, grid.n_edges, 12) == total
     assert B.compulsory_bytes_per_step(grid.n_cells, grid.n_edges, 12, 5) == 2 * 6 * total
+
+
+def test_chunked_kernels_count_their_bytes_per_step():
+    """The learned step's networks and increments run in row chunks: their
+    captured bytes are per unit of a whole step (cells for the GEMMs), so
+    the number of chunk launches does not multiply them."""
+    B = _bench()
+    nc, ne, nv = _sizes(6)
+    nlev = 90
+    table = {"mlp_gemm_tc": 1000.0, "lc_apply_col": 2.0, "va_edge_pre_f32": 3.0, "va_edge_pre": 3.0}
+    saved = _with_table(B, {"sources_sha256": B.sources_sha256(), "nlev": 90, "legs": {"learned": table}})
+    try:
+        for chunks in (1, 4):
+            prof = {"mlp_gemm_tc": (3 * chunks, 1.0), "lc_apply_col": (chunks, 1.0), "va_edge_pre_f32": (6, 1.0)}
+            r = B.dram_measured("learned", prof, 1, 10.0, (nc, ne, nv), nlev, 3)
+            want = 1000.0 * nc + 2.0 * nc * (3 * nlev - 1) + 3.0 * ne * nlev * 6
+            assert abs(r["bytes_per_step"] - want) < 1e-9 * want
+    finally:
+        B.DRAM_PER_UNIT.clear()
+        B.DRAM_PER_UNIT.update(saved)
