@@ -109,7 +109,13 @@ def test_roofline_takes_the_longest_family_and_counts_its_flops():
     # a larger edge-tendency time moves the report to that kernel, at its flops per edge-half-level
     prof["va_edge_tend"] = (10, 30.0)
     r = B.roofline(prof, nc, ne, nv, nlev)
-    assert r["kernel"] == "va_edge_tend" and r["traffic"] is None
+    assert r["kernel"] == "va_edge_tend"
+    tab = B.dram_table("fp64", nlev)
+    if tab is None:   # no capture of the running sources: no traffic figure
+        assert r["traffic"] is None
+    else:             # the captured bytes per unit times the units of one launch
+        want = tab["va_edge_tend"] * ne * (nlev + 1)
+        assert abs(r["traffic"] - want) < 1e-9 * want and r["hbm"]["achieved_gbs"] > 0
     f = B.FLOPS_PER_UNIT["va_edge_tend"]
     assert abs(r["achieved"] - f * ne * (nlev + 1) * 10 / 0.030 / 1e12) < 1e-12 * r["achieved"]
 
