@@ -66,7 +66,7 @@ FLOPS_PER_UNIT = {
     "va_edge_pre": 15, "va_cell_vert": 14, "va_edge_tend": 21, "va_cell_w": 11,
     "sn_cell_grad": 32, "sn_edge_pred": 24, "sn_cell_div": 5, "sn_cell_fluxdiv": 27,
     "sn_edge_flux": 6, "sn_cell_fluxsum": 12,
-    "sn_column_pred": 84, "sn_edge_corr": 11, "sn_column_corr": 82,
+    "sn_column_pred": 83, "sn_edge_corr": 11, "sn_column_corr": 84,
     "diff_div_curl_uv": 30, "diff_edge_smag": 46, "diff_second": 30,
     "diff_edge_update": 12, "diff_cell_update": 12, "va_concorr": 20,
 }
