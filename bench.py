@@ -402,6 +402,13 @@ def dram_measured(leg, prof, nsteps, ms_per_step, sizes, nlev, ndyn):
                     % (DRAM_PER_UNIT["bisections"], DRAM_PER_UNIT["nlev"], src)}
 
 
+# FP64 instructions per unit (DADD + DMUL + DFMA) where ncu counted them
+# (`smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on`, R2B5 L90, the
+# sources of DRAM_PER_UNIT): the FP64 pipe issues one of any kind per slot, so
+# the instruction rate against the pipe's (half the FMA flop rate) is how busy
+# the pipe is, whatever the mix of adds and FMAs.
+FP64_INSTR_PER_UNIT = {"sn_column_pred": 59.1, "sn_column_corr": 60.0}
+
 # The column solve's predictor and corrector launches are one kernel (one
 # function, two forms); the roofline treats them together.
 FAMILY = {"sn_column_pred": "sn_column", "sn_column_corr": "sn_column"}
@@ -423,6 +430,15 @@ def roofline(prof, nc, ne, nv, nlev, leg="fp64"):
         a[4].append(b)
     name, (n, ms, flops, units, members) = max(fam.items(), key=lambda kv: kv[1][1])
     achieved = flops / (ms / 1000.0) / 1e12
+    issue = None
+    if all(m in FP64_INSTR_PER_UNIT for m in members):
+        instr = sum(FP64_INSTR_PER_UNIT[base_name(k)] * units_per_launch(k, nc, ne, nv, nlev) * prof[k][0]
+                    for k in prof if FAMILY.get(base_name(k), base_name(k)) == name)
+        rate = instr / (ms / 1000.0) / 1e12
+        issue = {"achieved": rate, "peak": FP64_PEAK_TFLOPS / 2, "unit": "T FP64 instructions/s",
+                 "frac": rate / (FP64_PEAK_TFLOPS / 2),
+                 "note": "DADD + DMUL + DFMA per unit from ncu counters x units / event time, against the FP64 "
+                         "pipe's instruction rate"}
     tab = dram_table(leg, nlev)
     traffic, hbm = None, None
     if tab is not None and all(m in tab for m in members):
@@ -433,7 +449,7 @@ def roofline(prof, nc, ne, nv, nlev, leg="fp64"):
         gbs = byts / (ms / 1000.0) / 1e9
         hbm = {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak, "peak_source": src}
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "hbm": hbm,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "hbm": hbm, "fp64_issue": issue,
             "note": "FP64 algorithmic flops per launch / event-timed launch duration (CUDA events around every "
                     "launch on the library's stream); peak = nominal FP64 rate from unit counts and clock "
                     "(1.2 TFLOP/s measured by a DFMA probe); traffic = DRAM bytes per launch from the one-kernel "
