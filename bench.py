@@ -28,6 +28,7 @@ each step a bounded sample: one substep and one diffusion call on R2B4 L90,
 extrapolated to a full R2B6 L90 step (x5 substeps, x16 cells).
 """
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -773,12 +774,18 @@ def run_ours(args):
                                  use_graph=1, synchronous=1, stream=stream.cuda_stream))
         D2.step(host)  # warm-up: allocates the device staging copy and captures the graph
         torch.cuda.synchronize(dev)
-        # each call is synchronous (copies in, step, copies out): timed one by one
+        # each call is synchronous (copies in, step, copies out): timed one by
+        # one, with Python's garbage collector held off (its pauses are the
+        # harness's, not the library's)
         times = []
-        for _ in range(e2e_steps):
-            t0 = time.perf_counter()
-            D2.step(host)
-            times.append(time.perf_counter() - t0)
+        gc.disable()
+        try:
+            for _ in range(e2e_steps):
+                t0 = time.perf_counter()
+                D2.step(host)
+                times.append(time.perf_counter() - t0)
+        finally:
+            gc.enable()
         D2.close()
         med = statistics.median(times)
         e2e = {"value": 1.0 / med, "unit": "steps/s", "h2d_bytes_per_step": sb, "d2h_bytes_per_step": sb,
