@@ -468,7 +468,8 @@ PRECISIONS = {"fp64": "ICON_PREC_FP64", "mixed": "ICON_PREC_MIXED", "mixed_f64co
 
 def leg_params(P, wl, leg, stream, **over):
     d = dict(dtime=wl["dtime"], ndyn_substeps=wl["ndyn"], rayleigh_coeff=wl["rayleigh"],
-             precision=getattr(P, PRECISIONS[leg]), use_graph=1, synchronous=0, stream=stream.cuda_stream)
+             precision=getattr(P, PRECISIONS[leg]), use_graph=1, synchronous=0, stream=stream.cuda_stream,
+             fused_advection=int(wl.get("fused_advection", 0)))
     d.update(over)
     return d
 
@@ -857,11 +858,15 @@ def main():
                     help="RnBm bisections (default 6 = R2B6); other grids for profiler captures and scaling runs")
     ap.add_argument("--dtime", type=float, default=WORKLOAD["dtime"],
                     help="time step in s (default 360, the R2B6 step; 180 at R2B7)")
+    ap.add_argument("--fused-advection", action="store_true",
+                    help="mixed legs: the velocity tendencies in the one fused kernel over cell patches "
+                         "instead of four kernels (same bits, slower on GB300)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     WORKLOAD["bisections"] = args.grid
     WORKLOAD["dtime"] = args.dtime
+    WORKLOAD["fused_advection"] = int(args.fused_advection)
     legs = [x for x in args.legs.split(",") if x]
     if args.no_mixed:
         legs = [x for x in legs if x not in ("mixed", "mixed_f64col", "learned")]

@@ -36,6 +36,7 @@ module icon_dycore
     integer(c_int32_t) :: steep_hpg
     real(c_double) :: hdiff_tenh_fac, hdiff_tenh_thresh
     integer(c_int32_t) :: hdiff_tenh_levels
+    integer(c_int32_t) :: fused_advection
   end type
 
   type, bind(c), public :: icon_state_t

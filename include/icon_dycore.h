@@ -141,6 +141,11 @@ typedef struct icon_dycore_params {
   double hdiff_tenh_thresh;  /* K: e_c = min(1, (|theta_c - mean of its 3 neighbours| - thresh)/thresh) */
   int32_t hdiff_tenh_levels; /* the lowest levels where e_c may be nonzero
                                 (>= 0; more than nlev means every level) */
+  int32_t fused_advection;  /* logical (default 0), mixed precision over flat
+                               ground: the velocity tendencies (rows A1-A4) in one
+                               kernel over patches of 128 cells, intermediates in
+                               shared memory; the same bits as the four separate
+                               kernels, and on GB300 about 1.3x their time */
 } icon_dycore_params_t;
 
 /* Writes the defaults (Sec. 4.1 names the scheme's parts, not its values;

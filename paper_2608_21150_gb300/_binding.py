@@ -62,7 +62,8 @@ class icon_dycore_params_t(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("synchronous", ctypes.c_int32), ("stream", ctypes.c_void_p), ("column_chunk", ctypes.c_int32),
                 ("steep_hpg", ctypes.c_int32), ("hdiff_tenh_fac", ctypes.c_double),
-                ("hdiff_tenh_thresh", ctypes.c_double), ("hdiff_tenh_levels", ctypes.c_int32)]
+                ("hdiff_tenh_thresh", ctypes.c_double), ("hdiff_tenh_levels", ctypes.c_int32),
+                ("fused_advection", ctypes.c_int32)]
 
 
 class icon_state_t(ctypes.Structure):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libicondycore.so")
-SOURCES = ["api.cu", "kernels_stencil.cu", "kernels_column.cu", "kernels_column_terrain.cu", "kernels_diag.cu", "mlp.cu", "mlp_api.cu", "mlp_data.cu", "learned.cu", "blocked.cu", "terrain_setup.cpp",
+SOURCES = ["api.cu", "kernels_stencil.cu", "kernels_column.cu", "kernels_column_terrain.cu", "kernels_diag.cu", "mlp.cu", "mlp_api.cu", "mlp_data.cu", "learned.cu", "blocked.cu", "terrain_setup.cpp", "patch_setup.cpp",
            "grid_setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -151,6 +151,7 @@ void icon_dycore_params_default(icon_dycore_params_t* p) {
   p->hdiff_tenh_fac = 0.0;
   p->hdiff_tenh_thresh = 5.0;
   p->hdiff_tenh_levels = 5;
+  p->fused_advection = 0;
 }
 
 int icon_grid_create(const icon_grid_desc_t* d, icon_grid_t** out) {
@@ -671,6 +672,69 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
     en.c64.g = en.g64;
   } else {
     build_ctx(en.c32, float{});
+    if (!z_cols && p->fused_advection) {
+      // rows A1-A4 of the FP32 stencils in one launch over patches of 128 cells
+      HostVaPatches hp;
+      const std::string err = build_va_patches(h, 128, &hp);
+      if (!err.empty()) {
+        A.release();
+        delete d;
+        return fail(ICON_ERR_ARG, fname + ": " + err);
+      }
+      // the grid factors the kernel reads, in patch order, rounded to FP32 as
+      // the context's own factors are
+      std::vector<float> e1_w(5 * hp.e1_g.size()), c3_w(4 * hp.c0_g.size(), 0.0f),
+          v3_w(12 * hp.v3_g.size()), e4_w(4 * hp.e4_g.size(), 0.0f), own_w(4 * (size_t)nc, 0.0f);
+      for (size_t i = 0; i < hp.e1_g.size(); ++i)
+        for (int j = 0; j < 5; ++j) e1_w[5 * i + j] = (float)h.vt_w[5 * (size_t)hp.e1_g[i] + j];
+      for (int q = 0; q < hp.n_patches; ++q)
+        for (int i = 0; i < hp.n_c3[q]; ++i) {
+          const size_t r = (size_t)hp.off_c0[q] + i;
+          for (int j = 0; j < 3; ++j) c3_w[4 * r + j] = (float)h.e2c_w[3 * (size_t)hp.c0_g[r] + j];
+        }
+      for (size_t i = 0; i < hp.v3_g.size(); ++i)
+        for (int j = 0; j < 6; ++j) {
+          v3_w[12 * i + j] = (float)h.curl_v[6 * (size_t)hp.v3_g[i] + j];
+          v3_w[12 * i + 6 + j] = (float)h.c2v_w[6 * (size_t)hp.v3_g[i] + j];
+        }
+      for (size_t i = 0; i < hp.e4_g.size(); ++i) {
+        const int e = hp.e4_g[i];
+        e4_w[4 * i] = (float)fe[e];
+        e4_w[4 * i + 1] = (float)hinv_d[e];
+        e4_w[4 * i + 2] = (float)d_o_l[e];
+      }
+      for (int c = 0; c < nc; ++c)
+        for (int j = 0; j < 3; ++j) own_w[4 * (size_t)c + j] = (float)e2c_wd[3 * (size_t)c + j];
+      VaPatchT& vp = en.c32.vp;
+      vp.P = hp.P;
+      vp.n_patches = hp.n_patches;
+      vp.max_e0 = hp.max_e0;
+      vp.max_e1 = hp.max_e1;
+      vp.max_c3 = hp.max_c3;
+      vp.max_c0 = hp.max_c0;
+      vp.max_v3 = hp.max_v3;
+      vp.max_e4 = hp.max_e4;
+      vp.off_e0 = A.upload(hp.off_e0);
+      vp.off_e1 = A.upload(hp.off_e1);
+      vp.off_c0 = A.upload(hp.off_c0);
+      vp.off_v3 = A.upload(hp.off_v3);
+      vp.off_e4 = A.upload(hp.off_e4);
+      vp.n_c3 = A.upload(hp.n_c3);
+      vp.n_w4 = A.upload(hp.n_w4);
+      vp.e0_g = A.upload(hp.e0_g);
+      vp.c0_g = A.upload(hp.c0_g);
+      vp.e4_g = A.upload(hp.e4_g);
+      vp.e1_i = A.upload(hp.e1_i);
+      vp.c3_i = A.upload(hp.c3_i);
+      vp.v3_i = A.upload(hp.v3_i);
+      vp.e4_i = A.upload(hp.e4_i);
+      vp.own_i = A.upload(hp.own_i);
+      vp.e1_w = A.upload(e1_w);
+      vp.c3_w = A.upload(c3_w);
+      vp.v3_w = A.upload(v3_w);
+      vp.e4_w = A.upload(e4_w);
+      vp.own_w = A.upload(own_w);
+    }
     Mirrors& m = en.m;
     m.vn = A.alloc<float>(ef);
     m.w = A.alloc<float>(ch);
@@ -746,6 +810,7 @@ int create_dycore(const icon_grid_t* grid, int nlev, const double* z_ifc, const 
   if (A.status == cudaSuccess) {
     cudaError_t e = init_column_kernels();
     if (e == cudaSuccess && z_cols) e = init_column_terrain_kernels();
+    if (e == cudaSuccess && en.c32.vp.n_patches > 0) e = init_va_fused(en.c32.vp);
     if (e != cudaSuccess) A.status = e;
   }
   if (A.status != cudaSuccess) {

@@ -192,6 +192,22 @@ inline std::vector<float> level_pairs(int nlev, const double* colc, const double
   return t;
 }
 
+// Device copy of HostVaPatches with the grid factors the fused kernel reads,
+// gathered into patch order in FP32 (n_patches 0: no fused velocity advection).
+// Packed tables are 16-byte aligned rows of 16-bit local indices.
+struct VaPatchT {
+  int P, n_patches;
+  int max_e0, max_e1, max_c3, max_c0, max_v3, max_e4;
+  const int *off_e0, *off_e1, *off_c0, *off_v3, *off_e4, *n_c3, *n_w4;
+  const int *e0_g, *c0_g, *e4_g;
+  const uint16_t *e1_i, *c3_i, *v3_i, *e4_i, *own_i;
+  const float *e1_w;   // [5] per E1 item: vt_w
+  const float *c3_w;   // [4] per C0 item (C3 prefix): e2c_w, 0
+  const float *v3_w;   // [12] per V3 item: curl_v, c2v_w
+  const float *e4_w;   // [4] per E4 item: f_e, 1/(2d), d/l, 0
+  const float *own_w;  // [4] per cell: e2c_wd, 0
+};
+
 // Work arrays of the stencil kernels, compute type T.
 template <class T>
 struct WorkT {
@@ -280,6 +296,26 @@ struct HostTerrain {
   std::vector<double> steep_w;                                    // [6 n_steep]
   int n_ray = 0;  // the largest count of Rayleigh-damped top levels of a column
 };
+// Patches of the fused velocity-advection kernel (patch_setup.cpp): per
+// list, the patches' entries concatenated, off_*[p] .. off_*[p+1]; C3 is the
+// first n_c3[p] entries of the patch's C0 list.
+struct HostVaPatches {
+  int P = 0, n_patches = 0;
+  int max_e0 = 0, max_e1 = 0, max_c3 = 0, max_c0 = 0, max_v3 = 0, max_e4 = 0;
+  std::vector<int> off_e0, off_e1, off_c0, off_v3, off_e4, n_c3, n_w4;
+  std::vector<int> e0_g;             // global edges whose vn the patch reads
+  std::vector<int> e1_g, c0_g, v3_g, e4_g;
+  std::vector<uint16_t> e1_i;  // [8]: local E0 of the edge and of its e2c2e, pad
+  std::vector<uint16_t> c3_i;  // [4] per C0 entry: local E1 of c2e (C3 entries), pad
+  std::vector<uint16_t> v3_i;  // [16]: local E0 of v2e, local C0 of v2c, pad
+  std::vector<uint16_t> e4_i;  // [8]: local E1, local E0, local C0 of e2c[0], e2c[1],
+                               //      local V3 of e2v[0], e2v[1], 0, 0 (the first
+                               //      n_w4[p] edges are written by this patch)
+  std::vector<uint16_t> own_i; // [4] per cell (global order): local E4 of c2e, 0
+};
+// Builds the patches of P consecutive cells; returns an error message or "".
+std::string build_va_patches(const HostGrid& g, int P, HostVaPatches* out);
+
 // Validates the per-column heights z_ifc[nc*(nlev+1)] (finite, strictly
 // decreasing in every column, one common model top) and derives the terrain
 // metrics; returns an error message or "".

@@ -63,7 +63,10 @@ struct Ctx {
   ScalT<T> s;
   WorkT<T> w;
   TerrT<T> tr;   // terrain metrics (all null over flat ground)
+  VaPatchT vp{};  // patches of the fused velocity advection (mixed precision, flat; n_patches 0: off)
 };
+// The fused velocity-advection kernel's shared-memory limit for these patches.
+cudaError_t init_va_fused(const VaPatchT& pt);
 
 // Device-side state of one dycore: FP64 factors and column-solve work, the
 // FP32 mirrors (mixed mode) and the stencil context of the active mode.

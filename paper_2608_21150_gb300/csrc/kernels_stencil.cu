@@ -350,6 +350,296 @@ __global__ void va_cell_w(GridT<T> g, VertT<T> v, const T* __restrict__ w, const
 }
 
 // -------------------------------------------------------------------------
+// A1-A4 in one launch (mixed precision, flat ground): one CTA per patch of
+// consecutive cells (the refinement order makes patches compact), chunks of
+// kVaL levels.  Per chunk, vn on every edge the patch reads and w on every
+// cell it reads come into shared memory (coalesced runs of levels); then, one
+// thread per edge, cell or vertex looping over the chunk's levels: vt and 2K
+// on the edges of the patch's cells and their neighbours, 2K at those cells,
+// vorticity and w at the vertices, the vn tendency and w's horizontal
+// advection on the own cells' edges, the w tendency of the own cells -- each
+// stage from shared memory, where the four kernels above pass through HBM.
+// Results are staged in shared memory and stored as runs of levels.  Halo
+// values are computed again by every patch that needs them; an edge's
+// tendency and vt are written by the patch of its first cell.  Local indices
+// and the grid factors come in patch order (16-bit index rows, FP32 factor
+// rows), so every item's table is one or two vector loads per chunk.  Every
+// value is the same expression as in the four kernels (the same bits).
+// -------------------------------------------------------------------------
+constexpr int kVaL = 8;          // levels per chunk
+constexpr int kVaS = kVaL + 1;   // shared-memory stride of a per-item run of L or L + 1 levels (odd)
+constexpr int kVaSn = kVaL + 3;  // stride of the staged vn and w runs of L + 2 levels (odd)
+constexpr int kVaThreads = 512;
+
+__host__ __device__ inline size_t va_fused_smem_floats(int max_e0, int max_e1, int max_c3, int max_c0, int max_v3,
+                                                       int max_e4) {
+  return 2 * (size_t)kVaSn * ((size_t)max_e0 + max_c0) +
+         (size_t)kVaS * (2 * (size_t)max_e1 + 2 * (size_t)max_e4 + max_c3 + 2 * (size_t)max_v3);
+}
+
+__device__ __forceinline__ int lo16(unsigned x) { return (int)(x & 0xffffu); }
+__device__ __forceinline__ int hi16(unsigned x) { return (int)(x >> 16); }
+
+// 4-byte asynchronous global->shared copy; cp_commit closes the thread's
+// group, cp_wait_all waits for every group it issued
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kVaThreads, 2) va_fused(GridT<float> g, VertT<float> v, VaPatchT pt,
+                                                          const float* __restrict__ vn, const float* __restrict__ w,
+                                                          float* __restrict__ vt_out, float* __restrict__ ddt_vn,
+                                                          float* __restrict__ ddt_w, const float* __restrict__ divd,
+                                                          float* __restrict__ divd2) {
+  extern __shared__ float sf[];
+  constexpr int L = kVaL, S = kVaS, Sn = kVaSn;
+  const int p = blockIdx.x;
+  const int nlev = v.nlev, nlevp = nlev + 1;
+  const int e0a = pt.off_e0[p], ne0 = pt.off_e0[p + 1] - e0a;
+  const int e1a = pt.off_e1[p], ne1 = pt.off_e1[p + 1] - e1a;
+  const int c0a = pt.off_c0[p], nc0 = pt.off_c0[p + 1] - c0a, nc3 = pt.n_c3[p];
+  const int v3a = pt.off_v3[p], nv3 = pt.off_v3[p + 1] - v3a;
+  const int e4a = pt.off_e4[p], ne4 = pt.off_e4[p + 1] - e4a, nw4 = pt.n_w4[p];
+  const int c_begin = p * pt.P, ncown = min(pt.P, g.nc - c_begin);
+  // two stages of [e0][Sn] vn at full levels k0-1 .. k0+L and [c0][Sn] w at
+  // half levels k0-1 .. k0+L: the next chunk's copies run during this one
+  const size_t stage = (size_t)(pt.max_e0 + pt.max_c0) * Sn;
+  float* vt_s = sf + 2 * stage;                // [e1][S]: vt at full levels k0-1 .. k0+L-1
+  float* ek_s = vt_s + (size_t)pt.max_e1 * S;  // [e1][S]: 2K at full levels k0 .. k0+L-1; then ddt_vn of E4
+  float* vi_s = ek_s + (size_t)pt.max_e1 * S;  // [e4][S]: vn at half levels k0 .. k0+L
+  float* gw_s = vi_s + (size_t)pt.max_e4 * S;  // [e4][S]: w's horizontal advection, half levels k0 .. k0+L-1
+  float* kc_s = gw_s + (size_t)pt.max_e4 * S;  // [c3][S]: 2K at the cells; then ddt_w of the own cells
+  float* ze_s = kc_s + (size_t)pt.max_c3 * S;  // [v3][S]: vorticity, full levels
+  float* wv_s = ze_s + (size_t)pt.max_v3 * S;  // [v3][S]: w at the vertices, half levels
+  float* dv_s = ek_s;
+  float* dw_s = kc_s;
+  // consecutive threads copy consecutive levels of one row (coalesced)
+  auto issue = [&](int kc, float* vs) {
+    float* ws = vs + (size_t)pt.max_e0 * Sn;
+    for (int i = threadIdx.x; i < (ne0 + nc0) * (L + 2); i += blockDim.x) {
+      const int it = i / (L + 2), lv = i - it * (L + 2);
+      if (it < ne0) {
+        const int k = min(max(kc - 1 + lv, 0), nlev - 1);
+        cp_async4(vs + it * Sn + lv, vn + (size_t)pt.e0_g[e0a + it] * nlev + k);
+      } else {
+        const int kh = min(max(kc - 1 + lv, 0), nlev);
+        const int ic = it - ne0;
+        cp_async4(ws + ic * Sn + lv, w + (size_t)pt.c0_g[c0a + ic] * nlevp + kh);
+      }
+    }
+    cp_commit();
+  };
+  issue(0, sf);
+  for (int k0 = 0, b = 0; k0 <= nlev + L; k0 += L, b ^= 1) {
+    cp_wait_all();
+    __syncthreads();
+    if (k0 > 0) {  // the previous chunk's w tendencies (own cells), coalesced along the levels
+      const int kp = k0 - L;
+      for (int i = threadIdx.x; i < ncown * L; i += blockDim.x) {
+        const int it = i / L, lv = i - it * L, k = kp + lv;
+        if (k <= nlev) ddt_w[(size_t)(c_begin + it) * nlevp + k] = dw_s[it * S + lv];
+      }
+    }
+    if (k0 > nlev) break;
+    if (k0 + L <= nlev) issue(k0 + L, sf + (b ^ 1) * stage);
+    const float* vn_s = sf + b * stage;
+    const float* w_s = vn_s + (size_t)pt.max_e0 * Sn;
+    // A1: vt and 2K on the E1 edges; vn at the half levels of the E4 edges
+    for (int i = threadIdx.x; i < ne1 + ne4; i += blockDim.x) {
+      if (i < ne1) {
+        const int it = i;
+        const uint4 nb = *reinterpret_cast<const uint4*>(pt.e1_i + 8 * (size_t)(e1a + it));
+        const float* n0 = vn_s + lo16(nb.x) * Sn;
+        const float* n1 = vn_s + hi16(nb.x) * Sn;
+        const float* n2 = vn_s + lo16(nb.y) * Sn;
+        const float* n3 = vn_s + hi16(nb.y) * Sn;
+        const float* n4 = vn_s + lo16(nb.z) * Sn;
+        const float* wt = pt.e1_w + 5 * (size_t)(e1a + it);
+        const float w0 = wt[0], w1 = wt[1], w2 = wt[2], w3 = wt[3], w4 = wt[4];
+#pragma unroll
+        for (int lv = 0; lv <= L; ++lv) {
+          const int k = k0 - 1 + lv;
+          if (k < 0 || k >= nlev) continue;
+          const float vne = n0[lv];
+          float t = w0 * vne;
+          t = fmat(w1, n1[lv], t);
+          t = fmat(w2, n2[lv], t);
+          t = fmat(w3, n3[lv], t);
+          t = fmat(w4, n4[lv], t);
+          vt_s[it * S + lv] = t;
+          if (lv >= 1) ek_s[it * S + lv - 1] = fmat(vne, vne, t * t);
+        }
+      } else {
+        const int it = i - ne1;
+        const float* x = vn_s + (int)pt.e4_i[8 * (size_t)(e4a + it) + 1] * Sn;
+#pragma unroll
+        for (int lv = 0; lv <= L; ++lv) {
+          const int kh = k0 + lv;
+          if (kh > nlev) break;
+          float vi;
+          if (kh == 0) {
+            vi = x[lv + 1];
+          } else if (kh == nlev) {
+            vi = x[lv];
+          } else {
+            const float vne = x[lv + 1];
+            vi = fmat(v.wgt[kh], x[lv] - vne, vne);
+          }
+          vi_s[it * S + lv] = vi;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nw4 * L; i += blockDim.x) {  // vt of the edges this patch writes
+      const int it = i / L, lv = i - it * L, k = k0 + lv;
+      if (k < nlev) vt_out[(size_t)pt.e4_g[e4a + it] * nlev + k] = vt_s[(int)pt.e4_i[8 * (size_t)(e4a + it)] * S + lv + 1];
+    }
+    if (divd2) {  // the corrector's divergence-damping Laplacian at the own cells
+      for (int i = threadIdx.x; i < ncown * L; i += blockDim.x) {
+        const int it = i / L, lv = i - it * L, k = k0 + lv;
+        if (k >= nlev) continue;
+        const int c = c_begin + it;
+        const int* cc = g.c2e2c + 3 * (size_t)c;
+        const float* Lw = g.lap_c + 3 * (size_t)c;
+        const size_t ic = (size_t)c * nlev + k;
+        const float dc = divd[ic];
+        const float d0 = divd[(size_t)cc[0] * nlev + k], d1 = divd[(size_t)cc[1] * nlev + k],
+                    d2 = divd[(size_t)cc[2] * nlev + k];
+        float r = Lw[0] * (d0 - dc);
+        r += Lw[1] * (d1 - dc);
+        r += Lw[2] * (d2 - dc);
+        divd2[ic] = r;
+      }
+    }
+    // A2: 2K at the C3 cells (all levels of the chunk); vorticity and w at the
+    // V3 vertices (each vertex in two halves of the chunk's levels)
+    for (int i = threadIdx.x; i < nc3 + 2 * nv3; i += blockDim.x) {
+      if (i < nc3) {
+        const int it = i;
+        const uint2 ce = *reinterpret_cast<const uint2*>(pt.c3_i + 4 * (size_t)(c0a + it));
+        const float* k0p = ek_s + lo16(ce.x) * S;
+        const float* k1p = ek_s + hi16(ce.x) * S;
+        const float* k2p = ek_s + lo16(ce.y) * S;
+        const float4 q = *reinterpret_cast<const float4*>(pt.c3_w + 4 * (size_t)(c0a + it));
+#pragma unroll
+        for (int lv = 0; lv < L; ++lv) {
+          const int k = k0 + lv;
+          if (k >= nlev) break;
+          float sk = q.x * k0p[lv];
+          sk += q.y * k1p[lv];
+          sk += q.z * k2p[lv];
+          kc_s[it * S + lv] = sk;
+        }
+      } else {
+        const int it = (i - nc3) >> 1, l0 = ((i - nc3) & 1) * (L / 2);
+        const uint4* xi = reinterpret_cast<const uint4*>(pt.v3_i + 16 * (size_t)(v3a + it));
+        const uint4 xa = xi[0], xb = xi[1];
+        const float4* wp = reinterpret_cast<const float4*>(pt.v3_w + 12 * (size_t)(v3a + it));
+        const float4 wa = wp[0], wb = wp[1], wc = wp[2];
+        const float* ep[6] = {vn_s + lo16(xa.x) * Sn + 1, vn_s + hi16(xa.x) * Sn + 1, vn_s + lo16(xa.y) * Sn + 1,
+                              vn_s + hi16(xa.y) * Sn + 1, vn_s + lo16(xa.z) * Sn + 1, vn_s + hi16(xa.z) * Sn + 1};
+        const float* cp[6] = {w_s + lo16(xa.w) * Sn + 1, w_s + hi16(xa.w) * Sn + 1, w_s + lo16(xb.x) * Sn + 1,
+                              w_s + hi16(xb.x) * Sn + 1, w_s + lo16(xb.y) * Sn + 1, w_s + hi16(xb.y) * Sn + 1};
+        const float cwl[6] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y};
+        const float rwl[6] = {wb.z, wb.w, wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+        for (int j = 0; j < L / 2; ++j) {
+          const int lv = l0 + j, k = k0 + lv;
+          if (k > nlev) break;
+          if (k < nlev) {
+            float z = 0;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) z += cwl[m] * ep[m][lv];
+            ze_s[it * S + lv] = z;
+          }
+          float sw = 0;
+#pragma unroll
+          for (int m = 0; m < 6; ++m) sw += rwl[m] * cp[m][lv];
+          wv_s[it * S + lv] = sw;
+        }
+      }
+    }
+    __syncthreads();
+    // A3: the vn tendency (edges this patch writes) and w's horizontal
+    // advection (times d) on the E4 edges, each edge in two halves of the levels
+    for (int i = threadIdx.x; i < 2 * ne4; i += blockDim.x) {
+      const int it = i >> 1, l0 = (i & 1) * (L / 2);
+      const uint4 x = *reinterpret_cast<const uint4*>(pt.e4_i + 8 * (size_t)(e4a + it));
+      const float4 cf = *reinterpret_cast<const float4*>(pt.e4_w + 4 * (size_t)(e4a + it));
+      const float* vt1 = vt_s + lo16(x.x) * S;
+      const int lc0 = lo16(x.y), lc1 = hi16(x.y);
+      const float* kc0 = kc_s + lc0 * S;
+      const float* kc1 = kc_s + lc1 * S;
+      const float* w0 = w_s + lc0 * Sn;
+      const float* w1 = w_s + lc1 * Sn;
+      const float* zm = ze_s + lo16(x.z) * S;
+      const float* zp = ze_s + hi16(x.z) * S;
+      const float* wvm = wv_s + lo16(x.z) * S;
+      const float* wvp = wv_s + hi16(x.z) * S;
+      const bool own = it < nw4;
+      const float* vie = vi_s + it * S;
+#pragma unroll
+      for (int j = 0; j < L / 2; ++j) {
+        const int lv = l0 + j, k = k0 + lv;
+        if (k > nlev) break;
+        const float vnie_k = vie[lv];
+        if (k < nlev && own) {
+          const float vnie_k1 = vie[lv + 1];
+          const float ws = (w0[lv + 1] + w0[lv + 2]) + (w1[lv + 1] + w1[lv + 2]);
+          const float adv = (ws * (vnie_k - vnie_k1)) * v.qdz[k];
+          const float zf = fmat(0.5f, zm[lv] + zp[lv], cf.x);
+          const float dk = kc0[lv] - kc1[lv];
+          dv_s[it * S + lv] = fmat(dk, cf.y, fmat(zf, vt1[lv + 1], -adv));
+        }
+        float gw = 0;
+        if (k > 0 && k < nlev) {
+          const float wg = v.wgt[k];
+          const float vtk = vt1[lv + 1];
+          const float vtie = vtk + wg * (vt1[lv] - vtk);
+          const float dwn = w1[lv + 1] - w0[lv + 1];
+          const float dwt = (wvp[lv] - wvm[lv]) * cf.z;
+          gw = fmat(vnie_k, dwn, vtie * dwt);
+        }
+        gw_s[it * S + lv] = gw;
+      }
+    }
+    __syncthreads();
+    // A4: the w tendency of the own cells, each cell in four quarters of the
+    // levels (stored at the next chunk's start); the vn tendencies of the
+    // edges this patch writes
+    for (int i = threadIdx.x; i < 4 * ncown; i += blockDim.x) {
+      const int it = i >> 2, l0 = (i & 3) * (L / 4);
+      const int c = c_begin + it;
+      const uint2 ce = *reinterpret_cast<const uint2*>(pt.own_i + 4 * (size_t)c);
+      const float* g0 = gw_s + lo16(ce.x) * S;
+      const float* g1 = gw_s + hi16(ce.x) * S;
+      const float* g2 = gw_s + lo16(ce.y) * S;
+      const float4 q = *reinterpret_cast<const float4*>(pt.own_w + 4 * (size_t)c);
+      const float* wc = w_s + it * Sn;  // wc[lv + 1]: half level k0 + lv
+#pragma unroll
+      for (int j = 0; j < L / 4; ++j) {
+        const int lv = l0 + j, k = k0 + lv;
+        if (k > nlev) break;
+        float r = 0.0f;
+        if (k > 0 && k < nlev) {
+          const float h = fmat(q.z, g2[lv], fmat(q.y, g1[lv], q.x * g0[lv]));
+          const float wa = wc[lv + 1];
+          r = fmat(-(wa * (wc[lv] - wc[lv + 2])), v.qdzh[k], -h);
+        }
+        dw_s[it * S + lv] = r;
+      }
+    }
+    for (int i = threadIdx.x; i < nw4 * L; i += blockDim.x) {
+      const int it = i / L, lv = i - it * L, k = k0 + lv;
+      if (k < nlev) ddt_vn[(size_t)pt.e4_g[e4a + it] * nlev + k] = dv_s[it * S + lv];
+    }
+  }
+}
+
+// -------------------------------------------------------------------------
 // A5 (predictor): Green-Gauss gradients of rho and theta_v (perturbations in
 // mixed mode: the reference is horizontally uniform) in each cell's local
 // frame: grad4 = (drho_x, drho_y, dth_x, dth_y) as 4 planes [4][nc*nlev].
@@ -973,6 +1263,16 @@ void launch_velocity_tendencies(const Ctx<T>& x, const T* vn, const T* w, T* ddt
   const TerrT<T>& tr = x.tr;
   const int nlev = v.nlev, nlevp = nlev + 1;
   const bool terr = tr.wgt_e != nullptr && wcc != nullptr;
+  if constexpr (kMixed<T>) {
+    if (x.vp.n_patches > 0 && !terr) {  // rows A1-A4 in one launch
+      const VaPatchT& pt = x.vp;
+      const size_t smem =
+          va_fused_smem_floats(pt.max_e0, pt.max_e1, pt.max_c3, pt.max_c0, pt.max_v3, pt.max_e4) * sizeof(float);
+      ICON_LAUNCH_SMEM("va_fused_f32", (unsigned)pt.n_patches, kVaThreads, smem, s, va_fused, g, v, pt, vn, w, wk.vt,
+                       ddt_vn, ddt_w, divd, divd2);
+      return;
+    }
+  }
   ICON_LAUNCH(kname<T>("va_edge_pre", "va_edge_pre_f32"), blocks_by_shape(SH(0), g.ne, nlev, TH(0)), TH(0), s,
               va_edge_pre<T>, g, v, vn, wk.vt, wk.ekin_e, wk.vn_ie, terr ? tr.wgt_e : nullptr, SH(0));
   if (terr)
@@ -1127,6 +1427,12 @@ __global__ void fill_kernel(double* p, size_t n, double v) {
   if (i < n) p[i] = v;
 }
 }  // namespace
+
+cudaError_t init_va_fused(const VaPatchT& pt) {
+  const size_t bytes = va_fused_smem_floats(pt.max_e0, pt.max_e1, pt.max_c3, pt.max_c0, pt.max_v3, pt.max_e4) * sizeof(float);
+  if (bytes > 227 * 1024) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(va_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
   fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);

@@ -1,7 +1,7 @@
 """Bitwise run-to-run determinism of the step (no atomics or order-dependent
 reductions in the stencils or the column solve): the same input stepped twice
 by one dycore, and once more by a second dycore whose launch shapes were
-autotuned on its own, gives the same bits, in FP64 and in mixed precision."""
+autotuned on its own, gives the same bits, in FP64 and in both mixed modes."""
 import numpy as np
 import pytest
 
@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 FIELDS = ("vn", "w", "rho", "exner", "theta_v", "exner_pr")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_f64col"])
 def test_repeated_steps_are_bitwise_identical(built_lib, cuda, precision):
     import paper_2608_21150_gb300 as P
-    prec = P.ICON_PREC_FP64 if precision == "fp64" else P.ICON_PREC_MIXED
+    prec = {"fp64": P.ICON_PREC_FP64, "mixed": P.ICON_PREC_MIXED, "mixed_f64col": P.ICON_PREC_MIXED_F64COL}[precision]
     grid, z, op, od, st = setup(4, 30, 720.0, seed=3, rayleigh=0.05)
     g = P.Grid(grid, radius=op.radius)
     runs = []
