@@ -1,6 +1,7 @@
 """FP64 CPU oracle of the learned corrector's data path (test infrastructure only).
 
-The corrector is an extension beyond the paper (its step has no learned part):
+Row A13.  The corrector is an extension beyond the paper (its step has no
+learned part):
 after a step with fewer acoustic substeps (Sec. 3.2's substep loop with a
 smaller ndyn_substeps) two networks propose increments towards the plain step
 taken from the same input.  Definitions, in the order the step applies them:
@@ -28,8 +29,7 @@ from . import mlp
 
 
 def east_north(C):
-    """Unit east and north vectors at the unit position vectors C [n, 3].
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    """Unit east and north vectors at the unit position vectors C [n, 3]."""
     east = np.cross(np.array([0.0, 0.0, 1.0]), C)
     east /= np.linalg.norm(east, axis=1)[:, None]
     north = np.cross(C, east)
@@ -37,8 +37,7 @@ def east_north(C):
 
 
 def column_features(dycore, st):
-    """[nc, 5 nlev] float64 features of the state (see the module docstring).
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    """[nc, 5 nlev] float64 features of the state (see the module docstring)."""
     g = dycore.g
     th_ref, ex_ref = dycore.reference_state()
     w = st["w"]
@@ -53,8 +52,7 @@ def column_features(dycore, st):
 
 
 def edge_features(dycore, st, col_x=None):
-    """[ne, 11 nlev] float64 features: the two adjacent columns, then vn.
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    """[ne, 11 nlev] float64 features: the two adjacent columns, then vn."""
     g = dycore.g
     if col_x is None:
         col_x = column_features(dycore, st)
@@ -62,9 +60,7 @@ def edge_features(dycore, st, col_x=None):
 
 
 def targets(reduced, plain):
-    """Training targets plain - reduced: column [nc, 3 nlev - 1], edge [ne, nlev].
-    Row A13: the learned corrector, an extension beyond the paper, whose step has
-    no learned part."""
+    """Training targets plain - reduced: column [nc, 3 nlev - 1], edge [ne, nlev]."""
     dw = plain["w"][:, 1:-1] - reduced["w"][:, 1:-1]
     col = np.concatenate([dw, plain["exner"] - reduced["exner"], plain["theta_v"] - reduced["theta_v"]], axis=1)
     return col, plain["vn"] - reduced["vn"]
@@ -73,16 +69,14 @@ def targets(reduced, plain):
 def network(params, dims, stats, x):
     """Denormalised increments of a network on raw features x.
     dims = (n_in, n_hidden, n_out); stats = (x_mean, x_std, y_mean, y_std).
-    Returns (increments, normalised outputs).
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    Returns (increments, normalised outputs)."""
     xm, xs, ym, ys = [np.asarray(a, dtype=np.float64) for a in stats]
     y, _ = mlp.forward(params, (x - xm) / xs, *dims)
     return y * ys + ym, y
 
 
 def apply(st, col_inc, edge_inc):
-    """The corrected state: increments added to interior w, exner, theta_v and vn.
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    """The corrected state: increments added to interior w, exner, theta_v and vn."""
     out = {k: v.copy() for k, v in st.items()}
     nlev = st["exner"].shape[1]
     out["w"][:, 1:-1] += col_inc[:, :nlev - 1]
@@ -93,8 +87,7 @@ def apply(st, col_inc, edge_inc):
 
 
 def check_value(col_y, edge_y, corrected):
-    """max of the two RMS normalised outputs; NaN when anything corrected (or rho) is not finite.
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    """max of the two RMS normalised outputs; NaN when anything corrected (or rho) is not finite."""
     r = max(np.sqrt(np.mean(col_y ** 2)), np.sqrt(np.mean(edge_y ** 2)))
     fields = ("vn", "w", "exner", "theta_v", "rho")
     if not all(np.all(np.isfinite(corrected[k])) for k in fields):
@@ -104,8 +97,7 @@ def check_value(col_y, edge_y, corrected):
 
 def step_learned(reduced, plain, col_net, edge_net, st, max_norm):
     """One learned step.  reduced/plain are oracle Dycore objects sharing the grid;
-    col_net and edge_net are (params, dims, stats).  Returns (state, used_fallback, check value).
-    Row A13: the learned corrector, an extension beyond the paper, whose step has no learned part."""
+    col_net and edge_net are (params, dims, stats).  Returns (state, used_fallback, check value)."""
     sr = reduced.step(st)
     cx = column_features(reduced, sr)
     ex = edge_features(reduced, sr, cx)

@@ -27,34 +27,31 @@ import numpy as np
 
 
 def _norm(x):
-    """Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+    """Euclidean norm over the last axis."""
     return np.linalg.norm(x, axis=-1)
 
 
 def arc(p, q):
-    """Great-circle angle between unit vectors (radians).
-    Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+    """Great-circle angle between unit vectors (radians)."""
     return np.arctan2(_norm(np.cross(p, q)), np.sum(p * q, axis=-1))
 
 
 def tri_area(p, q, r):
-    """Spherical excess of the triangle (p, q, r) on the unit sphere.
-    Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+    """Spherical excess of the triangle (p, q, r) on the unit sphere."""
     num = np.abs(np.sum(p * np.cross(q, r), axis=-1))
     den = 1.0 + np.sum(p * q, -1) + np.sum(q * r, -1) + np.sum(r * p, -1)
     return 2.0 * np.arctan2(num, den)
 
 
 def project(v, x):
-    """Project vectors v (..., 3) onto the tangent plane at unit x (..., 3).
-    Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+    """Project vectors v (..., 3) onto the tangent plane at unit x (..., 3)."""
     return v - np.sum(v * x, axis=-1, keepdims=True) * x
 
 
 class Geometry:
-    """Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+    """The factors of the module docstring for one grid on a sphere of radius a (row A0)."""
     def __init__(self, grid, radius):
-        """Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+        """Derives every factor from the grid's tables and unit position vectors."""
         a = float(radius)
         self.a = a
         V, C, E = grid.vert_xyz, grid.cell_xyz, grid.edge_xyz
@@ -133,5 +130,5 @@ class Geometry:
         self.vert_vert_length = a * arc(V[self.e2c2v[:, 2]], V[self.e2c2v[:, 3]])
 
     def coriolis(self, omega):
-        """Row A0: spherical geometry of the RnBm grid (Sec. 5.1)."""
+        """f_e = 2 omega sin(lat_e) at the edge midpoints."""
         return 2.0 * omega * self.E[:, 2]

@@ -1,5 +1,8 @@
 """FP64 CPU oracle of the learned corrector's MLP (test infrastructure only).
 
+Row A13, an extension beyond the paper.  GELU in the erf form (Hendrycks and
+Gimpel 2016), Adam (Kingma and Ba 2015).
+
 y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3 with GELU(u) = u Phi(u) =
 u (1 + erf(u / sqrt 2)) / 2, its exact gradients by the chain rule, the mean
 squared error and one Adam step (Kingma & Ba, bias-corrected moments).
@@ -11,20 +14,17 @@ from scipy.special import erf
 
 
 def gelu(u):
-    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """GELU(u) = u Phi(u), Phi the standard normal CDF."""
     return 0.5 * u * (1.0 + erf(u / np.sqrt(2.0)))
 
 
 def gelu_grad(u):
-    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """GELU'(u) = Phi(u) + u phi(u)."""
     return 0.5 * (1.0 + erf(u / np.sqrt(2.0))) + u * np.exp(-0.5 * u * u) / np.sqrt(2.0 * np.pi)
 
 
 def unpack(params, n_in, n_hid, n_out):
-    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """The six parameter arrays W1, b1, W2, b2, W3, b3 from the flat vector."""
     shapes = [(n_hid, n_in), (n_hid,), (n_hid, n_hid), (n_hid,), (n_out, n_hid), (n_out,)]
     out, off = [], 0
     for s in shapes:
@@ -35,8 +35,7 @@ def unpack(params, n_in, n_hid, n_out):
 
 
 def forward(params, x, n_in, n_hid, n_out):
-    """Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """Outputs y [rows, n_out] and the activations the backward pass needs."""
     W1, b1, W2, b2, W3, b3 = unpack(params, n_in, n_hid, n_out)
     z1 = x @ W1.T + b1
     h1 = gelu(z1)
@@ -47,9 +46,7 @@ def forward(params, x, n_in, n_hid, n_out):
 
 
 def backward(params, cache, dy, n_in, n_hid, n_out):
-    """Gradients of all parameters (flat, library layout) for dL/dy.
-    Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """Gradients of all parameters (flat, library layout) for dL/dy."""
     W1, b1, W2, b2, W3, b3 = unpack(params, n_in, n_hid, n_out)
     x, z1, h1, z2, h2 = cache
     gW3 = dy.T @ h2
@@ -64,17 +61,13 @@ def backward(params, cache, dy, n_in, n_hid, n_out):
 
 
 def mse(y, t):
-    """Mean squared error and its gradient with respect to y.
-    Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """Mean squared error and its gradient with respect to y."""
     d = y - t
     return float(np.mean(d * d)), 2.0 * d / d.size
 
 
 def adam_step(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
-    """One Adam update (step number t >= 1); returns new params, m, v.
-    Row A13 (an extension beyond the paper): the corrector's MLP; GELU in the erf form (Hendrycks
-    and Gimpel 2016), Adam (Kingma and Ba 2015)."""
+    """One Adam update (step number t >= 1); returns new params, m, v."""
     m = b1 * m + (1 - b1) * grads
     v = b2 * v + (1 - b2) * grads * grads
     mh = m / (1 - b1 ** t)
