@@ -84,6 +84,15 @@ constexpr size_t smem_bytes() {
   return (size_t)lev_offset_bytes<T, KC, kCorrTiles, kTerr>() + 16 * (size_t)(KC + 1) * sizeof(double);
 }
 constexpr size_t kSmem = smem_bytes<double, kKC, true>();
+// CTAs of a form that fit one SM by shared memory (233 472 bytes an SM, 1 KB
+// of it reserved per CTA), at most 8: the launch bound's minimum, so that the
+// compiler may use the registers the shared-memory limit leaves free
+template <class T, int KC, bool kCorrTiles, bool kTerr = false>
+constexpr int col_min_blocks() {
+  return (int)(233472 / (smem_bytes<T, KC, kCorrTiles, kTerr>() + 1024)) < 1   ? 1
+         : (int)(233472 / (smem_bytes<T, KC, kCorrTiles, kTerr>() + 1024)) > 8 ? 8
+                                                                              : (int)(233472 / (smem_bytes<T, KC, kCorrTiles, kTerr>() + 1024));
+}
 
 // column coefficients: CTHI the reference theta_v at the half level (theta_ic
 // is it plus the interpolated perturbation); the explicit part
@@ -403,7 +412,7 @@ __device__ __forceinline__ R get(const double* p) {
 // w - wcc (zero at the top and the ground, where w = wcc: the kinematic
 // ground condition); the fluxes rho_ic w and the Rayleigh damping act on it.
 template <class T, bool kOwnZb = false, int KC = kKC, class R = double, int kCorr = -1, bool kTerr = false>
-__global__ void __launch_bounds__(kCW, 8) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector_arg,
+__global__ void __launch_bounds__(kCW, (col_min_blocks<T, KC, kCorr != 0, kTerr>())) sn_column_tiled(int nc, DevVert v, Scalars sc, int corrector_arg,
                                                           ColArgs<T> a) {
   const bool corrector = kCorr < 0 ? corrector_arg != 0 : kCorr == 1;
   using A = Ar<R>;
