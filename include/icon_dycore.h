@@ -216,7 +216,11 @@ int icon_dycore_destroy(icon_dycore_t* dycore);
  *                                icon_dycore_reference_state)
  * Either all six are device pointers (no copies; the calls enqueue on the
  * dycore's stream), or all six are host pointers (the library copies in and
- * out around the call, a slow path for testing and end-to-end timing).
+ * out around the call and returns when the copies back are done; pinned
+ * memory copies fastest).  In a full step of host arrays, rho, exner,
+ * theta_v and exner_pr are copied in on a second, library-owned stream while
+ * the first velocity tendencies run, and rho and exner_pr back while the
+ * diffusion runs; the results are those of a device-array step, bit for bit.
  */
 typedef struct icon_state {
   double* vn;

@@ -84,6 +84,7 @@ struct icon_grid {
 
 struct GraphEntry {
   StateView key{};
+  bool io = false;  // captured with the host-copy events (staging state of a host-array step)
   cudaGraphExec_t exec = nullptr;
   unsigned long long last_use = 0;
 };
@@ -102,6 +103,10 @@ struct icon_dycore {
   unsigned long long use_counter = 0;
   StateView staging{};                 // device copy used when the caller passes host arrays
   bool have_staging = false;
+  // host-array steps: a private stream for the copies of the fields the step
+  // reads late or finishes early, and the events that order them with the step
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_start = nullptr, io_in = nullptr, io_out = nullptr;
   // learned corrector (allocated on first use): saved input state, features, norm partials
   StateView saved{};
   float* colx = nullptr;                                  // raw column features [nc][5 nlev]
@@ -860,6 +865,13 @@ int icon_dycore_destroy(icon_dycore_t* d) {
   if (!d) return ICON_OK;
   cudaStreamSynchronize(d->stream);
   free_graphs(d);
+  if (d->io_stream) {
+    cudaStreamSynchronize(d->io_stream);
+    cudaStreamDestroy(d->io_stream);
+    cudaEventDestroy(d->io_start);
+    cudaEventDestroy(d->io_in);
+    cudaEventDestroy(d->io_out);
+  }
   if (d->have_staging) {
     cudaFree(d->staging.vn);
     cudaFree(d->staging.w);
@@ -912,17 +924,26 @@ Where locate(const icon_state_t* s) {
 
 enum class Op { kStep, kSubstep, kDiffusion };
 
-void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s) {
+// io (whole steps of host arrays only): the step waits on d->io_in before
+// it reads rho, theta_v, exner or exner_pr (after the first predictor's
+// velocity tendencies in FP64; before the mirrors are refreshed in the mixed
+// modes) and records d->io_out once rho and exner_pr are final (after the
+// last corrector; the diffusion changes neither).
+void enqueue(icon_dycore* d, Op op, const StateView& st, cudaStream_t s, bool io = false) {
   if (op == Op::kStep || op == Op::kSubstep) {
     int n = op == Op::kStep ? d->params.ndyn_substeps : 1;
     const bool mixed = is_mixed(d->en.precision);
+    if (io && mixed) stream_wait_io(s, d->io_in);
     if (mixed) launch_refresh_mirrors(d->en, st, s);
     for (int i = 0; i < n; ++i) {
+      d->en.io_wait = io && !mixed && i == 0 ? d->io_in : nullptr;
       if (mixed)
         launch_substep<float>(d->en, d->en.c32, st, s);
       else
         launch_substep<double>(d->en, d->en.c64, st, s);
+      d->en.io_wait = nullptr;
     }
+    if (io) stream_record_io(s, d->io_out);
   }
   if (op == Op::kStep || op == Op::kDiffusion) {
     if (is_mixed(d->en.precision)) {
@@ -969,17 +990,17 @@ int summarise(const Prof& prof, int max_kernels, char* names, int32_t* launches,
   return ICON_OK;
 }
 
-bool same(const StateView& a, const StateView& b) {
+bool same_state(const StateView& a, const StateView& b) {
   return a.vn == b.vn && a.w == b.w && a.rho == b.rho && a.exner == b.exner && a.theta_v == b.theta_v &&
          a.exner_pr == b.exner_pr;
 }
 
 // Graph of one full step for this set of state pointers; a cache of two
 // entries covers double-buffered callers (as the paper's descriptor cache).
-int step_graph(icon_dycore* d, const StateView& st, cudaGraphExec_t* exec) {
+int step_graph(icon_dycore* d, const StateView& st, bool io, cudaGraphExec_t* exec) {
   ++d->use_counter;
   for (auto& e : d->graphs)
-    if (e.exec && same(e.key, st)) {
+    if (e.exec && same_state(e.key, st) && e.io == io) {
       e.last_use = d->use_counter;
       *exec = e.exec;
       return ICON_OK;
@@ -994,7 +1015,7 @@ int step_graph(icon_dycore* d, const StateView& st, cudaGraphExec_t* exec) {
   }
   cudaGraph_t graph = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal));
-  enqueue(d, Op::kStep, st, d->cap_stream);
+  enqueue(d, Op::kStep, st, d->cap_stream, io);
   cudaError_t le = cudaGetLastError();
   cudaError_t ee = cudaStreamEndCapture(d->cap_stream, &graph);
   if (le != cudaSuccess) {
@@ -1006,6 +1027,7 @@ int step_graph(icon_dycore* d, const StateView& st, cudaGraphExec_t* exec) {
   cudaGraphDestroy(graph);
   CUDA_TRY(ie);
   slot->key = st;
+  slot->io = io;
   slot->last_use = d->use_counter;
   *exec = slot->exec;
   return ICON_OK;
@@ -1023,6 +1045,10 @@ int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
     return fail(ICON_ERR_ARG, std::string(name) + ": state mixes host and device pointers");
   StateView st{s->vn, s->w, s->rho, s->exner, s->theta_v, s->exner_pr};
   cudaStream_t stream = d->stream;
+  // a whole step of host arrays overlaps the copies of rho, exner, theta_v
+  // and exner_pr with the first velocity tendencies and the copies of rho and
+  // exner_pr back with the diffusion (on a private stream, ordered by events)
+  const bool io = where == Where::kHost && op == Op::kStep;
   if (where == Where::kHost) {
     if (!d->have_staging) {
       StateView& g = d->staging;
@@ -1034,33 +1060,49 @@ int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
       CUDA_TRY(cudaMalloc(&g.exner_pr, cf * 8));
       d->have_staging = true;
     }
+    if (io && !d->io_stream) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&d->io_stream, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&d->io_start, cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&d->io_in, cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&d->io_out, cudaEventDisableTiming));
+    }
     const StateView& g = d->staging;
     CUDA_TRY(cudaMemcpyAsync(g.vn, s->vn, ef * 8, cudaMemcpyHostToDevice, stream));
     CUDA_TRY(cudaMemcpyAsync(g.w, s->w, ch * 8, cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaMemcpyAsync(g.rho, s->rho, cf * 8, cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaMemcpyAsync(g.exner, s->exner, cf * 8, cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaMemcpyAsync(g.theta_v, s->theta_v, cf * 8, cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaMemcpyAsync(g.exner_pr, s->exner_pr, cf * 8, cudaMemcpyHostToDevice, stream));
+    // the other fields on the copy stream, after whatever the caller's stream holds
+    cudaStream_t cs = io ? d->io_stream : stream;
+    if (io) {
+      CUDA_TRY(cudaEventRecord(d->io_start, stream));
+      CUDA_TRY(cudaStreamWaitEvent(cs, d->io_start, 0));
+    }
+    CUDA_TRY(cudaMemcpyAsync(g.rho, s->rho, cf * 8, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(g.exner, s->exner, cf * 8, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(g.theta_v, s->theta_v, cf * 8, cudaMemcpyHostToDevice, cs));
+    CUDA_TRY(cudaMemcpyAsync(g.exner_pr, s->exner_pr, cf * 8, cudaMemcpyHostToDevice, cs));
+    if (io) CUDA_TRY(cudaEventRecord(d->io_in, cs));
     st = g;
   }
   if (op == Op::kStep && d->params.use_graph && !g_prof) {
     cudaGraphExec_t exec = nullptr;
-    int rc = step_graph(d, st, &exec);
+    int rc = step_graph(d, st, io, &exec);
     if (rc != ICON_OK) return rc;
     CUDA_TRY(cudaGraphLaunch(exec, stream));
   } else {
-    enqueue(d, op, st, stream);
+    enqueue(d, op, st, stream, io);
     CUDA_TRY(cudaGetLastError());
   }
   if (where == Where::kHost) {
     const StateView& g = d->staging;
+    cudaStream_t cs = io ? d->io_stream : stream;
+    if (io) CUDA_TRY(cudaStreamWaitEvent(cs, d->io_out, 0));
+    CUDA_TRY(cudaMemcpyAsync(s->rho, g.rho, cf * 8, cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(cudaMemcpyAsync(s->exner_pr, g.exner_pr, cf * 8, cudaMemcpyDeviceToHost, cs));
     CUDA_TRY(cudaMemcpyAsync(s->vn, g.vn, ef * 8, cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaMemcpyAsync(s->w, g.w, ch * 8, cudaMemcpyDeviceToHost, stream));
-    CUDA_TRY(cudaMemcpyAsync(s->rho, g.rho, cf * 8, cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaMemcpyAsync(s->exner, g.exner, cf * 8, cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaMemcpyAsync(s->theta_v, g.theta_v, cf * 8, cudaMemcpyDeviceToHost, stream));
-    CUDA_TRY(cudaMemcpyAsync(s->exner_pr, g.exner_pr, cf * 8, cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
+    if (io) CUDA_TRY(cudaStreamSynchronize(cs));
   } else if (d->params.synchronous) {
     CUDA_TRY(cudaStreamSynchronize(stream));
   }

@@ -93,6 +93,10 @@ struct Engine {
                    -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
   int col_kc = 4;
   bool terrain = false;  // per-column heights: the terrain forms of the kernels
+  // Host-array steps: when set, the first substep waits on this event right
+  // after its predictor's velocity tendencies (which read only vn and w), so
+  // that the copies of the other state fields overlap those kernels.
+  cudaEvent_t io_wait = nullptr;
 };
 
 // Rows A1-A4 on (vn, w) in compute type T: writes ddt_vn [ne*nlev] and ddt_w
@@ -109,6 +113,10 @@ constexpr int kNumStencils = 16;
 extern const char* const kStencilNames[kNumStencils];
 // Fill n doubles with v (the autotuner's temporary state).
 void launch_fill(double* p, size_t n, double v, cudaStream_t s);
+// Event wait / record on s; inside a stream capture they become the graph's
+// external event nodes.
+void stream_wait_io(cudaStream_t s, cudaEvent_t e);
+void stream_record_io(cudaStream_t s, cudaEvent_t e);
 // Rows A5-A9: one predictor + corrector substep, state updated in place.
 template <class T>
 void launch_substep(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s);

@@ -1320,6 +1320,20 @@ void launch_fluxdiv(const Engine& en, const Ctx<T>& x, const T* vn, const char* 
 
 // Rows A5-A9 of one substep; kTerr: the terrain forms, with the contravariant
 // corrections of the predictor's and the corrector's winds in x.tr.wcc0/wcc1.
+// s waits for event e: as an external event node when s is being captured
+// into a graph (the wait then happens at every launch of the graph), else as
+// a plain stream wait
+void stream_wait_io(cudaStream_t s, cudaEvent_t e) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  cudaStreamWaitEvent(s, e, cs == cudaStreamCaptureStatusActive ? cudaEventWaitExternal : 0);
+}
+void stream_record_io(cudaStream_t s, cudaEvent_t e) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0);
+}
+
 template <class T, bool kTerr>
 void substep_impl(const Engine& en, const Ctx<T>& x, const StateView& st, cudaStream_t s) {
   const int* threads = en.threads;
@@ -1350,6 +1364,7 @@ void substep_impl(const Engine& en, const Ctx<T>& x, const StateView& st, cudaSt
   // ---------------- predictor ----------------
   launch_velocity_tendencies<T>(x, s_vn, s_w, wk.ddt_vn0, wk.ddt_w0, nullptr, nullptr, s, threads,
                                 kTerr ? tr.wcc0 : nullptr, shapes);
+  if (en.io_wait) stream_wait_io(s, en.io_wait);  // rho, theta_v, exner, exner_pr from here on
   ICON_LAUNCH(nm_grad, blocks_for(nce, TH(4)), TH(4), s, (sn_cell_grad<T, kTerr>), g, v, s_rho, s_th, wk.grad4,
               st.exner, st.exner_pr, en.sc.exfac, en.wk.pex, ex_ref_c);
   ICON_LAUNCH(nm_pred, blocks_for(nee, TH(5)), TH(5), s, (sn_edge_pred<T, kTerr>), g, v, x.s, s_vn, wk.vt,
