@@ -98,6 +98,7 @@ def units_per_launch(name, nc, ne, nv, nlev):
         "diff_div_curl_uv": full["c"] + full["v"], "diff_edge_smag": full["e"],
         "diff_second": half["c"] + full["v"], "diff_edge_update": full["e"], "diff_cell_update": half["c"],
         "mx_refresh": full["e"] + half["c"], "lc_col_inputs": full["c"], "lc_edge_inputs": full["e"],
+        "va_fused": half["c"],  # rows A1-A4 over cell patches: per cell and half level
     }[base_name(name)]
 
 
