@@ -318,30 +318,30 @@ def config_dict(prec):
 # whole step instead (PER_STEP_UNITS).  Valid while the sources that define
 # the timed kernels are the ones captured (SHA-256 over KERNEL_SOURCES).
 DRAM_PER_UNIT = {
-    "sources_sha256": "65c24ed5e422ac7d77f5fa9ff2b1a10857ba6b5f284b3dd4d5d25a6b5f2c1760",
+    "sources_sha256": "1c755f8073d4233f8d10e6c746013f70051ad72effbae2380259e228a05b1090",
     "bisections": 5, "nlev": 90,
     "legs": {
         "fp64": {
-            "diff_cell_update": 57.637, "diff_div_curl_uv": 29.18, "diff_edge_smag": 30.836,
-            "diff_edge_update": 38.808, "diff_second": 52.885, "sn_cell_div": 31.104, "sn_cell_fluxsum": 36.268,
-            "sn_cell_grad": 67.049, "sn_column_corr": 273.655, "sn_column_pred": 208.599, "sn_edge_corr": 44.127,
-            "sn_edge_flux": 42.924, "sn_edge_pred": 92.476, "va_cell_vert": 41.94, "va_cell_w": 25.692,
-            "va_edge_pre": 27.771, "va_edge_tend": 51.881},
+            "diff_cell_update": 57.627, "diff_div_curl_uv": 29.152, "diff_edge_smag": 30.742,
+            "diff_edge_update": 38.763, "diff_second": 52.87, "sn_cell_div": 31.13, "sn_cell_fluxsum": 36.227,
+            "sn_cell_grad": 66.955, "sn_column_corr": 274.264, "sn_column_pred": 208.707, "sn_edge_corr": 44.137,
+            "sn_edge_flux": 42.929, "sn_edge_pred": 92.494, "va_cell_vert": 41.95, "va_cell_w": 25.65,
+            "va_edge_pre": 27.746, "va_edge_tend": 51.936},
         "mixed": {
-            "diff_cell_update": 56.147, "diff_div_curl_uv": 10.536, "diff_edge_smag": 13.69,
-            "diff_edge_update": 28.828, "diff_second": 24.742, "mx_refresh": 19.994, "sn_cell_div": 20.812,
-            "sn_cell_fluxdiv": 34.434, "sn_cell_grad": 42.76, "sn_column_corr": 304.774, "sn_column_pred": 201.916,
-            "sn_edge_corr": 31.229, "sn_edge_pred": 47.915, "va_cell_vert": 19.994, "va_cell_w": 11.257,
-            "va_edge_pre": 11.152, "va_edge_tend": 24.867},
+            "diff_cell_update": 56.156, "diff_div_curl_uv": 10.468, "diff_edge_smag": 13.727,
+            "diff_edge_update": 28.821, "diff_second": 24.801, "mx_refresh": 20.004, "sn_cell_div": 20.767,
+            "sn_cell_fluxdiv": 34.433, "sn_cell_grad": 42.77, "sn_column_corr": 304.048, "sn_column_pred": 201.923,
+            "sn_edge_corr": 31.213, "sn_edge_pred": 47.884, "va_cell_vert": 20.033, "va_cell_w": 11.302,
+            "va_edge_pre": 11.198, "va_edge_tend": 24.854, "va_fused": 44.53},
         # the learned step: the mixed kernels (their R2B5 figures) and its own
         "learned": {
-            "diff_cell_update": 56.147, "diff_div_curl_uv": 10.536, "diff_edge_smag": 13.69,
-            "diff_edge_update": 28.828, "diff_second": 24.742, "lc_apply_col": 20.921, "lc_apply_edge": 15.445,
-            "lc_col_inputs": 61.535, "lc_edge_inputs": 39.928, "lc_reduce_status": 527360.0,
-            "lc_reduce_status2": 10240.0, "mlp_gemm_tc": 12963.203, "mx_refresh": 19.994, "sn_cell_div": 20.812,
-            "sn_cell_fluxdiv": 34.434, "sn_cell_grad": 42.76, "sn_column_corr": 304.774, "sn_column_pred": 201.916,
-            "sn_edge_corr": 31.229, "sn_edge_pred": 47.915, "va_cell_vert": 19.994, "va_cell_w": 11.257,
-            "va_edge_pre": 11.152, "va_edge_tend": 24.867},
+            "diff_cell_update": 56.156, "diff_div_curl_uv": 10.468, "diff_edge_smag": 13.727,
+            "diff_edge_update": 28.821, "diff_second": 24.801, "lc_apply_col": 20.923, "lc_apply_edge": 15.437,
+            "lc_col_inputs": 61.505, "lc_edge_inputs": 39.974, "lc_reduce_status": 527360.0,
+            "lc_reduce_status2": 9728.0, "mlp_gemm_tc": 12979.303, "mx_refresh": 20.004, "sn_cell_div": 20.767,
+            "sn_cell_fluxdiv": 34.433, "sn_cell_grad": 42.77, "sn_column_corr": 304.048, "sn_column_pred": 201.923,
+            "sn_edge_corr": 31.213, "sn_edge_pred": 47.884, "va_cell_vert": 20.033, "va_cell_w": 11.302,
+            "va_edge_pre": 11.198, "va_edge_tend": 24.854},
     }}
 
 # The files whose code runs on the device in the timed steps.
