@@ -1060,11 +1060,21 @@ int run(icon_dycore* d, const icon_state_t* s, Op op, const char* name) {
       CUDA_TRY(cudaMalloc(&g.exner_pr, cf * 8));
       d->have_staging = true;
     }
-    if (io && !d->io_stream) {
-      CUDA_TRY(cudaStreamCreateWithFlags(&d->io_stream, cudaStreamNonBlocking));
-      CUDA_TRY(cudaEventCreateWithFlags(&d->io_start, cudaEventDisableTiming));
-      CUDA_TRY(cudaEventCreateWithFlags(&d->io_in, cudaEventDisableTiming));
-      CUDA_TRY(cudaEventCreateWithFlags(&d->io_out, cudaEventDisableTiming));
+    if (io && !d->io_stream) {  // all four or none
+      cudaStream_t cs = nullptr;
+      cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        for (cudaEvent_t x : ev)
+          if (x) cudaEventDestroy(x);
+        if (cs) cudaStreamDestroy(cs);
+        return fail(ICON_ERR_CUDA, std::string(name) + ": copy stream: " + cudaGetErrorString(e));
+      }
+      d->io_stream = cs;
+      d->io_start = ev[0];
+      d->io_in = ev[1];
+      d->io_out = ev[2];
     }
     const StateView& g = d->staging;
     CUDA_TRY(cudaMemcpyAsync(g.vn, s->vn, ef * 8, cudaMemcpyHostToDevice, stream));
