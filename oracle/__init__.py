@@ -16,9 +16,10 @@ discretisation.  Every formula here is therefore a reading of an ICON-type
 scheme on the triangular C-grid; the module docstrings name each one.
 
 Everything is plain numpy in float64, vectorised over the horizontal index
-only where that does not reorder the arithmetic of one point.  Parity with
-ICON itself is unpinned (no ICON code or data exist to compare against); the
-oracle is pinned by invariants, closed forms and convergence (tests/).
+only where that does not reorder the arithmetic of one point.  No ICON code
+or data exist to compare against, so agreement with ICON itself cannot be
+checked; every function of the oracle is pinned by invariants, closed forms
+and convergence (tests/).
 """
 from .params import DycoreParams  # noqa: F401
 from .geometry import Geometry  # noqa: F401
